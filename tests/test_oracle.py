@@ -1,0 +1,304 @@
+"""Pins for the CPU oracle (no GPU).
+
+The oracle is checked against things other than itself: brute-force triple
+enumeration and dense matrix powers on tiny graphs, textbook closed forms,
+scipy's sparse product for the algebraic form C = A A o A (Sec. VI-B), Python
+set intersection for Alg. 1/2, hand-evaluated cases of Eq. 3, exact rational
+LCC values, and invariants (relabelling, edge order, repeated pairs).
+"""
+from __future__ import annotations
+
+from math import comb
+
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+import graphgen
+import oracle
+from tests import families as F
+
+
+def run(n, src, dst):
+    return oracle.triangles(n, src, dst)
+
+
+# --------------------------------------------------------------------------
+# Alg. 1, Alg. 2, Eq. 3
+
+def _sorted_unique(rng, k, hi):
+    return np.unique(rng.integers(0, hi, size=k)).astype(np.int32)
+
+
+@pytest.mark.parametrize("seed", range(40))
+def test_ssi_and_binary_search_match_set_intersection(seed):
+    rng = np.random.default_rng(seed)
+    A = _sorted_unique(rng, int(rng.integers(0, 60)), 200)
+    B = _sorted_unique(rng, int(rng.integers(0, 300)), 200)
+    want = len(set(A.tolist()) & set(B.tolist()))
+    assert oracle.ssi(A, B) == want
+    assert oracle.ssi(B, A) == want
+    assert oracle.binary_search(A, B) == want
+    assert oracle.binary_search(B, A) == want
+
+
+def test_binary_search_finds_matches_at_both_ends():
+    # The listing as printed never tests B[0] or B[|B|-1]; the textbook reading must.
+    B = np.array([3, 5, 7, 9, 11], dtype=np.int32)
+    assert oracle.binary_search(np.array([3], np.int32), B) == 1
+    assert oracle.binary_search(np.array([11], np.int32), B) == 1
+    assert oracle.binary_search(np.array([3, 11], np.int32), B) == 2
+    assert oracle.binary_search(np.array([2, 4, 12], np.int32), B) == 0
+    assert oracle.binary_search(np.array([], np.int32), B) == 0
+    assert oracle.ssi(np.array([], np.int32), B) == 0
+
+
+@pytest.mark.parametrize("a,b,want", [
+    (8, 16, True),    # 16/8 = 2 <= log2(16) - 1 = 3
+    (4, 16, False),   # 4 > 3
+    (16, 16, True),   # 1 <= 3
+    (4, 8, True),     # tie: 8/4 = 2 = log2(8) - 1 -> SSI
+    (8, 32, True),    # tie: 4 = 4
+    (7, 32, False),   # 4.57 > 4
+    (1, 1, False),    # 1 > log2(1) - 1 = -1
+    (2, 4, False),    # 2 > 1
+    (100, 1000, False),  # 10 > log2(1000) - 1 = 8.97
+    (200, 1000, True),   # 5 <= 8.97
+])
+def test_eq3_rule(a, b, want):
+    assert oracle.prefer_ssi(a, b) is want
+    assert oracle.prefer_ssi(b, a) is want  # the rule orders the lists itself
+
+
+# --------------------------------------------------------------------------
+# Closed forms
+
+@pytest.mark.parametrize("n", [3, 4, 5, 9, 17, 40])
+def test_complete_graph(n):
+    nn, (s, d) = F.complete(n)
+    r = run(nn, s, d)
+    assert r["T"] == comb(n, 3)
+    assert (r["t"] == comb(n - 1, 2)).all()
+    assert (r["lcc"] == 1.0).all()
+
+
+@pytest.mark.parametrize("make", [lambda: F.star(30), lambda: F.cycle(4), lambda: F.cycle(9),
+                                  lambda: F.path(20), lambda: F.grid(7, 9),
+                                  lambda: F.complete_bipartite(6, 11),
+                                  lambda: F.random_tree(200, np.random.default_rng(3))])
+def test_triangle_free(make):
+    n, (s, d) = make()
+    r = run(n, s, d)
+    assert r["T"] == 0
+    assert (r["t"] == 0).all()
+    assert (r["lcc"] == 0.0).all()
+
+
+def test_triangle_is_cycle3():
+    n, (s, d) = F.cycle(3)
+    r = run(n, s, d)
+    assert r["T"] == 1 and (r["t"] == 1).all() and (r["lcc"] == 1.0).all()
+
+
+@pytest.mark.parametrize("n", [5, 6, 7, 12, 33])
+def test_wheel(n):
+    nn, (s, d) = F.wheel(n)
+    r = run(nn, s, d)
+    assert r["T"] == n - 1
+    assert r["t"][0] == n - 1 and (r["t"][1:] == 2).all()
+    assert r["lcc"][0] == 2.0 / (n - 2)
+    assert (r["lcc"][1:] == 2.0 / 3.0).all()
+
+
+def test_wheel4_is_k4():
+    n, (s, d) = F.wheel(4)
+    assert run(n, s, d)["T"] == 4
+
+
+@pytest.mark.parametrize("k", [1, 2, 5, 13])
+def test_friendship(k):
+    n, (s, d) = F.friendship(k)
+    r = run(n, s, d)
+    assert r["T"] == k
+    assert r["t"][0] == k and (r["t"][1:] == 1).all()
+    assert r["lcc"][0] == 1.0 / (2 * k - 1)
+    assert (r["lcc"][1:] == 1.0).all()
+
+
+@pytest.mark.parametrize("a,b,c", [(1, 1, 1), (2, 3, 4), (5, 1, 7), (6, 6, 6)])
+def test_complete_tripartite(a, b, c):
+    n, (s, d) = F.complete_tripartite(a, b, c)
+    r = run(n, s, d)
+    assert r["T"] == a * b * c
+    assert (r["t"][:a] == b * c).all()
+    assert (r["t"][a:a + b] == a * c).all()
+    assert (r["t"][a + b:] == a * b).all()
+
+
+# --------------------------------------------------------------------------
+# Brute force on tiny random graphs (with loops and repeated pairs injected)
+
+def _tiny(seed):
+    rng = np.random.default_rng(seed)
+    n = int(rng.integers(3, 48))
+    if seed % 2 == 0:
+        s, d = graphgen.er(n, int(rng.integers(0, n * (n - 1) // 2 + 1)), seed=seed)
+    else:
+        scale = max(1, int(np.ceil(np.log2(n))))
+        s, d = graphgen.rmat(scale, int(rng.integers(1, 6 * n)), seed=seed, n=n)
+    # inject repeats (both orientations) and self-loops
+    k = len(s)
+    if k:
+        pick = rng.integers(0, k, size=k // 3 + 1)
+        s = np.concatenate([s, d[pick], s[pick[: len(pick) // 2]]])
+        d = np.concatenate([d, s[: k][pick], d[pick[: len(pick) // 2]]])
+    loops = rng.integers(0, n, size=3).astype(np.int32)
+    s = np.concatenate([s, loops]).astype(np.int32)
+    d = np.concatenate([d, loops]).astype(np.int32)
+    perm = rng.permutation(len(s))
+    return n, s[perm], d[perm]
+
+
+@pytest.mark.parametrize("seed", range(60))
+def test_brute_force_tiny(seed):
+    n, s, d = _tiny(seed)
+    r = run(n, s, d)
+    T1, t1 = F.brute_triples(n, s, d)
+    T2, t2 = F.brute_matrix(n, s, d)
+    assert r["T"] == T1 == T2
+    np.testing.assert_array_equal(r["t"], t1)
+    np.testing.assert_array_equal(r["t"], t2)
+    np.testing.assert_array_equal(r["lcc"], F.exact_lcc(t1, F.dense_adjacency(n, s, d).sum(1)))
+
+
+# --------------------------------------------------------------------------
+# Algebraic form (Sec. VI-B): C = A A o A, t = rowsum(C) / 2, with scipy.sparse
+
+def _scipy_t(n, s, d):
+    keep = s != d
+    A = sp.coo_matrix((np.ones(keep.sum(), dtype=np.int64), (s[keep], d[keep])), shape=(n, n)).tocsr()
+    A = ((A + A.T) > 0).astype(np.int64)
+    C = (A @ A).multiply(A)
+    return np.asarray(C.sum(axis=1)).ravel().astype(np.uint64) // 2, np.asarray(A.sum(axis=1)).ravel()
+
+
+@pytest.mark.parametrize("name", ["er4096"])
+def test_algebraic_form_er4096(name):
+    w = graphgen.workload(name)
+    s, d = w.edges()
+    r = run(w.n, s, d)
+    t, deg = _scipy_t(w.n, s, d)
+    np.testing.assert_array_equal(r["t"], t)
+    np.testing.assert_array_equal(r["degree"], deg)
+    np.testing.assert_array_equal(r["lcc"], F.exact_lcc(t, deg))
+    assert r["m_simple"] == 32768 and r["loops_dropped"] == 0 and r["dups_dropped"] == 0
+
+
+@pytest.mark.parametrize("scale,ef,seed", [(10, 16, 5), (12, 8, 6)])
+def test_algebraic_form_rmat(scale, ef, seed):
+    n = 1 << scale
+    s, d = graphgen.rmat(scale, ef * n, seed=seed)
+    r = run(n, s, d)
+    t, deg = _scipy_t(n, s, d)
+    np.testing.assert_array_equal(r["t"], t)
+    np.testing.assert_array_equal(r["lcc"], F.exact_lcc(t, deg))
+
+
+# --------------------------------------------------------------------------
+# The paper's per-vertex formula (Alg. 3) against the oriented count
+
+@pytest.mark.parametrize("scale,ef,seed", [(11, 16, 1), (13, 8, 2)])
+def test_per_vertex_formula_agrees(scale, ef, seed):
+    n = 1 << scale
+    s, d = graphgen.rmat(scale, ef * n, seed=seed)
+    off, adj, _ = oracle.build_csr(n, s, d)
+    op, ap = oracle.orient(n, off, adj)
+    t_or = oracle.tc_oriented(n, op, ap)
+    t_v = oracle.tc_vertex(n, off, adj, np.arange(n, dtype=np.int32))
+    np.testing.assert_array_equal(t_or, t_v)
+    # the threaded split gives the same result
+    np.testing.assert_array_equal(oracle.tc_oriented(n, op, ap, threads=4), t_or)
+
+
+def test_orientation_by_id_gives_same_counts():
+    # Sec. II-C orients by id (j < k); the (degree, id) order must agree.
+    n = 1 << 11
+    s, d = graphgen.rmat(11, 8 * n, seed=9)
+    off, adj, _ = oracle.build_csr(n, s, d)
+    rows = np.repeat(np.arange(n), np.diff(off))
+    keep = adj > rows
+    op = np.zeros(n + 1, dtype=np.int64)
+    op[1:] = np.cumsum(np.bincount(rows[keep], minlength=n))
+    ap = adj[keep]
+    np.testing.assert_array_equal(oracle.tc_oriented(n, op, ap), run(n, s, d)["t"])
+
+
+# --------------------------------------------------------------------------
+# Invariants and input handling
+
+def test_relabel_edge_order_and_repeats():
+    n = 1 << 10
+    s, d = graphgen.rmat(10, 16 * n, seed=11)
+    base = run(n, s, d)
+    rng = np.random.default_rng(0)
+    perm = rng.permutation(n).astype(np.int32)      # new id of old vertex
+    r = run(n, perm[s], perm[d])
+    np.testing.assert_array_equal(r["t"][perm], base["t"])
+    np.testing.assert_array_equal(r["lcc"][perm], base["lcc"])
+    order = rng.permutation(len(s))
+    r = run(n, d[order], s[order])                   # reversed pairs, shuffled
+    np.testing.assert_array_equal(r["t"], base["t"])
+    r = run(n, np.concatenate([s, d, s]), np.concatenate([d, s, d]))
+    np.testing.assert_array_equal(r["t"], base["t"])
+    assert r["m_simple"] == base["m_simple"]
+    assert r["dups_dropped"] == base["dups_dropped"] + 2 * (len(s) - base["loops_dropped"])
+
+
+def test_sum_t_is_three_T_and_bounds():
+    w = graphgen.workload("er4096")
+    s, d = w.edges()
+    r = run(w.n, s, d)
+    assert int(r["t"].sum()) == 3 * r["T"]
+    deg = r["degree"]
+    assert (r["t"] <= deg * (deg - 1) // 2).all()
+    assert ((r["lcc"] >= 0) & (r["lcc"] <= 1)).all()
+
+
+def test_loop_and_duplicate_accounting():
+    s = np.array([0, 1, 1, 2, 2, 0, 3, 3, 1], dtype=np.int32)
+    d = np.array([1, 0, 2, 1, 2, 2, 3, 0, 2], dtype=np.int32)
+    r = run(4, s, d)
+    # edges {0,1} x2, {1,2} x3, {0,2}, {0,3}; loops (2,2), (3,3)
+    assert r["loops_dropped"] == 2
+    assert r["m_simple"] == 4
+    assert r["dups_dropped"] == 3
+    assert r["T"] == 1
+    assert r["t"].tolist() == [1, 1, 1, 0]
+    assert r["degree"].tolist() == [3, 2, 2, 1]
+    assert r["lcc"].tolist() == [1.0 / 3.0, 1.0, 1.0, 0.0]
+
+
+def test_bad_ids_rejected():
+    with pytest.raises(ValueError):
+        oracle.build_csr(3, np.array([0, 3], np.int32), np.array([1, 1], np.int32))
+    with pytest.raises(ValueError):
+        oracle.build_csr(3, np.array([-1], np.int32), np.array([1], np.int32))
+
+
+def test_empty_and_isolated():
+    r = run(0, np.array([], np.int32), np.array([], np.int32))
+    assert r["T"] == 0 and len(r["t"]) == 0
+    r = run(5, np.array([], np.int32), np.array([], np.int32))
+    assert r["T"] == 0 and (r["lcc"] == 0).all()
+
+
+def test_csr_input_reads_every_entry_as_a_pair():
+    n, (s, d) = F.wheel(9)
+    off, adj, _ = oracle.build_csr(n, s, d)
+    r = oracle.triangles_csr(n, off, adj)
+    assert r["T"] == 8
+    # an asymmetric, unsorted CSR with repeats describes the same simple graph
+    off2 = np.array([0, 2, 3, 5], dtype=np.int64)
+    adj2 = np.array([2, 1, 2, 0, 1], dtype=np.int32)
+    r2 = oracle.triangles_csr(3, off2, adj2)
+    assert r2["T"] == 1 and r2["m_simple"] == 3 and r2["dups_dropped"] == 2
