@@ -1,0 +1,172 @@
+/*
+ * tc.h -- triangle counting (TC) and local clustering coefficient (LCC) on one
+ * GB300 GPU (sm_103a).  C ABI: plain pointers and sizes, no C++ or framework types.
+ *
+ * Problem statement (arxiv 2202.13976): the input is read as a simple, unweighted,
+ * undirected graph G = (V, E), |V| = n (Sec. II-A), given as an edge list or in
+ * CSR form (Sec. II-B).  The library computes
+ *   t(v)   = number of triangles that contain v            (Sec. I, Sec. II-D)
+ *   T      = (1/3) * sum_v t(v)                             (Sec. II-C)
+ *   LCC(v) = 2 t(v) / (deg(v) (deg(v) - 1)), 0 if deg(v) < 2 (Eq. 2)
+ * exactly: counts are unsigned 64-bit integers and LCC is one correctly rounded
+ * IEEE fp64 division of two exact integers.
+ *
+ * Conventions shared by every call:
+ *  - Vertex ids are int32 in [0, n); n <= 2^31 - 1.  Edge counts are int64 and at
+ *    most 2^31 - 1 pairs are accepted.
+ *  - Input semantics: (u, v) and (v, u) are the same edge; self-loops and repeated
+ *    pairs are dropped and counted (tc_graph_info).  An id outside [0, n) makes the
+ *    call fail with TC_EINVAL.
+ *  - mem_kind says where a caller pointer lives: TC_MEM_HOST (pageable or pinned
+ *    host memory) or TC_MEM_DEVICE (device memory of the current CUDA device).
+ *  - Ownership: the library copies what it needs from the inputs before the call
+ *    returns; the caller keeps ownership of every buffer it passes.  Outputs are
+ *    caller-allocated.
+ *  - Streams: a graph is bound to the CUDA stream given at creation (NULL = the
+ *    legacy default stream); all device work of that graph is ordered on it.  Calls
+ *    that return host data synchronise that stream before returning.
+ *  - Errors never abort the process: every failure is a tc_status.  Device-side
+ *    checks raise a flag that the host turns into a status.
+ *  - Thread safety: distinct graphs may be used from distinct host threads; one
+ *    graph must not be used from two threads at once.
+ */
+#ifndef TC_H
+#define TC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum tc_status {
+    TC_OK = 0,
+    TC_EINVAL = 1,   /* bad argument: id outside [0, n), size out of range, NULL */
+    TC_ENOMEM = 2,   /* device or host allocation failed */
+    TC_ECUDA = 3,    /* a CUDA runtime call failed (no device, launch failure, ...) */
+    TC_ETIMEOUT = 4, /* a bounded device-side wait gave up */
+    TC_EBUSY = 5,    /* the object is in use (server admission full) */
+    TC_EINTERNAL = 6 /* an internal consistency check failed (sum t != 0 mod 3, ...) */
+} tc_status;
+
+enum { TC_MEM_HOST = 0, TC_MEM_DEVICE = 1 };
+
+typedef struct tc_graph tc_graph;
+
+/*
+ * Build a graph from an undirected edge list (Sec. II-A/B, Alg. 3 "build CSR").
+ *   n            number of vertices (>= 0)
+ *   m            number of pairs (0 <= m <= 2^31 - 1)
+ *   src, dst     m int32 ids each; may be NULL when m == 0
+ *   mem_kind     where src/dst live
+ *   cuda_stream  a cudaStream_t (as void*), or NULL
+ *   out          receives the new graph; *out is NULL on failure
+ * The device copy holds the simple graph's degree-oriented CSR; the triangle count
+ * itself runs at the first tc_count / lcc_compute.
+ * Errors: TC_EINVAL (n < 0, m out of range, NULL pointers, id outside [0, n)),
+ *         TC_ENOMEM, TC_ECUDA.
+ */
+tc_status tc_graph_create_from_edges(int32_t n, int64_t m, const int32_t* src, const int32_t* dst,
+                                     int mem_kind, void* cuda_stream, tc_graph** out);
+
+/*
+ * Build a graph from CSR arrays (Sec. II-B, Fig. 2): row i lists
+ * adj[offsets[i] .. offsets[i+1]).  Every entry (i, adj[k]) is read as the
+ * undirected pair {i, adj[k]}, so rows need not be sorted, symmetric or free of
+ * repeats; the library re-normalises.
+ *   offsets  n + 1 int64 values, offsets[0] == 0, non-decreasing,
+ *            offsets[n] <= 2^31 - 1
+ *   adj      offsets[n] int32 ids
+ * Errors: as tc_graph_create_from_edges, plus TC_EINVAL for bad offsets.
+ */
+tc_status tc_graph_create_from_csr(int32_t n, const int64_t* offsets, const int32_t* adj,
+                                   int mem_kind, void* cuda_stream, tc_graph** out);
+
+/*
+ * Global triangle count T = (1/3) sum_v t(v) (Sec. II-C), written to the host
+ * scalar *T_out.  Runs the intersection if it has not run yet; synchronises the
+ * graph's stream.  Errors: TC_EINVAL (NULL), TC_ECUDA, TC_EINTERNAL (sum t is not
+ * a multiple of 3).
+ */
+tc_status tc_count(tc_graph* g, uint64_t* T_out);
+
+/*
+ * Per-vertex triangle counts t[n] (uint64) and LCC[n] (fp64, Eq. 2), in the
+ * caller's vertex ids.  Either output may be NULL to skip it.  mem_kind says where
+ * the outputs live; with TC_MEM_DEVICE the results are written by kernels on the
+ * graph's stream, with TC_MEM_HOST they are copied back and the stream is
+ * synchronised.  Degree-0/1 vertices report t = 0 and LCC = +0.0.
+ */
+tc_status lcc_compute(tc_graph* g, uint64_t* t_out, double* lcc_out, int mem_kind);
+
+/*
+ * Input accounting: number of distinct undirected edges, self-loops dropped and
+ * repeated pairs dropped.  Any pointer may be NULL.  Synchronises the stream.
+ */
+tc_status tc_graph_info(const tc_graph* g, int64_t* m_simple, int64_t* loops_dropped,
+                        int64_t* dups_dropped);
+
+/* Number of vertices and of oriented edges (= distinct undirected edges). */
+tc_status tc_graph_size(const tc_graph* g, int32_t* n, int64_t* m_oriented);
+
+/* Release the graph's device memory (back to the library's device pool). NULL is a no-op. */
+void tc_graph_destroy(tc_graph* g);
+
+/* Static, NUL-terminated description of a status code. */
+const char* tc_status_str(tc_status s);
+
+/* Detail of the last failure on the calling host thread (CUDA error text or the
+   failed check), NUL-terminated; empty if none.  Valid until the next call. */
+const char* tc_last_error_detail(void);
+
+/*
+ * Intersection strategies (Sec. II-C, Sec. IV-C).  The result never depends on the
+ * strategy, only the speed.
+ *   TC_STRAT_AUTO      per-edge choice by the hybrid rule of Eq. 3 (with the
+ *                      tunable factor below), bitmap probing for hub lists
+ *   TC_STRAT_MERGE     warp-cooperative merge path (the SSI of Alg. 2, split
+ *                      across lanes along the diagonals of the merge)
+ *   TC_STRAT_SEARCH    binary search of every key of the shorter list in the
+ *                      longer one (Alg. 1)
+ *   TC_STRAT_PROBE     each element of the neighbour's list probes the staged
+ *                      list of the source vertex (sorted, in shared memory)
+ *   TC_STRAT_BITMAP    like PROBE, against a bitmap of the staged list
+ */
+enum {
+    TC_STRAT_AUTO = 0,
+    TC_STRAT_MERGE = 1,
+    TC_STRAT_SEARCH = 2,
+    TC_STRAT_PROBE = 3,
+    TC_STRAT_BITMAP = 4
+};
+
+/*
+ * Degree buckets of the planner: vertices are grouped by their oriented
+ * out-degree d+ (the length of their staged list).
+ *   TC_BUCKET_WARP  2 <= d+ <= 32: one warp per vertex
+ *   TC_BUCKET_CTA   d+ > 32: one thread block per vertex
+ */
+enum { TC_BUCKET_WARP = 0, TC_BUCKET_CTA = 1, TC_NUM_BUCKETS = 2 };
+
+/*
+ * Per-graph tuning, applied at the next intersection (set before tc_count).
+ *   strategy  one of TC_STRAT_* for the bucket
+ *   factor    Eq. 3 is applied as  |B| / |A| <= factor * (log2|B| - 1)  when the
+ *             strategy is TC_STRAT_AUTO; factor = 1 is the paper's rule.
+ * Errors: TC_EINVAL for an unknown bucket or strategy, or a strategy the bucket
+ * cannot run (BITMAP in the warp bucket).
+ */
+tc_status tc_graph_set_strategy(tc_graph* g, int bucket, int strategy, double factor);
+
+/*
+ * Timing of the last intersection, in milliseconds per bucket kernel and in total
+ * (CUDA events on the graph's stream).  Synchronises the stream.
+ */
+tc_status tc_graph_last_timing(const tc_graph* g, float* ms_warp, float* ms_cta, float* ms_total);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TC_H */

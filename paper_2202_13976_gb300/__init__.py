@@ -1,0 +1,250 @@
+"""Triangle counting and LCC on a GB300 GPU: Python binding of libtc (include/tc.h).
+
+The binding only marshals arguments: every step of the computation runs in the
+CUDA library.  The functions carry the C ABI's names; device buffers are passed as
+PyTorch CUDA tensors (PyTorch supplies device memory and streams only), host
+buffers as numpy arrays.  There is no CPU path: if libtc.so cannot be loaded every
+call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from ._build import LIB, build as _build_lib, up_to_date
+
+TC_OK, TC_EINVAL, TC_ENOMEM, TC_ECUDA, TC_ETIMEOUT, TC_EBUSY, TC_EINTERNAL = range(7)
+TC_MEM_HOST, TC_MEM_DEVICE = 0, 1
+TC_STRAT_AUTO, TC_STRAT_MERGE, TC_STRAT_SEARCH, TC_STRAT_PROBE, TC_STRAT_BITMAP = range(5)
+TC_BUCKET_WARP, TC_BUCKET_CTA = 0, 1
+STRATEGIES = {"auto": TC_STRAT_AUTO, "merge": TC_STRAT_MERGE, "search": TC_STRAT_SEARCH,
+              "probe": TC_STRAT_PROBE, "bitmap": TC_STRAT_BITMAP}
+
+# Every symbol include/tc.h declares.
+EXPORTS = ["tc_graph_create_from_edges", "tc_graph_create_from_csr", "tc_count", "lcc_compute",
+           "tc_graph_info", "tc_graph_size", "tc_graph_destroy", "tc_status_str",
+           "tc_last_error_detail", "tc_graph_set_strategy", "tc_graph_last_timing"]
+
+_lib = None
+
+
+class TCError(RuntimeError):
+    def __init__(self, status: int, detail: str = ""):
+        self.status = status
+        msg = _lib.tc_status_str(status).decode() if _lib else f"status {status}"
+        super().__init__(f"{msg}{': ' + detail if detail else ''}")
+
+
+def build(force: bool = False) -> str:
+    """Compile libtc.so for sm_103a (nvcc) if it is missing or stale."""
+    return _build_lib(force=force)
+
+
+def load(path: str | None = None):
+    """Load libtc.so (building it first when stale) and declare the C signatures."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if path is None:
+        if not up_to_date():
+            build()
+        path = LIB
+    lib = ctypes.CDLL(path)
+    P = ctypes.c_void_p
+    i32, i64, u64 = ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64
+    st = ctypes.c_int
+    lib.tc_graph_create_from_edges.restype = st
+    lib.tc_graph_create_from_edges.argtypes = [i32, i64, P, P, ctypes.c_int, P, ctypes.POINTER(P)]
+    lib.tc_graph_create_from_csr.restype = st
+    lib.tc_graph_create_from_csr.argtypes = [i32, P, P, ctypes.c_int, P, ctypes.POINTER(P)]
+    lib.tc_count.restype = st
+    lib.tc_count.argtypes = [P, ctypes.POINTER(u64)]
+    lib.lcc_compute.restype = st
+    lib.lcc_compute.argtypes = [P, P, P, ctypes.c_int]
+    lib.tc_graph_info.restype = st
+    lib.tc_graph_info.argtypes = [P, ctypes.POINTER(i64), ctypes.POINTER(i64), ctypes.POINTER(i64)]
+    lib.tc_graph_size.restype = st
+    lib.tc_graph_size.argtypes = [P, ctypes.POINTER(i32), ctypes.POINTER(i64)]
+    lib.tc_graph_destroy.restype = None
+    lib.tc_graph_destroy.argtypes = [P]
+    lib.tc_status_str.restype = ctypes.c_char_p
+    lib.tc_status_str.argtypes = [st]
+    lib.tc_last_error_detail.restype = ctypes.c_char_p
+    lib.tc_last_error_detail.argtypes = []
+    lib.tc_graph_set_strategy.restype = st
+    lib.tc_graph_set_strategy.argtypes = [P, ctypes.c_int, ctypes.c_int, ctypes.c_double]
+    lib.tc_graph_last_timing.restype = st
+    lib.tc_graph_last_timing.argtypes = [P, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_float),
+                                         ctypes.POINTER(ctypes.c_float)]
+    _lib = lib
+    return lib
+
+
+def lib():
+    return load()
+
+
+def _check(status: int):
+    if status != TC_OK:
+        raise TCError(status, _lib.tc_last_error_detail().decode())
+
+
+def _is_device(x) -> bool:
+    return hasattr(x, "data_ptr") and getattr(x, "is_cuda", False)
+
+
+def _ptr_kind(*arrays):
+    """(pointers, mem_kind) for numpy arrays (host) or torch CUDA tensors (device)."""
+    dev = [_is_device(a) for a in arrays if a is not None]
+    if dev and any(dev) != all(dev):
+        raise ValueError("mix of host and device buffers")
+    kind = TC_MEM_DEVICE if dev and dev[0] else TC_MEM_HOST
+    ptrs = []
+    for a in arrays:
+        if a is None:
+            ptrs.append(None)
+        elif kind == TC_MEM_DEVICE:
+            if not a.is_contiguous():
+                raise ValueError("device buffers must be contiguous")
+            ptrs.append(a.data_ptr())
+        else:
+            if not (isinstance(a, np.ndarray) and a.flags.c_contiguous):
+                raise ValueError("host buffers must be C-contiguous numpy arrays")
+            ptrs.append(a.ctypes.data)
+    return ptrs, kind
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        return None
+    return getattr(stream, "cuda_stream", stream)
+
+
+def tc_graph_create_from_edges(n: int, src, dst, stream=None) -> int:
+    """Graph handle from int32 pairs (numpy arrays on the host or CUDA tensors)."""
+    load()
+    if len(src) != len(dst):
+        raise ValueError("src and dst differ in length")
+    _check_dtype(src, "int32")
+    _check_dtype(dst, "int32")
+    (ps, pd), kind = _ptr_kind(src, dst)
+    out = ctypes.c_void_p()
+    _check(_lib.tc_graph_create_from_edges(n, len(src), ps, pd, kind, _stream_ptr(stream), ctypes.byref(out)))
+    return out.value
+
+
+def tc_graph_create_from_csr(n: int, offsets, adj, stream=None) -> int:
+    """Graph handle from CSR arrays (int64 offsets[n+1], int32 adj)."""
+    load()
+    _check_dtype(offsets, "int64")
+    _check_dtype(adj, "int32")
+    (po, pa), kind = _ptr_kind(offsets, adj)
+    out = ctypes.c_void_p()
+    _check(_lib.tc_graph_create_from_csr(n, po, pa, kind, _stream_ptr(stream), ctypes.byref(out)))
+    return out.value
+
+
+def _check_dtype(a, name):
+    dt = str(getattr(a, "dtype", ""))
+    if not dt.endswith(name):
+        raise TypeError(f"expected {name} buffer, got {dt}")
+
+
+def tc_count(g: int) -> int:
+    T = ctypes.c_uint64()
+    _check(_lib.tc_count(g, ctypes.byref(T)))
+    return int(T.value)
+
+
+def lcc_compute(g: int, t_out=None, lcc_out=None):
+    """Fill caller-allocated t_out (uint64[n]) and lcc_out (float64[n]); either may be None."""
+    if t_out is not None:
+        _check_dtype(t_out, "int64")
+    if lcc_out is not None:
+        _check_dtype(lcc_out, "float64")
+    (pt, pl), kind = _ptr_kind(t_out, lcc_out)
+    _check(_lib.lcc_compute(g, pt, pl, kind))
+
+
+def tc_graph_info(g: int) -> dict:
+    a, b, c = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+    _check(_lib.tc_graph_info(g, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
+    return {"m_simple": a.value, "loops_dropped": b.value, "dups_dropped": c.value}
+
+
+def tc_graph_size(g: int) -> tuple[int, int]:
+    n, m = ctypes.c_int32(), ctypes.c_int64()
+    _check(_lib.tc_graph_size(g, ctypes.byref(n), ctypes.byref(m)))
+    return n.value, m.value
+
+
+def tc_graph_destroy(g: int) -> None:
+    if g:
+        _lib.tc_graph_destroy(g)
+
+
+def tc_graph_set_strategy(g: int, bucket: int, strategy, factor: float = 1.0) -> None:
+    if isinstance(strategy, str):
+        strategy = STRATEGIES[strategy]
+    _check(_lib.tc_graph_set_strategy(g, bucket, strategy, factor))
+
+
+def tc_graph_last_timing(g: int) -> dict:
+    a, b, c = ctypes.c_float(), ctypes.c_float(), ctypes.c_float()
+    _check(_lib.tc_graph_last_timing(g, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
+    return {"warp_ms": a.value, "cta_ms": b.value, "total_ms": c.value}
+
+
+class Graph:
+    """Owning wrapper around a tc_graph handle."""
+
+    def __init__(self, handle: int, n: int):
+        self.handle = handle
+        self.n = n
+
+    @classmethod
+    def from_edges(cls, n, src, dst, stream=None) -> "Graph":
+        return cls(tc_graph_create_from_edges(n, src, dst, stream), n)
+
+    @classmethod
+    def from_csr(cls, n, offsets, adj, stream=None) -> "Graph":
+        return cls(tc_graph_create_from_csr(n, offsets, adj, stream), n)
+
+    def count(self) -> int:
+        return tc_count(self.handle)
+
+    def lcc(self, t_out=None, lcc_out=None):
+        """Host numpy results when no buffers are given; else fills the buffers."""
+        if t_out is None and lcc_out is None:
+            t_out = np.empty(self.n, dtype=np.uint64)
+            lcc_out = np.empty(self.n, dtype=np.float64)
+        lcc_compute(self.handle, t_out, lcc_out)
+        return t_out, lcc_out
+
+    def info(self) -> dict:
+        return tc_graph_info(self.handle)
+
+    def set_strategy(self, bucket, strategy, factor=1.0):
+        tc_graph_set_strategy(self.handle, bucket, strategy, factor)
+
+    def timing(self) -> dict:
+        return tc_graph_last_timing(self.handle)
+
+    def close(self):
+        tc_graph_destroy(self.handle)
+        self.handle = 0
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            if self.handle and _lib is not None:
+                self.close()
+        except Exception:
+            pass

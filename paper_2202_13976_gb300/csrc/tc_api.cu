@@ -1,0 +1,468 @@
+// C ABI of the library (include/tc.h): graph objects, device memory and the order
+// of the device phases.
+//
+// Device memory comes from one stream-ordered pool per device (cudaMemPool with an
+// unlimited release threshold), so repeated create/destroy cycles reuse memory
+// without returning it to the driver and without device-wide synchronisation.
+#include <cuda_runtime.h>
+
+#include <climits>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <vector>
+
+#include "tc_internal.h"
+
+using namespace tcg;
+
+namespace {
+
+thread_local char g_last_error[256] = "";
+
+void set_error(const char* where, cudaError_t e) {
+    snprintf(g_last_error, sizeof(g_last_error), "%s: %s", where, cudaGetErrorString(e));
+}
+
+struct DeviceState {
+    bool ready = false;
+    int sms = 0;
+    cudaMemPool_t pool = nullptr;
+};
+
+std::mutex g_dev_mutex;
+DeviceState g_dev[64];
+
+tc_status init_device(int dev, DeviceState** out) {
+    if (dev < 0 || dev >= 64) return TC_ECUDA;
+    std::lock_guard<std::mutex> lock(g_dev_mutex);
+    DeviceState& D = g_dev[dev];
+    if (!D.ready) {
+        cudaError_t e = cudaDeviceGetAttribute(&D.sms, cudaDevAttrMultiProcessorCount, dev);
+        if (e != cudaSuccess) {
+            set_error("cudaDeviceGetAttribute", e);
+            return TC_ECUDA;
+        }
+        cudaMemPoolProps props;
+        memset(&props, 0, sizeof(props));
+        props.allocType = cudaMemAllocationTypePinned;
+        props.handleTypes = cudaMemHandleTypeNone;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = dev;
+        e = cudaMemPoolCreate(&D.pool, &props);
+        if (e != cudaSuccess) {
+            set_error("cudaMemPoolCreate", e);
+            return TC_ECUDA;
+        }
+        uint64_t thr = UINT64_MAX;
+        cudaMemPoolSetAttribute(D.pool, cudaMemPoolAttrReleaseThreshold, &thr);
+        if ((e = build_init_attributes()) != cudaSuccess || (e = intersect_init_attributes()) != cudaSuccess) {
+            set_error("cudaFuncSetAttribute", e);
+            return TC_ECUDA;
+        }
+        D.ready = true;
+    }
+    *out = &D;
+    return TC_OK;
+}
+
+}  // namespace
+
+struct tc_graph {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    cudaMemPool_t pool = nullptr;
+    Launch L{};
+    int32_t n = 0;
+    int64_t m_in = 0;
+    int32_t* rank = nullptr;
+    int64_t* rowstart = nullptr;
+    int32_t* rowlen = nullptr;
+    int32_t* col = nullptr;
+    int32_t* deg = nullptr;
+    int32_t* warp_list = nullptr;
+    int32_t* cta_list = nullptr;
+    unsigned long long* t_rank = nullptr;
+    DevStats* stats = nullptr;
+    std::vector<void*> blocks;
+    bool counted = false;
+    Strategy strat{};
+    cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
+    bool timed = false;
+};
+
+namespace {
+
+tc_status cuda_fail(const char* where, cudaError_t e) {
+    set_error(where, e);
+    return TC_ECUDA;
+}
+
+#define TC_CK(call)                                                 \
+    do {                                                            \
+        cudaError_t e_ = (call);                                    \
+        if (e_ != cudaSuccess) return cuda_fail(#call, e_);         \
+    } while (0)
+
+template <typename T>
+tc_status dalloc(tc_graph* g, T** p, size_t count, std::vector<void*>* track) {
+    size_t bytes = count * sizeof(T);
+    if (bytes == 0) bytes = 16;
+    bytes = (bytes + 255) & ~(size_t)255;
+    void* q = nullptr;
+    cudaError_t e = cudaMallocFromPoolAsync(&q, bytes, g->pool, g->stream);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        set_error("cudaMallocFromPoolAsync", e);
+        return TC_ENOMEM;
+    }
+    track->push_back(q);
+    *p = static_cast<T*>(q);
+    return TC_OK;
+}
+
+void free_list(tc_graph* g, std::vector<void*>* list) {
+    for (void* p : *list) cudaFreeAsync(p, g->stream);
+    list->clear();
+}
+
+tc_status new_graph(int32_t n, void* stream, tc_graph** out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail("cudaGetDevice", e);
+    DeviceState* D = nullptr;
+    tc_status st = init_device(dev, &D);
+    if (st != TC_OK) return st;
+    tc_graph* g = new (std::nothrow) tc_graph();
+    if (!g) return TC_ENOMEM;
+    g->device = dev;
+    g->stream = static_cast<cudaStream_t>(stream);
+    g->pool = D->pool;
+    g->L.stream = g->stream;
+    g->L.sms = D->sms;
+    g->n = n;
+    for (int b = 0; b < TC_NUM_BUCKETS; ++b) {
+        g->strat.strat[b] = TC_STRAT_AUTO;
+        g->strat.factor[b] = 1.0f;
+    }
+    *out = g;
+    return TC_OK;
+}
+
+tc_status read_stats(const tc_graph* g, DevStats* h) {
+    TC_CK(cudaMemcpyAsync(h, g->stats, sizeof(DevStats), cudaMemcpyDeviceToHost, g->stream));
+    TC_CK(cudaStreamSynchronize(g->stream));
+    return TC_OK;
+}
+
+int bits_for(unsigned x) {
+    int b = 0;
+    while (b < 32 && (x >> b) != 0) ++b;
+    return b;
+}
+
+// Builds the oriented CSR from device-resident pairs (src, dst) of length m.
+tc_status build_graph(tc_graph* g, const int32_t* src, const int32_t* dst, int64_t m) {
+    const int32_t n = g->n;
+    const size_t nn = (size_t)n;
+    tc_status st;
+    std::vector<void*>& keep = g->blocks;
+    if ((st = dalloc(g, &g->stats, 1, &keep)) || (st = dalloc(g, &g->rank, nn, &keep)) ||
+        (st = dalloc(g, &g->rowstart, nn + 1, &keep)) || (st = dalloc(g, &g->rowlen, nn, &keep)) ||
+        (st = dalloc(g, &g->col, (size_t)m, &keep)) || (st = dalloc(g, &g->deg, nn, &keep)) ||
+        (st = dalloc(g, &g->warp_list, nn, &keep)) || (st = dalloc(g, &g->cta_list, nn, &keep)) ||
+        (st = dalloc(g, &g->t_rank, nn, &keep)))
+        return st;
+    std::vector<void*> scratch;
+    BuildBuffers B{};
+    B.src = src;
+    B.dst = dst;
+    B.m = m;
+    B.n = n;
+    size_t tmp_bytes = scan_tmp_bytes((int64_t)nn + 1);
+    size_t rt = radix_tmp_bytes((int64_t)nn);
+    if (rt > tmp_bytes) tmp_bytes = rt;
+    char* tmp = nullptr;
+    if ((st = dalloc(g, &B.dmulti, nn, &scratch)) || (st = dalloc(g, &B.keys, nn, &scratch)) ||
+        (st = dalloc(g, &B.keys_alt, nn, &scratch)) || (st = dalloc(g, &B.rowcnt, nn + 1, &scratch)) ||
+        (st = dalloc(g, &B.cursor, nn, &scratch)) || (st = dalloc(g, &B.longlist, nn, &scratch)) ||
+        (st = dalloc(g, &tmp, tmp_bytes, &scratch))) {
+        free_list(g, &scratch);
+        return st;
+    }
+    B.tmp = tmp;
+    B.rank = g->rank;
+    B.rowstart = g->rowstart;
+    B.rowlen = g->rowlen;
+    B.col = g->col;
+    B.deg = g->deg;
+    B.stats = g->stats;
+    cudaMemsetAsync(g->stats, 0, sizeof(DevStats), g->stream);
+    cudaMemsetAsync(B.dmulti, 0, sizeof(uint32_t) * nn, g->stream);
+    launch_canon_degree(B, g->L);
+    DevStats h;
+    if ((st = read_stats(g, &h)) != TC_OK) {
+        free_list(g, &scratch);
+        return st;
+    }
+    if (h.err & ERR_BAD_ID) {
+        free_list(g, &scratch);
+        snprintf(g_last_error, sizeof(g_last_error), "vertex id outside [0, n)");
+        return TC_EINVAL;
+    }
+    launch_rank(B, bits_for(h.max_deg), g->L);
+    launch_orient(B, g->L);
+    CountBuffers C{n, g->rowstart, g->rowlen, g->col, g->warp_list, g->cta_list, g->t_rank, g->stats};
+    launch_plan(C, g->L);
+    free_list(g, &scratch);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail("build kernels", e);
+    return TC_OK;
+}
+
+tc_status run_count(tc_graph* g) {
+    if (g->counted) return TC_OK;
+    if (!g->ev[0]) {
+        for (int i = 0; i < 3; ++i) TC_CK(cudaEventCreate(&g->ev[i]));
+    }
+    TC_CK(cudaMemsetAsync(g->t_rank, 0, sizeof(unsigned long long) * (size_t)g->n, g->stream));
+    TC_CK(cudaMemsetAsync(&g->stats->sum_t, 0, sizeof(unsigned long long), g->stream));
+    CountBuffers C{g->n, g->rowstart, g->rowlen, g->col, g->warp_list, g->cta_list, g->t_rank, g->stats};
+    launch_intersect(C, g->strat, g->ev, g->L);
+    launch_sum_t(C, g->L);
+    TC_CK(cudaGetLastError());
+    g->counted = true;
+    g->timed = true;
+    return TC_OK;
+}
+
+void destroy(tc_graph* g) {
+    if (!g) return;
+    free_list(g, &g->blocks);
+    for (int i = 0; i < 3; ++i)
+        if (g->ev[i]) cudaEventDestroy(g->ev[i]);
+    delete g;
+}
+
+tc_status finish_create(tc_graph* g, tc_status st, tc_graph** out) {
+    if (st != TC_OK) {
+        destroy(g);
+        *out = nullptr;
+        return st;
+    }
+    *out = g;
+    return TC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+tc_status tc_graph_create_from_edges(int32_t n, int64_t m, const int32_t* src, const int32_t* dst,
+                                     int mem_kind, void* cuda_stream, tc_graph** out) {
+    if (!out) return TC_EINVAL;
+    *out = nullptr;
+    if (n < 0 || m < 0 || m > INT_MAX || (m > 0 && (!src || !dst)) ||
+        (mem_kind != TC_MEM_HOST && mem_kind != TC_MEM_DEVICE))
+        return TC_EINVAL;
+    tc_graph* g = nullptr;
+    tc_status st = new_graph(n, cuda_stream, &g);
+    if (st != TC_OK) return st;
+    g->m_in = m;
+    if (mem_kind == TC_MEM_DEVICE) return finish_create(g, build_graph(g, src, dst, m), out);
+    std::vector<void*> tmp;
+    int32_t *ds = nullptr, *dd = nullptr;
+    if ((st = dalloc(g, &ds, (size_t)m, &tmp)) || (st = dalloc(g, &dd, (size_t)m, &tmp))) {
+        free_list(g, &tmp);
+        return finish_create(g, st, out);
+    }
+    if (m > 0) {
+        cudaError_t e = cudaMemcpyAsync(ds, src, sizeof(int32_t) * (size_t)m, cudaMemcpyHostToDevice, g->stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(dd, dst, sizeof(int32_t) * (size_t)m, cudaMemcpyHostToDevice, g->stream);
+        if (e != cudaSuccess) {
+            free_list(g, &tmp);
+            return finish_create(g, cuda_fail("cudaMemcpyAsync", e), out);
+        }
+    }
+    st = build_graph(g, ds, dd, m);
+    free_list(g, &tmp);
+    return finish_create(g, st, out);
+}
+
+tc_status tc_graph_create_from_csr(int32_t n, const int64_t* offsets, const int32_t* adj, int mem_kind,
+                                   void* cuda_stream, tc_graph** out) {
+    if (!out) return TC_EINVAL;
+    *out = nullptr;
+    if (n < 0 || !offsets || (mem_kind != TC_MEM_HOST && mem_kind != TC_MEM_DEVICE)) return TC_EINVAL;
+    int64_t m = 0;
+    if (mem_kind == TC_MEM_HOST) {
+        if (offsets[0] != 0) return TC_EINVAL;
+        for (int32_t i = 0; i < n; ++i)
+            if (offsets[i + 1] < offsets[i]) return TC_EINVAL;
+        m = offsets[n];
+        if (m > INT_MAX) return TC_EINVAL;
+        if (m > 0 && !adj) return TC_EINVAL;
+    }
+    tc_graph* g = nullptr;
+    tc_status st = new_graph(n, cuda_stream, &g);
+    if (st != TC_OK) return st;
+    std::vector<void*> tmp;
+    const int64_t* doff = offsets;
+    const int32_t* dadj = adj;
+    DevStats* dstat = nullptr;
+    if ((st = dalloc(g, &dstat, 1, &tmp))) {
+        free_list(g, &tmp);
+        return finish_create(g, st, out);
+    }
+    cudaMemsetAsync(dstat, 0, sizeof(DevStats), g->stream);
+    if (mem_kind == TC_MEM_HOST) {
+        int64_t* o = nullptr;
+        int32_t* a = nullptr;
+        if ((st = dalloc(g, &o, (size_t)n + 1, &tmp)) || (st = dalloc(g, &a, (size_t)m, &tmp))) {
+            free_list(g, &tmp);
+            return finish_create(g, st, out);
+        }
+        cudaMemcpyAsync(o, offsets, sizeof(int64_t) * ((size_t)n + 1), cudaMemcpyHostToDevice, g->stream);
+        if (m > 0) cudaMemcpyAsync(a, adj, sizeof(int32_t) * (size_t)m, cudaMemcpyHostToDevice, g->stream);
+        doff = o;
+        dadj = a;
+    } else {
+        launch_check_offsets(doff, n, INT_MAX, dstat, g->L);
+        DevStats h;
+        int64_t last = 0;
+        cudaError_t e = cudaMemcpyAsync(&h, dstat, sizeof(DevStats), cudaMemcpyDeviceToHost, g->stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(&last, doff + n, sizeof(int64_t), cudaMemcpyDeviceToHost, g->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(g->stream);
+        if (e != cudaSuccess) {
+            free_list(g, &tmp);
+            return finish_create(g, cuda_fail("offsets check", e), out);
+        }
+        if (h.err || (last > 0 && !adj)) {
+            free_list(g, &tmp);
+            return finish_create(g, TC_EINVAL, out);
+        }
+        m = last;
+    }
+    int32_t* rows = nullptr;
+    if ((st = dalloc(g, &rows, (size_t)m, &tmp))) {
+        free_list(g, &tmp);
+        return finish_create(g, st, out);
+    }
+    launch_expand_csr(doff, n, rows, dstat, g->L);
+    g->m_in = m;
+    st = build_graph(g, rows, dadj, m);
+    free_list(g, &tmp);
+    return finish_create(g, st, out);
+}
+
+tc_status tc_count(tc_graph* g, uint64_t* T_out) {
+    if (!g || !T_out) return TC_EINVAL;
+    tc_status st = run_count(g);
+    if (st != TC_OK) return st;
+    DevStats h;
+    if ((st = read_stats(g, &h)) != TC_OK) return st;
+    if (h.sum_t % 3 != 0) {
+        snprintf(g_last_error, sizeof(g_last_error), "sum of t is not a multiple of 3");
+        return TC_EINTERNAL;
+    }
+    *T_out = h.sum_t / 3;
+    return TC_OK;
+}
+
+tc_status lcc_compute(tc_graph* g, uint64_t* t_out, double* lcc_out, int mem_kind) {
+    if (!g || (mem_kind != TC_MEM_HOST && mem_kind != TC_MEM_DEVICE)) return TC_EINVAL;
+    tc_status st = run_count(g);
+    if (st != TC_OK) return st;
+    if (!t_out && !lcc_out) return TC_OK;
+    if (mem_kind == TC_MEM_DEVICE) {
+        launch_finalize(g->n, g->rank, g->t_rank, g->deg, reinterpret_cast<unsigned long long*>(t_out), lcc_out,
+                        g->L);
+        TC_CK(cudaGetLastError());
+        return TC_OK;
+    }
+    std::vector<void*> tmp;
+    unsigned long long* dt = nullptr;
+    double* dl = nullptr;
+    if ((t_out && (st = dalloc(g, &dt, (size_t)g->n, &tmp))) || (lcc_out && (st = dalloc(g, &dl, (size_t)g->n, &tmp)))) {
+        free_list(g, &tmp);
+        return st;
+    }
+    launch_finalize(g->n, g->rank, g->t_rank, g->deg, dt, dl, g->L);
+    cudaError_t e = cudaSuccess;
+    if (t_out && g->n > 0)
+        e = cudaMemcpyAsync(t_out, dt, sizeof(uint64_t) * (size_t)g->n, cudaMemcpyDeviceToHost, g->stream);
+    if (e == cudaSuccess && lcc_out && g->n > 0)
+        e = cudaMemcpyAsync(lcc_out, dl, sizeof(double) * (size_t)g->n, cudaMemcpyDeviceToHost, g->stream);
+    free_list(g, &tmp);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(g->stream);
+    if (e != cudaSuccess) return cuda_fail("lcc_compute copy", e);
+    return TC_OK;
+}
+
+tc_status tc_graph_info(const tc_graph* g, int64_t* m_simple, int64_t* loops_dropped, int64_t* dups_dropped) {
+    if (!g) return TC_EINVAL;
+    DevStats h;
+    tc_status st = read_stats(g, &h);
+    if (st != TC_OK) return st;
+    if (m_simple) *m_simple = (int64_t)h.m_simple;
+    if (loops_dropped) *loops_dropped = (int64_t)h.loops;
+    if (dups_dropped) *dups_dropped = g->m_in - (int64_t)h.loops - (int64_t)h.m_simple;
+    return TC_OK;
+}
+
+tc_status tc_graph_size(const tc_graph* g, int32_t* n, int64_t* m_oriented) {
+    if (!g) return TC_EINVAL;
+    if (n) *n = g->n;
+    if (m_oriented) {
+        DevStats h;
+        tc_status st = read_stats(g, &h);
+        if (st != TC_OK) return st;
+        *m_oriented = (int64_t)h.m_simple;
+    }
+    return TC_OK;
+}
+
+void tc_graph_destroy(tc_graph* g) { destroy(g); }
+
+const char* tc_status_str(tc_status s) {
+    switch (s) {
+        case TC_OK: return "TC_OK: success";
+        case TC_EINVAL: return "TC_EINVAL: invalid argument";
+        case TC_ENOMEM: return "TC_ENOMEM: out of memory";
+        case TC_ECUDA: return "TC_ECUDA: CUDA runtime error";
+        case TC_ETIMEOUT: return "TC_ETIMEOUT: device-side wait timed out";
+        case TC_EBUSY: return "TC_EBUSY: resource busy";
+        case TC_EINTERNAL: return "TC_EINTERNAL: internal consistency check failed";
+    }
+    return "unknown tc_status";
+}
+
+const char* tc_last_error_detail(void) { return g_last_error; }
+
+tc_status tc_graph_set_strategy(tc_graph* g, int bucket, int strategy, double factor) {
+    if (!g || bucket < 0 || bucket >= TC_NUM_BUCKETS || strategy < TC_STRAT_AUTO || strategy > TC_STRAT_BITMAP ||
+        !(factor > 0.0))
+        return TC_EINVAL;
+    if (bucket == TC_BUCKET_WARP && strategy == TC_STRAT_BITMAP) return TC_EINVAL;
+    g->strat.strat[bucket] = strategy;
+    g->strat.factor[bucket] = (float)factor;
+    g->counted = false;
+    return TC_OK;
+}
+
+tc_status tc_graph_last_timing(const tc_graph* g, float* ms_warp, float* ms_cta, float* ms_total) {
+    if (!g) return TC_EINVAL;
+    if (!g->timed) return TC_EINVAL;
+    TC_CK(cudaEventSynchronize(g->ev[2]));
+    float a = 0, b = 0;
+    TC_CK(cudaEventElapsedTime(&a, g->ev[0], g->ev[1]));
+    TC_CK(cudaEventElapsedTime(&b, g->ev[1], g->ev[2]));
+    if (ms_warp) *ms_warp = a;
+    if (ms_cta) *ms_cta = b;
+    if (ms_total) *ms_total = a + b;
+    return TC_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,381 @@
+// Graph build on the device: simple-graph normalisation (Sec. II-A), CSR
+// (Sec. II-B) and the degree orientation that replaces the id-order upper
+// triangle of Sec. II-C.
+//
+// Pipeline (all in device memory, ids are int32):
+//  1. canon_degree  drop self-loops, count every non-loop pair at both ends
+//                   (multigraph degree), flag ids outside [0, n)
+//  2. rank          sort vertices by (degree, id): rank[v] = position
+//  3. orient        every non-loop pair {u, v} becomes the oriented entry
+//                   min(rank u, rank v) -> max(rank u, rank v); rows are filled by a
+//                   counting sort on the source rank
+//  4. segsort       each row is sorted (bitonic network in shared memory or, for very
+//                   long rows, in global memory) and repeated entries are removed;
+//                   the simple-graph degree of every vertex is counted from the
+//                   surviving entries
+// Any strict total order finds each triangle once; the (degree, id) order keeps
+// every oriented row short (d+(u) <= sqrt(2m)).  The degree used for the order is
+// the count of non-loop input pairs at a vertex, which equals the simple degree
+// unless the input repeats pairs; LCC always uses the simple degree.
+#include <climits>
+
+#include "tc_device.cuh"
+#include "tc_internal.h"
+
+namespace tcg {
+
+namespace {
+
+constexpr int THREADS = 256;
+constexpr int WARP_SORT_MAX = 1024;   // rows up to this length: one warp, shared memory
+constexpr int CTA_SORT_MAX = 16384;   // rows up to this length: one block, shared memory
+constexpr int SEG_WARPS = 8;          // warps per block in the warp sorter
+
+// CSR offsets check: offsets[0] == 0, non-decreasing, offsets[n] <= limit.
+__global__ void k_check_offsets(const int64_t* __restrict__ offsets, int32_t n, int64_t limit, DevStats* stats) {
+    int bad = 0;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
+        if (offsets[i + 1] < offsets[i]) bad = 1;
+    if (blockIdx.x == 0 && threadIdx.x == 0 && (offsets[0] != 0 || offsets[n] > limit || offsets[n] < 0)) bad = 1;
+    bad = __reduce_or_sync(FULL, bad);
+    if (lane_id() == 0 && bad) atomicOr(&stats->err, ERR_BAD_OFFSETS);
+}
+
+// Row expansion of a CSR input: rows[k] = i for offsets[i] <= k < offsets[i+1].
+// One warp per row.  Offsets must start at 0 and not decrease.
+__global__ void k_expand_csr(const int64_t* __restrict__ offsets, int32_t n, int32_t* __restrict__ rows,
+                             DevStats* stats) {
+    const int lane = lane_id();
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < n; i += warps) {
+        int64_t a = offsets[i], b = offsets[i + 1];
+        if (b < a || a < 0) {
+            if (lane == 0) atomicOr(&stats->err, ERR_BAD_OFFSETS);
+            continue;
+        }
+        for (int64_t k = a + lane; k < b; k += 32) rows[k] = (int32_t)i;
+    }
+}
+
+__global__ void k_canon_degree(const int32_t* __restrict__ src, const int32_t* __restrict__ dst,
+                               int64_t m, int32_t n, uint32_t* __restrict__ dmulti, DevStats* stats) {
+    unsigned long long loops = 0;
+    int err = 0;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += stride) {
+        int32_t u = src[i], v = dst[i];
+        if ((uint32_t)u >= (uint32_t)n || (uint32_t)v >= (uint32_t)n) {
+            err = ERR_BAD_ID;
+            continue;
+        }
+        if (u == v) {
+            ++loops;
+            continue;
+        }
+        atomicAdd(&dmulti[u], 1u);
+        atomicAdd(&dmulti[v], 1u);
+    }
+    loops = warp_sum(loops);
+    err = __reduce_or_sync(FULL, err);
+    if (lane_id() == 0) {
+        if (loops) atomicAdd(&stats->loops, loops);
+        if (err) atomicOr(&stats->err, err);
+    }
+}
+
+__global__ void k_max_deg(const uint32_t* __restrict__ dmulti, int32_t n, DevStats* stats) {
+    uint32_t mx = 0;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
+        mx = max(mx, dmulti[i]);
+    mx = __reduce_max_sync(FULL, mx);
+    if (lane_id() == 0 && mx) atomicMax(&stats->max_deg, mx);
+}
+
+__global__ void k_rank_keys(const uint32_t* __restrict__ dmulti, int32_t n, uint64_t* __restrict__ keys) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
+        keys[i] = ((uint64_t)dmulti[i] << 32) | (uint32_t)i;
+}
+
+__global__ void k_rank_invert(const uint64_t* __restrict__ sorted, int32_t n, int32_t* __restrict__ rank) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += stride)
+        rank[(uint32_t)sorted[r]] = (int32_t)r;
+}
+
+__global__ void k_orient_count(const int32_t* __restrict__ src, const int32_t* __restrict__ dst, int64_t m,
+                               const int32_t* __restrict__ rank, uint32_t* __restrict__ rowcnt) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += stride) {
+        int32_t u = src[i], v = dst[i];
+        if (u == v) continue;
+        int32_t a = rank[u], b = rank[v];
+        atomicAdd(&rowcnt[min(a, b)], 1u);
+    }
+}
+
+__global__ void k_orient_scatter(const int32_t* __restrict__ src, const int32_t* __restrict__ dst, int64_t m,
+                                 const int32_t* __restrict__ rank, const int64_t* __restrict__ rowstart,
+                                 uint32_t* __restrict__ cursor, int32_t* __restrict__ col) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += stride) {
+        int32_t u = src[i], v = dst[i];
+        if (u == v) continue;
+        int32_t a = rank[u], b = rank[v];
+        int32_t s = min(a, b), t = max(a, b);
+        int64_t p = rowstart[s] + atomicAdd(&cursor[s], 1u);
+        col[p] = t;
+    }
+}
+
+struct WarpSync {
+    __device__ __forceinline__ void operator()() const { __syncwarp(); }
+};
+struct BlockSync {
+    __device__ __forceinline__ void operator()() const { __syncthreads(); }
+};
+
+// Bitonic sorting network over P (power of two) elements of `s`, ascending, in the
+// form where every comparator sends the minimum to the lower index: the first
+// comparator layer of each merge compares mirrored positions, the later layers are
+// half-cleaners.  Padding with INT_MAX at the end is therefore inert.  `lanes`
+// workers with ids `me` share the work; `sync` orders the layers.
+template <typename Sync>
+__device__ __forceinline__ void bitonic_sort(int32_t* s, int P, int me, int lanes, Sync sync) {
+    for (int k = 2; k <= P; k <<= 1) {
+        const int half = k >> 1;
+        for (int i = me; i < (P >> 1); i += lanes) {
+            int blk = i / half, off = i - blk * half;
+            int lo = blk * k + off, hi = blk * k + k - 1 - off;
+            int32_t x = s[lo], y = s[hi];
+            if (x > y) {
+                s[lo] = y;
+                s[hi] = x;
+            }
+        }
+        sync();
+        for (int j = half >> 1; j >= 1; j >>= 1) {
+            for (int i = me; i < (P >> 1); i += lanes) {
+                int blk = i / j, off = i - blk * j;
+                int lo = blk * 2 * j + off, hi = lo + j;
+                int32_t x = s[lo], y = s[hi];
+                if (x > y) {
+                    s[lo] = y;
+                    s[hi] = x;
+                }
+            }
+            sync();
+        }
+    }
+}
+
+// Same network on a global-memory row of arbitrary length len (virtual +inf
+// padding up to the next power of two): comparators touching a padded slot are
+// skipped.
+__device__ void bitonic_sort_global(int32_t* s, int len, int me, int lanes) {
+    const int P = next_pow2_int(len);
+    for (int k = 2; k <= P; k <<= 1) {
+        const int half = k >> 1;
+        for (int i = me; i < (P >> 1); i += lanes) {
+            int blk = i / half, off = i - blk * half;
+            int lo = blk * k + off, hi = blk * k + k - 1 - off;
+            if (hi < len) {
+                int32_t x = s[lo], y = s[hi];
+                if (x > y) {
+                    s[lo] = y;
+                    s[hi] = x;
+                }
+            }
+        }
+        __syncthreads();
+        for (int j = half >> 1; j >= 1; j >>= 1) {
+            for (int i = me; i < (P >> 1); i += lanes) {
+                int blk = i / j, off = i - blk * j;
+                int lo = blk * 2 * j + off, hi = lo + j;
+                if (hi < len) {
+                    int32_t x = s[lo], y = s[hi];
+                    if (x > y) {
+                        s[lo] = y;
+                        s[hi] = x;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    }
+}
+
+// One warp per row.  Rows longer than WARP_SORT_MAX are left to k_segsort_block.
+__global__ void __launch_bounds__(SEG_WARPS * 32) k_segsort_warp(int32_t n, const int64_t* __restrict__ rowstart,
+                                                                 const uint32_t* __restrict__ rowcnt,
+                                                                 int32_t* __restrict__ col, int32_t* __restrict__ rowlen,
+                                                                 int32_t* __restrict__ deg, int32_t* __restrict__ longlist,
+                                                                 DevStats* stats) {
+    __shared__ int32_t sh[SEG_WARPS][WARP_SORT_MAX];
+    const int lane = lane_id(), w = threadIdx.x >> 5;
+    int32_t* s = sh[w];
+    const int64_t warps = (int64_t)gridDim.x * SEG_WARPS;
+    unsigned long long kept_total = 0;
+    for (int64_t r = (int64_t)blockIdx.x * SEG_WARPS + w; r < n; r += warps) {
+        const int len = (int)rowcnt[r];
+        const int64_t base = rowstart[r];
+        if (len == 0) {
+            if (lane == 0) rowlen[r] = 0;
+            continue;
+        }
+        if (len == 1) {
+            if (lane == 0) {
+                rowlen[r] = 1;
+                atomicAdd(&deg[col[base]], 1);
+                atomicAdd(&deg[r], 1);
+                kept_total += 1;
+            }
+            continue;
+        }
+        if (len > WARP_SORT_MAX) {
+            if (lane == 0) longlist[atomicAdd(&stats->long_count, 1u)] = (int32_t)r;
+            continue;
+        }
+        const int P = max(32, next_pow2_int(len));
+        for (int i = lane; i < P; i += 32) s[i] = i < len ? col[base + i] : INT_MAX;
+        __syncwarp();
+        bitonic_sort(s, P, lane, 32, WarpSync());
+        int kept = 0;
+        for (int c = 0; c < len; c += 32) {
+            int i = c + lane;
+            bool keep = i < len && (i == 0 || s[i] != s[i - 1]);
+            unsigned mk = __ballot_sync(FULL, keep);
+            if (keep) {
+                col[base + kept + __popc(mk & lanemask_lt())] = s[i];
+                atomicAdd(&deg[s[i]], 1);
+            }
+            kept += __popc(mk);
+        }
+        if (lane == 0) {
+            rowlen[r] = kept;
+            atomicAdd(&deg[r], kept);
+            kept_total += (unsigned long long)kept;
+        }
+        __syncwarp();
+    }
+    if (lane == 0 && kept_total) atomicAdd(&stats->m_simple, kept_total);
+}
+
+// One block per long row: shared-memory network up to CTA_SORT_MAX, global-memory
+// network beyond; then in-place compaction of repeated entries.
+__global__ void __launch_bounds__(1024) k_segsort_block(const int64_t* __restrict__ rowstart,
+                                                        const uint32_t* __restrict__ rowcnt,
+                                                        int32_t* __restrict__ col, int32_t* __restrict__ rowlen,
+                                                        int32_t* __restrict__ deg,
+                                                        const int32_t* __restrict__ longlist,
+                                                        DevStats* stats) {
+    extern __shared__ int32_t sh[];  // CTA_SORT_MAX entries
+    __shared__ int wk[32];
+    __shared__ int32_t boundary;
+    const int lane = lane_id(), w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const unsigned nlong = stats->long_count;
+    for (unsigned q = blockIdx.x; q < nlong; q += gridDim.x) {
+        const int32_t r = longlist[q];
+        const int len = (int)rowcnt[r];
+        const int64_t base = rowstart[r];
+        int32_t* s;
+        if (len <= CTA_SORT_MAX) {
+            const int P = next_pow2_int(len);
+            for (int i = threadIdx.x; i < P; i += blockDim.x) sh[i] = i < len ? col[base + i] : INT_MAX;
+            __syncthreads();
+            bitonic_sort(sh, P, threadIdx.x, blockDim.x, BlockSync());
+            s = sh;
+        } else {
+            bitonic_sort_global(col + base, len, threadIdx.x, blockDim.x);
+            s = col + base;
+        }
+        // compaction in chunks of blockDim; the last element of the previous chunk
+        // is kept in `boundary` because in-place writes may overwrite it.
+        int kept = 0;
+        if (threadIdx.x == 0) boundary = 0;
+        __syncthreads();
+        for (int c = 0; c < len; c += blockDim.x) {
+            int i = c + threadIdx.x;
+            int32_t x = i < len ? s[i] : 0;
+            int32_t prev = (i > 0 && threadIdx.x > 0 && i < len) ? s[i - 1] : boundary;
+            bool keep = i < len && (i == 0 || x != prev);
+            unsigned mk = __ballot_sync(FULL, keep);
+            if (lane == 0) wk[w] = __popc(mk);
+            __syncthreads();
+            int before = 0, tot = 0;
+            for (int k = 0; k < nw; ++k) {
+                before += k < w ? wk[k] : 0;
+                tot += wk[k];
+            }
+            int32_t last = s[min(c + (int)blockDim.x, len) - 1];
+            __syncthreads();
+            if (keep) {
+                col[base + kept + before + __popc(mk & lanemask_lt())] = x;
+                atomicAdd(&deg[x], 1);
+            }
+            kept += tot;
+            if (threadIdx.x == 0) boundary = last;
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) {
+            rowlen[r] = kept;
+            atomicAdd(&deg[r], kept);
+            atomicAdd(&stats->m_simple, (unsigned long long)kept);
+        }
+        __syncthreads();
+    }
+}
+
+}  // namespace
+
+void launch_check_offsets(const int64_t* offsets, int32_t n, int64_t limit, DevStats* stats, const Launch& L) {
+    k_check_offsets<<<grid_for(n + 1, THREADS, L.sms), THREADS, 0, L.stream>>>(offsets, n, limit, stats);
+}
+
+void launch_expand_csr(const int64_t* offsets, int32_t n, int32_t* rows, DevStats* stats, const Launch& L) {
+    if (n <= 0) return;
+    k_expand_csr<<<grid_for((int64_t)n * 32, THREADS, L.sms), THREADS, 0, L.stream>>>(offsets, n, rows, stats);
+}
+
+void launch_canon_degree(const BuildBuffers& B, const Launch& L) {
+    if (B.m > 0)
+        k_canon_degree<<<grid_for(B.m, THREADS, L.sms), THREADS, 0, L.stream>>>(B.src, B.dst, B.m, B.n, B.dmulti,
+                                                                              B.stats);
+    if (B.n > 0) k_max_deg<<<grid_for(B.n, THREADS, L.sms), THREADS, 0, L.stream>>>(B.dmulti, B.n, B.stats);
+}
+
+void launch_rank(const BuildBuffers& B, int deg_bits, const Launch& L) {
+    if (B.n <= 0) return;
+    k_rank_keys<<<grid_for(B.n, THREADS, L.sms), THREADS, 0, L.stream>>>(B.dmulti, B.n, B.keys);
+    // the keys start in id order, so a stable sort on the degree bits yields (degree, id)
+    uint64_t* sorted = radix_sort_u64(B.keys, B.keys_alt, B.n, 32, 32 + deg_bits, B.tmp, L);
+    k_rank_invert<<<grid_for(B.n, THREADS, L.sms), THREADS, 0, L.stream>>>(sorted, B.n, B.rank);
+}
+
+void launch_orient(const BuildBuffers& B, const Launch& L) {
+    if (B.n <= 0) return;
+    cudaMemsetAsync(B.rowcnt, 0, sizeof(uint32_t) * (size_t)B.n, L.stream);
+    cudaMemsetAsync(B.cursor, 0, sizeof(uint32_t) * (size_t)B.n, L.stream);
+    cudaMemsetAsync(B.deg, 0, sizeof(int32_t) * (size_t)B.n, L.stream);
+    if (B.m > 0)
+        k_orient_count<<<grid_for(B.m, THREADS, L.sms), THREADS, 0, L.stream>>>(B.src, B.dst, B.m, B.rank,
+                                                                              B.rowcnt);
+    scan_u32_to_i64(B.rowcnt, B.rowstart, B.n, B.tmp, L);
+    if (B.m > 0)
+        k_orient_scatter<<<grid_for(B.m, THREADS, L.sms), THREADS, 0, L.stream>>>(
+            B.src, B.dst, B.m, B.rank, B.rowstart, B.cursor, B.col);
+    k_segsort_warp<<<grid_for((int64_t)B.n * 32, SEG_WARPS * 32, L.sms, 4), SEG_WARPS * 32, 0, L.stream>>>(
+        B.n, B.rowstart, B.rowcnt, B.col, B.rowlen, B.deg, B.longlist, B.stats);
+    k_segsort_block<<<L.sms * 2, 1024, CTA_SORT_MAX * sizeof(int32_t), L.stream>>>(
+        B.rowstart, B.rowcnt, B.col, B.rowlen, B.deg, B.longlist, B.stats);
+}
+
+// 64 KB of dynamic shared memory for the block sorter.
+cudaError_t build_init_attributes() {
+    return cudaFuncSetAttribute(k_segsort_block, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                CTA_SORT_MAX * (int)sizeof(int32_t));
+}
+
+}  // namespace tcg

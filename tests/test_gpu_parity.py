@@ -1,0 +1,181 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle: T, t[] bit-exact,
+LCC bit-exact (0 ulp), input accounting exact."""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+
+import graphgen
+import oracle
+from tests import families as F
+from tests.gpu_util import assert_matches_oracle, gpu_run
+
+pytestmark = pytest.mark.gpu
+
+ALL_STRATEGIES = [("auto", 1.0), ("auto", 4.0), ("auto", 0.25), ("merge", 1.0), ("search", 1.0),
+                  ("probe", 1.0)]
+
+
+@pytest.fixture(scope="module")
+def er4096():
+    w = graphgen.workload("er4096")
+    s, d = w.edges()
+    return w.n, s, d, oracle.triangles(w.n, s, d)
+
+
+@pytest.fixture(scope="module")
+def rmat14():
+    n = 1 << 14
+    s, d = graphgen.rmat(14, 16 * n, seed=2)
+    return n, s, d, oracle.triangles(n, s, d)
+
+
+def test_er4096_host_io(tc, er4096):
+    n, s, d, ref = er4096
+    assert_matches_oracle(tc, n, s, d, ref=ref)
+
+
+def test_er4096_device_io(tc, er4096):
+    n, s, d, ref = er4096
+    assert_matches_oracle(tc, n, s, d, ref=ref, device_io=True)
+
+
+@pytest.mark.parametrize("make", [
+    lambda: F.complete(3), lambda: F.complete(34), lambda: F.complete(90), lambda: F.wheel(5),
+    lambda: F.wheel(40), lambda: F.friendship(7), lambda: F.complete_tripartite(3, 5, 40),
+    lambda: F.star(100), lambda: F.grid(20, 30), lambda: F.complete_bipartite(40, 50),
+    lambda: F.cycle(3), lambda: F.cycle(10)])
+def test_closed_forms(tc, make):
+    n, (s, d) = make()
+    assert_matches_oracle(tc, n, s, d)
+
+
+@pytest.mark.parametrize("seed", range(24))
+def test_tiny_random_with_loops_and_repeats(tc, seed):
+    from tests.test_oracle import _tiny
+    n, s, d = _tiny(seed)
+    assert_matches_oracle(tc, n, s, d)
+
+
+@pytest.mark.parametrize("warp", ALL_STRATEGIES)
+@pytest.mark.parametrize("cta", ALL_STRATEGIES + [("bitmap", 1.0)])
+def test_every_strategy_agrees(tc, rmat14, warp, cta):
+    n, s, d, ref = rmat14
+    strategies = {tc.TC_BUCKET_WARP: warp, tc.TC_BUCKET_CTA: cta}
+    assert_matches_oracle(tc, n, s, d, ref=ref, strategies=strategies)
+
+
+def test_strategy_rejects_bitmap_in_warp_bucket(tc, er4096):
+    n, s, d, _ = er4096
+    g = tc.Graph.from_edges(n, s, d)
+    with pytest.raises(tc.TCError):
+        g.set_strategy(tc.TC_BUCKET_WARP, "bitmap")
+    g.close()
+
+
+def test_csr_input_host_and_device(tc, rmat14):
+    n, s, d, ref = rmat14
+    off, adj, _ = oracle.build_csr(n, s, d)
+    for dev in (False, True):
+        T, t, lc, _ = gpu_run(tc, n, None, None, device_io=dev, csr=(off, adj))
+        assert T == ref["T"]
+        np.testing.assert_array_equal(t, ref["t"])
+        np.testing.assert_array_equal(lc, ref["lcc"])
+    # asymmetric, unsorted, with repeats and loops
+    rng = np.random.default_rng(5)
+    rows = rng.integers(0, 300, 4000).astype(np.int32)
+    cols = rng.integers(0, 300, 4000).astype(np.int32)
+    order = np.argsort(rows, kind="stable")
+    rows, cols = rows[order], cols[order]
+    off2 = np.zeros(301, dtype=np.int64)
+    off2[1:] = np.cumsum(np.bincount(rows, minlength=300))
+    ref2 = oracle.triangles(300, rows, cols)
+    for dev in (False, True):
+        T, t, lc, info = gpu_run(tc, 300, None, None, device_io=dev, csr=(off2, cols))
+        assert T == ref2["T"]
+        np.testing.assert_array_equal(t, ref2["t"])
+        np.testing.assert_array_equal(lc, ref2["lcc"])
+        assert info["m_simple"] == ref2["m_simple"]
+
+
+def test_empty_and_degenerate(tc):
+    e = np.array([], dtype=np.int32)
+    for n in (0, 1, 7):
+        T, t, lc, info = gpu_run(tc, n, e, e)
+        assert T == 0 and len(t) == n and (lc == 0).all() and info["m_simple"] == 0
+    loops = np.arange(5, dtype=np.int32)
+    T, t, lc, info = gpu_run(tc, 5, loops, loops)
+    assert T == 0 and info["loops_dropped"] == 5 and info["m_simple"] == 0
+    s = np.array([0, 1, 0, 0], np.int32)
+    d = np.array([1, 0, 1, 1], np.int32)
+    T, t, lc, info = gpu_run(tc, 2, s, d)
+    assert T == 0 and info["m_simple"] == 1 and info["dups_dropped"] == 3
+
+
+def test_bad_input_is_rejected(tc):
+    with pytest.raises(tc.TCError) as e:
+        tc.Graph.from_edges(4, np.array([0, 4], np.int32), np.array([1, 1], np.int32))
+    assert e.value.status == tc.TC_EINVAL
+    with pytest.raises(tc.TCError):
+        tc.Graph.from_edges(4, np.array([0, -1], np.int32), np.array([1, 1], np.int32))
+    import torch
+    bad = torch.tensor([0, 3, 2], dtype=torch.int64, device="cuda")
+    adj = torch.zeros(3, dtype=torch.int32, device="cuda")
+    with pytest.raises(tc.TCError):
+        tc.Graph.from_csr(2, bad, adj)
+    # the library stays usable after rejected inputs
+    n, (s, d) = F.complete(6)
+    assert_matches_oracle(tc, n, s, d)
+
+
+def test_long_rows_use_block_and_global_sorters(tc):
+    """Rows longer than the warp sorter (1024) and the shared-memory block sorter
+    (16384) before deduplication: vertex 0 joins 100 hubs, each pair repeated 200
+    times (row length 20000); each hub carries 25000 copies of an edge to its own
+    satellite so that it outranks vertex 0; consecutive hubs are joined."""
+    src, dst = [], []
+    hubs = np.arange(1, 101, dtype=np.int32)
+    for h in hubs:
+        src += [0] * 200
+        dst += [int(h)] * 200
+        src += [int(h)] * 25000
+        dst += [int(h) + 100] * 25000
+    for a, b in zip(hubs[:-1], hubs[1:]):
+        src.append(int(a))
+        dst.append(int(b))
+    # a K_1500 block gives rows of up to 1499 entries (block sorter, shared memory)
+    kn = 1500
+    iu, ju = np.triu_indices(kn, 1)
+    s = np.concatenate([np.array(src, np.int32), (iu + 300).astype(np.int32)])
+    d = np.concatenate([np.array(dst, np.int32), (ju + 300).astype(np.int32)])
+    perm = np.random.default_rng(0).permutation(len(s))
+    assert_matches_oracle(tc, 300 + kn, s[perm], d[perm])
+
+
+@pytest.mark.parametrize("scale,ef,seed", [(12, 4, 1), (16, 16, 3), (17, 8, 4)])
+def test_rmat_several_tiles(tc, scale, ef, seed):
+    n = 1 << scale
+    s, d = graphgen.rmat(scale, ef * n, seed=seed)
+    assert_matches_oracle(tc, n, s, d)
+
+
+def test_er_ragged_sizes(tc):
+    for n, m in [(1000, 7777), (65537, 400001), (3, 3)]:
+        s, d = graphgen.er(n, m, seed=n)
+        assert_matches_oracle(tc, n, s, d)
+
+
+def test_non_default_stream(tc, er4096):
+    import torch
+    n, s, d, ref = er4096
+    st = torch.cuda.Stream()
+    T, t, lc, _ = gpu_run(tc, n, s, d, device_io=True, stream=st)
+    assert T == ref["T"]
+    np.testing.assert_array_equal(t, ref["t"])
+
+
+def test_repeated_create_destroy_is_stable(tc, er4096):
+    n, s, d, ref = er4096
+    for _ in range(5):
+        T, t, _, _ = gpu_run(tc, n, s, d)
+        assert T == ref["T"]
