@@ -1,0 +1,347 @@
+#!/usr/bin/env python3
+"""Benchmark of the triangle-count + LCC hot path on GB300.
+
+One step = the whole single-graph path on one synthetic graph already resident in
+HBM: build (self-loop and repeat removal, CSR, (degree, id) orientation, planning),
+intersection (T and t[]), and LCC written to device buffers, through the C ABI.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--workload rmat20]
+    python bench.py --impl reference ...     # the CPU oracle as the reference arm
+
+Prints one JSON line (rank 0).  Metric: oriented edges intersected per second
+(every oriented edge of the simple graph counts once per step).  Timing: CUDA
+events on the launching stream around each step, L2 flushed (512 MB write)
+between steps, W warm-up steps; N > 1 runs one independent replica per GPU and
+takes the slowest rank.
+"""
+from __future__ import annotations
+
+import argparse
+import csv
+import io
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "oriented edges intersected/sec"
+UNIT = "edges/s"
+# Table II of the paper: R-MAT S20 EF16, hybrid intersection, 0.425 edges per
+# microsecond on a 16-thread Xeon Gold 6154 (context; another machine).
+PAPER_RMAT20_EDGES_PER_S = 0.425e6
+DEVSTATS_BYTES = 88
+FALLBACK_HBM_GBS = 6800.0
+WORKLOAD_TEXT = {
+    "rmat20": "R-MAT scale 20, edge factor 16, (a,b,c,d)=(0.57,0.19,0.19,0.05), seed 2",
+    "rmat23": "R-MAT scale 23, edge factor 8, (a,b,c,d)=(0.57,0.19,0.19,0.05), seed 3",
+    "er23": "Erdos-Renyi G(8388608, 60000000), seed 3 stream 1",
+    "er4096": "Erdos-Renyi G(4096, 32768), seed 1",
+}
+
+
+def parse_args():
+    p = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=60)
+    p.add_argument("--warmup", type=int, default=5)
+    p.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    p.add_argument("--workload", default="rmat20", choices=sorted(WORKLOAD_TEXT))
+    p.add_argument("--e2e-steps", type=int, default=10)
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--strategy", default=None,
+                   help="override as small:name[:factor],cta:name[:factor],hub:name,hubs:mindeg:max")
+    return p.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def measured_peak():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+    FIELDS = ["index", "clocks.sm", "clocks.max.sm", "power.draw", "clocks_event_reasons.active",
+              "clocks_event_reasons.hw_slowdown", "clocks_event_reasons.hw_thermal_slowdown",
+              "clocks_event_reasons.sw_thermal_slowdown", "clocks_event_reasons.sw_power_cap"]
+
+    def __init__(self, gpu_index: int):
+        self.proc = None
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(gpu_index), "--query-gpu=" + ",".join(self.FIELDS),
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        time.sleep(0.15)
+        self.proc.terminate()
+        out, _ = self.proc.communicate(timeout=10)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for row in csv.reader(io.StringIO(out)):
+            if len(row) < len(self.FIELDS):
+                continue
+            row = [c.strip() for c in row]
+            try:
+                sm.append(float(row[1]))
+                smax.append(float(row[2]))
+            except ValueError:
+                continue
+            for name, val in zip(names, row[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def apply_strategy(g, spec, tc):
+    if not spec:
+        return
+    for part in spec.split(","):
+        bucket, name, *rest = part.split(":")
+        if bucket == "hubs":
+            g.set_hubs(int(name), int(rest[0]))
+            continue
+        g.set_strategy(tc.BUCKETS[bucket], name, float(rest[0]) if rest else 1.0)
+
+
+def cpu_baseline(workload, src, dst):
+    """The oracle as it stands, whole pipeline on the same workload, host cores."""
+    import oracle
+    cores = len(os.sched_getaffinity(0))
+    oracle.build()
+    t0 = time.perf_counter()
+    r = oracle.triangles(workload.n, src, dst, threads=cores)
+    dt = time.perf_counter() - t0
+    return {"value": r["m_simple"] / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"full {workload.name} workload, whole pipeline (std::sort CSR build, orientation, "
+                      f"Alg. 2 oriented count split over {cores} threads, LCC) in {dt:.2f} s",
+            "T": r["T"]}, r
+
+
+def run_reference(args, rank, world):
+    """Reference arm: the CPU oracle timed on the host cores, rank 0 only."""
+    if rank != 0:
+        return
+    import graphgen
+    import oracle
+    oracle.build()
+    w = graphgen.workload(args.workload)
+    src, dst = w.edges()
+    cores = len(os.sched_getaffinity(0))
+    for _ in range(args.warmup):
+        oracle.triangles(w.n, src, dst, threads=cores)
+    times = []
+    m = 0
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        r = oracle.triangles(w.n, src, dst, threads=cores)
+        times.append(time.perf_counter() - t0)
+        m = r["m_simple"]
+    ms = 1000.0 * sum(times) / len(times)
+    value = m / (ms / 1000.0)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": value / PAPER_RMAT20_EDGES_PER_S if args.workload == "rmat20" else None,
+            "dtype": "int32", "data": "synthetic",
+            "config": {"workload": args.workload, "graph": WORKLOAD_TEXT[args.workload], "n": w.n,
+                       "m_generated": w.m, "m_simple": m},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"each step: full {args.workload} workload, whole oracle pipeline"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args, rank, world, local):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    import graphgen
+    import paper_2202_13976_gb300 as tc
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    tc.load()
+    w = graphgen.workload(args.workload)
+    src_h, dst_h = w.edges()
+    n = w.n
+    m_in = len(src_h)
+    stream = torch.cuda.current_stream()
+    src = torch.from_numpy(src_h).to(dev)
+    dst = torch.from_numpy(dst_h).to(dev)
+    t_out = torch.empty(n, dtype=torch.int64, device=dev)
+    lcc_out = torch.empty(n, dtype=torch.float64, device=dev)
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+
+    def step():
+        g = tc.Graph.from_edges(n, src, dst, stream)
+        try:
+            apply_strategy(g, args.strategy, tc)
+            T = g.count()
+            g.lcc(t_out, lcc_out)
+            tim = g.timing()
+        finally:
+            g.close()
+        return T, tim
+
+    # plan statistics (outside any timed region)
+    g = tc.Graph.from_edges(n, src, dst, stream)
+    plan = g.plan_stats()
+    m_simple = g.info()["m_simple"]
+    g.close()
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clocks = Clocks(local)
+    launches0 = tc.tc_launch_count()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    timings = []
+    Ts = set()
+    torch.cuda.synchronize()
+    for k in range(args.steps):
+        flush.zero_()
+        evs[k][0].record(stream)
+        T, tim = step()
+        evs[k][1].record(stream)
+        timings.append(tim)
+        Ts.add(T)
+    torch.cuda.synchronize()
+    launches = tc.tc_launch_count() - launches0
+    if world > 1:
+        dist.barrier()
+    clk = clocks.stop()
+    step_ms = [a.elapsed_time(b) for a, b in evs]
+    total_ms = sum(step_ms)
+    if world > 1:
+        tt = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        total_ms = float(tt.item())
+    ms_per_step = total_ms / args.steps
+    value = world * m_simple / (ms_per_step / 1000.0)
+
+    # dominant intersection kernel and its roofline (algorithmic bytes of the survey's
+    # per-edge figure: 4 (d+u + d+v) adjacency bytes + 8 edge bytes + 16 offset bytes)
+    phase = {k: statistics.mean(t[k] for t in timings) for k in timings[0]}
+    kernels = {"k_tc_small": ("small_ms", "small"), "k_tc_cta": ("cta_ms", "cta"), "k_tc_hub": ("hub_ms", "hub")}
+    name = max(kernels, key=lambda k: phase[kernels[k][0]])
+    kms = phase[kernels[name][0]]
+    b = plan[kernels[name][1]]
+    alg_bytes = 4 * b["ids"] + 24 * b["edges"]
+    peak, peak_kind = measured_peak()
+    achieved = alg_bytes / (kms / 1000.0) / 1e9
+    traffic = None
+    tpath = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        rec = json.load(open(tpath)).get(args.workload, {}).get(name)
+        if rec and rec.get("source_sha256") == tc.source_digest():
+            traffic = rec["dram_bytes_per_launch"]
+    except Exception:
+        traffic = None
+    roofline = {"bound": "hbm", "kernel": name, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": traffic, "peak_source": f"{peak_kind} hbm_gbs",
+                "algorithmic_bytes": alg_bytes, "kernel_ms": kms,
+                "note": "of measured" if peak_kind == "measured" else "of fallback"}
+
+    # end to end through the public API with host buffers (pinned), copies inside
+    src_p = torch.from_numpy(src_h).pin_memory()
+    dst_p = torch.from_numpy(dst_h).pin_memory()
+    t_p = torch.empty(n, dtype=torch.int64).pin_memory()
+    l_p = torch.empty(n, dtype=torch.float64).pin_memory()
+    s_np, d_np, t_np, l_np = src_p.numpy(), dst_p.numpy(), t_p.numpy().view(np.uint64), l_p.numpy()
+
+    def e2e_step():
+        g = tc.Graph.from_edges(n, s_np, d_np, stream)
+        try:
+            apply_strategy(g, args.strategy, tc)
+            T = g.count()
+            g.lcc(t_np, l_np)
+        finally:
+            g.close()
+        return T
+
+    e2e_step()
+    torch.cuda.synchronize()
+    e2e_times = []
+    for _ in range(args.e2e_steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        Ts.add(e2e_step())
+        torch.cuda.synchronize()
+        e2e_times.append(time.perf_counter() - t0)
+    e2e_s = sum(e2e_times) / len(e2e_times)
+    e2e = {"value": world * m_simple / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 8 * m_in,
+           "d2h_bytes_per_step": 16 * n + 8 + 2 * DEVSTATS_BYTES, "ms_per_step": 1000.0 * e2e_s}
+
+    if rank != 0:
+        return
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        cpu, ref = cpu_baseline(w, src_h, dst_h)
+        ok = (cpu["T"] in Ts and len(Ts) == 1)
+        cpu["parity_T"] = ok
+        del cpu["T"]
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": value / PAPER_RMAT20_EDGES_PER_S if args.workload == "rmat20" else None,
+        "dtype": "int32", "data": "synthetic",
+        "config": {"workload": args.workload, "graph": WORKLOAD_TEXT[args.workload], "n": n,
+                   "m_generated": m_in, "m_simple": m_simple, "T": sorted(Ts)[0],
+                   "l2": "flushed between steps (512 MB write)",
+                   "parallelism": f"replicas x{world}" if world > 1 else "1 GPU",
+                   "strategy": args.strategy or "default",
+                   "phase_ms": phase,
+                   "plan": plan,
+                   "vs_baseline_ref": "Table II, R-MAT S20 EF16, hybrid, 0.425 edges/us, 16-thread Xeon Gold 6154"},
+        "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+        "gpu_launches_per_step": launches / args.steps, "clocks": clk, "impl": "ours",
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse_args()
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    try:
+        run_ours(args, rank, world, local)
+    finally:
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -124,14 +124,14 @@ const char* tc_last_error_detail(void);
  * Intersection strategies (Sec. II-C, Sec. IV-C).  The result never depends on the
  * strategy, only the speed.
  *   TC_STRAT_AUTO      per-edge choice by the hybrid rule of Eq. 3 (with the
- *                      tunable factor below), bitmap probing for hub lists
- *   TC_STRAT_MERGE     warp-cooperative merge path (the SSI of Alg. 2, split
- *                      across lanes along the diagonals of the merge)
- *   TC_STRAT_SEARCH    binary search of every key of the shorter list in the
- *                      longer one (Alg. 1)
- *   TC_STRAT_PROBE     each element of the neighbour's list probes the staged
- *                      list of the source vertex (sorted, in shared memory)
- *   TC_STRAT_BITMAP    like PROBE, against a bitmap of the staged list
+ *                      tunable factor below); bitmap staging in the hub bucket
+ *   TC_STRAT_MERGE     merge of the two sorted lists (Alg. 2, SSI); in the block
+ *                      bucket split across a warp along merge-path diagonals
+ *   TC_STRAT_SEARCH    binary search of every key of one list in the other (Alg. 1)
+ *   TC_STRAT_PROBE     the staged list (shared memory, sorted) is probed by binary
+ *                      search with every element of the streamed list
+ *   TC_STRAT_BITMAP    the staged list is a bitmap over its rank window, probed
+ *                      with one shared-memory load per streamed element
  */
 enum {
     TC_STRAT_AUTO = 0,
@@ -142,28 +142,64 @@ enum {
 };
 
 /*
- * Degree buckets of the planner: vertices are grouped by their oriented
- * out-degree d+ (the length of their staged list).
- *   TC_BUCKET_WARP  2 <= d+ <= 32: one warp per vertex
- *   TC_BUCKET_CTA   d+ > 32: one thread block per vertex
+ * Buckets of the planner.  Vertices are ranked by (degree, id); every edge is
+ * oriented from the lower to the higher rank, and N+(u) is the oriented row of u.
+ *   TC_BUCKET_SMALL  edges (u, v), v not a hub, 2 <= |N+(u)| <= 32: groups of 8, 16
+ *                    or 32 lanes per source vertex, one lane per edge
+ *                    (strategies AUTO, MERGE, SEARCH)
+ *   TC_BUCKET_CTA    edges (u, v), v not a hub, |N+(u)| > 32: one thread block per
+ *                    source vertex, N+(u) staged in shared memory, one warp per
+ *                    edge (AUTO, MERGE, SEARCH, PROBE, BITMAP)
+ *   TC_BUCKET_HUB    edges (u, v) into a hub v: one thread block per hub, N+(v)
+ *                    staged in shared memory once, then every edge that hits v
+ *                    streams its suffix of N+(u) against it (AUTO = BITMAP, PROBE)
+ * Hubs are the highest-ranked vertices whose degree reaches a threshold
+ * (tc_graph_set_hubs).
  */
-enum { TC_BUCKET_WARP = 0, TC_BUCKET_CTA = 1, TC_NUM_BUCKETS = 2 };
+enum { TC_BUCKET_SMALL = 0, TC_BUCKET_CTA = 1, TC_BUCKET_HUB = 2, TC_NUM_BUCKETS = 3 };
 
 /*
  * Per-graph tuning, applied at the next intersection (set before tc_count).
  *   strategy  one of TC_STRAT_* for the bucket
  *   factor    Eq. 3 is applied as  |B| / |A| <= factor * (log2|B| - 1)  when the
  *             strategy is TC_STRAT_AUTO; factor = 1 is the paper's rule.
- * Errors: TC_EINVAL for an unknown bucket or strategy, or a strategy the bucket
- * cannot run (BITMAP in the warp bucket).
+ * Errors: TC_EINVAL for an unknown bucket or strategy, a strategy the bucket
+ * cannot run (see the bucket list), or factor <= 0.
  */
 tc_status tc_graph_set_strategy(tc_graph* g, int bucket, int strategy, double factor);
 
 /*
- * Timing of the last intersection, in milliseconds per bucket kernel and in total
- * (CUDA events on the graph's stream).  Synchronises the stream.
+ * Hub selection: vertices with degree >= min_degree are candidates, and at most
+ * max_hubs of the highest-ranked candidates are staged (max_hubs is capped at
+ * 131072, the bitmap window of one thread block).  max_hubs = 0 disables the hub
+ * bucket.  Defaults: min_degree 32, max_hubs 131072.  Errors: TC_EINVAL for
+ * negative values.
  */
-tc_status tc_graph_last_timing(const tc_graph* g, float* ms_warp, float* ms_cta, float* ms_total);
+tc_status tc_graph_set_hubs(tc_graph* g, int32_t min_degree, int32_t max_hubs);
+
+/*
+ * Timing of the last intersection in milliseconds (CUDA events on the graph's
+ * stream): ms[0] planning (bucket lists and hub in-edge lists), ms[1] small
+ * bucket, ms[2] block bucket, ms[3] hub bucket, ms[4] total.  count is the length
+ * of ms (up to 5).  Synchronises the stream.  Errors: TC_EINVAL before the first
+ * count.
+ */
+tc_status tc_graph_last_timing(const tc_graph* g, float* ms, int count);
+
+/*
+ * Work accounting of the planned intersection, per bucket (b = TC_BUCKET_*):
+ *   edges[b]  oriented edges handled by bucket b
+ *   ids[b]    sum over those edges (u, v) of |N+(u)| + |N+(v)|: the adjacency
+ *             entries that a merge of the two full lists reads (4 bytes each)
+ * Edges whose source has |N+(u)| < 2 and whose target is not a hub have an empty
+ * intersection and are reported in edges[TC_NUM_BUCKETS] (arrays hold
+ * TC_NUM_BUCKETS + 1 entries).  Runs the planner if needed; synchronises the
+ * stream; not meant for timed regions.
+ */
+tc_status tc_graph_plan_stats(tc_graph* g, int64_t* edges, int64_t* ids);
+
+/* Number of kernels this library has launched in the process so far (all devices). */
+uint64_t tc_launch_count(void);
 
 #ifdef __cplusplus
 }

@@ -13,19 +13,22 @@ import os
 
 import numpy as np
 
-from ._build import LIB, build as _build_lib, up_to_date
+from ._build import LIB, build as _build_lib, source_digest, up_to_date
 
 TC_OK, TC_EINVAL, TC_ENOMEM, TC_ECUDA, TC_ETIMEOUT, TC_EBUSY, TC_EINTERNAL = range(7)
 TC_MEM_HOST, TC_MEM_DEVICE = 0, 1
 TC_STRAT_AUTO, TC_STRAT_MERGE, TC_STRAT_SEARCH, TC_STRAT_PROBE, TC_STRAT_BITMAP = range(5)
-TC_BUCKET_WARP, TC_BUCKET_CTA = 0, 1
+TC_BUCKET_SMALL, TC_BUCKET_CTA, TC_BUCKET_HUB = 0, 1, 2
+BUCKETS = {"small": TC_BUCKET_SMALL, "cta": TC_BUCKET_CTA, "hub": TC_BUCKET_HUB}
+PHASES = ["plan_ms", "small_ms", "cta_ms", "hub_ms", "total_ms"]
 STRATEGIES = {"auto": TC_STRAT_AUTO, "merge": TC_STRAT_MERGE, "search": TC_STRAT_SEARCH,
               "probe": TC_STRAT_PROBE, "bitmap": TC_STRAT_BITMAP}
 
 # Every symbol include/tc.h declares.
 EXPORTS = ["tc_graph_create_from_edges", "tc_graph_create_from_csr", "tc_count", "lcc_compute",
            "tc_graph_info", "tc_graph_size", "tc_graph_destroy", "tc_status_str",
-           "tc_last_error_detail", "tc_graph_set_strategy", "tc_graph_last_timing"]
+           "tc_last_error_detail", "tc_graph_set_strategy", "tc_graph_last_timing",
+           "tc_graph_plan_stats", "tc_launch_count", "tc_graph_set_hubs"]
 
 _lib = None
 
@@ -76,8 +79,13 @@ def load(path: str | None = None):
     lib.tc_graph_set_strategy.restype = st
     lib.tc_graph_set_strategy.argtypes = [P, ctypes.c_int, ctypes.c_int, ctypes.c_double]
     lib.tc_graph_last_timing.restype = st
-    lib.tc_graph_last_timing.argtypes = [P, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_float),
-                                         ctypes.POINTER(ctypes.c_float)]
+    lib.tc_graph_last_timing.argtypes = [P, ctypes.POINTER(ctypes.c_float), ctypes.c_int]
+    lib.tc_graph_set_hubs.restype = st
+    lib.tc_graph_set_hubs.argtypes = [P, i32, i32]
+    lib.tc_graph_plan_stats.restype = st
+    lib.tc_graph_plan_stats.argtypes = [P, ctypes.POINTER(i64), ctypes.POINTER(i64)]
+    lib.tc_launch_count.restype = u64
+    lib.tc_launch_count.argtypes = []
     _lib = lib
     return lib
 
@@ -185,16 +193,36 @@ def tc_graph_destroy(g: int) -> None:
         _lib.tc_graph_destroy(g)
 
 
-def tc_graph_set_strategy(g: int, bucket: int, strategy, factor: float = 1.0) -> None:
+def tc_graph_set_strategy(g: int, bucket, strategy, factor: float = 1.0) -> None:
+    if isinstance(bucket, str):
+        bucket = BUCKETS[bucket]
     if isinstance(strategy, str):
         strategy = STRATEGIES[strategy]
     _check(_lib.tc_graph_set_strategy(g, bucket, strategy, factor))
 
 
+def tc_graph_set_hubs(g: int, min_degree: int, max_hubs: int) -> None:
+    _check(_lib.tc_graph_set_hubs(g, min_degree, max_hubs))
+
+
 def tc_graph_last_timing(g: int) -> dict:
-    a, b, c = ctypes.c_float(), ctypes.c_float(), ctypes.c_float()
-    _check(_lib.tc_graph_last_timing(g, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
-    return {"warp_ms": a.value, "cta_ms": b.value, "total_ms": c.value}
+    ms = (ctypes.c_float * len(PHASES))()
+    _check(_lib.tc_graph_last_timing(g, ms, len(PHASES)))
+    return {k: ms[i] for i, k in enumerate(PHASES)}
+
+
+def tc_graph_plan_stats(g: int) -> dict:
+    """Per bucket: oriented edges and sum of d+(u) + d+(v) ("ids") over them."""
+    nb = TC_BUCKET_HUB + 2
+    e = (ctypes.c_int64 * nb)()
+    i = (ctypes.c_int64 * nb)()
+    _check(_lib.tc_graph_plan_stats(g, e, i))
+    names = ["small", "cta", "hub", "trivial"]
+    return {names[b]: {"edges": e[b], "ids": i[b]} for b in range(nb)}
+
+
+def tc_launch_count() -> int:
+    return int(load().tc_launch_count())
 
 
 class Graph:
@@ -229,8 +257,14 @@ class Graph:
     def set_strategy(self, bucket, strategy, factor=1.0):
         tc_graph_set_strategy(self.handle, bucket, strategy, factor)
 
+    def set_hubs(self, min_degree: int, max_hubs: int):
+        tc_graph_set_hubs(self.handle, min_degree, max_hubs)
+
     def timing(self) -> dict:
         return tc_graph_last_timing(self.handle)
+
+    def plan_stats(self) -> dict:
+        return tc_graph_plan_stats(self.handle)
 
     def close(self):
         tc_graph_destroy(self.handle)

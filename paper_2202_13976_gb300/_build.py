@@ -38,6 +38,17 @@ def _inputs() -> list[str]:
         [os.path.join(ROOT, "include", "tc.h")]
 
 
+def source_digest() -> str:
+    """sha256 over the library sources (identifies the kernels a profile was taken on)."""
+    import hashlib
+    h = hashlib.sha256()
+    for p in sorted(_inputs()):
+        h.update(os.path.basename(p).encode())
+        with open(p, "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()
+
+
 def up_to_date() -> bool:
     if not os.path.exists(LIB):
         return False

@@ -6,7 +6,9 @@
 // without returning it to the driver and without device-wide synchronisation.
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <climits>
+#include <cstddef>
 #include <cstdio>
 #include <cstring>
 #include <mutex>
@@ -16,6 +18,12 @@
 #include "tc_internal.h"
 
 using namespace tcg;
+
+namespace tcg {
+static std::atomic<uint64_t> g_launches{0};
+void count_launch(int k) { g_launches.fetch_add((uint64_t)k, std::memory_order_relaxed); }
+uint64_t launch_total() { return g_launches.load(std::memory_order_relaxed); }
+}  // namespace tcg
 
 namespace {
 
@@ -76,19 +84,29 @@ struct tc_graph {
     Launch L{};
     int32_t n = 0;
     int64_t m_in = 0;
+    int64_t m_alloc = 0;  // capacity of col / in-edge arrays
     int32_t* rank = nullptr;
     int64_t* rowstart = nullptr;
     int32_t* rowlen = nullptr;
     int32_t* col = nullptr;
     int32_t* deg = nullptr;
-    int32_t* warp_list = nullptr;
+    int32_t* small_list[3] = {nullptr, nullptr, nullptr};
     int32_t* cta_list = nullptr;
+    int32_t hub_cap = 0;
+    uint32_t* hub_cnt = nullptr;
+    int64_t* hub_start = nullptr;
+    uint32_t* hub_cur = nullptr;
+    int32_t* in_u = nullptr;
+    int32_t* in_b = nullptr;
+    int32_t* in_e = nullptr;
+    void* plan_tmp = nullptr;
     unsigned long long* t_rank = nullptr;
     DevStats* stats = nullptr;
     std::vector<void*> blocks;
+    bool planned = false;
     bool counted = false;
     Strategy strat{};
-    cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
+    cudaEvent_t ev[PH_EVENTS] = {};
     bool timed = false;
 };
 
@@ -146,6 +164,9 @@ tc_status new_graph(int32_t n, void* stream, tc_graph** out) {
         g->strat.strat[b] = TC_STRAT_AUTO;
         g->strat.factor[b] = 1.0f;
     }
+    g->strat.strat[TC_BUCKET_CTA] = TC_STRAT_BITMAP;
+    g->strat.hub_min_degree = 32;
+    g->strat.hub_max = HUB_BM_BITS;
     *out = g;
     return TC_OK;
 }
@@ -168,10 +189,18 @@ tc_status build_graph(tc_graph* g, const int32_t* src, const int32_t* dst, int64
     const size_t nn = (size_t)n;
     tc_status st;
     std::vector<void*>& keep = g->blocks;
+    g->m_alloc = m;
+    g->hub_cap = n < HUB_BM_BITS ? n : HUB_BM_BITS;
+    const size_t hc = (size_t)g->hub_cap;
     if ((st = dalloc(g, &g->stats, 1, &keep)) || (st = dalloc(g, &g->rank, nn, &keep)) ||
         (st = dalloc(g, &g->rowstart, nn + 1, &keep)) || (st = dalloc(g, &g->rowlen, nn, &keep)) ||
         (st = dalloc(g, &g->col, (size_t)m, &keep)) || (st = dalloc(g, &g->deg, nn, &keep)) ||
-        (st = dalloc(g, &g->warp_list, nn, &keep)) || (st = dalloc(g, &g->cta_list, nn, &keep)) ||
+        (st = dalloc(g, &g->small_list[0], nn, &keep)) || (st = dalloc(g, &g->small_list[1], nn, &keep)) ||
+        (st = dalloc(g, &g->small_list[2], nn, &keep)) || (st = dalloc(g, &g->cta_list, nn, &keep)) ||
+        (st = dalloc(g, &g->hub_cnt, hc + 1, &keep)) || (st = dalloc(g, &g->hub_start, hc + 1, &keep)) ||
+        (st = dalloc(g, &g->hub_cur, hc + 1, &keep)) || (st = dalloc(g, &g->in_u, (size_t)m, &keep)) ||
+        (st = dalloc(g, &g->in_b, (size_t)m, &keep)) || (st = dalloc(g, &g->in_e, (size_t)m, &keep)) ||
+        (st = dalloc(g, (char**)&g->plan_tmp, scan_tmp_bytes((int64_t)hc + 1), &keep)) ||
         (st = dalloc(g, &g->t_rank, nn, &keep)))
         return st;
     std::vector<void*> scratch;
@@ -213,22 +242,67 @@ tc_status build_graph(tc_graph* g, const int32_t* src, const int32_t* dst, int64
     }
     launch_rank(B, bits_for(h.max_deg), g->L);
     launch_orient(B, g->L);
-    CountBuffers C{n, g->rowstart, g->rowlen, g->col, g->warp_list, g->cta_list, g->t_rank, g->stats};
-    launch_plan(C, g->L);
     free_list(g, &scratch);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail("build kernels", e);
     return TC_OK;
 }
 
+CountBuffers count_buffers(tc_graph* g) {
+    CountBuffers C{};
+    C.n = g->n;
+    C.rowstart = g->rowstart;
+    C.rowlen = g->rowlen;
+    C.col = g->col;
+    C.deg = g->deg;
+    for (int i = 0; i < 3; ++i) C.small_list[i] = g->small_list[i];
+    C.cta_list = g->cta_list;
+    C.hub_cap = g->hub_cap;
+    C.hub_cnt = g->hub_cnt;
+    C.hub_start = g->hub_start;
+    C.hub_cur = g->hub_cur;
+    C.in_u = g->in_u;
+    C.in_b = g->in_b;
+    C.in_e = g->in_e;
+    C.tmp = g->plan_tmp;
+    C.t_rank = g->t_rank;
+    C.stats = g->stats;
+    return C;
+}
+
+tc_status ensure_events(tc_graph* g) {
+    if (!g->ev[0])
+        for (int i = 0; i < PH_EVENTS; ++i) TC_CK(cudaEventCreate(&g->ev[i]));
+    return TC_OK;
+}
+
+// Planning (a4): bucket lists and hub in-edge lists; rerun when hub settings change.
+tc_status run_plan(tc_graph* g) {
+    if (g->planned) return TC_OK;
+    tc_status st = ensure_events(g);
+    if (st != TC_OK) return st;
+    const size_t off = offsetof(DevStats, small_count);
+    TC_CK(cudaMemsetAsync(reinterpret_cast<char*>(g->stats) + off, 0, sizeof(DevStats) - off, g->stream));
+    TC_CK(cudaEventRecord(g->ev[PH_PLAN], g->stream));
+    launch_plan(count_buffers(g), g->strat, g->L);
+    TC_CK(cudaGetLastError());
+    g->planned = true;
+    g->counted = false;
+    return TC_OK;
+}
+
 tc_status run_count(tc_graph* g) {
     if (g->counted) return TC_OK;
-    if (!g->ev[0]) {
-        for (int i = 0; i < 3; ++i) TC_CK(cudaEventCreate(&g->ev[i]));
+    tc_status st = ensure_events(g);
+    if (st != TC_OK) return st;
+    if (g->planned) {
+        TC_CK(cudaEventRecord(g->ev[PH_PLAN], g->stream));  // planning already done: empty phase
+    } else if ((st = run_plan(g)) != TC_OK) {
+        return st;
     }
     TC_CK(cudaMemsetAsync(g->t_rank, 0, sizeof(unsigned long long) * (size_t)g->n, g->stream));
     TC_CK(cudaMemsetAsync(&g->stats->sum_t, 0, sizeof(unsigned long long), g->stream));
-    CountBuffers C{g->n, g->rowstart, g->rowlen, g->col, g->warp_list, g->cta_list, g->t_rank, g->stats};
+    CountBuffers C = count_buffers(g);
     launch_intersect(C, g->strat, g->ev, g->L);
     launch_sum_t(C, g->L);
     TC_CK(cudaGetLastError());
@@ -240,7 +314,7 @@ tc_status run_count(tc_graph* g) {
 void destroy(tc_graph* g) {
     if (!g) return;
     free_list(g, &g->blocks);
-    for (int i = 0; i < 3; ++i)
+    for (int i = 0; i < PH_EVENTS; ++i)
         if (g->ev[i]) cudaEventDestroy(g->ev[i]);
     delete g;
 }
@@ -445,24 +519,58 @@ tc_status tc_graph_set_strategy(tc_graph* g, int bucket, int strategy, double fa
     if (!g || bucket < 0 || bucket >= TC_NUM_BUCKETS || strategy < TC_STRAT_AUTO || strategy > TC_STRAT_BITMAP ||
         !(factor > 0.0))
         return TC_EINVAL;
-    if (bucket == TC_BUCKET_WARP && strategy == TC_STRAT_BITMAP) return TC_EINVAL;
+    if (bucket == TC_BUCKET_SMALL && (strategy == TC_STRAT_PROBE || strategy == TC_STRAT_BITMAP)) return TC_EINVAL;
+    if (bucket == TC_BUCKET_HUB && (strategy == TC_STRAT_MERGE || strategy == TC_STRAT_SEARCH)) return TC_EINVAL;
     g->strat.strat[bucket] = strategy;
     g->strat.factor[bucket] = (float)factor;
     g->counted = false;
     return TC_OK;
 }
 
-tc_status tc_graph_last_timing(const tc_graph* g, float* ms_warp, float* ms_cta, float* ms_total) {
-    if (!g) return TC_EINVAL;
-    if (!g->timed) return TC_EINVAL;
-    TC_CK(cudaEventSynchronize(g->ev[2]));
-    float a = 0, b = 0;
-    TC_CK(cudaEventElapsedTime(&a, g->ev[0], g->ev[1]));
-    TC_CK(cudaEventElapsedTime(&b, g->ev[1], g->ev[2]));
-    if (ms_warp) *ms_warp = a;
-    if (ms_cta) *ms_cta = b;
-    if (ms_total) *ms_total = a + b;
+tc_status tc_graph_set_hubs(tc_graph* g, int32_t min_degree, int32_t max_hubs) {
+    if (!g || min_degree < 0 || max_hubs < 0) return TC_EINVAL;
+    g->strat.hub_min_degree = min_degree;
+    g->strat.hub_max = max_hubs < HUB_BM_BITS ? max_hubs : HUB_BM_BITS;
+    g->planned = false;
+    g->counted = false;
     return TC_OK;
 }
+
+tc_status tc_graph_last_timing(const tc_graph* g, float* ms, int count) {
+    if (!g || !ms || count < 0) return TC_EINVAL;
+    if (!g->timed) return TC_EINVAL;
+    TC_CK(cudaEventSynchronize(g->ev[PH_END]));
+    float v[5] = {0, 0, 0, 0, 0};
+    TC_CK(cudaEventElapsedTime(&v[0], g->ev[PH_PLAN], g->ev[PH_SMALL]));
+    TC_CK(cudaEventElapsedTime(&v[1], g->ev[PH_SMALL], g->ev[PH_CTA]));
+    TC_CK(cudaEventElapsedTime(&v[2], g->ev[PH_CTA], g->ev[PH_HUB]));
+    TC_CK(cudaEventElapsedTime(&v[3], g->ev[PH_HUB], g->ev[PH_END]));
+    TC_CK(cudaEventElapsedTime(&v[4], g->ev[PH_PLAN], g->ev[PH_END]));
+    for (int i = 0; i < count && i < 5; ++i) ms[i] = v[i];
+    return TC_OK;
+}
+
+tc_status tc_graph_plan_stats(tc_graph* g, int64_t* edges, int64_t* ids) {
+    if (!g || !edges || !ids) return TC_EINVAL;
+    tc_status st = run_plan(g);
+    if (st != TC_OK) return st;
+    const int nb = TC_NUM_BUCKETS + 1;
+    unsigned long long* d = nullptr;
+    TC_CK(cudaMallocFromPoolAsync((void**)&d, sizeof(unsigned long long) * 2 * nb, g->pool, g->stream));
+    unsigned long long h[2 * (TC_NUM_BUCKETS + 1)] = {};
+    cudaMemsetAsync(d, 0, sizeof(h), g->stream);
+    launch_plan_stats(count_buffers(g), d, g->L);
+    cudaError_t e = cudaMemcpyAsync(h, d, sizeof(h), cudaMemcpyDeviceToHost, g->stream);
+    cudaFreeAsync(d, g->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(g->stream);
+    if (e != cudaSuccess) return cuda_fail("tc_graph_plan_stats", e);
+    for (int b = 0; b < nb; ++b) {
+        edges[b] = (int64_t)h[b];
+        ids[b] = (int64_t)h[nb + b];
+    }
+    return TC_OK;
+}
+
+uint64_t tc_launch_count(void) { return launch_total(); }
 
 }  // extern "C"

@@ -331,27 +331,27 @@ __global__ void __launch_bounds__(1024) k_segsort_block(const int64_t* __restric
 }  // namespace
 
 void launch_check_offsets(const int64_t* offsets, int32_t n, int64_t limit, DevStats* stats, const Launch& L) {
-    k_check_offsets<<<grid_for(n + 1, THREADS, L.sms), THREADS, 0, L.stream>>>(offsets, n, limit, stats);
+    k_check_offsets<<<grid_for(n + 1, THREADS, L.sms), THREADS, 0, L.stream>>>(offsets, n, limit, stats); count_launch();
 }
 
 void launch_expand_csr(const int64_t* offsets, int32_t n, int32_t* rows, DevStats* stats, const Launch& L) {
     if (n <= 0) return;
-    k_expand_csr<<<grid_for((int64_t)n * 32, THREADS, L.sms), THREADS, 0, L.stream>>>(offsets, n, rows, stats);
+    k_expand_csr<<<grid_for((int64_t)n * 32, THREADS, L.sms), THREADS, 0, L.stream>>>(offsets, n, rows, stats); count_launch();
 }
 
 void launch_canon_degree(const BuildBuffers& B, const Launch& L) {
-    if (B.m > 0)
+    if (B.m > 0) {
         k_canon_degree<<<grid_for(B.m, THREADS, L.sms), THREADS, 0, L.stream>>>(B.src, B.dst, B.m, B.n, B.dmulti,
-                                                                              B.stats);
-    if (B.n > 0) k_max_deg<<<grid_for(B.n, THREADS, L.sms), THREADS, 0, L.stream>>>(B.dmulti, B.n, B.stats);
+                                                                              B.stats); count_launch(); }
+    if (B.n > 0) { k_max_deg<<<grid_for(B.n, THREADS, L.sms), THREADS, 0, L.stream>>>(B.dmulti, B.n, B.stats); count_launch(); }
 }
 
 void launch_rank(const BuildBuffers& B, int deg_bits, const Launch& L) {
     if (B.n <= 0) return;
-    k_rank_keys<<<grid_for(B.n, THREADS, L.sms), THREADS, 0, L.stream>>>(B.dmulti, B.n, B.keys);
+    k_rank_keys<<<grid_for(B.n, THREADS, L.sms), THREADS, 0, L.stream>>>(B.dmulti, B.n, B.keys); count_launch();
     // the keys start in id order, so a stable sort on the degree bits yields (degree, id)
     uint64_t* sorted = radix_sort_u64(B.keys, B.keys_alt, B.n, 32, 32 + deg_bits, B.tmp, L);
-    k_rank_invert<<<grid_for(B.n, THREADS, L.sms), THREADS, 0, L.stream>>>(sorted, B.n, B.rank);
+    k_rank_invert<<<grid_for(B.n, THREADS, L.sms), THREADS, 0, L.stream>>>(sorted, B.n, B.rank); count_launch();
 }
 
 void launch_orient(const BuildBuffers& B, const Launch& L) {
@@ -359,17 +359,17 @@ void launch_orient(const BuildBuffers& B, const Launch& L) {
     cudaMemsetAsync(B.rowcnt, 0, sizeof(uint32_t) * (size_t)B.n, L.stream);
     cudaMemsetAsync(B.cursor, 0, sizeof(uint32_t) * (size_t)B.n, L.stream);
     cudaMemsetAsync(B.deg, 0, sizeof(int32_t) * (size_t)B.n, L.stream);
-    if (B.m > 0)
+    if (B.m > 0) {
         k_orient_count<<<grid_for(B.m, THREADS, L.sms), THREADS, 0, L.stream>>>(B.src, B.dst, B.m, B.rank,
-                                                                              B.rowcnt);
+                                                                              B.rowcnt); count_launch(); }
     scan_u32_to_i64(B.rowcnt, B.rowstart, B.n, B.tmp, L);
-    if (B.m > 0)
+    if (B.m > 0) {
         k_orient_scatter<<<grid_for(B.m, THREADS, L.sms), THREADS, 0, L.stream>>>(
-            B.src, B.dst, B.m, B.rank, B.rowstart, B.cursor, B.col);
+            B.src, B.dst, B.m, B.rank, B.rowstart, B.cursor, B.col); count_launch(); }
     k_segsort_warp<<<grid_for((int64_t)B.n * 32, SEG_WARPS * 32, L.sms, 4), SEG_WARPS * 32, 0, L.stream>>>(
-        B.n, B.rowstart, B.rowcnt, B.col, B.rowlen, B.deg, B.longlist, B.stats);
+        B.n, B.rowstart, B.rowcnt, B.col, B.rowlen, B.deg, B.longlist, B.stats); count_launch();
     k_segsort_block<<<L.sms * 2, 1024, CTA_SORT_MAX * sizeof(int32_t), L.stream>>>(
-        B.rowstart, B.rowcnt, B.col, B.rowlen, B.deg, B.longlist, B.stats);
+        B.rowstart, B.rowcnt, B.col, B.rowlen, B.deg, B.longlist, B.stats); count_launch();
 }
 
 // 64 KB of dynamic shared memory for the block sorter.

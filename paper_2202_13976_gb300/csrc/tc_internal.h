@@ -22,12 +22,16 @@ struct DevStats {
     unsigned long long sum_t;      // sum over v of t(v)
     unsigned int max_deg;          // largest multigraph degree
     int err;                       // ERR_* flags
-    unsigned int warp_count;       // planner: vertices in the warp bucket
-    unsigned int cta_count;        // planner: vertices in the block bucket
     unsigned int long_count;       // build: rows sorted by whole blocks
-    unsigned int work_next;        // dynamic work counter of the block bucket
-    unsigned int pad[6];
+    unsigned int small_count[3];   // planner: vertices per small-list class (d+ <= 8, 16, 32)
+    unsigned int cta_count;        // planner: vertices with d+ > 32
+    unsigned int cta_next;         // dynamic work counter of the block push kernel
+    unsigned int hub_count;        // vertices staged as hubs (ranks n - hub_count .. n-1)
+    unsigned int hub_next;         // dynamic work counter of the hub kernel
+    unsigned int hub_candidates;   // vertices whose degree reaches the hub threshold
+    unsigned int pad[5];
 };
+static_assert(sizeof(DevStats) == 88, "DevStats layout");
 
 struct Launch {
     cudaStream_t stream;
@@ -83,30 +87,57 @@ void launch_orient(const BuildBuffers& B, const Launch& L);
 cudaError_t build_init_attributes();
 
 // ---- plan + intersect + finalize (tc_intersect.cu) ---------------------------
+// Buckets (include/tc.h): small lists (push, lane per edge), large lists (push,
+// block per source vertex), hubs (pull, block per staged hub list).
 struct Strategy {
     int strat[TC_NUM_BUCKETS];
     float factor[TC_NUM_BUCKETS];
+    int hub_min_degree;   // vertices of degree >= this are hub candidates (<= 0: no hubs)
+    int hub_max;          // at most this many hubs (the highest ranks)
 };
+
+// Capacity of the hub kernel's shared-memory bitmap (ranks above the hub).
+constexpr int HUB_BM_BITS = 131072;
 
 struct CountBuffers {
     int32_t n;
     const int64_t* rowstart;
     const int32_t* rowlen;
     const int32_t* col;
-    int32_t* warp_list;   // n
-    int32_t* cta_list;    // n
+    const int32_t* deg;
+    int32_t* small_list[3];  // n each
+    int32_t* cta_list;       // n
+    // hub in-edges (transpose of the oriented edges that point into the hub ranks)
+    int32_t hub_cap;         // min(n, HUB_BM_BITS): slots for ranks n - hub_cap .. n-1
+    uint32_t* hub_cnt;       // hub_cap + 1
+    int64_t* hub_start;      // hub_cap + 1
+    uint32_t* hub_cur;       // hub_cap
+    int32_t* in_u;           // m: source vertex of the in-edge
+    int32_t* in_b;           // m: first suffix entry (index into col)
+    int32_t* in_e;           // m: end of the source row (index into col)
+    void* tmp;               // scan scratch, scan_tmp_bytes(hub_cap + 1)
     unsigned long long* t_rank;  // n
     DevStats* stats;
 };
 
-void launch_plan(const CountBuffers& C, const Launch& L);
+enum { PH_PLAN = 0, PH_SMALL, PH_CTA, PH_HUB, PH_END, PH_EVENTS };
+
+// Builds the bucket lists and the hub in-edge lists.
+void launch_plan(const CountBuffers& C, const Strategy& S, const Launch& L);
 cudaError_t intersect_init_attributes();
-// Runs both bucket kernels; events (may be null) bracket each for timing.
-void launch_intersect(const CountBuffers& C, const Strategy& S, cudaEvent_t ev[3], const Launch& L);
+// Runs the three bucket kernels; ev (may be null) holds PH_EVENTS events.
+void launch_intersect(const CountBuffers& C, const Strategy& S, cudaEvent_t* ev, const Launch& L);
 void launch_sum_t(const CountBuffers& C, const Launch& L);
 void launch_finalize(int32_t n, const int32_t* rank, const unsigned long long* t_rank,
                      const int32_t* deg, unsigned long long* t_out, double* lcc_out,
                      const Launch& L);
+
+// Kernel launch accounting (tc_launch_count).
+void count_launch(int k = 1);
+uint64_t launch_total();
+
+void launch_plan_stats(const CountBuffers& C, unsigned long long* out /* 2*TC_NUM_BUCKETS+1 */,
+                       const Launch& L);
 
 inline int grid_for(int64_t work, int threads, int sms, int per_sm = 8) {
     int64_t g = (work + threads - 1) / threads;

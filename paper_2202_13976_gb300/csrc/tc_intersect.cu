@@ -1,33 +1,36 @@
 // Per-edge set intersection over the degree-oriented CSR (Sec. II-C, Sec. IV-C),
-// the planner that groups source vertices into degree buckets, and the final
-// reduction to T (Sec. II-C) and LCC (Eq. 2).
+// the planner that splits the edges into buckets, and the final reduction to T
+// (Sec. II-C) and LCC (Eq. 2).
 //
-// Counting rule.  In rank space every oriented row N+(u) is sorted and holds only
-// ranks above u.  For the oriented edge (u, v) with v = N+(u)[j], the common
-// neighbours are W = N+(u)[j+1 ..] ∩ N+(v): an element of N+(v) exceeds v, so only
-// the suffix of N+(u) after v can match.  With c = |W|, a triangle {u, v, w}
-// (u < v < w in rank order) is met exactly once, and t[u] += c, t[v] += c,
-// t[w] += 1 for every w in W.
+// Counting rule.  Vertices are ranked by (degree, id) and every oriented row N+(u)
+// is sorted and holds only ranks above u.  For the oriented edge (u, v) with
+// v = N+(u)[j], the common neighbours are W = N+(u)[j+1 ..] ∩ N+(v): every element
+// of N+(v) exceeds v, so only the suffix of N+(u) after v can match.  With c = |W|,
+// a triangle {u, v, w} (u < v < w in rank order) is met exactly once, and t[u] += c,
+// t[v] += c, t[w] += 1 for every w in W.
 //
-// Source-vertex staging.  One warp (d+(u) <= 32) or one thread block (d+(u) > 32)
-// owns u: N+(u) is copied into shared memory once and reused by all d+(u) edges of
-// u, and every increment aimed at an entry of N+(u) (t[v] += c and t[w] += 1) is
-// first added to a shared-memory counter for that position.  One global atomic per
-// non-zero counter and one for t[u] flush them.  This is the on-chip analogue of the
-// paper's reuse of adjacency lists (Sec. IV-B): the staged list plays the role of a
-// cached entry, kept for as long as its owner is processed.
-//
-// Methods for one edge (a warp; A = suffix of N+(u), B = N+(v)):
-//  MERGE   merge path: the merge of A and B is cut into 32 equal diagonal ranges,
-//          one per lane; each lane runs Alg. 2 over its range (Sec. II-C, SSI)
-//  SEARCH  every key of A is looked up in B by binary search (Alg. 1)
-//  PROBE   every element of B is looked up in A (staged, shared memory) by binary
-//          search; the scan of B stops at the first element above max(N+(u))
-//  BITMAP  like PROBE, but N+(u) is a bitmap over the rank window (u, max N+(u)]
-//          with per-word prefix counts, so a probe is one shared-memory load
-//  AUTO    Eq. 3 per edge: if |B|/|A| <= f (log2|B| - 1) with |A| <= |B| the
-//          lists are merged (MERGE), otherwise the keys of the shorter list are
-//          searched in the longer (SEARCH when A is shorter, PROBE when B is)
+// Buckets (each oriented edge belongs to exactly one):
+//  hub    edges into the highest-ranked vertices ("hubs").  One thread block per hub
+//         v stages N+(v) once in shared memory (a bitmap over its rank window with
+//         per-word prefix counts, or the sorted list), then streams the suffix
+//         N+(u)[j+1 ..] of every in-edge (u, v) against it.  This is the on-chip
+//         analogue of the paper's caching of remote adjacency lists ranked by degree
+//         (Sec. IV-B, Observations 1 and 2): the list that most edges need is read
+//         from memory once and reused by all of them.  t[w] increments are summed
+//         per position of N+(v) in shared memory and flushed once per hub.
+//  small  other edges whose source has 2 <= |N+(u)| <= 32: a group of 8, 16 or 32
+//         lanes stages N+(u); lane j intersects edge j sequentially, by SSI (Alg. 2)
+//         or binary search (Alg. 1), chosen per edge by Eq. 3.
+//  block  other edges whose source has |N+(u)| > 32: one thread block stages N+(u),
+//         one warp per edge, methods:
+//           MERGE   merge path: the merge of A (suffix) and B = N+(v) is cut into 32
+//                   equal diagonal ranges, one per lane, each running Alg. 2
+//           SEARCH  every key of A is looked up in B by binary search (Alg. 1)
+//           PROBE   every element of B is looked up in A (shared memory) by binary
+//                   search; the scan of B stops above max N+(u)
+//           BITMAP  like PROBE against a bitmap of N+(u) over its rank window
+//           AUTO    Eq. 3 per edge: merge if |B|/|A| <= f (log2|B| - 1) (|A| <= |B|),
+//                   else the keys of the shorter list are searched in the longer
 #include <climits>
 
 #include "tc_device.cuh"
@@ -38,11 +41,15 @@ namespace tcg {
 namespace {
 
 constexpr int THREADS = 256;
-constexpr int WK_WARPS = 8;            // warps per block in the warp-bucket kernel
-constexpr int CTA_THREADS = 256;       // block-bucket kernel
+constexpr int SMALL_WARPS = 8;         // warps per block in the small-bucket kernel
+constexpr int CTA_THREADS = 256;       // block push kernel
 constexpr int CTA_WARPS = CTA_THREADS / 32;
-constexpr int CTA_LIST_MAX = 2048;     // staged list capacity of one block
-constexpr int BITMAP_WORDS = 4096;     // bitmap window of one block: 131072 ranks
+constexpr int CTA_LIST_MAX = 2048;     // staged list capacity of the block push kernel
+constexpr int BITMAP_WORDS = 4096;     // its bitmap window: 131072 ranks
+constexpr int HUB_THREADS = 256;
+constexpr int HUB_WARPS = HUB_THREADS / 32;
+constexpr int HUB_BM_WORDS = HUB_BM_BITS / 32;
+constexpr int HUB_CNT_MAX = 4096;      // hub lists longer than this count matches globally
 
 struct Sink {
     uint32_t* cnt;               // per-position counters (shared), or null
@@ -56,7 +63,7 @@ struct Sink {
     }
 };
 
-// Number of elements of sorted B[0, b) that are <= x (warp-uniform inputs).
+// Number of elements of sorted B[0, b) that are <= x.
 __device__ __forceinline__ int count_le(const int32_t* __restrict__ B, int b, int32_t x) {
     int lo = 0, hi = b;
     while (lo < hi) {
@@ -68,6 +75,13 @@ __device__ __forceinline__ int count_le(const int32_t* __restrict__ B, int b, in
     }
     return lo;
 }
+
+__device__ __forceinline__ bool eq3_prefers_merge(int a, int b, float factor) {
+    int s = min(a, b), l = max(a, b);
+    return (float)l <= factor * (log2f((float)l) - 1.0f) * (float)s;
+}
+
+// ---- warp-cooperative methods (block push kernel) -----------------------------
 
 __device__ uint32_t edge_merge(const Sink& S, int a0, int du, const int32_t* __restrict__ B, int b) {
     const int lane = lane_id();
@@ -139,7 +153,7 @@ __device__ uint32_t edge_probe(const Sink& S, int a0, int du, const int32_t* __r
 }
 
 // Bitmap over ranks (u, maxu]: bit (x - u - 1) set iff x in N+(u); pre[w] = number of
-// set bits in words before w, i.e. the position in N+(u) of the word's first member.
+// set bits in the words before w, i.e. the position in N+(u) of the word's first member.
 __device__ uint32_t edge_bitmap(const uint32_t* bm, const uint16_t* pre, int32_t u, int32_t maxu,
                                 uint32_t* cnt, const int32_t* __restrict__ B, int b) {
     const int lane = lane_id();
@@ -160,13 +174,6 @@ __device__ uint32_t edge_bitmap(const uint32_t* bm, const uint16_t* pre, int32_t
     return warp_sum(c);
 }
 
-__device__ __forceinline__ int auto_method(int a, int b, float factor) {
-    int s = min(a, b), l = max(a, b);
-    bool ssi = (float)l <= factor * (log2f((float)l) - 1.0f) * (float)s;
-    if (ssi) return TC_STRAT_MERGE;
-    return a <= b ? TC_STRAT_SEARCH : TC_STRAT_PROBE;
-}
-
 __device__ __forceinline__ uint32_t edge_dispatch(int method, const Sink& S, int a0, int du,
                                                   const int32_t* __restrict__ B, int b) {
     switch (method) {
@@ -176,65 +183,245 @@ __device__ __forceinline__ uint32_t edge_dispatch(int method, const Sink& S, int
     }
 }
 
+// Builds the bitmap of the staged list L[0, d) over ranks (base, base + 32 W] and its
+// per-word prefix counts; a whole block calls it.
+template <int THREADS_>
+__device__ void build_bitmap(uint32_t* bm, uint16_t* pre, uint32_t* slice, const int32_t* __restrict__ L, int d,
+                             int32_t base, int W) {
+    const int lane = lane_id(), w = threadIdx.x >> 5;
+    constexpr int WARPS = THREADS_ / 32;
+    for (int i = threadIdx.x; i < W; i += THREADS_) bm[i] = 0;
+    __syncthreads();
+    for (int p = threadIdx.x; p < d; p += THREADS_) {
+        int off = L[p] - base - 1;
+        atomicOr(&bm[off >> 5], 1u << (off & 31));
+    }
+    __syncthreads();
+    // exclusive prefix of per-word popcounts: within 32-word slices (one warp each),
+    // then over slice totals (warp 0), then the slice offsets are added
+    const int slices = (W + 31) >> 5;
+    for (int s = w; s < slices; s += WARPS) {
+        const int i = s * 32 + lane;
+        const int pc = i < W ? __popc(bm[i]) : 0;
+        const int inc = warp_inclusive_scan(pc);
+        if (i < W) pre[i] = (uint16_t)(inc - pc);
+        if (lane == 31) slice[s] = (uint32_t)inc;
+    }
+    __syncthreads();
+    if (w == 0) {
+        uint32_t carry = 0;
+        for (int c0 = 0; c0 < slices; c0 += 32) {
+            const int i = c0 + lane;
+            const uint32_t v = i < slices ? slice[i] : 0u;
+            const uint32_t inc = warp_inclusive_scan(v);
+            if (i < slices) slice[i] = carry + inc - v;
+            carry += __shfl_sync(FULL, inc, 31);
+        }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < W; i += THREADS_) pre[i] = (uint16_t)(pre[i] + slice[i >> 5]);
+    __syncthreads();
+}
+
+// ---- lane-sequential methods (small bucket) -----------------------------------
+// A = Lu[a0, du) (shared, sorted), B = N+(v) (global, sorted).  A match at position
+// p of Lu adds one to cnt[p].
+
+__device__ uint32_t lane_merge(const int32_t* Lu, int a0, int du, const int32_t* __restrict__ B, int b,
+                               uint32_t* cnt) {
+    if (a0 >= du || b == 0) return 0;
+    uint32_t c = 0;
+    int i = a0, k = 0;
+    int32_t x = Lu[i], y = B[0];
+    for (;;) {
+        if (x == y) {
+            atomicAdd(&cnt[i], 1u);
+            ++c;
+            if (++i >= du || ++k >= b) break;
+            x = Lu[i];
+            y = B[k];
+        } else if (x < y) {
+            if (++i >= du) break;
+            x = Lu[i];
+        } else {
+            if (++k >= b) break;
+            y = B[k];
+        }
+    }
+    return c;
+}
+
+// keys of A looked up in B
+__device__ uint32_t lane_search(const int32_t* Lu, int a0, int du, const int32_t* __restrict__ B, int b,
+                                uint32_t* cnt) {
+    uint32_t c = 0;
+    int lo = 0;
+    for (int i = a0; i < du && lo < b; ++i) {
+        const int32_t x = Lu[i];
+        const int p = lower_bound(B, lo, b, x);
+        lo = p;
+        if (p < b && B[p] == x) {
+            atomicAdd(&cnt[i], 1u);
+            ++c;
+        }
+    }
+    return c;
+}
+
+// keys of B looked up in A
+__device__ uint32_t lane_search_rev(const int32_t* Lu, int a0, int du, const int32_t* __restrict__ B, int b,
+                                    uint32_t* cnt) {
+    uint32_t c = 0;
+    int lo = a0;
+    const int32_t mx = Lu[du - 1];
+    for (int k = 0; k < b && lo < du; ++k) {
+        const int32_t y = B[k];
+        if (y > mx) break;
+        const int p = lower_bound(Lu, lo, du, y);
+        lo = p;
+        if (p < du && Lu[p] == y) {
+            atomicAdd(&cnt[p], 1u);
+            ++c;
+        }
+    }
+    return c;
+}
+
 // ---- planner -----------------------------------------------------------------
 
-__global__ void k_plan(int32_t n, const int32_t* __restrict__ rowlen, int32_t* __restrict__ warp_list,
-                       int32_t* __restrict__ cta_list, DevStats* stats) {
+__global__ void k_hub_candidates(int32_t n, const int32_t* __restrict__ deg, int min_degree, DevStats* stats) {
+    unsigned c = 0;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += stride)
+        c += deg[r] >= min_degree ? 1u : 0u;
+    c = warp_sum(c);
+    if (lane_id() == 0 && c) atomicAdd(&stats->hub_candidates, c);
+}
+
+__global__ void k_hub_count(int32_t hub_cap, int hub_max, DevStats* stats) {
+    unsigned k = stats->hub_candidates;
+    k = min(k, (unsigned)hub_max);
+    k = min(k, (unsigned)hub_cap);
+    stats->hub_count = k;
+}
+
+// In-degree d-(v) = deg(v) - d+(v) of every hub slot (0 for slots below the hubs).
+__global__ void k_hub_indeg(int32_t n, int32_t hub_cap, const int32_t* __restrict__ deg,
+                            const int32_t* __restrict__ rowlen, uint32_t* __restrict__ cnt, DevStats* stats) {
+    const int32_t R = n - (int32_t)stats->hub_count;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < hub_cap; i += stride) {
+        const int32_t r = n - hub_cap + (int32_t)i;
+        cnt[i] = r >= R ? (uint32_t)(deg[r] - rowlen[r]) : 0u;
+    }
+}
+
+// Every oriented entry (u -> v) with v a hub becomes an in-edge of v: (u, the index
+// after v in N+(u), the end of N+(u)).  One warp per row.
+__global__ void k_hub_scatter(int32_t n, int32_t hub_cap, const int64_t* __restrict__ rowstart,
+                              const int32_t* __restrict__ rowlen, const int32_t* __restrict__ col,
+                              const int64_t* __restrict__ hub_start, uint32_t* __restrict__ hub_cur,
+                              int32_t* __restrict__ in_u, int32_t* __restrict__ in_b, int32_t* __restrict__ in_e,
+                              DevStats* stats) {
+    const int32_t R = n - (int32_t)stats->hub_count;
+    const int lane = lane_id();
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t u = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; u < n; u += warps) {
+        const int du = rowlen[u];
+        if (du == 0) continue;
+        const int64_t base = rowstart[u];
+        if (col[base + du - 1] < R) continue;  // no hub in this row
+        for (int p = lane; p < du; p += 32) {
+            const int32_t v = col[base + p];
+            if (v >= R) {
+                const int i = v - (n - hub_cap);
+                const int64_t slot = hub_start[i] + atomicAdd(&hub_cur[i], 1u);
+                in_u[slot] = (int32_t)u;
+                in_b[slot] = (int32_t)(base + p + 1);
+                in_e[slot] = (int32_t)(base + du);
+            }
+        }
+    }
+}
+
+// Push lists: sources with at least one non-hub target and a non-empty suffix.
+__global__ void k_plan(int32_t n, const int64_t* __restrict__ rowstart, const int32_t* __restrict__ rowlen,
+                       const int32_t* __restrict__ col, int32_t* __restrict__ l8, int32_t* __restrict__ l16,
+                       int32_t* __restrict__ l32, int32_t* __restrict__ lcta, DevStats* stats) {
+    const int32_t R = n - (int32_t)stats->hub_count;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     // the loop bound is uniform across a warp, as warp_append needs all 32 lanes
     for (int64_t b = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); b < n; b += stride) {
         const int64_t u = b + lane_id();
-        const int d = u < n ? rowlen[u] : 0;
-        const bool w = d >= 2 && d <= 32, c = d > 32;
-        const unsigned pw = warp_append(w, &stats->warp_count);
-        const unsigned pc = warp_append(c, &stats->cta_count);
-        if (w) warp_list[pw] = (int32_t)u;
-        if (c) cta_list[pc] = (int32_t)u;
+        int d = u < n ? rowlen[u] : 0;
+        if (d >= 2 && col[rowstart[u]] >= R) d = 0;  // every target is a hub
+        const bool c8 = d >= 2 && d <= 8, c16 = d > 8 && d <= 16, c32 = d > 16 && d <= 32, cc = d > 32;
+        const unsigned p8 = warp_append(c8, &stats->small_count[0]);
+        const unsigned p16 = warp_append(c16, &stats->small_count[1]);
+        const unsigned p32 = warp_append(c32, &stats->small_count[2]);
+        const unsigned pc = warp_append(cc, &stats->cta_count);
+        if (c8) l8[p8] = (int32_t)u;
+        if (c16) l16[p16] = (int32_t)u;
+        if (c32) l32[p32] = (int32_t)u;
+        if (cc) lcta[pc] = (int32_t)u;
     }
 }
 
-// ---- warp bucket: 2 <= d+(u) <= 32 ------------------------------------------------
+// ---- small bucket: groups of G lanes, one lane per edge -----------------------
 
-__global__ void __launch_bounds__(WK_WARPS * 32) k_tc_warp(const int64_t* __restrict__ rowstart,
-                                                           const int32_t* __restrict__ rowlen,
-                                                           const int32_t* __restrict__ col,
-                                                           const int32_t* __restrict__ list,
-                                                           unsigned long long* __restrict__ t,
-                                                           DevStats* stats, int strategy, float factor) {
-    __shared__ int32_t sLu[WK_WARPS][32];
-    __shared__ uint32_t sCnt[WK_WARPS][32];
+template <int G>
+__global__ void __launch_bounds__(SMALL_WARPS * 32) k_tc_small(int32_t n, const int64_t* __restrict__ rowstart,
+                                                               const int32_t* __restrict__ rowlen,
+                                                               const int32_t* __restrict__ col,
+                                                               const int32_t* __restrict__ list, int cls,
+                                                               unsigned long long* __restrict__ t, DevStats* stats,
+                                                               int strategy, float factor) {
+    constexpr int GPW = 32 / G;
+    __shared__ int32_t sLu[SMALL_WARPS * 32];
+    __shared__ uint32_t sCnt[SMALL_WARPS * 32];
     const int lane = lane_id(), w = threadIdx.x >> 5;
-    const unsigned count = stats->warp_count;
-    const unsigned warps = gridDim.x * WK_WARPS;
-    for (unsigned q = blockIdx.x * WK_WARPS + w; q < count; q += warps) {
+    const int grp = lane / G, g = lane % G;
+    const unsigned gmask = G == 32 ? FULL : (((1u << G) - 1u) << (grp * G));
+    int32_t* Lu = sLu + w * 32 + grp * G;
+    uint32_t* cnt = sCnt + w * 32 + grp * G;
+    const unsigned count = stats->small_count[cls];
+    const int32_t R = n - (int32_t)stats->hub_count;
+    const unsigned groups = gridDim.x * SMALL_WARPS * GPW;
+    for (unsigned q = (blockIdx.x * SMALL_WARPS + w) * GPW + grp; q < count; q += groups) {
         const int32_t u = list[q];
         const int du = rowlen[u];
         const int64_t base = rowstart[u];
-        sLu[w][lane] = lane < du ? col[base + lane] : INT_MAX;
-        sCnt[w][lane] = 0;
-        __syncwarp();
-        Sink S{sCnt[w], t, sLu[w]};
-        unsigned long long utot = 0;
-        for (int j = 0; j < du - 1; ++j) {
-            const int32_t v = sLu[w][j];
-            const int dv = rowlen[v];
-            if (dv == 0) continue;
-            const int32_t* B = col + rowstart[v];
-            const int a = du - j - 1;
-            int method = strategy == TC_STRAT_AUTO ? auto_method(a, dv, factor) : strategy;
-            uint32_t c = edge_dispatch(method, S, j + 1, du, B, dv);
-            if (lane == 0 && c) atomicAdd(&sCnt[w][j], c);
-            utot += c;
+        Lu[g] = g < du ? col[base + g] : INT_MAX;
+        cnt[g] = 0;
+        __syncwarp(gmask);
+        uint32_t c = 0;
+        if (g < du - 1) {
+            const int32_t v = Lu[g];
+            const int dv = v < R ? rowlen[v] : 0;
+            if (dv > 0) {
+                const int32_t* B = col + rowstart[v];
+                const int a = du - g - 1;
+                int method = strategy;
+                if (method == TC_STRAT_AUTO)
+                    method = eq3_prefers_merge(a, dv, factor) ? TC_STRAT_MERGE : TC_STRAT_SEARCH;
+                if (method == TC_STRAT_MERGE)
+                    c = lane_merge(Lu, g + 1, du, B, dv, cnt);
+                else
+                    c = a <= dv ? lane_search(Lu, g + 1, du, B, dv, cnt) : lane_search_rev(Lu, g + 1, du, B, dv, cnt);
+                if (c) atomicAdd(&cnt[g], c);
+            }
         }
-        __syncwarp();
-        uint32_t cv = sCnt[w][lane];
-        if (lane < du && cv) atomicAdd(&t[sLu[w][lane]], (unsigned long long)cv);
-        if (lane == 0 && utot) atomicAdd(&t[u], utot);
-        __syncwarp();
+#pragma unroll
+        for (int o = G / 2; o > 0; o >>= 1) c += __shfl_down_sync(gmask, c, o, G);
+        __syncwarp(gmask);
+        const uint32_t cv = cnt[g];
+        if (g < du && cv) atomicAdd(&t[Lu[g]], (unsigned long long)cv);
+        if (g == 0 && c) atomicAdd(&t[u], (unsigned long long)c);
+        __syncwarp(gmask);
     }
 }
 
-// ---- block bucket: d+(u) > 32 ----------------------------------------------------
+// ---- block bucket: |N+(u)| > 32, non-hub targets ------------------------------
 
 struct CtaShared {
     int32_t Lu[CTA_LIST_MAX];
@@ -246,7 +433,7 @@ struct CtaShared {
     int q;
 };
 
-__global__ void __launch_bounds__(CTA_THREADS) k_tc_cta(const int64_t* __restrict__ rowstart,
+__global__ void __launch_bounds__(CTA_THREADS) k_tc_cta(int32_t n, const int64_t* __restrict__ rowstart,
                                                         const int32_t* __restrict__ rowlen,
                                                         const int32_t* __restrict__ col,
                                                         const int32_t* __restrict__ list,
@@ -256,8 +443,9 @@ __global__ void __launch_bounds__(CTA_THREADS) k_tc_cta(const int64_t* __restric
     CtaShared& sh = *reinterpret_cast<CtaShared*>(smem_raw);
     const int lane = lane_id(), w = threadIdx.x >> 5;
     const unsigned count = stats->cta_count;
+    const int32_t R = n - (int32_t)stats->hub_count;
     for (;;) {
-        if (threadIdx.x == 0) sh.q = (int)atomicAdd(&stats->work_next, 1u);
+        if (threadIdx.x == 0) sh.q = (int)atomicAdd(&stats->cta_next, 1u);
         __syncthreads();
         const int q = sh.q;
         if ((unsigned)q >= count) break;
@@ -271,49 +459,16 @@ __global__ void __launch_bounds__(CTA_THREADS) k_tc_cta(const int64_t* __restric
                 sh.cnt[p] = 0;
             }
         }
+        __syncthreads();
         const int32_t* Lu = staged ? sh.Lu : col + base;
-        const int32_t maxu = col[base + du - 1];
+        const int32_t maxu = Lu[du - 1];
+        const int jh = min(du - 1, lower_bound(Lu, 0, du, R));  // edges into non-hubs
         const int span = maxu - u;  // ranks u+1 .. maxu
         const bool bitmap = staged && strategy == TC_STRAT_BITMAP && span <= BITMAP_WORDS * 32;
-        const int W = (span + 31) >> 5;
-        if (bitmap) {
-            for (int i = threadIdx.x; i < W; i += CTA_THREADS) sh.bm[i] = 0;
-        }
-        __syncthreads();
-        if (bitmap) {
-            for (int p = threadIdx.x; p < du; p += CTA_THREADS) {
-                int off = sh.Lu[p] - u - 1;
-                atomicOr(&sh.bm[off >> 5], 1u << (off & 31));
-            }
-            __syncthreads();
-            // exclusive prefix of per-word popcounts: within 32-word slices (one warp
-            // each), then over slice totals (warp 0), then the slice offsets are added
-            const int slices = (W + 31) >> 5;
-            for (int s = w; s < slices; s += CTA_WARPS) {
-                const int i = s * 32 + lane;
-                const int pc = i < W ? __popc(sh.bm[i]) : 0;
-                const int inc = warp_inclusive_scan(pc);
-                if (i < W) sh.pre[i] = (uint16_t)(inc - pc);
-                if (lane == 31) sh.slice[s] = (uint32_t)inc;
-            }
-            __syncthreads();
-            if (w == 0) {
-                uint32_t carry = 0;
-                for (int c0 = 0; c0 < slices; c0 += 32) {
-                    const int i = c0 + lane;
-                    const uint32_t v = i < slices ? sh.slice[i] : 0u;
-                    const uint32_t inc = warp_inclusive_scan(v);
-                    if (i < slices) sh.slice[i] = carry + inc - v;
-                    carry += __shfl_sync(FULL, inc, 31);
-                }
-            }
-            __syncthreads();
-            for (int i = threadIdx.x; i < W; i += CTA_THREADS) sh.pre[i] = (uint16_t)(sh.pre[i] + sh.slice[i >> 5]);
-            __syncthreads();
-        }
+        if (bitmap) build_bitmap<CTA_THREADS>(sh.bm, sh.pre, sh.slice, sh.Lu, du, u, (span + 31) >> 5);
         Sink S{staged ? sh.cnt : nullptr, t, Lu};
         unsigned long long utot = 0;
-        for (int j = w; j < du - 1; j += CTA_WARPS) {
+        for (int j = w; j < jh; j += CTA_WARPS) {
             const int32_t v = Lu[j];
             const int dv = rowlen[v];
             if (dv == 0) continue;
@@ -322,8 +477,14 @@ __global__ void __launch_bounds__(CTA_THREADS) k_tc_cta(const int64_t* __restric
             if (bitmap) {
                 c = edge_bitmap(sh.bm, sh.pre, u, maxu, sh.cnt, B, dv);
             } else {
-                int method = strategy == TC_STRAT_AUTO ? auto_method(du - j - 1, dv, factor)
-                                                       : (strategy == TC_STRAT_BITMAP ? TC_STRAT_PROBE : strategy);
+                int method = strategy;
+                if (method == TC_STRAT_AUTO) {
+                    const int a = du - j - 1;
+                    method = eq3_prefers_merge(a, dv, factor) ? TC_STRAT_MERGE
+                                                              : (a <= dv ? TC_STRAT_SEARCH : TC_STRAT_PROBE);
+                } else if (method == TC_STRAT_BITMAP) {
+                    method = TC_STRAT_PROBE;
+                }
                 c = edge_dispatch(method, S, j + 1, du, B, dv);
             }
             if (lane == 0 && c) {
@@ -338,7 +499,7 @@ __global__ void __launch_bounds__(CTA_THREADS) k_tc_cta(const int64_t* __restric
         __syncthreads();
         if (staged) {
             for (int p = threadIdx.x; p < du; p += CTA_THREADS) {
-                uint32_t cv = sh.cnt[p];
+                const uint32_t cv = sh.cnt[p];
                 if (cv) atomicAdd(&t[sh.Lu[p]], (unsigned long long)cv);
             }
         }
@@ -346,6 +507,158 @@ __global__ void __launch_bounds__(CTA_THREADS) k_tc_cta(const int64_t* __restric
             unsigned long long s = 0;
             for (int k = 0; k < CTA_WARPS; ++k) s += sh.utot[k];
             if (s) atomicAdd(&t[u], s);
+        }
+        __syncthreads();
+    }
+}
+
+// ---- hub bucket: one block per hub, in-edges streamed against the staged list --
+
+struct HubShared {
+    union {
+        struct {
+            uint32_t bm[HUB_BM_WORDS];
+            uint16_t pre[HUB_BM_WORDS];
+        } b;
+        int32_t list[HUB_CNT_MAX];
+    } s;
+    uint32_t cnt[HUB_CNT_MAX];
+    uint32_t slice[HUB_BM_WORDS / 32];
+    uint32_t cw[HUB_WARPS][32];
+    unsigned long long vt[HUB_WARPS];
+    int q;
+};
+
+__global__ void __launch_bounds__(HUB_THREADS) k_tc_hub(int32_t n, int32_t hub_cap, const int64_t* __restrict__ rowstart,
+                                                        const int32_t* __restrict__ rowlen,
+                                                        const int32_t* __restrict__ col,
+                                                        const int64_t* __restrict__ hub_start,
+                                                        const int32_t* __restrict__ in_u,
+                                                        const int32_t* __restrict__ in_b,
+                                                        const int32_t* __restrict__ in_e,
+                                                        unsigned long long* __restrict__ t, DevStats* stats,
+                                                        int probe_mode) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    HubShared& sh = *reinterpret_cast<HubShared*>(smem_raw);
+    const int lane = lane_id(), w = threadIdx.x >> 5;
+    const unsigned K = stats->hub_count;
+    for (;;) {
+        if (threadIdx.x == 0) sh.q = (int)atomicAdd(&stats->hub_next, 1u);
+        __syncthreads();
+        const int q = sh.q;
+        if ((unsigned)q >= K) break;
+        const int32_t v = n - 1 - q;  // highest ranks (largest hubs) first
+        const int hi = v - (n - hub_cap);
+        const int64_t e0 = hub_start[hi], e1 = hub_start[hi + 1];
+        const int dv = rowlen[v];
+        if (dv == 0 || e1 == e0) {
+            __syncthreads();
+            continue;
+        }
+        const int64_t base = rowstart[v];
+        const int32_t maxv = col[base + dv - 1];
+        const bool staged = dv <= HUB_CNT_MAX;
+        const int W = (maxv - v + 31) >> 5;  // maxv - v < hub_cap <= HUB_BM_BITS
+        if (staged)
+            for (int p = threadIdx.x; p < dv; p += HUB_THREADS) sh.cnt[p] = 0;
+        if (!probe_mode) {
+            build_bitmap<HUB_THREADS>(sh.s.b.bm, sh.s.b.pre, sh.slice, col + base, dv, v, W);
+        } else if (staged) {
+            for (int p = threadIdx.x; p < dv; p += HUB_THREADS) sh.s.list[p] = col[base + p];
+            __syncthreads();
+        } else {
+            __syncthreads();
+        }
+        const int32_t* Lv = staged ? sh.s.list : col + base;
+        unsigned long long vtot = 0;
+        for (int64_t bb = e0 + (int64_t)w * 32; bb < e1; bb += HUB_WARPS * 32) {
+            const int64_t k = bb + lane;
+            const bool ok = k < e1;
+            int32_t uu = ok ? in_u[k] : 0;
+            int32_t b0 = ok ? in_b[k] : 0;
+            int a = ok ? in_e[k] - b0 : 0;
+            const unsigned nz = __ballot_sync(FULL, a > 0);
+            const int cz = __popc(nz);
+            if (cz == 0) continue;
+            // lane L takes the L-th in-edge with a non-empty suffix
+            const int src = lane < cz ? (int)__fns(nz, 0, lane + 1) : lane;
+            uu = __shfl_sync(FULL, uu, src);
+            b0 = __shfl_sync(FULL, b0, src);
+            a = __shfl_sync(FULL, a, src);
+            if (lane >= cz) a = 0;
+            int incl = warp_inclusive_scan(a);
+            const int total = __shfl_sync(FULL, incl, 31);
+            const int excl = incl - a;
+            if (lane >= cz) incl = INT_MAX;
+            sh.cw[w][lane] = 0;
+            __syncwarp();
+            // the suffixes, laid end to end, are read 32 entries at a time
+            for (int r = 0; r < total; r += 32) {
+                const int i0 = __popc(__ballot_sync(FULL, incl <= r));
+                unsigned mk = (lane > i0 && lane < cz && excl - r < 32) ? (1u << (excl - r)) : 0u;
+                mk = __reduce_or_sync(FULL, mk);
+                int idx = i0 + __popc(mk & (lane == 31 ? FULL : ((2u << lane) - 1u)));
+                idx = min(idx, 31);
+                const int bi = __shfl_sync(FULL, b0, idx);
+                const int xi = __shfl_sync(FULL, excl, idx);
+                const int item = r + lane;
+                if (item < total) {
+                    const int32_t x = col[bi + (item - xi)];
+                    if (x <= maxv) {
+                        int p = -1;
+                        if (!probe_mode) {
+                            const int off = x - v - 1;
+                            const uint32_t word = sh.s.b.bm[off >> 5], bit = 1u << (off & 31);
+                            if (word & bit) p = sh.s.b.pre[off >> 5] + __popc(word & (bit - 1));
+                        } else {
+                            const int pp = lower_bound(Lv, 0, dv, x);
+                            if (Lv[pp] == x) p = pp;
+                        }
+                        if (p >= 0) {
+                            if (staged)
+                                atomicAdd(&sh.cnt[p], 1u);
+                            else
+                                atomicAdd(&t[x], 1ull);
+                            atomicAdd(&sh.cw[w][idx], 1u);
+                        }
+                    }
+                }
+            }
+            __syncwarp();
+            const uint32_t cu = sh.cw[w][lane];
+            if (lane < cz && cu) {
+                atomicAdd(&t[uu], (unsigned long long)cu);
+                vtot += cu;
+            }
+            __syncwarp();
+        }
+        vtot = warp_sum(vtot);
+        if (lane == 0) sh.vt[w] = vtot;
+        __syncthreads();
+        if (staged) {
+            if (!probe_mode) {
+                for (int i = threadIdx.x; i < W; i += HUB_THREADS) {
+                    const uint32_t word = sh.s.b.bm[i];
+                    uint32_t rest = word;
+                    while (rest) {
+                        const int bpos = __ffs(rest) - 1;
+                        rest &= rest - 1;
+                        const int p = sh.s.b.pre[i] + __popc(word & ((1u << bpos) - 1u));
+                        const uint32_t c = sh.cnt[p];
+                        if (c) atomicAdd(&t[v + 1 + i * 32 + bpos], (unsigned long long)c);
+                    }
+                }
+            } else {
+                for (int p = threadIdx.x; p < dv; p += HUB_THREADS) {
+                    const uint32_t c = sh.cnt[p];
+                    if (c) atomicAdd(&t[sh.s.list[p]], (unsigned long long)c);
+                }
+            }
+        }
+        if (threadIdx.x == 0) {
+            unsigned long long s = 0;
+            for (int k = 0; k < HUB_WARPS; ++k) s += sh.vt[k];
+            if (s) atomicAdd(&t[v], s);
         }
         __syncthreads();
     }
@@ -378,43 +691,116 @@ __global__ void k_finalize(int32_t n, const int32_t* __restrict__ rank, const un
     }
 }
 
+// Per-bucket work: edges and sum of d+(u) + d+(v) over them (one thread per u).
+__global__ void k_plan_stats(int32_t n, const int64_t* __restrict__ rowstart, const int32_t* __restrict__ rowlen,
+                             const int32_t* __restrict__ col, const DevStats* stats,
+                             unsigned long long* __restrict__ out) {
+    const int32_t R = n - (int32_t)stats->hub_count;
+    unsigned long long e[TC_NUM_BUCKETS + 1] = {}, ids[TC_NUM_BUCKETS + 1] = {};
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < n; u += stride) {
+        const int d = rowlen[u];
+        for (int k = 0; k < d; ++k) {
+            const int32_t v = col[rowstart[u] + k];
+            const int b = v >= R ? TC_BUCKET_HUB : (d < 2 ? TC_NUM_BUCKETS : (d <= 32 ? TC_BUCKET_SMALL : TC_BUCKET_CTA));
+            e[b] += 1;
+            ids[b] += (unsigned long long)(d + rowlen[v]);
+        }
+    }
+#pragma unroll
+    for (int b = 0; b <= TC_NUM_BUCKETS; ++b) {
+        const unsigned long long x = warp_sum(e[b]), y = warp_sum(ids[b]);
+        if (lane_id() == 0) {
+            if (x) atomicAdd(&out[b], x);
+            if (y) atomicAdd(&out[TC_NUM_BUCKETS + 1 + b], y);
+        }
+    }
+}
+
 }  // namespace
 
-void launch_plan(const CountBuffers& C, const Launch& L) {
+void launch_plan_stats(const CountBuffers& C, unsigned long long* out, const Launch& L) {
     if (C.n <= 0) return;
-    k_plan<<<grid_for(C.n, THREADS, L.sms), THREADS, 0, L.stream>>>(C.n, C.rowlen, C.warp_list, C.cta_list,
-                                                                   C.stats);
+    k_plan_stats<<<grid_for(C.n, THREADS, L.sms), THREADS, 0, L.stream>>>(C.n, C.rowstart, C.rowlen, C.col,
+                                                                         C.stats, out);
+    count_launch();
 }
 
-size_t cta_smem_bytes() { return sizeof(CtaShared); }
+void launch_plan(const CountBuffers& C, const Strategy& S, const Launch& L) {
+    if (C.n <= 0) return;
+    const int hub_max = S.hub_max < 0 ? 0 : S.hub_max;
+    const bool hubs = C.hub_cap > 0 && hub_max > 0;
+    if (hubs) {
+        k_hub_candidates<<<grid_for(C.n, THREADS, L.sms), THREADS, 0, L.stream>>>(C.n, C.deg, S.hub_min_degree,
+                                                                                 C.stats);
+        count_launch();
+    }
+    k_hub_count<<<1, 1, 0, L.stream>>>(C.hub_cap, hub_max, C.stats);
+    count_launch();
+    if (hubs) {
+        k_hub_indeg<<<grid_for(C.hub_cap, THREADS, L.sms), THREADS, 0, L.stream>>>(C.n, C.hub_cap, C.deg, C.rowlen,
+                                                                                  C.hub_cnt, C.stats);
+        count_launch();
+        scan_u32_to_i64(C.hub_cnt, C.hub_start, C.hub_cap, C.tmp, L);
+        cudaMemsetAsync(C.hub_cur, 0, sizeof(uint32_t) * (size_t)C.hub_cap, L.stream);
+        k_hub_scatter<<<grid_for((int64_t)C.n * 32, THREADS, L.sms), THREADS, 0, L.stream>>>(
+            C.n, C.hub_cap, C.rowstart, C.rowlen, C.col, C.hub_start, C.hub_cur, C.in_u, C.in_b, C.in_e, C.stats);
+        count_launch();
+    }
+    k_plan<<<grid_for(C.n, THREADS, L.sms), THREADS, 0, L.stream>>>(C.n, C.rowstart, C.rowlen, C.col,
+                                                                   C.small_list[0], C.small_list[1],
+                                                                   C.small_list[2], C.cta_list, C.stats);
+    count_launch();
+}
 
 cudaError_t intersect_init_attributes() {
-    return cudaFuncSetAttribute(k_tc_cta, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(CtaShared));
+    cudaError_t e = cudaFuncSetAttribute(k_tc_cta, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(CtaShared));
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(k_tc_hub, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(HubShared));
 }
 
-void launch_intersect(const CountBuffers& C, const Strategy& S, cudaEvent_t ev[3], const Launch& L) {
+void launch_intersect(const CountBuffers& C, const Strategy& S, cudaEvent_t* ev, const Launch& L) {
     if (C.n <= 0) return;
-    if (ev) cudaEventRecord(ev[0], L.stream);
-    k_tc_warp<<<L.sms * 8, WK_WARPS * 32, 0, L.stream>>>(C.rowstart, C.rowlen, C.col, C.warp_list, C.t_rank,
-                                                        C.stats, S.strat[TC_BUCKET_WARP],
-                                                        S.factor[TC_BUCKET_WARP]);
-    if (ev) cudaEventRecord(ev[1], L.stream);
-    cudaMemsetAsync(&C.stats->work_next, 0, sizeof(unsigned), L.stream);
-    k_tc_cta<<<L.sms * 4, CTA_THREADS, sizeof(CtaShared), L.stream>>>(C.rowstart, C.rowlen, C.col, C.cta_list,
+    if (ev) cudaEventRecord(ev[PH_SMALL], L.stream);
+    const int ss = S.strat[TC_BUCKET_SMALL];
+    const float sf = S.factor[TC_BUCKET_SMALL];
+    k_tc_small<8><<<L.sms * 8, SMALL_WARPS * 32, 0, L.stream>>>(C.n, C.rowstart, C.rowlen, C.col, C.small_list[0],
+                                                               0, C.t_rank, C.stats, ss, sf);
+    count_launch();
+    k_tc_small<16><<<L.sms * 8, SMALL_WARPS * 32, 0, L.stream>>>(C.n, C.rowstart, C.rowlen, C.col, C.small_list[1],
+                                                                1, C.t_rank, C.stats, ss, sf);
+    count_launch();
+    k_tc_small<32><<<L.sms * 8, SMALL_WARPS * 32, 0, L.stream>>>(C.n, C.rowstart, C.rowlen, C.col, C.small_list[2],
+                                                                2, C.t_rank, C.stats, ss, sf);
+    count_launch();
+    if (ev) cudaEventRecord(ev[PH_CTA], L.stream);
+    cudaMemsetAsync(&C.stats->cta_next, 0, sizeof(unsigned), L.stream);
+    k_tc_cta<<<L.sms * 4, CTA_THREADS, sizeof(CtaShared), L.stream>>>(C.n, C.rowstart, C.rowlen, C.col, C.cta_list,
                                                                      C.t_rank, C.stats, S.strat[TC_BUCKET_CTA],
                                                                      S.factor[TC_BUCKET_CTA]);
-    if (ev) cudaEventRecord(ev[2], L.stream);
+    count_launch();
+    if (ev) cudaEventRecord(ev[PH_HUB], L.stream);
+    if (C.hub_cap > 0) {
+        cudaMemsetAsync(&C.stats->hub_next, 0, sizeof(unsigned), L.stream);
+        k_tc_hub<<<L.sms * 4, HUB_THREADS, sizeof(HubShared), L.stream>>>(
+            C.n, C.hub_cap, C.rowstart, C.rowlen, C.col, C.hub_start, C.in_u, C.in_b, C.in_e, C.t_rank, C.stats,
+            S.strat[TC_BUCKET_HUB] == TC_STRAT_PROBE ? 1 : 0);
+        count_launch();
+    }
+    if (ev) cudaEventRecord(ev[PH_END], L.stream);
 }
 
 void launch_sum_t(const CountBuffers& C, const Launch& L) {
     if (C.n <= 0) return;
     k_sum_t<<<grid_for(C.n, THREADS, L.sms), THREADS, 0, L.stream>>>(C.n, C.t_rank, C.stats);
+    count_launch();
 }
 
 void launch_finalize(int32_t n, const int32_t* rank, const unsigned long long* t_rank, const int32_t* deg,
                      unsigned long long* t_out, double* lcc_out, const Launch& L) {
     if (n <= 0) return;
     k_finalize<<<grid_for(n, THREADS, L.sms), THREADS, 0, L.stream>>>(n, rank, t_rank, deg, t_out, lcc_out);
+    count_launch();
 }
 
 }  // namespace tcg

@@ -111,9 +111,9 @@ void scan_impl(const In* in, Out* out, int64_t count, void* tmp, const Launch& L
     int64_t tiles = (count + SCAN_TILE - 1) / SCAN_TILE;
     if (tiles < 1) tiles = 1;
     Acc* partials = static_cast<Acc*>(tmp);
-    k_tile_reduce<In, Acc><<<(unsigned)tiles, SCAN_THREADS, 0, L.stream>>>(in, count, partials);
-    k_scan_partials<Acc><<<1, SCAN_THREADS, 0, L.stream>>>(partials, tiles);
-    k_tile_scan<In, Out, Acc><<<(unsigned)tiles, SCAN_THREADS, 0, L.stream>>>(in, out, count, partials, tiles);
+    k_tile_reduce<In, Acc><<<(unsigned)tiles, SCAN_THREADS, 0, L.stream>>>(in, count, partials); count_launch();
+    k_scan_partials<Acc><<<1, SCAN_THREADS, 0, L.stream>>>(partials, tiles); count_launch();
+    k_tile_scan<In, Out, Acc><<<(unsigned)tiles, SCAN_THREADS, 0, L.stream>>>(in, out, count, partials, tiles); count_launch();
 }
 
 // ---- radix sort --------------------------------------------------------------
@@ -234,9 +234,9 @@ uint64_t* radix_sort_u64(uint64_t* keys, uint64_t* alt, int64_t count, int lo, i
     uint64_t* b = alt;
     for (int shift = lo; shift < hi; shift += 8) {
         int bits = hi - shift < 8 ? hi - shift : 8;
-        k_radix_hist<<<(unsigned)tiles, RADIX_THREADS, 0, L.stream>>>(a, count, shift, bits, hist, tiles);
+        k_radix_hist<<<(unsigned)tiles, RADIX_THREADS, 0, L.stream>>>(a, count, shift, bits, hist, tiles); count_launch();
         scan_u32_to_u32(hist, hist, RADIX_BINS * tiles, scan_tmp, L);
-        k_radix_scatter<<<(unsigned)tiles, RADIX_THREADS, 0, L.stream>>>(a, b, count, shift, bits, hist, tiles);
+        k_radix_scatter<<<(unsigned)tiles, RADIX_THREADS, 0, L.stream>>>(a, b, count, shift, bits, hist, tiles); count_launch();
         uint64_t* t = a;
         a = b;
         b = t;

@@ -7,11 +7,12 @@ import numpy as np
 import oracle
 
 
-def gpu_run(tc, n, src, dst, device_io=False, strategies=None, csr=None, stream=None):
+def gpu_run(tc, n, src, dst, device_io=False, strategies=None, csr=None, stream=None, hubs=None):
     """T, t, lcc and input accounting from the CUDA library.
 
     device_io: inputs and outputs as CUDA tensors (TC_MEM_DEVICE), else numpy.
     strategies: {bucket: (strategy, factor)} applied before counting.
+    hubs: (min_degree, max_hubs) for the hub bucket.
     csr: (offsets, adj) to build from CSR instead of the edge list."""
     import torch
     if csr is not None:
@@ -27,6 +28,8 @@ def gpu_run(tc, n, src, dst, device_io=False, strategies=None, csr=None, stream=
     try:
         for bucket, (s, f) in (strategies or {}).items():
             g.set_strategy(bucket, s, f)
+        if hubs is not None:
+            g.set_hubs(*hubs)
         T = g.count()
         if device_io:
             t = torch.empty(n, dtype=torch.int64, device="cuda")

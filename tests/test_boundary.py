@@ -56,6 +56,8 @@ def test_argument_errors_before_device_work(tc):
     assert lib.tc_count(None, None) == tc.TC_EINVAL
     assert lib.lcc_compute(None, None, None, 0) == tc.TC_EINVAL
     assert lib.tc_graph_set_strategy(None, 0, 0, 1.0) == tc.TC_EINVAL
+    assert lib.tc_graph_set_hubs(None, 32, 10) == tc.TC_EINVAL
+    assert lib.tc_graph_last_timing(None, None, 0) == tc.TC_EINVAL
     lib.tc_graph_destroy(None)
 
 

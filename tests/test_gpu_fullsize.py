@@ -1,0 +1,32 @@
+"""Parity at the full workload sizes, in the launch configuration the benchmark
+times (default strategies): T and every t[v] and LCC[v] against the oracle (its
+oriented count split over the host cores)."""
+from __future__ import annotations
+
+import os
+
+import numpy as np
+import pytest
+
+import graphgen
+import oracle
+from tests.gpu_util import gpu_run
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.mark.parametrize("name", ["rmat20", "er23", "rmat23"])
+def test_full_workload(tc, name):
+    w = graphgen.workload(name)
+    s, d = w.edges()
+    T, t, lc, info = gpu_run(tc, w.n, s, d, device_io=True)
+    ref = oracle.triangles(w.n, s, d, threads=len(os.sched_getaffinity(0)))
+    assert T == ref["T"]
+    assert info["m_simple"] == ref["m_simple"]
+    assert info["loops_dropped"] == ref["loops_dropped"]
+    np.testing.assert_array_equal(t, ref["t"])
+    np.testing.assert_array_equal(lc.view(np.uint64), ref["lcc"].view(np.uint64))
+    # properties that hold at any size
+    assert int(t.sum()) == 3 * T
+    deg = ref["degree"]
+    assert (t <= deg * (deg - 1) // 2).all()

@@ -12,8 +12,12 @@ from tests.gpu_util import assert_matches_oracle, gpu_run
 
 pytestmark = pytest.mark.gpu
 
-ALL_STRATEGIES = [("auto", 1.0), ("auto", 4.0), ("auto", 0.25), ("merge", 1.0), ("search", 1.0),
-                  ("probe", 1.0)]
+SMALL_STRATEGIES = [("auto", 1.0), ("auto", 8.0), ("auto", 0.125), ("merge", 1.0), ("search", 1.0)]
+CTA_STRATEGIES = [("auto", 1.0), ("auto", 4.0), ("auto", 0.25), ("merge", 1.0), ("search", 1.0),
+                  ("probe", 1.0), ("bitmap", 1.0)]
+HUB_STRATEGIES = [("auto", 1.0), ("bitmap", 1.0), ("probe", 1.0)]
+# (min_degree, max_hubs): default, none, every vertex of degree >= 1, a handful
+HUB_SETTINGS = [(32, 131072), (32, 0), (1, 131072), (64, 50)]
 
 
 @pytest.fixture(scope="module")
@@ -57,20 +61,46 @@ def test_tiny_random_with_loops_and_repeats(tc, seed):
     assert_matches_oracle(tc, n, s, d)
 
 
-@pytest.mark.parametrize("warp", ALL_STRATEGIES)
-@pytest.mark.parametrize("cta", ALL_STRATEGIES + [("bitmap", 1.0)])
-def test_every_strategy_agrees(tc, rmat14, warp, cta):
+@pytest.mark.parametrize("hubs", HUB_SETTINGS)
+@pytest.mark.parametrize("small", SMALL_STRATEGIES)
+@pytest.mark.parametrize("cta", CTA_STRATEGIES)
+def test_every_strategy_agrees(tc, rmat14, small, cta, hubs):
     n, s, d, ref = rmat14
-    strategies = {tc.TC_BUCKET_WARP: warp, tc.TC_BUCKET_CTA: cta}
-    assert_matches_oracle(tc, n, s, d, ref=ref, strategies=strategies)
+    strategies = {tc.TC_BUCKET_SMALL: small, tc.TC_BUCKET_CTA: cta}
+    assert_matches_oracle(tc, n, s, d, ref=ref, strategies=strategies, hubs=hubs)
 
 
-def test_strategy_rejects_bitmap_in_warp_bucket(tc, er4096):
+@pytest.mark.parametrize("hub", HUB_STRATEGIES)
+@pytest.mark.parametrize("hubs", HUB_SETTINGS)
+def test_hub_strategies_agree(tc, rmat14, hub, hubs):
+    n, s, d, ref = rmat14
+    assert_matches_oracle(tc, n, s, d, ref=ref, strategies={tc.TC_BUCKET_HUB: hub}, hubs=hubs)
+
+
+def test_strategy_rejects_unsupported_pairs(tc, er4096):
     n, s, d, _ = er4096
     g = tc.Graph.from_edges(n, s, d)
+    for bucket, strat in [("small", "bitmap"), ("small", "probe"), ("hub", "merge"), ("hub", "search")]:
+        with pytest.raises(tc.TCError):
+            g.set_strategy(bucket, strat)
     with pytest.raises(tc.TCError):
-        g.set_strategy(tc.TC_BUCKET_WARP, "bitmap")
+        g.set_hubs(-1, 10)
     g.close()
+
+
+def test_plan_accounts_for_every_edge(tc, rmat14):
+    n, s, d, ref = rmat14
+    for hubs in HUB_SETTINGS:
+        g = tc.Graph.from_edges(n, s, d)
+        g.set_hubs(*hubs)
+        p = g.plan_stats()
+        assert sum(b["edges"] for b in p.values()) == ref["m_simple"]
+        if hubs[1] == 0:
+            assert p["hub"]["edges"] == 0
+        assert g.count() == ref["T"]
+        tim = g.timing()
+        assert tim["total_ms"] > 0
+        g.close()
 
 
 def test_csr_input_host_and_device(tc, rmat14):
