@@ -96,6 +96,8 @@ struct tc_graph {
     uint32_t* hub_cnt = nullptr;
     int64_t* hub_start = nullptr;
     uint32_t* hub_cur = nullptr;
+    int32_t* big_list = nullptr;
+    int32_t* med_list = nullptr;
     int32_t* in_u = nullptr;
     int32_t* in_b = nullptr;
     int32_t* in_e = nullptr;
@@ -198,7 +200,8 @@ tc_status build_graph(tc_graph* g, const int32_t* src, const int32_t* dst, int64
         (st = dalloc(g, &g->small_list[0], nn, &keep)) || (st = dalloc(g, &g->small_list[1], nn, &keep)) ||
         (st = dalloc(g, &g->small_list[2], nn, &keep)) || (st = dalloc(g, &g->cta_list, nn, &keep)) ||
         (st = dalloc(g, &g->hub_cnt, hc + 1, &keep)) || (st = dalloc(g, &g->hub_start, hc + 1, &keep)) ||
-        (st = dalloc(g, &g->hub_cur, hc + 1, &keep)) || (st = dalloc(g, &g->in_u, (size_t)m, &keep)) ||
+        (st = dalloc(g, &g->hub_cur, hc + 1, &keep)) || (st = dalloc(g, &g->big_list, hc + 1, &keep)) ||
+        (st = dalloc(g, &g->med_list, hc + 1, &keep)) || (st = dalloc(g, &g->in_u, (size_t)m, &keep)) ||
         (st = dalloc(g, &g->in_b, (size_t)m, &keep)) || (st = dalloc(g, &g->in_e, (size_t)m, &keep)) ||
         (st = dalloc(g, (char**)&g->plan_tmp, scan_tmp_bytes((int64_t)hc + 1), &keep)) ||
         (st = dalloc(g, &g->t_rank, nn, &keep)))
@@ -261,6 +264,8 @@ CountBuffers count_buffers(tc_graph* g) {
     C.hub_cnt = g->hub_cnt;
     C.hub_start = g->hub_start;
     C.hub_cur = g->hub_cur;
+    C.big_list = g->big_list;
+    C.med_list = g->med_list;
     C.in_u = g->in_u;
     C.in_b = g->in_b;
     C.in_e = g->in_e;

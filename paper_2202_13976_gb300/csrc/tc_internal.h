@@ -27,9 +27,11 @@ struct DevStats {
     unsigned int cta_count;        // planner: vertices with d+ > 32
     unsigned int cta_next;         // dynamic work counter of the block push kernel
     unsigned int hub_count;        // vertices staged as hubs (ranks n - hub_count .. n-1)
-    unsigned int hub_next;         // dynamic work counter of the hub kernel
+    unsigned int hub_next;         // dynamic work counter of the hub kernel (big hubs)
+    unsigned int hub_next2;        // dynamic work counter of the hub kernel (medium hubs)
     unsigned int hub_candidates;   // vertices whose degree reaches the hub threshold
-    unsigned int pad[5];
+    unsigned int hub_big;          // hubs processed by whole blocks
+    unsigned int pad[3];
 };
 static_assert(sizeof(DevStats) == 88, "DevStats layout");
 
@@ -111,7 +113,9 @@ struct CountBuffers {
     int32_t hub_cap;         // min(n, HUB_BM_BITS): slots for ranks n - hub_cap .. n-1
     uint32_t* hub_cnt;       // hub_cap + 1
     int64_t* hub_start;      // hub_cap + 1
-    uint32_t* hub_cur;       // hub_cap
+    uint32_t* hub_cur;       // hub_cap + 1
+    int32_t* big_list;       // hub_cap: big hubs, highest rank first
+    int32_t* med_list;       // hub_cap: the other hubs, highest rank first
     int32_t* in_u;           // m: source vertex of the in-edge
     int32_t* in_b;           // m: first suffix entry (index into col)
     int32_t* in_e;           // m: end of the source row (index into col)

@@ -50,6 +50,8 @@ constexpr int HUB_THREADS = 256;
 constexpr int HUB_WARPS = HUB_THREADS / 32;
 constexpr int HUB_BM_WORDS = HUB_BM_BITS / 32;
 constexpr int HUB_CNT_MAX = 4096;      // hub lists longer than this count matches globally
+constexpr int HUB_BIG_IN = 256;        // hubs with at least this in-degree get a whole block
+constexpr int HUB_WARP_MAX = 448;      // longest N+(v) a single warp stages
 
 struct Sink {
     uint32_t* cnt;               // per-position counters (shared), or null
@@ -344,6 +346,34 @@ __global__ void k_hub_scatter(int32_t n, int32_t hub_cap, const int64_t* __restr
     }
 }
 
+// Hub slot i (0 = highest rank) is big when its in-degree reaches HUB_BIG_IN or its
+// list is too long for one warp.
+__global__ void k_hub_flags(int32_t n, const int32_t* __restrict__ rowlen, const uint32_t* __restrict__ indeg,
+                            int32_t hub_cap, uint32_t* __restrict__ big, DevStats* stats) {
+    const int64_t K = stats->hub_count;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < K; i += stride) {
+        const int32_t v = n - 1 - (int32_t)i;
+        const uint32_t din = indeg[v - (n - hub_cap)];
+        big[i] = (din >= (uint32_t)HUB_BIG_IN || rowlen[v] > HUB_WARP_MAX) && rowlen[v] > 0 && din > 0 ? 1u : 0u;
+    }
+}
+
+// Ordered split of the hubs (highest rank first) into the big and medium lists.
+__global__ void k_hub_lists(int32_t n, const uint32_t* __restrict__ big, const uint32_t* __restrict__ pos,
+                            int32_t* __restrict__ big_list, int32_t* __restrict__ med_list, DevStats* stats) {
+    const int64_t K = stats->hub_count;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < K; i += stride) {
+        const int32_t v = n - 1 - (int32_t)i;
+        if (big[i])
+            big_list[pos[i]] = v;
+        else
+            med_list[i - pos[i]] = v;
+        if (i == K - 1) stats->hub_big = pos[i] + big[i];
+    }
+}
+
 // Push lists: sources with at least one non-hub target and a non-empty suffix.
 __global__ void k_plan(int32_t n, const int64_t* __restrict__ rowstart, const int32_t* __restrict__ rowlen,
                        const int32_t* __restrict__ col, int32_t* __restrict__ l8, int32_t* __restrict__ l16,
@@ -512,18 +542,139 @@ __global__ void __launch_bounds__(CTA_THREADS) k_tc_cta(int32_t n, const int64_t
     }
 }
 
-// ---- hub bucket: one block per hub, in-edges streamed against the staged list --
+// ---- hub bucket ----------------------------------------------------------------
+// Big hubs (in-degree >= HUB_BIG_IN, or lists too long for one warp) are processed
+// by a whole block over a bitmap of N+(v); the remaining hubs by one warp each over
+// the sorted list N+(v) in shared memory.  One persistent kernel drains the big-hub
+// queue first, then every warp takes medium hubs independently.
+
+
+struct BitmapProbe {
+    const uint32_t* bm;
+    const uint16_t* pre;
+    int32_t v;
+    __device__ __forceinline__ int operator()(int32_t x) const {
+        const int off = x - v - 1;
+        const uint32_t word = bm[off >> 5], bit = 1u << (off & 31);
+        return (word & bit) ? (int)pre[off >> 5] + __popc(word & (bit - 1)) : -1;
+    }
+};
+
+struct ListProbe {
+    const int32_t* L;
+    int d;
+    __device__ __forceinline__ int operator()(int32_t x) const {
+        const int p = lower_bound(L, 0, d, x);  // x <= max(L), so p < d
+        return L[p] == x ? p : -1;
+    }
+};
+
+// One batch of up to 32 in-edges [k0, min(k0 + 32, e1)) of hub v, processed by one
+// warp.  Suffixes of 32 or more entries are read one in-edge at a time by all lanes
+// (the read stops above max N+(v)); shorter ones are laid end to end and read 32
+// entries at a time.  Matches add to cnt[p] (or t[x] when cnt is null) and to the
+// per-in-edge total, which goes to t[u].  Returns the batch total (all lanes).
+template <class Probe>
+__device__ uint32_t hub_batch(int64_t k0, int64_t e1, const int32_t* __restrict__ in_u,
+                              const int32_t* __restrict__ in_b, const int32_t* __restrict__ in_e,
+                              const int32_t* __restrict__ col, int32_t maxv, const Probe& probe, uint32_t* cnt,
+                              unsigned long long* __restrict__ t, uint32_t* cw) {
+    const int lane = lane_id();
+    const int64_t k = k0 + lane;
+    const bool ok = k < e1;
+    int32_t uu = ok ? in_u[k] : 0;
+    int32_t b0 = ok ? in_b[k] : 0;
+    int a = ok ? in_e[k] - b0 : 0;
+    uint32_t total_c = 0;
+    unsigned longm = __ballot_sync(FULL, a >= 32);
+    while (longm) {
+        const int L = __ffs(longm) - 1;
+        longm &= longm - 1;
+        const int32_t bL = __shfl_sync(FULL, b0, L);
+        const int aL = __shfl_sync(FULL, a, L);
+        uint32_t c = 0;
+        for (int o0 = 0; o0 < aL; o0 += 32) {
+            const int o = o0 + lane;
+            const int32_t x = o < aL ? col[bL + o] : INT_MAX;
+            if (x <= maxv) {
+                const int p = probe(x);
+                if (p >= 0) {
+                    if (cnt)
+                        atomicAdd(&cnt[p], 1u);
+                    else
+                        atomicAdd(&t[x], 1ull);
+                    ++c;
+                }
+            }
+            if (__any_sync(FULL, x > maxv)) break;  // the suffix is sorted
+        }
+        c = __reduce_add_sync(FULL, c);
+        total_c += c;
+        if (c && lane == L) atomicAdd(&t[uu], (unsigned long long)c);
+    }
+    if (a >= 32) a = 0;  // done above
+    const unsigned nz = __ballot_sync(FULL, a > 0);
+    const int cz = __popc(nz);
+    if (cz == 0) return total_c;
+    // lane i takes the i-th short in-edge
+    const int src = lane < cz ? (int)__fns(nz, 0, lane + 1) : lane;
+    uu = __shfl_sync(FULL, uu, src);
+    b0 = __shfl_sync(FULL, b0, src);
+    a = __shfl_sync(FULL, a, src);
+    if (lane >= cz) a = 0;
+    int incl = warp_inclusive_scan(a);
+    const int total = __shfl_sync(FULL, incl, 31);
+    const int excl = incl - a;
+    if (lane >= cz) incl = INT_MAX;
+    cw[lane] = 0;
+    __syncwarp();
+    for (int r = 0; r < total; r += 32) {
+        const int i0 = __popc(__ballot_sync(FULL, incl <= r));
+        unsigned mk = (lane > i0 && lane < cz && excl - r < 32) ? (1u << (excl - r)) : 0u;
+        mk = __reduce_or_sync(FULL, mk);
+        const int idx = min(i0 + __popc(mk & (lane == 31 ? FULL : ((2u << lane) - 1u))), 31);
+        const int bi = __shfl_sync(FULL, b0, idx);
+        const int xi = __shfl_sync(FULL, excl, idx);
+        const int item = r + lane;
+        if (item < total) {
+            const int32_t x = col[bi + (item - xi)];
+            if (x <= maxv) {
+                const int p = probe(x);
+                if (p >= 0) {
+                    if (cnt)
+                        atomicAdd(&cnt[p], 1u);
+                    else
+                        atomicAdd(&t[x], 1ull);
+                    atomicAdd(&cw[idx], 1u);
+                }
+            }
+        }
+    }
+    __syncwarp();
+    const uint32_t cu = cw[lane];
+    if (lane < cz && cu) atomicAdd(&t[uu], (unsigned long long)cu);
+    __syncwarp();
+    return total_c + __reduce_add_sync(FULL, lane < cz ? cu : 0u);
+}
 
 struct HubShared {
     union {
-        struct {
-            uint32_t bm[HUB_BM_WORDS];
-            uint16_t pre[HUB_BM_WORDS];
-        } b;
-        int32_t list[HUB_CNT_MAX];
-    } s;
-    uint32_t cnt[HUB_CNT_MAX];
-    uint32_t slice[HUB_BM_WORDS / 32];
+        struct {  // big hub, one block
+            union {
+                struct {
+                    uint32_t bm[HUB_BM_WORDS];
+                    uint16_t pre[HUB_BM_WORDS];
+                } b;
+                int32_t list[HUB_CNT_MAX];
+            } s;
+            uint32_t cnt[HUB_CNT_MAX];
+            uint32_t slice[HUB_BM_WORDS / 32];
+        } big;
+        struct {  // medium hubs, one per warp
+            int32_t list[HUB_WARPS][HUB_WARP_MAX];
+            uint32_t cnt[HUB_WARPS][HUB_WARP_MAX];
+        } med;
+    } u;
     uint32_t cw[HUB_WARPS][32];
     unsigned long long vt[HUB_WARPS];
     int q;
@@ -533,6 +684,8 @@ __global__ void __launch_bounds__(HUB_THREADS) k_tc_hub(int32_t n, int32_t hub_c
                                                         const int32_t* __restrict__ rowlen,
                                                         const int32_t* __restrict__ col,
                                                         const int64_t* __restrict__ hub_start,
+                                                        const int32_t* __restrict__ big_list,
+                                                        const int32_t* __restrict__ med_list,
                                                         const int32_t* __restrict__ in_u,
                                                         const int32_t* __restrict__ in_b,
                                                         const int32_t* __restrict__ in_e,
@@ -541,117 +694,60 @@ __global__ void __launch_bounds__(HUB_THREADS) k_tc_hub(int32_t n, int32_t hub_c
     extern __shared__ __align__(16) unsigned char smem_raw[];
     HubShared& sh = *reinterpret_cast<HubShared*>(smem_raw);
     const int lane = lane_id(), w = threadIdx.x >> 5;
-    const unsigned K = stats->hub_count;
+    const unsigned nbig = stats->hub_big, nmed = stats->hub_count - stats->hub_big;
+    // phase 1: big hubs, one block each
     for (;;) {
         if (threadIdx.x == 0) sh.q = (int)atomicAdd(&stats->hub_next, 1u);
         __syncthreads();
         const int q = sh.q;
-        if ((unsigned)q >= K) break;
-        const int32_t v = n - 1 - q;  // highest ranks (largest hubs) first
+        if ((unsigned)q >= nbig) break;
+        const int32_t v = big_list[q];
         const int hi = v - (n - hub_cap);
         const int64_t e0 = hub_start[hi], e1 = hub_start[hi + 1];
         const int dv = rowlen[v];
-        if (dv == 0 || e1 == e0) {
-            __syncthreads();
-            continue;
-        }
         const int64_t base = rowstart[v];
-        const int32_t maxv = col[base + dv - 1];
+        const int32_t maxv = col[base + dv - 1];  // big hubs have dv >= 1
         const bool staged = dv <= HUB_CNT_MAX;
         const int W = (maxv - v + 31) >> 5;  // maxv - v < hub_cap <= HUB_BM_BITS
         if (staged)
-            for (int p = threadIdx.x; p < dv; p += HUB_THREADS) sh.cnt[p] = 0;
+            for (int p = threadIdx.x; p < dv; p += HUB_THREADS) sh.u.big.cnt[p] = 0;
         if (!probe_mode) {
-            build_bitmap<HUB_THREADS>(sh.s.b.bm, sh.s.b.pre, sh.slice, col + base, dv, v, W);
-        } else if (staged) {
-            for (int p = threadIdx.x; p < dv; p += HUB_THREADS) sh.s.list[p] = col[base + p];
-            __syncthreads();
+            build_bitmap<HUB_THREADS>(sh.u.big.s.b.bm, sh.u.big.s.b.pre, sh.u.big.slice, col + base, dv, v, W);
         } else {
+            if (staged)
+                for (int p = threadIdx.x; p < dv; p += HUB_THREADS) sh.u.big.s.list[p] = col[base + p];
             __syncthreads();
         }
-        const int32_t* Lv = staged ? sh.s.list : col + base;
+        uint32_t* cnt = staged ? sh.u.big.cnt : nullptr;
         unsigned long long vtot = 0;
-        for (int64_t bb = e0 + (int64_t)w * 32; bb < e1; bb += HUB_WARPS * 32) {
-            const int64_t k = bb + lane;
-            const bool ok = k < e1;
-            int32_t uu = ok ? in_u[k] : 0;
-            int32_t b0 = ok ? in_b[k] : 0;
-            int a = ok ? in_e[k] - b0 : 0;
-            const unsigned nz = __ballot_sync(FULL, a > 0);
-            const int cz = __popc(nz);
-            if (cz == 0) continue;
-            // lane L takes the L-th in-edge with a non-empty suffix
-            const int src = lane < cz ? (int)__fns(nz, 0, lane + 1) : lane;
-            uu = __shfl_sync(FULL, uu, src);
-            b0 = __shfl_sync(FULL, b0, src);
-            a = __shfl_sync(FULL, a, src);
-            if (lane >= cz) a = 0;
-            int incl = warp_inclusive_scan(a);
-            const int total = __shfl_sync(FULL, incl, 31);
-            const int excl = incl - a;
-            if (lane >= cz) incl = INT_MAX;
-            sh.cw[w][lane] = 0;
-            __syncwarp();
-            // the suffixes, laid end to end, are read 32 entries at a time
-            for (int r = 0; r < total; r += 32) {
-                const int i0 = __popc(__ballot_sync(FULL, incl <= r));
-                unsigned mk = (lane > i0 && lane < cz && excl - r < 32) ? (1u << (excl - r)) : 0u;
-                mk = __reduce_or_sync(FULL, mk);
-                int idx = i0 + __popc(mk & (lane == 31 ? FULL : ((2u << lane) - 1u)));
-                idx = min(idx, 31);
-                const int bi = __shfl_sync(FULL, b0, idx);
-                const int xi = __shfl_sync(FULL, excl, idx);
-                const int item = r + lane;
-                if (item < total) {
-                    const int32_t x = col[bi + (item - xi)];
-                    if (x <= maxv) {
-                        int p = -1;
-                        if (!probe_mode) {
-                            const int off = x - v - 1;
-                            const uint32_t word = sh.s.b.bm[off >> 5], bit = 1u << (off & 31);
-                            if (word & bit) p = sh.s.b.pre[off >> 5] + __popc(word & (bit - 1));
-                        } else {
-                            const int pp = lower_bound(Lv, 0, dv, x);
-                            if (Lv[pp] == x) p = pp;
-                        }
-                        if (p >= 0) {
-                            if (staged)
-                                atomicAdd(&sh.cnt[p], 1u);
-                            else
-                                atomicAdd(&t[x], 1ull);
-                            atomicAdd(&sh.cw[w][idx], 1u);
-                        }
-                    }
-                }
-            }
-            __syncwarp();
-            const uint32_t cu = sh.cw[w][lane];
-            if (lane < cz && cu) {
-                atomicAdd(&t[uu], (unsigned long long)cu);
-                vtot += cu;
-            }
-            __syncwarp();
+        if (!probe_mode) {
+            const BitmapProbe P{sh.u.big.s.b.bm, sh.u.big.s.b.pre, v};
+            for (int64_t bb = e0 + (int64_t)w * 32; bb < e1; bb += HUB_WARPS * 32)
+                vtot += hub_batch(bb, e1, in_u, in_b, in_e, col, maxv, P, cnt, t, sh.cw[w]);
+        } else {
+            const ListProbe P{staged ? sh.u.big.s.list : col + base, dv};
+            for (int64_t bb = e0 + (int64_t)w * 32; bb < e1; bb += HUB_WARPS * 32)
+                vtot += hub_batch(bb, e1, in_u, in_b, in_e, col, maxv, P, cnt, t, sh.cw[w]);
         }
-        vtot = warp_sum(vtot);
         if (lane == 0) sh.vt[w] = vtot;
         __syncthreads();
         if (staged) {
             if (!probe_mode) {
                 for (int i = threadIdx.x; i < W; i += HUB_THREADS) {
-                    const uint32_t word = sh.s.b.bm[i];
+                    const uint32_t word = sh.u.big.s.b.bm[i];
                     uint32_t rest = word;
                     while (rest) {
                         const int bpos = __ffs(rest) - 1;
                         rest &= rest - 1;
-                        const int p = sh.s.b.pre[i] + __popc(word & ((1u << bpos) - 1u));
-                        const uint32_t c = sh.cnt[p];
+                        const int p = sh.u.big.s.b.pre[i] + __popc(word & ((1u << bpos) - 1u));
+                        const uint32_t c = sh.u.big.cnt[p];
                         if (c) atomicAdd(&t[v + 1 + i * 32 + bpos], (unsigned long long)c);
                     }
                 }
             } else {
                 for (int p = threadIdx.x; p < dv; p += HUB_THREADS) {
-                    const uint32_t c = sh.cnt[p];
-                    if (c) atomicAdd(&t[sh.s.list[p]], (unsigned long long)c);
+                    const uint32_t c = sh.u.big.cnt[p];
+                    if (c) atomicAdd(&t[sh.u.big.s.list[p]], (unsigned long long)c);
                 }
             }
         }
@@ -661,6 +757,37 @@ __global__ void __launch_bounds__(HUB_THREADS) k_tc_hub(int32_t n, int32_t hub_c
             if (s) atomicAdd(&t[v], s);
         }
         __syncthreads();
+    }
+    // phase 2: medium hubs, one warp each (no block barriers from here on)
+    int32_t* L = sh.u.med.list[w];
+    uint32_t* cnt = sh.u.med.cnt[w];
+    for (;;) {
+        unsigned q = 0;
+        if (lane == 0) q = atomicAdd(&stats->hub_next2, 1u);
+        q = __shfl_sync(FULL, q, 0);
+        if (q >= nmed) break;
+        const int32_t v = med_list[q];
+        const int hi = v - (n - hub_cap);
+        const int64_t e0 = hub_start[hi], e1 = hub_start[hi + 1];
+        const int dv = rowlen[v];
+        if (dv == 0 || e1 == e0) continue;
+        const int64_t base = rowstart[v];
+        for (int p = lane; p < dv; p += 32) {
+            L[p] = col[base + p];
+            cnt[p] = 0;
+        }
+        __syncwarp();
+        const int32_t maxv = L[dv - 1];
+        const ListProbe P{L, dv};
+        unsigned long long vtot = 0;
+        for (int64_t bb = e0; bb < e1; bb += 32) vtot += hub_batch(bb, e1, in_u, in_b, in_e, col, maxv, P, cnt, t, sh.cw[w]);
+        __syncwarp();
+        for (int p = lane; p < dv; p += 32) {
+            const uint32_t c = cnt[p];
+            if (c) atomicAdd(&t[L[p]], (unsigned long long)c);
+        }
+        if (lane == 0 && vtot) atomicAdd(&t[v], vtot);
+        __syncwarp();
     }
 }
 
@@ -746,6 +873,15 @@ void launch_plan(const CountBuffers& C, const Strategy& S, const Launch& L) {
         k_hub_scatter<<<grid_for((int64_t)C.n * 32, THREADS, L.sms), THREADS, 0, L.stream>>>(
             C.n, C.hub_cap, C.rowstart, C.rowlen, C.col, C.hub_start, C.hub_cur, C.in_u, C.in_b, C.in_e, C.stats);
         count_launch();
+        // hub_cur is free again: it holds the big flags, hub_cnt (still the in-degrees
+        // until here) is overwritten by their exclusive scan
+        k_hub_flags<<<grid_for(C.hub_cap, THREADS, L.sms), THREADS, 0, L.stream>>>(C.n, C.rowlen, C.hub_cnt,
+                                                                                  C.hub_cap, C.hub_cur, C.stats);
+        count_launch();
+        scan_u32_to_u32(C.hub_cur, C.hub_cnt, C.hub_cap, C.tmp, L);
+        k_hub_lists<<<grid_for(C.hub_cap, THREADS, L.sms), THREADS, 0, L.stream>>>(C.n, C.hub_cur, C.hub_cnt,
+                                                                                  C.big_list, C.med_list, C.stats);
+        count_launch();
     }
     k_plan<<<grid_for(C.n, THREADS, L.sms), THREADS, 0, L.stream>>>(C.n, C.rowstart, C.rowlen, C.col,
                                                                    C.small_list[0], C.small_list[1],
@@ -781,10 +917,10 @@ void launch_intersect(const CountBuffers& C, const Strategy& S, cudaEvent_t* ev,
     count_launch();
     if (ev) cudaEventRecord(ev[PH_HUB], L.stream);
     if (C.hub_cap > 0) {
-        cudaMemsetAsync(&C.stats->hub_next, 0, sizeof(unsigned), L.stream);
-        k_tc_hub<<<L.sms * 4, HUB_THREADS, sizeof(HubShared), L.stream>>>(
-            C.n, C.hub_cap, C.rowstart, C.rowlen, C.col, C.hub_start, C.in_u, C.in_b, C.in_e, C.t_rank, C.stats,
-            S.strat[TC_BUCKET_HUB] == TC_STRAT_PROBE ? 1 : 0);
+        cudaMemsetAsync(&C.stats->hub_next, 0, 2 * sizeof(unsigned), L.stream);
+        k_tc_hub<<<L.sms * 5, HUB_THREADS, sizeof(HubShared), L.stream>>>(
+            C.n, C.hub_cap, C.rowstart, C.rowlen, C.col, C.hub_start, C.big_list, C.med_list, C.in_u, C.in_b, C.in_e,
+            C.t_rank, C.stats, S.strat[TC_BUCKET_HUB] == TC_STRAT_PROBE ? 1 : 0);
         count_launch();
     }
     if (ev) cudaEventRecord(ev[PH_END], L.stream);
