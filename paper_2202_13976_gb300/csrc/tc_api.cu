@@ -88,6 +88,7 @@ struct tc_graph {
     int32_t* rank = nullptr;
     int64_t* rowstart = nullptr;
     int32_t* rowlen = nullptr;
+    int2* rowinfo = nullptr;
     int32_t* col = nullptr;
     int32_t* deg = nullptr;
     int32_t* small_list[3] = {nullptr, nullptr, nullptr};
@@ -196,6 +197,7 @@ tc_status build_graph(tc_graph* g, const int32_t* src, const int32_t* dst, int64
     const size_t hc = (size_t)g->hub_cap;
     if ((st = dalloc(g, &g->stats, 1, &keep)) || (st = dalloc(g, &g->rank, nn, &keep)) ||
         (st = dalloc(g, &g->rowstart, nn + 1, &keep)) || (st = dalloc(g, &g->rowlen, nn, &keep)) ||
+        (st = dalloc(g, &g->rowinfo, nn, &keep)) ||
         (st = dalloc(g, &g->col, (size_t)m, &keep)) || (st = dalloc(g, &g->deg, nn, &keep)) ||
         (st = dalloc(g, &g->small_list[0], nn, &keep)) || (st = dalloc(g, &g->small_list[1], nn, &keep)) ||
         (st = dalloc(g, &g->small_list[2], nn, &keep)) || (st = dalloc(g, &g->cta_list, nn, &keep)) ||
@@ -219,6 +221,7 @@ tc_status build_graph(tc_graph* g, const int32_t* src, const int32_t* dst, int64
     if ((st = dalloc(g, &B.dmulti, nn, &scratch)) || (st = dalloc(g, &B.keys, nn, &scratch)) ||
         (st = dalloc(g, &B.keys_alt, nn, &scratch)) || (st = dalloc(g, &B.rowcnt, nn + 1, &scratch)) ||
         (st = dalloc(g, &B.cursor, nn, &scratch)) || (st = dalloc(g, &B.longlist, nn, &scratch)) ||
+        (st = dalloc(g, &B.midlist, nn, &scratch)) ||
         (st = dalloc(g, &tmp, tmp_bytes, &scratch))) {
         free_list(g, &scratch);
         return st;
@@ -227,6 +230,7 @@ tc_status build_graph(tc_graph* g, const int32_t* src, const int32_t* dst, int64
     B.rank = g->rank;
     B.rowstart = g->rowstart;
     B.rowlen = g->rowlen;
+    B.rowinfo = g->rowinfo;
     B.col = g->col;
     B.deg = g->deg;
     B.stats = g->stats;
@@ -256,6 +260,7 @@ CountBuffers count_buffers(tc_graph* g) {
     C.n = g->n;
     C.rowstart = g->rowstart;
     C.rowlen = g->rowlen;
+    C.rowinfo = g->rowinfo;
     C.col = g->col;
     C.deg = g->deg;
     for (int i = 0; i < 3; ++i) C.small_list[i] = g->small_list[i];

@@ -63,18 +63,27 @@ __global__ void k_canon_degree(const int32_t* __restrict__ src, const int32_t* _
     unsigned long long loops = 0;
     int err = 0;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += stride) {
-        int32_t u = src[i], v = dst[i];
-        if ((uint32_t)u >= (uint32_t)n || (uint32_t)v >= (uint32_t)n) {
-            err = ERR_BAD_ID;
-            continue;
+    const int lane = lane_id();
+    // warp-uniform loop: lanes of a warp that name the same vertex add their counts
+    // with one atomic (hub degrees collect most increments)
+    for (int64_t b = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); b < m; b += stride) {
+        const int64_t i = b + lane;
+        int32_t u = -1 - lane, v = -33 - lane;  // private values for lanes without a pair
+        if (i < m) {
+            const int32_t a = src[i], c = dst[i];
+            if ((uint32_t)a >= (uint32_t)n || (uint32_t)c >= (uint32_t)n) {
+                err = ERR_BAD_ID;
+            } else if (a == c) {
+                ++loops;
+            } else {
+                u = a;
+                v = c;
+            }
         }
-        if (u == v) {
-            ++loops;
-            continue;
-        }
-        atomicAdd(&dmulti[u], 1u);
-        atomicAdd(&dmulti[v], 1u);
+        const unsigned pu = __match_any_sync(FULL, u);
+        const unsigned pv = __match_any_sync(FULL, v);
+        if (u >= 0 && lane == __ffs(pu) - 1) atomicAdd(&dmulti[u], (uint32_t)__popc(pu));
+        if (v >= 0 && lane == __ffs(pv) - 1) atomicAdd(&dmulti[v], (uint32_t)__popc(pv));
     }
     loops = warp_sum(loops);
     err = __reduce_or_sync(FULL, err);
@@ -207,37 +216,99 @@ __device__ void bitonic_sort_global(int32_t* s, int len, int me, int lanes) {
     }
 }
 
-// One warp per row.  Rows longer than WARP_SORT_MAX are left to k_segsort_block.
-__global__ void __launch_bounds__(SEG_WARPS * 32) k_segsort_warp(int32_t n, const int64_t* __restrict__ rowstart,
+// Sorting network on N registers (bitonic, all indices known at compile time).
+template <int N>
+__device__ __forceinline__ void reg_bitonic(int32_t (&v)[N]) {
+#pragma unroll
+    for (int k = 2; k <= N; k <<= 1) {
+#pragma unroll
+        for (int j = k >> 1; j > 0; j >>= 1) {
+#pragma unroll
+            for (int i = 0; i < N; ++i) {
+                const int l = i ^ j;
+                if (l > i) {
+                    const int32_t a = v[i], b = v[l];
+                    if ((i & k) == 0) {
+                        v[i] = min(a, b);
+                        v[l] = max(a, b);
+                    } else {
+                        v[i] = max(a, b);
+                        v[l] = min(a, b);
+                    }
+                }
+            }
+        }
+    }
+}
+
+// Sorts a row of len <= N entries in registers, writes the distinct entries back
+// to its start and counts each kept entry at its target; returns how many were kept.
+template <int N>
+__device__ __forceinline__ int sort_row_regs(int32_t* __restrict__ row, int len, int32_t* __restrict__ deg) {
+    int32_t v[N];
+#pragma unroll
+    for (int i = 0; i < N; ++i) v[i] = i < len ? row[i] : INT_MAX;
+    reg_bitonic<N>(v);
+    int kept = 0;
+    int32_t prev = INT_MIN;
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+        if (i < len && v[i] != prev) {
+            row[kept++] = v[i];
+            atomicAdd(&deg[v[i]], 1);
+        }
+        prev = v[i];
+    }
+    return kept;
+}
+
+// One thread per row for rows of at most 16 entries; longer rows are listed for the
+// warp sorter (<= WARP_SORT_MAX) or the block sorter.
+__global__ void __launch_bounds__(256) k_segsort_thread(int32_t n, const int64_t* __restrict__ rowstart,
+                                                        const uint32_t* __restrict__ rowcnt, int32_t* __restrict__ col,
+                                                        int32_t* __restrict__ rowlen, int2* __restrict__ rowinfo,
+                                                        int32_t* __restrict__ deg, int32_t* __restrict__ midlist,
+                                                        int32_t* __restrict__ longlist, DevStats* stats) {
+    unsigned long long kept_total = 0;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    // the loop bound is uniform across a warp, as warp_append needs all 32 lanes
+    for (int64_t b = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); b < n; b += stride) {
+        const int64_t r = b + lane_id();
+        const int len = r < n ? (int)rowcnt[r] : 0;
+        const bool mid = len > 16 && len <= WARP_SORT_MAX, lng = len > WARP_SORT_MAX;
+        const unsigned pm = warp_append(mid, &stats->mid_count);
+        const unsigned pl = warp_append(lng, &stats->long_count);
+        if (mid) midlist[pm] = (int32_t)r;
+        if (lng) longlist[pl] = (int32_t)r;
+        if (r < n && len <= 16) {
+            const int64_t base = rowstart[r];
+            const int kept = len <= 8 ? sort_row_regs<8>(col + base, len, deg) : sort_row_regs<16>(col + base, len, deg);
+            rowlen[r] = kept;
+            rowinfo[r] = make_int2((int)base, kept);
+            if (kept) atomicAdd(&deg[r], kept);
+            kept_total += (unsigned long long)kept;
+        }
+    }
+    kept_total = warp_sum(kept_total);
+    if (lane_id() == 0 && kept_total) atomicAdd(&stats->m_simple, kept_total);
+}
+
+// One warp per listed row (17 .. WARP_SORT_MAX entries): bitonic network in shared memory.
+__global__ void __launch_bounds__(SEG_WARPS * 32) k_segsort_warp(const int64_t* __restrict__ rowstart,
                                                                  const uint32_t* __restrict__ rowcnt,
                                                                  int32_t* __restrict__ col, int32_t* __restrict__ rowlen,
-                                                                 int32_t* __restrict__ deg, int32_t* __restrict__ longlist,
-                                                                 DevStats* stats) {
+                                                                 int2* __restrict__ rowinfo, int32_t* __restrict__ deg,
+                                                                 const int32_t* __restrict__ midlist, DevStats* stats) {
     __shared__ int32_t sh[SEG_WARPS][WARP_SORT_MAX];
     const int lane = lane_id(), w = threadIdx.x >> 5;
     int32_t* s = sh[w];
-    const int64_t warps = (int64_t)gridDim.x * SEG_WARPS;
+    const unsigned nmid = stats->mid_count;
+    const unsigned warps = gridDim.x * SEG_WARPS;
     unsigned long long kept_total = 0;
-    for (int64_t r = (int64_t)blockIdx.x * SEG_WARPS + w; r < n; r += warps) {
+    for (unsigned q = blockIdx.x * SEG_WARPS + w; q < nmid; q += warps) {
+        const int32_t r = midlist[q];
         const int len = (int)rowcnt[r];
         const int64_t base = rowstart[r];
-        if (len == 0) {
-            if (lane == 0) rowlen[r] = 0;
-            continue;
-        }
-        if (len == 1) {
-            if (lane == 0) {
-                rowlen[r] = 1;
-                atomicAdd(&deg[col[base]], 1);
-                atomicAdd(&deg[r], 1);
-                kept_total += 1;
-            }
-            continue;
-        }
-        if (len > WARP_SORT_MAX) {
-            if (lane == 0) longlist[atomicAdd(&stats->long_count, 1u)] = (int32_t)r;
-            continue;
-        }
         const int P = max(32, next_pow2_int(len));
         for (int i = lane; i < P; i += 32) s[i] = i < len ? col[base + i] : INT_MAX;
         __syncwarp();
@@ -255,6 +326,7 @@ __global__ void __launch_bounds__(SEG_WARPS * 32) k_segsort_warp(int32_t n, cons
         }
         if (lane == 0) {
             rowlen[r] = kept;
+            rowinfo[r] = make_int2((int)base, kept);
             atomicAdd(&deg[r], kept);
             kept_total += (unsigned long long)kept;
         }
@@ -268,7 +340,7 @@ __global__ void __launch_bounds__(SEG_WARPS * 32) k_segsort_warp(int32_t n, cons
 __global__ void __launch_bounds__(1024) k_segsort_block(const int64_t* __restrict__ rowstart,
                                                         const uint32_t* __restrict__ rowcnt,
                                                         int32_t* __restrict__ col, int32_t* __restrict__ rowlen,
-                                                        int32_t* __restrict__ deg,
+                                                        int2* __restrict__ rowinfo, int32_t* __restrict__ deg,
                                                         const int32_t* __restrict__ longlist,
                                                         DevStats* stats) {
     extern __shared__ int32_t sh[];  // CTA_SORT_MAX entries
@@ -321,6 +393,7 @@ __global__ void __launch_bounds__(1024) k_segsort_block(const int64_t* __restric
         }
         if (threadIdx.x == 0) {
             rowlen[r] = kept;
+            rowinfo[r] = make_int2((int)base, kept);
             atomicAdd(&deg[r], kept);
             atomicAdd(&stats->m_simple, (unsigned long long)kept);
         }
@@ -366,10 +439,15 @@ void launch_orient(const BuildBuffers& B, const Launch& L) {
     if (B.m > 0) {
         k_orient_scatter<<<grid_for(B.m, THREADS, L.sms), THREADS, 0, L.stream>>>(
             B.src, B.dst, B.m, B.rank, B.rowstart, B.cursor, B.col); count_launch(); }
-    k_segsort_warp<<<grid_for((int64_t)B.n * 32, SEG_WARPS * 32, L.sms, 4), SEG_WARPS * 32, 0, L.stream>>>(
-        B.n, B.rowstart, B.rowcnt, B.col, B.rowlen, B.deg, B.longlist, B.stats); count_launch();
+    k_segsort_thread<<<grid_for(B.n, THREADS, L.sms), THREADS, 0, L.stream>>>(
+        B.n, B.rowstart, B.rowcnt, B.col, B.rowlen, B.rowinfo, B.deg, B.midlist, B.longlist, B.stats);
+    count_launch();
+    k_segsort_warp<<<L.sms * 4, SEG_WARPS * 32, 0, L.stream>>>(B.rowstart, B.rowcnt, B.col, B.rowlen, B.rowinfo,
+                                                              B.deg, B.midlist, B.stats);
+    count_launch();
     k_segsort_block<<<L.sms * 2, 1024, CTA_SORT_MAX * sizeof(int32_t), L.stream>>>(
-        B.rowstart, B.rowcnt, B.col, B.rowlen, B.deg, B.longlist, B.stats); count_launch();
+        B.rowstart, B.rowcnt, B.col, B.rowlen, B.rowinfo, B.deg, B.longlist, B.stats);
+    count_launch();
 }
 
 // 64 KB of dynamic shared memory for the block sorter.

@@ -31,7 +31,8 @@ struct DevStats {
     unsigned int hub_next2;        // dynamic work counter of the hub kernel (medium hubs)
     unsigned int hub_candidates;   // vertices whose degree reaches the hub threshold
     unsigned int hub_big;          // hubs processed by whole blocks
-    unsigned int pad[3];
+    unsigned int mid_count;        // build: rows sorted by one warp
+    unsigned int pad[2];
 };
 static_assert(sizeof(DevStats) == 88, "DevStats layout");
 
@@ -69,11 +70,13 @@ struct BuildBuffers {
     uint32_t* rowcnt;     // n + 1
     uint32_t* cursor;     // n
     int32_t* longlist;    // n
+    int32_t* midlist;     // n
     void* tmp;            // max(scan_tmp_bytes(n + 1), radix_tmp_bytes(n))
     // outputs (kept by the graph)
     int32_t* rank;        // n: rank of each input id in (degree, id) order
     int64_t* rowstart;    // n + 1 (rank space)
     int32_t* rowlen;      // n: oriented out-degree after deduplication
+    int2* rowinfo;        // n: {first index in col, rowlen} (rank space)
     int32_t* col;         // m: oriented adjacency (rank space), rows sorted
     int32_t* deg;         // n: simple-graph degree (rank space)
     DevStats* stats;
@@ -105,6 +108,7 @@ struct CountBuffers {
     int32_t n;
     const int64_t* rowstart;
     const int32_t* rowlen;
+    const int2* rowinfo;     // {first index in col, length} per row
     const int32_t* col;
     const int32_t* deg;
     int32_t* small_list[3];  // n each

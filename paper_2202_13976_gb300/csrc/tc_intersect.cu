@@ -253,6 +253,30 @@ __device__ uint32_t lane_merge(const int32_t* Lu, int a0, int du, const int32_t*
     return c;
 }
 
+// Merge with B read eight entries at a time (independent loads), A in shared memory.
+__device__ uint32_t lane_merge_batched(const int32_t* Lu, int a0, int du, const int32_t* __restrict__ B, int b,
+                                       uint32_t* cnt) {
+    uint32_t c = 0;
+    int i = a0;
+    const int32_t mx = Lu[du - 1];
+    for (int k0 = 0; k0 < b && i < du; k0 += 8) {
+        int32_t y[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) y[q] = k0 + q < b ? B[k0 + q] : INT_MAX;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            while (i < du && Lu[i] < y[q]) ++i;
+            if (i < du && Lu[i] == y[q]) {
+                atomicAdd(&cnt[i], 1u);
+                ++c;
+                ++i;
+            }
+        }
+        if (y[7] >= mx) break;
+    }
+    return c;
+}
+
 // keys of A looked up in B
 __device__ uint32_t lane_search(const int32_t* Lu, int a0, int du, const int32_t* __restrict__ B, int b,
                                 uint32_t* cnt) {
@@ -402,6 +426,7 @@ __global__ void k_plan(int32_t n, const int64_t* __restrict__ rowstart, const in
 template <int G>
 __global__ void __launch_bounds__(SMALL_WARPS * 32) k_tc_small(int32_t n, const int64_t* __restrict__ rowstart,
                                                                const int32_t* __restrict__ rowlen,
+                                                               const int2* __restrict__ rowinfo,
                                                                const int32_t* __restrict__ col,
                                                                const int32_t* __restrict__ list, int cls,
                                                                unsigned long long* __restrict__ t, DevStats* stats,
@@ -427,15 +452,16 @@ __global__ void __launch_bounds__(SMALL_WARPS * 32) k_tc_small(int32_t n, const 
         uint32_t c = 0;
         if (g < du - 1) {
             const int32_t v = Lu[g];
-            const int dv = v < R ? rowlen[v] : 0;
+            const int2 ri = v < R ? rowinfo[v] : make_int2(0, 0);
+            const int dv = ri.y;
             if (dv > 0) {
-                const int32_t* B = col + rowstart[v];
+                const int32_t* B = col + ri.x;
                 const int a = du - g - 1;
                 int method = strategy;
                 if (method == TC_STRAT_AUTO)
-                    method = eq3_prefers_merge(a, dv, factor) ? TC_STRAT_MERGE : TC_STRAT_SEARCH;
+                    method = eq3_prefers_merge(a, dv, factor) || dv < a ? TC_STRAT_MERGE : TC_STRAT_SEARCH;
                 if (method == TC_STRAT_MERGE)
-                    c = lane_merge(Lu, g + 1, du, B, dv, cnt);
+                    c = lane_merge_batched(Lu, g + 1, du, B, dv, cnt);
                 else
                     c = a <= dv ? lane_search(Lu, g + 1, du, B, dv, cnt) : lane_search_rev(Lu, g + 1, du, B, dv, cnt);
                 if (c) atomicAdd(&cnt[g], c);
@@ -465,6 +491,7 @@ struct CtaShared {
 
 __global__ void __launch_bounds__(CTA_THREADS) k_tc_cta(int32_t n, const int64_t* __restrict__ rowstart,
                                                         const int32_t* __restrict__ rowlen,
+                                                        const int2* __restrict__ rowinfo,
                                                         const int32_t* __restrict__ col,
                                                         const int32_t* __restrict__ list,
                                                         unsigned long long* __restrict__ t,
@@ -500,9 +527,10 @@ __global__ void __launch_bounds__(CTA_THREADS) k_tc_cta(int32_t n, const int64_t
         unsigned long long utot = 0;
         for (int j = w; j < jh; j += CTA_WARPS) {
             const int32_t v = Lu[j];
-            const int dv = rowlen[v];
+            const int2 ri = rowinfo[v];
+            const int dv = ri.y;
             if (dv == 0) continue;
-            const int32_t* B = col + rowstart[v];
+            const int32_t* B = col + ri.x;
             uint32_t c;
             if (bitmap) {
                 c = edge_bitmap(sh.bm, sh.pre, u, maxu, sh.cnt, B, dv);
@@ -900,18 +928,19 @@ void launch_intersect(const CountBuffers& C, const Strategy& S, cudaEvent_t* ev,
     if (ev) cudaEventRecord(ev[PH_SMALL], L.stream);
     const int ss = S.strat[TC_BUCKET_SMALL];
     const float sf = S.factor[TC_BUCKET_SMALL];
-    k_tc_small<8><<<L.sms * 8, SMALL_WARPS * 32, 0, L.stream>>>(C.n, C.rowstart, C.rowlen, C.col, C.small_list[0],
+    k_tc_small<8><<<L.sms * 8, SMALL_WARPS * 32, 0, L.stream>>>(C.n, C.rowstart, C.rowlen, C.rowinfo, C.col, C.small_list[0],
                                                                0, C.t_rank, C.stats, ss, sf);
     count_launch();
-    k_tc_small<16><<<L.sms * 8, SMALL_WARPS * 32, 0, L.stream>>>(C.n, C.rowstart, C.rowlen, C.col, C.small_list[1],
+    k_tc_small<16><<<L.sms * 8, SMALL_WARPS * 32, 0, L.stream>>>(C.n, C.rowstart, C.rowlen, C.rowinfo, C.col, C.small_list[1],
                                                                 1, C.t_rank, C.stats, ss, sf);
     count_launch();
-    k_tc_small<32><<<L.sms * 8, SMALL_WARPS * 32, 0, L.stream>>>(C.n, C.rowstart, C.rowlen, C.col, C.small_list[2],
+    k_tc_small<32><<<L.sms * 8, SMALL_WARPS * 32, 0, L.stream>>>(C.n, C.rowstart, C.rowlen, C.rowinfo, C.col, C.small_list[2],
                                                                 2, C.t_rank, C.stats, ss, sf);
     count_launch();
     if (ev) cudaEventRecord(ev[PH_CTA], L.stream);
     cudaMemsetAsync(&C.stats->cta_next, 0, sizeof(unsigned), L.stream);
-    k_tc_cta<<<L.sms * 4, CTA_THREADS, sizeof(CtaShared), L.stream>>>(C.n, C.rowstart, C.rowlen, C.col, C.cta_list,
+    k_tc_cta<<<L.sms * 4, CTA_THREADS, sizeof(CtaShared), L.stream>>>(C.n, C.rowstart, C.rowlen, C.rowinfo, C.col,
+                                                                     C.cta_list,
                                                                      C.t_rank, C.stats, S.strat[TC_BUCKET_CTA],
                                                                      S.factor[TC_BUCKET_CTA]);
     count_launch();
