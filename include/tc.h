@@ -198,6 +198,38 @@ tc_status tc_graph_last_timing(const tc_graph* g, float* ms, int count);
  */
 tc_status tc_graph_plan_stats(tc_graph* g, int64_t* edges, int64_t* ids);
 
+/*
+ * Count without allocating (an addition of this library; the paper has no
+ * counterpart).  For callers that cannot allocate device memory while they run: a
+ * program that has handed all free HBM to its own caching allocator, code being
+ * recorded into a CUDA stream capture (where cudaMalloc is not allowed), or
+ * real-time code that forbids allocation after start-up.
+ *
+ * Computes the same T, t[] and LCC[] as tc_graph_create_from_edges + tc_count +
+ * lcc_compute for a small graph, in one kernel launch whose intermediate arrays
+ * live in a fixed device array of TC_NOALLOC_SCRATCH_BYTES bytes inside the
+ * library.  Every GPU that loads the library holds that array until the process
+ * exits.  The call itself allocates nothing and calls no allocating routine.
+ *   n, m        0 <= n <= TC_NOALLOC_MAX_N, 0 <= m <= TC_NOALLOC_MAX_M
+ *   src, dst    m int32 ids each, DEVICE memory (may be NULL when m == 0)
+ *   T_out       host scalar, receives T
+ *   t_out       n uint64 in device memory, or NULL
+ *   lcc_out     n fp64 in device memory, or NULL
+ *   cuda_stream a cudaStream_t (as void*), or NULL; the call synchronises it
+ * The first call on a device looks up the device address of the array (once per
+ * device, with that device current); make that first call before any stream
+ * capture begins.  All calls share the array and it keeps the previous call's
+ * contents (the kernel clears what it needs): calls whose work overlaps on the GPU
+ * (other streams or host threads) race on it and must be ordered by the caller.
+ * Errors: TC_EINVAL for sizes beyond the limits, NULL pointers or an id outside
+ * [0, n); TC_ECUDA; TC_EINTERNAL.
+ */
+#define TC_NOALLOC_MAX_N 16384
+#define TC_NOALLOC_MAX_M 262144
+#define TC_NOALLOC_SCRATCH_BYTES 3735688
+tc_status tc_count_noalloc(int32_t n, int64_t m, const int32_t* src, const int32_t* dst, uint64_t* T_out,
+                           uint64_t* t_out, double* lcc_out, void* cuda_stream);
+
 /* Number of kernels this library has launched in the process so far (all devices). */
 uint64_t tc_launch_count(void);
 

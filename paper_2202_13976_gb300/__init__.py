@@ -28,7 +28,8 @@ STRATEGIES = {"auto": TC_STRAT_AUTO, "merge": TC_STRAT_MERGE, "search": TC_STRAT
 EXPORTS = ["tc_graph_create_from_edges", "tc_graph_create_from_csr", "tc_count", "lcc_compute",
            "tc_graph_info", "tc_graph_size", "tc_graph_destroy", "tc_status_str",
            "tc_last_error_detail", "tc_graph_set_strategy", "tc_graph_last_timing",
-           "tc_graph_plan_stats", "tc_launch_count", "tc_graph_set_hubs"]
+           "tc_graph_plan_stats", "tc_launch_count", "tc_graph_set_hubs", "tc_count_noalloc"]
+TC_NOALLOC_MAX_N, TC_NOALLOC_MAX_M = 16384, 262144
 
 _lib = None
 
@@ -86,6 +87,8 @@ def load(path: str | None = None):
     lib.tc_graph_plan_stats.argtypes = [P, ctypes.POINTER(i64), ctypes.POINTER(i64)]
     lib.tc_launch_count.restype = u64
     lib.tc_launch_count.argtypes = []
+    lib.tc_count_noalloc.restype = st
+    lib.tc_count_noalloc.argtypes = [i32, i64, P, P, ctypes.POINTER(u64), P, P, P]
     _lib = lib
     return lib
 
@@ -219,6 +222,21 @@ def tc_graph_plan_stats(g: int) -> dict:
     _check(_lib.tc_graph_plan_stats(g, e, i))
     names = ["small", "cta", "hub", "trivial"]
     return {names[b]: {"edges": e[b], "ids": i[b]} for b in range(nb)}
+
+
+def tc_count_noalloc(n: int, src, dst, t_out=None, lcc_out=None, stream=None) -> int:
+    """T of a small graph without any allocation by the library (CUDA tensors only);
+    fills t_out (int64/uint64 [n]) and lcc_out (float64 [n]) when given."""
+    load()
+    for a in (src, dst, t_out, lcc_out):
+        if a is not None and not _is_device(a):
+            raise ValueError("tc_count_noalloc takes device buffers")
+    _check_dtype(src, "int32")
+    _check_dtype(dst, "int32")
+    (ps, pd, pt, pl), _ = _ptr_kind(src, dst, t_out, lcc_out)
+    T = ctypes.c_uint64()
+    _check(_lib.tc_count_noalloc(n, len(src), ps, pd, ctypes.byref(T), pt, pl, _stream_ptr(stream)))
+    return int(T.value)
 
 
 def tc_launch_count() -> int:
