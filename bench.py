@@ -53,6 +53,9 @@ def parse_args():
     p.add_argument("--workload", default="rmat20", choices=sorted(WORKLOAD_TEXT))
     p.add_argument("--e2e-steps", type=int, default=10)
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--mode", choices=["single", "batch"], default="single",
+                   help="single: one graph per step; batch: the 20,000-graph batch per step")
+    p.add_argument("--batch-graphs", type=int, default=20000)
     p.add_argument("--strategy", default=None,
                    help="override as small:name[:factor],cta:name[:factor],hub:name,hubs:mindeg:max")
     return p.parse_args()
@@ -324,11 +327,133 @@ def run_ours(args, rank, world, local):
     print(json.dumps(line), flush=True)
 
 
+def gen_batch(G, seed=4):
+    """The batched workload (graphgen.batch_workloads), generated on the host cores."""
+    from concurrent.futures import ThreadPoolExecutor
+
+    import numpy as np
+
+    import graphgen
+    ws = graphgen.batch_workloads(G, seed=seed)
+    with ThreadPoolExecutor(max_workers=len(os.sched_getaffinity(0))) as ex:
+        edges = list(ex.map(lambda w: w.edges(), ws))
+    n = np.array([w.n for w in ws], dtype=np.int32)
+    off = np.zeros(G + 1, dtype=np.int64)
+    off[1:] = np.cumsum([len(e[0]) for e in edges])
+    src = np.concatenate([e[0] for e in edges]).astype(np.int32)
+    dst = np.concatenate([e[1] for e in edges]).astype(np.int32)
+    return n, off, src, dst
+
+
+def run_batch(args, rank, world, local):
+    """Batched workload: all graphs per step through the batch entry point, against
+    the plain per-graph path (one create/count/LCC/destroy per graph) on the same GPU."""
+    import numpy as np
+    import torch
+
+    import paper_2202_13976_gb300 as tc
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    tc.load()
+    t0 = time.perf_counter()
+    n, off, src_h, dst_h = gen_batch(args.batch_graphs)
+    gen_s = time.perf_counter() - t0
+    G = len(n)
+    nt = int(n.sum())
+    src = torch.from_numpy(src_h).to(dev)
+    dst = torch.from_numpy(dst_h).to(dev)
+    t_out = torch.empty(nt, dtype=torch.int64, device=dev)
+    l_out = torch.empty(nt, dtype=torch.float64, device=dev)
+    T_dev = torch.empty(G, dtype=torch.int64, device=dev)
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def batched():
+        g = tc.Graph.batch(n, off, src, dst, stream)
+        try:
+            apply_strategy(g, args.strategy, tc)
+            g.batch_count(T_dev)
+            g.lcc(t_out, l_out)
+            m_simple = g.info()["m_simple"]
+        finally:
+            g.close()
+        return m_simple
+
+    for _ in range(max(args.warmup, 3)):
+        m_simple = batched()
+    torch.cuda.synchronize()
+    launches0 = tc.tc_launch_count()
+    clocks = Clocks(local)
+    ms = []
+    for _ in range(args.steps):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        batched()
+        b.record(stream)
+        b.synchronize()
+        ms.append(a.elapsed_time(b))
+    clk = clocks.stop()
+    launches = tc.tc_launch_count() - launches0
+    T_batch = T_dev.cpu().numpy().view(np.uint64).copy()
+    ms_batch = sum(ms) / len(ms)
+
+    # plain per-graph path on the same device arrays (one pass, after one warm pass)
+    vb = np.zeros(G + 1, dtype=np.int64)
+    vb[1:] = np.cumsum(n)
+
+    def per_graph():
+        Ts = np.empty(G, dtype=np.uint64)
+        for i in range(G):
+            a, b = int(off[i]), int(off[i + 1])
+            g = tc.Graph.from_edges(int(n[i]), src[a:b], dst[a:b], stream)
+            Ts[i] = g.count()
+            g.lcc(t_out[vb[i]:vb[i + 1]], l_out[vb[i]:vb[i + 1]])
+            g.close()
+        return Ts
+
+    per_graph()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    T_plain = per_graph()
+    torch.cuda.synchronize()
+    plain_s = time.perf_counter() - t0
+    if rank != 0:
+        return
+    line = {"metric": "batched graphs/sec", "value": world * G / (ms_batch / 1000.0), "unit": "graphs/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_batch,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+            "data": "synthetic",
+            "config": {"workload": f"batch of {G} graphs (n log-uniform [32, 65536], avg degree U(4, 32), "
+                                   "R-MAT/ER alternating, seed 4)", "graphs": G, "vertices": nt,
+                       "pairs": int(off[-1]), "m_simple": m_simple, "generation_s": gen_s,
+                       "l2": "flushed between steps (512 MB write)", "strategy": args.strategy or "default"},
+            "batched_edges_per_s": m_simple / (ms_batch / 1000.0),
+            "per_graph_path": {"graphs_per_s": G / plain_s, "edges_per_s": m_simple / plain_s, "s": plain_s},
+            "speedup_vs_per_graph": plain_s / (ms_batch / 1000.0),
+            "identical_T": bool((T_batch == T_plain).all()),
+            "gpu_launches": launches, "clocks": clk, "impl": "ours"}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse_args()
     rank, world, local = dist_env()
     if args.impl == "reference":
         run_reference(args, rank, world)
+        return
+    if args.mode == "batch":
+        if world > 1:
+            import torch
+            import torch.distributed as dist
+            torch.cuda.set_device(local)
+            dist.init_process_group("nccl")
+        try:
+            run_batch(args, rank, world, local)
+        finally:
+            if world > 1:
+                import torch.distributed as dist
+                dist.destroy_process_group()
         return
     if world > 1:
         import torch

@@ -199,6 +199,31 @@ tc_status tc_graph_last_timing(const tc_graph* g, float* ms, int count);
 tc_status tc_graph_plan_stats(tc_graph* g, int64_t* edges, int64_t* ids);
 
 /*
+ * Batches: G independent graphs in one object (north-star pattern "batching";
+ * the paper has no counterpart).  Graph g has n[g] vertices with local ids
+ * [0, n[g]) and the pairs src/dst[edge_off[g] .. edge_off[g+1]).  The batch is
+ * counted as one disjoint union: vertex (g, i) becomes union id vbase[g] + i with
+ * vbase[g] = n[0] + ... + n[g-1].  t[] and LCC[] from lcc_compute on a batch are
+ * indexed by union id (graph after graph); T per graph comes from tc_batch_count.
+ *   G           number of graphs (>= 0)
+ *   n, edge_off HOST arrays of G and G + 1 entries; edge_off[0] == 0, non-decreasing;
+ *               sum of n and edge_off[G] at most 2^31 - 1
+ *   src, dst    edge_off[G] int32 local ids each, in mem_kind memory
+ * Ids outside [0, n[g]) are reported by tc_batch_count (TC_EINVAL); creation
+ * itself does not wait for the device after copying the host arrays.
+ */
+tc_status tc_batch_create(int32_t G, const int32_t* n, const int64_t* edge_off, const int32_t* src,
+                          const int32_t* dst, int mem_kind, void* cuda_stream, tc_graph** out);
+
+/* T of every graph of a batch: T_out[G] (uint64) in mem_kind memory.  Runs the
+   count if needed; synchronises the stream.  Errors: TC_EINVAL (not a batch, NULL,
+   an id outside its graph), TC_ECUDA, TC_EINTERNAL. */
+tc_status tc_batch_count(tc_graph* g, uint64_t* T_out, int mem_kind);
+
+/* Number of graphs of a batch (TC_EINVAL for a single graph). */
+tc_status tc_batch_size(const tc_graph* g, int32_t* G);
+
+/*
  * Count without allocating (an addition of this library; the paper has no
  * counterpart).  For callers that cannot allocate device memory while they run: a
  * program that has handed all free HBM to its own caching allocator, code being

@@ -28,7 +28,8 @@ STRATEGIES = {"auto": TC_STRAT_AUTO, "merge": TC_STRAT_MERGE, "search": TC_STRAT
 EXPORTS = ["tc_graph_create_from_edges", "tc_graph_create_from_csr", "tc_count", "lcc_compute",
            "tc_graph_info", "tc_graph_size", "tc_graph_destroy", "tc_status_str",
            "tc_last_error_detail", "tc_graph_set_strategy", "tc_graph_last_timing",
-           "tc_graph_plan_stats", "tc_launch_count", "tc_graph_set_hubs", "tc_count_noalloc"]
+           "tc_graph_plan_stats", "tc_launch_count", "tc_graph_set_hubs", "tc_count_noalloc",
+           "tc_batch_create", "tc_batch_count", "tc_batch_size"]
 TC_NOALLOC_MAX_N, TC_NOALLOC_MAX_M = 16384, 262144
 
 _lib = None
@@ -87,6 +88,12 @@ def load(path: str | None = None):
     lib.tc_graph_plan_stats.argtypes = [P, ctypes.POINTER(i64), ctypes.POINTER(i64)]
     lib.tc_launch_count.restype = u64
     lib.tc_launch_count.argtypes = []
+    lib.tc_batch_create.restype = st
+    lib.tc_batch_create.argtypes = [i32, P, P, P, P, ctypes.c_int, P, ctypes.POINTER(P)]
+    lib.tc_batch_count.restype = st
+    lib.tc_batch_count.argtypes = [P, P, ctypes.c_int]
+    lib.tc_batch_size.restype = st
+    lib.tc_batch_size.argtypes = [P, ctypes.POINTER(i32)]
     lib.tc_count_noalloc.restype = st
     lib.tc_count_noalloc.argtypes = [i32, i64, P, P, ctypes.POINTER(u64), P, P, P]
     _lib = lib
@@ -239,6 +246,35 @@ def tc_count_noalloc(n: int, src, dst, t_out=None, lcc_out=None, stream=None) ->
     return int(T.value)
 
 
+def tc_batch_create(n, edge_off, src, dst, stream=None) -> int:
+    """Batch handle: n (int32[G]) and edge_off (int64[G+1]) on the host, src/dst int32
+    local ids (numpy on the host or CUDA tensors)."""
+    load()
+    n = np.ascontiguousarray(n, dtype=np.int32)
+    edge_off = np.ascontiguousarray(edge_off, dtype=np.int64)
+    if len(edge_off) != len(n) + 1:
+        raise ValueError("edge_off needs G + 1 entries")
+    _check_dtype(src, "int32")
+    _check_dtype(dst, "int32")
+    (ps, pd), kind = _ptr_kind(src, dst)
+    out = ctypes.c_void_p()
+    _check(_lib.tc_batch_create(len(n), n.ctypes.data, edge_off.ctypes.data, ps, pd, kind, _stream_ptr(stream),
+                                ctypes.byref(out)))
+    return out.value
+
+
+def tc_batch_count(g: int, T_out=None):
+    """Per-graph T into T_out (uint64/int64 [G], host or device); returns T_out."""
+    G = ctypes.c_int32()
+    _check(_lib.tc_batch_size(g, ctypes.byref(G)))
+    if T_out is None:
+        T_out = np.empty(G.value, dtype=np.uint64)
+    _check_dtype(T_out, "int64")
+    (pt,), kind = _ptr_kind(T_out)
+    _check(_lib.tc_batch_count(g, pt, kind))
+    return T_out
+
+
 def tc_launch_count() -> int:
     return int(load().tc_launch_count())
 
@@ -257,6 +293,13 @@ class Graph:
     @classmethod
     def from_csr(cls, n, offsets, adj, stream=None) -> "Graph":
         return cls(tc_graph_create_from_csr(n, offsets, adj, stream), n)
+
+    @classmethod
+    def batch(cls, n, edge_off, src, dst, stream=None) -> "Graph":
+        return cls(tc_batch_create(n, edge_off, src, dst, stream), int(np.sum(n, dtype=np.int64)))
+
+    def batch_count(self, T_out=None):
+        return tc_batch_count(self.handle, T_out)
 
     def count(self) -> int:
         return tc_count(self.handle)

@@ -111,6 +111,10 @@ struct tc_graph {
     Strategy strat{};
     cudaEvent_t ev[PH_EVENTS] = {};
     bool timed = false;
+    // batch of graphs counted as one disjoint union (tc_batch_create)
+    int32_t batch_G = -1;
+    int32_t* batch_vbase = nullptr;   // device, G + 1
+    int* batch_err = nullptr;         // device flag of the relabel and the per-graph reduction
 };
 
 namespace {
@@ -170,6 +174,7 @@ tc_status new_graph(int32_t n, void* stream, tc_graph** out) {
     g->strat.strat[TC_BUCKET_CTA] = TC_STRAT_BITMAP;
     g->strat.hub_min_degree = 32;
     g->strat.hub_max = HUB_BM_BITS;
+    g->strat.hub_big_in = 256;
     *out = g;
     return TC_OK;
 }
@@ -187,7 +192,11 @@ int bits_for(unsigned x) {
 }
 
 // Builds the oriented CSR from device-resident pairs (src, dst) of length m.
-tc_status build_graph(tc_graph* g, const int32_t* src, const int32_t* dst, int64_t m) {
+// checked: read the id check back before continuing (one stream synchronisation)
+// so that create can fail with TC_EINVAL; otherwise the build never waits on the
+// device (the radix sort takes its degree bits from the bound 2m) and invalid ids
+// are reported by the first call that reads the statistics.
+tc_status build_graph(tc_graph* g, const int32_t* src, const int32_t* dst, int64_t m, bool checked = true) {
     const int32_t n = g->n;
     const size_t nn = (size_t)n;
     tc_status st;
@@ -237,17 +246,21 @@ tc_status build_graph(tc_graph* g, const int32_t* src, const int32_t* dst, int64
     cudaMemsetAsync(g->stats, 0, sizeof(DevStats), g->stream);
     cudaMemsetAsync(B.dmulti, 0, sizeof(uint32_t) * nn, g->stream);
     launch_canon_degree(B, g->L);
-    DevStats h;
-    if ((st = read_stats(g, &h)) != TC_OK) {
-        free_list(g, &scratch);
-        return st;
+    int deg_bits = bits_for((unsigned)(2 * m < (int64_t)UINT32_MAX ? 2 * m : (int64_t)UINT32_MAX));
+    if (checked) {
+        DevStats h;
+        if ((st = read_stats(g, &h)) != TC_OK) {
+            free_list(g, &scratch);
+            return st;
+        }
+        if (h.err & ERR_BAD_ID) {
+            free_list(g, &scratch);
+            snprintf(g_last_error, sizeof(g_last_error), "vertex id outside [0, n)");
+            return TC_EINVAL;
+        }
+        deg_bits = bits_for(h.max_deg);
     }
-    if (h.err & ERR_BAD_ID) {
-        free_list(g, &scratch);
-        snprintf(g_last_error, sizeof(g_last_error), "vertex id outside [0, n)");
-        return TC_EINVAL;
-    }
-    launch_rank(B, bits_for(h.max_deg), g->L);
+    launch_rank(B, deg_bits, g->L);
     launch_orient(B, g->L);
     free_list(g, &scratch);
     cudaError_t e = cudaGetLastError();
@@ -582,5 +595,140 @@ tc_status tc_graph_plan_stats(tc_graph* g, int64_t* edges, int64_t* ids) {
 }
 
 uint64_t tc_launch_count(void) { return launch_total(); }
+
+// ---- batches ------------------------------------------------------------------
+
+static tc_status batch_host_checks(int32_t G, const int32_t* n, const int64_t* edge_off, int64_t* n_total,
+                                   int64_t* m) {
+    if (G < 0 || (G > 0 && (!n || !edge_off))) return TC_EINVAL;
+    int64_t tot = 0;
+    if (G > 0 && edge_off[0] != 0) return TC_EINVAL;
+    for (int32_t g = 0; g < G; ++g) {
+        if (n[g] < 0 || edge_off[g + 1] < edge_off[g]) return TC_EINVAL;
+        tot += n[g];
+    }
+    if (tot > INT_MAX) return TC_EINVAL;
+    *n_total = tot;
+    *m = G > 0 ? edge_off[G] : 0;
+    if (*m > INT_MAX) return TC_EINVAL;
+    return TC_OK;
+}
+
+// Device pipeline of a batch (no host synchronisation: capturable).
+static tc_status batch_build(tc_graph* g, int32_t G, const int32_t* vbase_dev, const int64_t* eoff_dev,
+                             const int32_t* src, const int32_t* dst, int64_t m) {
+    std::vector<void*> tmp;
+    int32_t *us = nullptr, *ud = nullptr;
+    tc_status st;
+    if ((st = dalloc(g, &us, (size_t)m, &tmp)) || (st = dalloc(g, &ud, (size_t)m, &tmp))) {
+        free_list(g, &tmp);
+        return st;
+    }
+    launch_batch_relabel(G, eoff_dev, vbase_dev, src, dst, us, ud, g->batch_err, g->L);
+    st = build_graph(g, us, ud, m, false);
+    free_list(g, &tmp);
+    return st;
+}
+
+extern "C" tc_status tc_batch_create(int32_t G, const int32_t* n, const int64_t* edge_off, const int32_t* src,
+                                     const int32_t* dst, int mem_kind, void* cuda_stream, tc_graph** out) {
+    if (!out) return TC_EINVAL;
+    *out = nullptr;
+    int64_t n_total = 0, m = 0;
+    tc_status st = batch_host_checks(G, n, edge_off, &n_total, &m);
+    if (st != TC_OK) return st;
+    if ((m > 0 && (!src || !dst)) || (mem_kind != TC_MEM_HOST && mem_kind != TC_MEM_DEVICE)) return TC_EINVAL;
+    tc_graph* g = nullptr;
+    if ((st = new_graph((int32_t)n_total, cuda_stream, &g)) != TC_OK) return st;
+    g->m_in = m;
+    g->batch_G = G;
+    std::vector<int32_t> vb((size_t)G + 1, 0);
+    for (int32_t i = 0; i < G; ++i) vb[i + 1] = vb[i] + n[i];
+    std::vector<void*> tmp;
+    int64_t* eoff = nullptr;
+    if ((st = dalloc(g, &g->batch_vbase, (size_t)G + 1, &g->blocks)) || (st = dalloc(g, &g->batch_err, 1, &g->blocks)) ||
+        (st = dalloc(g, &eoff, (size_t)G + 1, &tmp)))
+        return finish_create(g, st, out);
+    cudaMemsetAsync(g->batch_err, 0, sizeof(int), g->stream);
+    cudaError_t e = cudaMemcpyAsync(g->batch_vbase, vb.data(), sizeof(int32_t) * vb.size(), cudaMemcpyHostToDevice,
+                                    g->stream);
+    if (e == cudaSuccess && G > 0)
+        e = cudaMemcpyAsync(eoff, edge_off, sizeof(int64_t) * ((size_t)G + 1), cudaMemcpyHostToDevice, g->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(g->stream);  // host arrays may be pageable and short-lived
+    if (e != cudaSuccess) {
+        free_list(g, &tmp);
+        return finish_create(g, cuda_fail("tc_batch_create copy", e), out);
+    }
+    const int32_t* s_dev = src;
+    const int32_t* d_dev = dst;
+    if (mem_kind == TC_MEM_HOST && m > 0) {
+        int32_t *hs = nullptr, *hd = nullptr;
+        if ((st = dalloc(g, &hs, (size_t)m, &tmp)) || (st = dalloc(g, &hd, (size_t)m, &tmp))) {
+            free_list(g, &tmp);
+            return finish_create(g, st, out);
+        }
+        e = cudaMemcpyAsync(hs, src, sizeof(int32_t) * (size_t)m, cudaMemcpyHostToDevice, g->stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(hd, dst, sizeof(int32_t) * (size_t)m, cudaMemcpyHostToDevice, g->stream);
+        if (e != cudaSuccess) {
+            free_list(g, &tmp);
+            return finish_create(g, cuda_fail("tc_batch_create copy", e), out);
+        }
+        s_dev = hs;
+        d_dev = hd;
+    }
+    st = batch_build(g, G, g->batch_vbase, eoff, s_dev, d_dev, m);
+    free_list(g, &tmp);
+    return finish_create(g, st, out);
+}
+
+static tc_status batch_count_device(tc_graph* g, unsigned long long* T_dev) {
+    tc_status st = run_count(g);
+    if (st != TC_OK) return st;
+    launch_batch_T(g->batch_G, g->batch_vbase, g->rank, g->t_rank, T_dev, g->batch_err, g->L);
+    TC_CK(cudaGetLastError());
+    return TC_OK;
+}
+
+static tc_status batch_check(tc_graph* g) {
+    int err = 0;
+    DevStats h;
+    TC_CK(cudaMemcpyAsync(&err, g->batch_err, sizeof(int), cudaMemcpyDeviceToHost, g->stream));
+    tc_status st = read_stats(g, &h);  // synchronises
+    if (st != TC_OK) return st;
+    if ((err | h.err) & ERR_BAD_ID) {
+        snprintf(g_last_error, sizeof(g_last_error), "vertex id outside [0, n_g) in a batch graph");
+        return TC_EINVAL;
+    }
+    if ((err & ERR_OVERFLOW) || h.sum_t % 3 != 0) return TC_EINTERNAL;
+    return TC_OK;
+}
+
+extern "C" tc_status tc_batch_count(tc_graph* g, uint64_t* T_out, int mem_kind) {
+    if (!g || g->batch_G < 0 || (g->batch_G > 0 && !T_out) || (mem_kind != TC_MEM_HOST && mem_kind != TC_MEM_DEVICE))
+        return TC_EINVAL;
+    const int32_t G = g->batch_G;
+    tc_status st;
+    if (mem_kind == TC_MEM_DEVICE) {
+        if ((st = batch_count_device(g, reinterpret_cast<unsigned long long*>(T_out))) != TC_OK) return st;
+        return batch_check(g);
+    }
+    std::vector<void*> tmp;
+    unsigned long long* dT = nullptr;
+    if ((st = dalloc(g, &dT, (size_t)G + 1, &tmp)) != TC_OK) return st;
+    if ((st = batch_count_device(g, dT)) == TC_OK) {
+        cudaError_t e = G > 0 ? cudaMemcpyAsync(T_out, dT, sizeof(uint64_t) * (size_t)G, cudaMemcpyDeviceToHost, g->stream)
+                              : cudaSuccess;
+        if (e != cudaSuccess) st = cuda_fail("tc_batch_count copy", e);
+    }
+    free_list(g, &tmp);
+    if (st != TC_OK) return st;
+    return batch_check(g);
+}
+
+extern "C" tc_status tc_batch_size(const tc_graph* g, int32_t* G) {
+    if (!g || !G || g->batch_G < 0) return TC_EINVAL;
+    *G = g->batch_G;
+    return TC_OK;
+}
 
 }  // extern "C"

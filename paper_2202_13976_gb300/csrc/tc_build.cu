@@ -115,23 +115,23 @@ __global__ void k_rank_invert(const uint64_t* __restrict__ sorted, int32_t n, in
 }
 
 __global__ void k_orient_count(const int32_t* __restrict__ src, const int32_t* __restrict__ dst, int64_t m,
-                               const int32_t* __restrict__ rank, uint32_t* __restrict__ rowcnt) {
+                               int32_t n, const int32_t* __restrict__ rank, uint32_t* __restrict__ rowcnt) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += stride) {
         int32_t u = src[i], v = dst[i];
-        if (u == v) continue;
+        if (u == v || (uint32_t)u >= (uint32_t)n || (uint32_t)v >= (uint32_t)n) continue;
         int32_t a = rank[u], b = rank[v];
         atomicAdd(&rowcnt[min(a, b)], 1u);
     }
 }
 
 __global__ void k_orient_scatter(const int32_t* __restrict__ src, const int32_t* __restrict__ dst, int64_t m,
-                                 const int32_t* __restrict__ rank, const int64_t* __restrict__ rowstart,
+                                 int32_t n, const int32_t* __restrict__ rank, const int64_t* __restrict__ rowstart,
                                  uint32_t* __restrict__ cursor, int32_t* __restrict__ col) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += stride) {
         int32_t u = src[i], v = dst[i];
-        if (u == v) continue;
+        if (u == v || (uint32_t)u >= (uint32_t)n || (uint32_t)v >= (uint32_t)n) continue;
         int32_t a = rank[u], b = rank[v];
         int32_t s = min(a, b), t = max(a, b);
         int64_t p = rowstart[s] + atomicAdd(&cursor[s], 1u);
@@ -433,12 +433,12 @@ void launch_orient(const BuildBuffers& B, const Launch& L) {
     cudaMemsetAsync(B.cursor, 0, sizeof(uint32_t) * (size_t)B.n, L.stream);
     cudaMemsetAsync(B.deg, 0, sizeof(int32_t) * (size_t)B.n, L.stream);
     if (B.m > 0) {
-        k_orient_count<<<grid_for(B.m, THREADS, L.sms), THREADS, 0, L.stream>>>(B.src, B.dst, B.m, B.rank,
+        k_orient_count<<<grid_for(B.m, THREADS, L.sms), THREADS, 0, L.stream>>>(B.src, B.dst, B.m, B.n, B.rank,
                                                                               B.rowcnt); count_launch(); }
     scan_u32_to_i64(B.rowcnt, B.rowstart, B.n, B.tmp, L);
     if (B.m > 0) {
         k_orient_scatter<<<grid_for(B.m, THREADS, L.sms), THREADS, 0, L.stream>>>(
-            B.src, B.dst, B.m, B.rank, B.rowstart, B.cursor, B.col); count_launch(); }
+            B.src, B.dst, B.m, B.n, B.rank, B.rowstart, B.cursor, B.col); count_launch(); }
     k_segsort_thread<<<grid_for(B.n, THREADS, L.sms), THREADS, 0, L.stream>>>(
         B.n, B.rowstart, B.rowcnt, B.col, B.rowlen, B.rowinfo, B.deg, B.midlist, B.longlist, B.stats);
     count_launch();

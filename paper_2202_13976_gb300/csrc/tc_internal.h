@@ -99,6 +99,7 @@ struct Strategy {
     float factor[TC_NUM_BUCKETS];
     int hub_min_degree;   // vertices of degree >= this are hub candidates (<= 0: no hubs)
     int hub_max;          // at most this many hubs (the highest ranks)
+    int hub_big_in;       // hubs with at least this in-degree get a whole block (else one warp)
 };
 
 // Capacity of the hub kernel's shared-memory bitmap (ranks above the hub).
@@ -139,6 +140,12 @@ void launch_sum_t(const CountBuffers& C, const Launch& L);
 void launch_finalize(int32_t n, const int32_t* rank, const unsigned long long* t_rank,
                      const int32_t* deg, unsigned long long* t_out, double* lcc_out,
                      const Launch& L);
+
+// ---- batch (tc_batch.cu) -------------------------------------------------------
+void launch_batch_relabel(int32_t G, const int64_t* edge_off, const int32_t* vbase, const int32_t* src,
+                          const int32_t* dst, int32_t* usrc, int32_t* udst, int* err, const Launch& L);
+void launch_batch_T(int32_t G, const int32_t* vbase, const int32_t* rank, const unsigned long long* t_rank,
+                    unsigned long long* T_out, int* err, const Launch& L);
 
 // Kernel launch accounting (tc_launch_count).
 void count_launch(int k = 1);

@@ -50,7 +50,6 @@ constexpr int HUB_THREADS = 256;
 constexpr int HUB_WARPS = HUB_THREADS / 32;
 constexpr int HUB_BM_WORDS = HUB_BM_BITS / 32;
 constexpr int HUB_CNT_MAX = 4096;      // hub lists longer than this count matches globally
-constexpr int HUB_BIG_IN = 256;        // hubs with at least this in-degree get a whole block
 constexpr int HUB_WARP_MAX = 448;      // longest N+(v) a single warp stages
 
 struct Sink {
@@ -370,16 +369,16 @@ __global__ void k_hub_scatter(int32_t n, int32_t hub_cap, const int64_t* __restr
     }
 }
 
-// Hub slot i (0 = highest rank) is big when its in-degree reaches HUB_BIG_IN or its
-// list is too long for one warp.
+// Hub slot i (0 = highest rank) is big when its in-degree reaches big_in or its list
+// is too long for one warp.
 __global__ void k_hub_flags(int32_t n, const int32_t* __restrict__ rowlen, const uint32_t* __restrict__ indeg,
-                            int32_t hub_cap, uint32_t* __restrict__ big, DevStats* stats) {
+                            int32_t hub_cap, int big_in, uint32_t* __restrict__ big, DevStats* stats) {
     const int64_t K = stats->hub_count;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < K; i += stride) {
         const int32_t v = n - 1 - (int32_t)i;
         const uint32_t din = indeg[v - (n - hub_cap)];
-        big[i] = (din >= (uint32_t)HUB_BIG_IN || rowlen[v] > HUB_WARP_MAX) && rowlen[v] > 0 && din > 0 ? 1u : 0u;
+        big[i] = (din >= (uint32_t)big_in || rowlen[v] > HUB_WARP_MAX) && rowlen[v] > 0 && din > 0 ? 1u : 0u;
     }
 }
 
@@ -571,7 +570,7 @@ __global__ void __launch_bounds__(CTA_THREADS) k_tc_cta(int32_t n, const int64_t
 }
 
 // ---- hub bucket ----------------------------------------------------------------
-// Big hubs (in-degree >= HUB_BIG_IN, or lists too long for one warp) are processed
+// Big hubs (in-degree >= the planner's threshold, or lists too long for one warp) are processed
 // by a whole block over a bitmap of N+(v); the remaining hubs by one warp each over
 // the sorted list N+(v) in shared memory.  One persistent kernel drains the big-hub
 // queue first, then every warp takes medium hubs independently.
@@ -903,8 +902,8 @@ void launch_plan(const CountBuffers& C, const Strategy& S, const Launch& L) {
         count_launch();
         // hub_cur is free again: it holds the big flags, hub_cnt (still the in-degrees
         // until here) is overwritten by their exclusive scan
-        k_hub_flags<<<grid_for(C.hub_cap, THREADS, L.sms), THREADS, 0, L.stream>>>(C.n, C.rowlen, C.hub_cnt,
-                                                                                  C.hub_cap, C.hub_cur, C.stats);
+        k_hub_flags<<<grid_for(C.hub_cap, THREADS, L.sms), THREADS, 0, L.stream>>>(
+            C.n, C.rowlen, C.hub_cnt, C.hub_cap, S.hub_big_in > 0 ? S.hub_big_in : 1, C.hub_cur, C.stats);
         count_launch();
         scan_u32_to_u32(C.hub_cur, C.hub_cnt, C.hub_cap, C.tmp, L);
         k_hub_lists<<<grid_for(C.hub_cap, THREADS, L.sms), THREADS, 0, L.stream>>>(C.n, C.hub_cur, C.hub_cnt,
