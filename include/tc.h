@@ -224,6 +224,53 @@ tc_status tc_batch_count(tc_graph* g, uint64_t* T_out, int mem_kind);
 tc_status tc_batch_size(const tc_graph* g, int32_t* G);
 
 /*
+ * Tuning of the intersection: strategy and Eq. 3 factor per bucket, and the hub
+ * selection (min_degree, max hubs) and block-versus-warp split of hubs (hubs with
+ * in-degree >= hub_big_in get a whole thread block, the others one warp).
+ */
+typedef struct tc_tuning {
+    int32_t strategy[TC_NUM_BUCKETS];
+    double factor[TC_NUM_BUCKETS];
+    int32_t hub_min_degree;
+    int32_t hub_max;
+    int32_t hub_big_in;
+} tc_tuning;
+
+tc_status tc_graph_get_tuning(const tc_graph* g, tc_tuning* out);
+/* Errors: TC_EINVAL for values the buckets cannot run (as tc_graph_set_strategy). */
+tc_status tc_graph_set_tuning(tc_graph* g, const tc_tuning* t);
+
+/*
+ * Autotuner: times the bucket kernels of g under candidate settings (hub threshold
+ * and block/warp split first, then each bucket's strategy, chosen per bucket from
+ * its own kernel time), applies the fastest and writes it to *out (may be NULL).
+ * Results are cached in the process by a signature of the planned work (edges and
+ * list lengths per bucket, rounded to powers of two); a graph with a cached
+ * signature gets the cached setting without trials unless force != 0.  Runs the
+ * count several times; synchronises the stream.
+ */
+tc_status tc_graph_autotune(tc_graph* g, int32_t force, tc_tuning* out);
+
+/*
+ * One call for a whole batch with device buffers: create, count, per-graph T,
+ * t[] and LCC[] (union ids), release.  src, dst, T_out (uint64[G]), t_out
+ * (uint64[sum n], may be NULL) and lcc_out (fp64[sum n], may be NULL) are DEVICE
+ * pointers; n and edge_off are host arrays as in tc_batch_create.  tuning may be
+ * NULL (defaults).  With flags & TC_RUN_GRAPH the device work is recorded once
+ * into a CUDA graph (cuda_stream must then not be NULL) and replayed by later calls
+ * with the same sizes, buffers and tuning; the library keeps the recorded graph and
+ * two small arrays per distinct call until tc_release_cached_graphs.  Synchronises
+ * the stream (to report errors).  Errors: as tc_batch_create / tc_batch_count.
+ */
+enum { TC_RUN_GRAPH = 1 };
+tc_status tc_batch_run(int32_t G, const int32_t* n, const int64_t* edge_off, const int32_t* src,
+                       const int32_t* dst, uint64_t* T_out, uint64_t* t_out, double* lcc_out,
+                       const tc_tuning* tuning, void* cuda_stream, int flags);
+
+/* Frees the CUDA graphs and arrays kept by tc_batch_run. */
+void tc_release_cached_graphs(void);
+
+/*
  * Count without allocating (an addition of this library; the paper has no
  * counterpart).  For callers that cannot allocate device memory while they run: a
  * program that has handed all free HBM to its own caching allocator, code being

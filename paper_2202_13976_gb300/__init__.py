@@ -29,7 +29,33 @@ EXPORTS = ["tc_graph_create_from_edges", "tc_graph_create_from_csr", "tc_count",
            "tc_graph_info", "tc_graph_size", "tc_graph_destroy", "tc_status_str",
            "tc_last_error_detail", "tc_graph_set_strategy", "tc_graph_last_timing",
            "tc_graph_plan_stats", "tc_launch_count", "tc_graph_set_hubs", "tc_count_noalloc",
-           "tc_batch_create", "tc_batch_count", "tc_batch_size"]
+           "tc_batch_create", "tc_batch_count", "tc_batch_size", "tc_graph_get_tuning",
+           "tc_graph_set_tuning", "tc_graph_autotune", "tc_batch_run", "tc_release_cached_graphs"]
+TC_RUN_GRAPH = 1
+
+
+class TcTuning(ctypes.Structure):
+    """struct tc_tuning of include/tc.h."""
+    _fields_ = [("strategy", ctypes.c_int32 * 3), ("factor", ctypes.c_double * 3),
+                ("hub_min_degree", ctypes.c_int32), ("hub_max", ctypes.c_int32), ("hub_big_in", ctypes.c_int32)]
+
+    def to_dict(self) -> dict:
+        names = {v: k for k, v in STRATEGIES.items()}
+        return {"strategy": {b: names[self.strategy[i]] for b, i in BUCKETS.items()},
+                "factor": {b: self.factor[i] for b, i in BUCKETS.items()},
+                "hub_min_degree": self.hub_min_degree, "hub_max": self.hub_max, "hub_big_in": self.hub_big_in}
+
+    @classmethod
+    def from_dict(cls, d: dict) -> "TcTuning":
+        t = cls()
+        for b, i in BUCKETS.items():
+            s = d["strategy"][b]
+            t.strategy[i] = STRATEGIES[s] if isinstance(s, str) else int(s)
+            t.factor[i] = float(d["factor"][b])
+        t.hub_min_degree = int(d["hub_min_degree"])
+        t.hub_max = int(d["hub_max"])
+        t.hub_big_in = int(d["hub_big_in"])
+        return t
 TC_NOALLOC_MAX_N, TC_NOALLOC_MAX_M = 16384, 262144
 
 _lib = None
@@ -94,6 +120,17 @@ def load(path: str | None = None):
     lib.tc_batch_count.argtypes = [P, P, ctypes.c_int]
     lib.tc_batch_size.restype = st
     lib.tc_batch_size.argtypes = [P, ctypes.POINTER(i32)]
+    TP = ctypes.POINTER(TcTuning)
+    lib.tc_graph_get_tuning.restype = st
+    lib.tc_graph_get_tuning.argtypes = [P, TP]
+    lib.tc_graph_set_tuning.restype = st
+    lib.tc_graph_set_tuning.argtypes = [P, TP]
+    lib.tc_graph_autotune.restype = st
+    lib.tc_graph_autotune.argtypes = [P, i32, TP]
+    lib.tc_batch_run.restype = st
+    lib.tc_batch_run.argtypes = [i32, P, P, P, P, P, P, P, TP, P, ctypes.c_int]
+    lib.tc_release_cached_graphs.restype = None
+    lib.tc_release_cached_graphs.argtypes = []
     lib.tc_count_noalloc.restype = st
     lib.tc_count_noalloc.argtypes = [i32, i64, P, P, ctypes.POINTER(u64), P, P, P]
     _lib = lib
@@ -275,6 +312,43 @@ def tc_batch_count(g: int, T_out=None):
     return T_out
 
 
+def tc_graph_get_tuning(g: int) -> dict:
+    t = TcTuning()
+    _check(_lib.tc_graph_get_tuning(g, ctypes.byref(t)))
+    return t.to_dict()
+
+
+def tc_graph_set_tuning(g: int, tuning: dict) -> None:
+    t = TcTuning.from_dict(tuning)
+    _check(_lib.tc_graph_set_tuning(g, ctypes.byref(t)))
+
+
+def tc_graph_autotune(g: int, force: bool = False) -> dict:
+    t = TcTuning()
+    _check(_lib.tc_graph_autotune(g, 1 if force else 0, ctypes.byref(t)))
+    return t.to_dict()
+
+
+def tc_batch_run(n, edge_off, src, dst, T_out, t_out=None, lcc_out=None, tuning=None, stream=None,
+                 graph: bool = False) -> None:
+    """Whole batch in one call, device buffers (CUDA tensors); graph=True records the
+    device work into a CUDA graph once and replays it on later identical calls."""
+    load()
+    n = np.ascontiguousarray(n, dtype=np.int32)
+    edge_off = np.ascontiguousarray(edge_off, dtype=np.int64)
+    for a in (src, dst, T_out, t_out, lcc_out):
+        if a is not None and not _is_device(a):
+            raise ValueError("tc_batch_run takes device buffers")
+    (ps, pd, pT, pt, pl), _ = _ptr_kind(src, dst, T_out, t_out, lcc_out)
+    tp = ctypes.byref(TcTuning.from_dict(tuning)) if tuning else None
+    _check(_lib.tc_batch_run(len(n), n.ctypes.data, edge_off.ctypes.data, ps, pd, pT, pt, pl, tp,
+                             _stream_ptr(stream), TC_RUN_GRAPH if graph else 0))
+
+
+def tc_release_cached_graphs() -> None:
+    load().tc_release_cached_graphs()
+
+
 def tc_launch_count() -> int:
     return int(load().tc_launch_count())
 
@@ -326,6 +400,15 @@ class Graph:
 
     def plan_stats(self) -> dict:
         return tc_graph_plan_stats(self.handle)
+
+    def tuning(self) -> dict:
+        return tc_graph_get_tuning(self.handle)
+
+    def set_tuning(self, tuning: dict):
+        tc_graph_set_tuning(self.handle, tuning)
+
+    def autotune(self, force: bool = False) -> dict:
+        return tc_graph_autotune(self.handle, force)
 
     def close(self):
         tc_graph_destroy(self.handle)

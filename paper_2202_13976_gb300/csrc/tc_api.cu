@@ -8,6 +8,8 @@
 
 #include <atomic>
 #include <climits>
+#include <cmath>
+#include <unordered_map>
 #include <cstddef>
 #include <cstdio>
 #include <cstring>
@@ -115,6 +117,7 @@ struct tc_graph {
     int32_t batch_G = -1;
     int32_t* batch_vbase = nullptr;   // device, G + 1
     int* batch_err = nullptr;         // device flag of the relabel and the per-graph reduction
+    bool capture = false;             // work is being recorded into a CUDA graph: no events
 };
 
 namespace {
@@ -136,7 +139,9 @@ tc_status dalloc(tc_graph* g, T** p, size_t count, std::vector<void*>* track) {
     if (bytes == 0) bytes = 16;
     bytes = (bytes + 255) & ~(size_t)255;
     void* q = nullptr;
-    cudaError_t e = cudaMallocFromPoolAsync(&q, bytes, g->pool, g->stream);
+    // while recording a CUDA graph the allocation becomes a graph memory node
+    cudaError_t e = g->capture ? cudaMallocAsync(&q, bytes, g->stream)
+                               : cudaMallocFromPoolAsync(&q, bytes, g->pool, g->stream);
     if (e != cudaSuccess) {
         cudaGetLastError();
         set_error("cudaMallocFromPoolAsync", e);
@@ -294,6 +299,7 @@ CountBuffers count_buffers(tc_graph* g) {
 }
 
 tc_status ensure_events(tc_graph* g) {
+    if (g->capture) return TC_OK;
     if (!g->ev[0])
         for (int i = 0; i < PH_EVENTS; ++i) TC_CK(cudaEventCreate(&g->ev[i]));
     return TC_OK;
@@ -306,7 +312,7 @@ tc_status run_plan(tc_graph* g) {
     if (st != TC_OK) return st;
     const size_t off = offsetof(DevStats, small_count);
     TC_CK(cudaMemsetAsync(reinterpret_cast<char*>(g->stats) + off, 0, sizeof(DevStats) - off, g->stream));
-    TC_CK(cudaEventRecord(g->ev[PH_PLAN], g->stream));
+    if (!g->capture) TC_CK(cudaEventRecord(g->ev[PH_PLAN], g->stream));
     launch_plan(count_buffers(g), g->strat, g->L);
     TC_CK(cudaGetLastError());
     g->planned = true;
@@ -319,18 +325,18 @@ tc_status run_count(tc_graph* g) {
     tc_status st = ensure_events(g);
     if (st != TC_OK) return st;
     if (g->planned) {
-        TC_CK(cudaEventRecord(g->ev[PH_PLAN], g->stream));  // planning already done: empty phase
+        if (!g->capture) TC_CK(cudaEventRecord(g->ev[PH_PLAN], g->stream));  // planning already done: empty phase
     } else if ((st = run_plan(g)) != TC_OK) {
         return st;
     }
     TC_CK(cudaMemsetAsync(g->t_rank, 0, sizeof(unsigned long long) * (size_t)g->n, g->stream));
     TC_CK(cudaMemsetAsync(&g->stats->sum_t, 0, sizeof(unsigned long long), g->stream));
     CountBuffers C = count_buffers(g);
-    launch_intersect(C, g->strat, g->ev, g->L);
+    launch_intersect(C, g->strat, g->capture ? nullptr : g->ev, g->L);
     launch_sum_t(C, g->L);
     TC_CK(cudaGetLastError());
     g->counted = true;
-    g->timed = true;
+    g->timed = !g->capture;
     return TC_OK;
 }
 
@@ -729,6 +735,311 @@ extern "C" tc_status tc_batch_size(const tc_graph* g, int32_t* G) {
     if (!g || !G || g->batch_G < 0) return TC_EINVAL;
     *G = g->batch_G;
     return TC_OK;
+}
+
+// ---- tuning and autotuner --------------------------------------------------------
+
+static tc_status tuning_check(const tc_tuning* t) {
+    if (!t) return TC_EINVAL;
+    for (int b = 0; b < TC_NUM_BUCKETS; ++b) {
+        const int s = t->strategy[b];
+        if (s < TC_STRAT_AUTO || s > TC_STRAT_BITMAP || !(t->factor[b] > 0.0)) return TC_EINVAL;
+        if (b == TC_BUCKET_SMALL && (s == TC_STRAT_PROBE || s == TC_STRAT_BITMAP)) return TC_EINVAL;
+        if (b == TC_BUCKET_HUB && (s == TC_STRAT_MERGE || s == TC_STRAT_SEARCH)) return TC_EINVAL;
+    }
+    if (t->hub_min_degree < 0 || t->hub_max < 0 || t->hub_big_in < 1) return TC_EINVAL;
+    return TC_OK;
+}
+
+static void tuning_get(const Strategy& S, tc_tuning* t) {
+    for (int b = 0; b < TC_NUM_BUCKETS; ++b) {
+        t->strategy[b] = S.strat[b];
+        t->factor[b] = S.factor[b];
+    }
+    t->hub_min_degree = S.hub_min_degree;
+    t->hub_max = S.hub_max;
+    t->hub_big_in = S.hub_big_in;
+}
+
+static void tuning_put(tc_graph* g, const tc_tuning* t) {
+    const bool replan = g->strat.hub_min_degree != t->hub_min_degree || g->strat.hub_max != t->hub_max ||
+                        g->strat.hub_big_in != t->hub_big_in;
+    for (int b = 0; b < TC_NUM_BUCKETS; ++b) {
+        g->strat.strat[b] = t->strategy[b];
+        g->strat.factor[b] = (float)t->factor[b];
+    }
+    g->strat.hub_min_degree = t->hub_min_degree;
+    g->strat.hub_max = t->hub_max < HUB_BM_BITS ? t->hub_max : HUB_BM_BITS;
+    g->strat.hub_big_in = t->hub_big_in;
+    if (replan) g->planned = false;
+    g->counted = false;
+}
+
+static tc_tuning default_tuning() {
+    tc_tuning t;
+    for (int b = 0; b < TC_NUM_BUCKETS; ++b) {
+        t.strategy[b] = TC_STRAT_AUTO;
+        t.factor[b] = 1.0;
+    }
+    t.strategy[TC_BUCKET_CTA] = TC_STRAT_BITMAP;
+    t.hub_min_degree = 32;
+    t.hub_max = HUB_BM_BITS;
+    t.hub_big_in = 256;
+    return t;
+}
+
+extern "C" tc_status tc_graph_get_tuning(const tc_graph* g, tc_tuning* out) {
+    if (!g || !out) return TC_EINVAL;
+    tuning_get(g->strat, out);
+    return TC_OK;
+}
+
+extern "C" tc_status tc_graph_set_tuning(tc_graph* g, const tc_tuning* t) {
+    if (!g) return TC_EINVAL;
+    tc_status st = tuning_check(t);
+    if (st != TC_OK) return st;
+    tuning_put(g, t);
+    return TC_OK;
+}
+
+static std::mutex g_tune_mutex;
+static std::unordered_map<uint64_t, tc_tuning> g_tune_cache;
+
+// Count once under the current settings and return the phase times (ms[0..4]).
+static tc_status timed_count(tc_graph* g, float* ms) {
+    g->counted = false;
+    tc_status st = run_count(g);
+    if (st != TC_OK) return st;
+    return tc_graph_last_timing(g, ms, 5);
+}
+
+extern "C" tc_status tc_graph_autotune(tc_graph* g, int32_t force, tc_tuning* out) {
+    if (!g) return TC_EINVAL;
+    tc_tuning best = default_tuning();
+    tuning_put(g, &best);
+    int64_t e[TC_NUM_BUCKETS + 1], ids[TC_NUM_BUCKETS + 1];
+    tc_status st = tc_graph_plan_stats(g, e, ids);
+    if (st != TC_OK) return st;
+    // signature: powers of two of the planned work per bucket and of the graph size
+    uint64_t sig = 1469598103934665603ull;
+    auto mix = [&](int64_t x) {
+        const uint64_t q = (uint64_t)std::llround(std::log2((double)x + 1.0));
+        sig = (sig ^ q) * 1099511628211ull;
+    };
+    mix(g->n);
+    for (int b = 0; b <= TC_NUM_BUCKETS; ++b) {
+        mix(e[b]);
+        mix(ids[b]);
+    }
+    if (!force) {
+        std::lock_guard<std::mutex> lock(g_tune_mutex);
+        auto it = g_tune_cache.find(sig);
+        if (it != g_tune_cache.end()) {
+            tuning_put(g, &it->second);
+            if (out) *out = it->second;
+            return TC_OK;
+        }
+    }
+    float ms[5];
+    // 1. hub threshold and block/warp split, default strategies
+    const int hub_cands[][2] = {{32, 256}, {16, 256}, {64, 256}, {128, 256}, {32, 64}, {32, 1024}};
+    float best_total = 1e30f;
+    for (const auto& hc : hub_cands) {
+        tc_tuning t = default_tuning();
+        t.hub_min_degree = hc[0];
+        t.hub_big_in = hc[1];
+        tuning_put(g, &t);
+        float tot = 1e30f;
+        for (int r = 0; r < 2; ++r) {
+            if ((st = timed_count(g, ms)) != TC_OK) return st;
+            tot = std::fmin(tot, ms[4]);
+        }
+        if (tot < best_total) {
+            best_total = tot;
+            best = t;
+        }
+    }
+    // 2. per-bucket strategy, each bucket judged by its own kernel time
+    const int sm_s[] = {TC_STRAT_AUTO, TC_STRAT_AUTO, TC_STRAT_AUTO, TC_STRAT_MERGE, TC_STRAT_SEARCH};
+    const double sm_f[] = {1.0, 4.0, 0.25, 1.0, 1.0};
+    const int cta_s[] = {TC_STRAT_BITMAP, TC_STRAT_AUTO, TC_STRAT_PROBE, TC_STRAT_SEARCH, TC_STRAT_MERGE};
+    const int hub_s[] = {TC_STRAT_BITMAP, TC_STRAT_PROBE, TC_STRAT_BITMAP, TC_STRAT_PROBE, TC_STRAT_BITMAP};
+    float best_b[3] = {1e30f, 1e30f, 1e30f};
+    tc_tuning pick = best;
+    for (int i = 0; i < 5; ++i) {
+        tc_tuning t = best;
+        t.strategy[TC_BUCKET_SMALL] = sm_s[i];
+        t.factor[TC_BUCKET_SMALL] = sm_f[i];
+        t.strategy[TC_BUCKET_CTA] = cta_s[i];
+        t.strategy[TC_BUCKET_HUB] = hub_s[i];
+        tuning_put(g, &t);
+        float b3[3] = {1e30f, 1e30f, 1e30f};
+        for (int r = 0; r < 2; ++r) {
+            if ((st = timed_count(g, ms)) != TC_OK) return st;
+            for (int k = 0; k < 3; ++k) b3[k] = std::fmin(b3[k], ms[1 + k]);
+        }
+        if (b3[0] < best_b[0]) {
+            best_b[0] = b3[0];
+            pick.strategy[TC_BUCKET_SMALL] = sm_s[i];
+            pick.factor[TC_BUCKET_SMALL] = sm_f[i];
+        }
+        if (b3[1] < best_b[1]) {
+            best_b[1] = b3[1];
+            pick.strategy[TC_BUCKET_CTA] = cta_s[i];
+        }
+        if (b3[2] < best_b[2]) {
+            best_b[2] = b3[2];
+            pick.strategy[TC_BUCKET_HUB] = hub_s[i];
+        }
+    }
+    tuning_put(g, &pick);
+    {
+        std::lock_guard<std::mutex> lock(g_tune_mutex);
+        g_tune_cache[sig] = pick;
+    }
+    if (out) *out = pick;
+    return TC_OK;
+}
+
+// ---- one-call batch, optionally recorded into a CUDA graph -----------------------
+
+struct RunEntry {
+    uint64_t key = 0;
+    int device = 0;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    int32_t* vbase = nullptr;
+    int64_t* eoff = nullptr;
+    int* status = nullptr;
+    uint64_t kernels = 0;  // kernel launches recorded in the graph
+};
+static std::mutex g_run_mutex;
+static std::vector<RunEntry> g_runs;
+
+static uint64_t fnv(uint64_t h, const void* p, size_t bytes) {
+    const unsigned char* c = static_cast<const unsigned char*>(p);
+    for (size_t i = 0; i < bytes; ++i) h = (h ^ c[i]) * 1099511628211ull;
+    return h;
+}
+
+// The device work of one batch call on g->stream (no host synchronisation).
+static tc_status batch_pipeline(tc_graph* g, int32_t G, int32_t* vbase, const int64_t* eoff, const int32_t* src,
+                                const int32_t* dst, int64_t m, uint64_t* T_out, uint64_t* t_out, double* lcc_out,
+                                int* status) {
+    g->batch_G = G;
+    g->batch_vbase = vbase;
+    tc_status st;
+    if ((st = dalloc(g, &g->batch_err, 1, &g->blocks)) != TC_OK) return st;
+    TC_CK(cudaMemsetAsync(g->batch_err, 0, sizeof(int), g->stream));
+    if ((st = batch_build(g, G, vbase, eoff, src, dst, m)) != TC_OK) return st;
+    if ((st = batch_count_device(g, reinterpret_cast<unsigned long long*>(T_out))) != TC_OK) return st;
+    if (t_out || lcc_out)
+        launch_finalize(g->n, g->rank, g->t_rank, g->deg, reinterpret_cast<unsigned long long*>(t_out), lcc_out, g->L);
+    launch_run_status(g->stats, g->batch_err, status, g->L);
+    TC_CK(cudaGetLastError());
+    return TC_OK;
+}
+
+extern "C" tc_status tc_batch_run(int32_t G, const int32_t* n, const int64_t* edge_off, const int32_t* src,
+                                  const int32_t* dst, uint64_t* T_out, uint64_t* t_out, double* lcc_out,
+                                  const tc_tuning* tuning, void* cuda_stream, int flags) {
+    int64_t n_total = 0, m = 0;
+    tc_status st = batch_host_checks(G, n, edge_off, &n_total, &m);
+    if (st != TC_OK) return st;
+    if ((m > 0 && (!src || !dst)) || (G > 0 && !T_out)) return TC_EINVAL;
+    if (tuning && (st = tuning_check(tuning)) != TC_OK) return st;
+    const bool graph_mode = (flags & TC_RUN_GRAPH) != 0;
+    cudaStream_t stream = static_cast<cudaStream_t>(cuda_stream);
+    if (graph_mode && !stream) return TC_EINVAL;
+    int dev = 0;
+    TC_CK(cudaGetDevice(&dev));
+    DeviceState* D = nullptr;
+    if ((st = init_device(dev, &D)) != TC_OK) return st;
+    const tc_tuning tun = tuning ? *tuning : default_tuning();
+    uint64_t key = 1469598103934665603ull;
+    key = fnv(key, &G, sizeof(G));
+    key = fnv(key, n, sizeof(int32_t) * (size_t)G);
+    key = fnv(key, edge_off, sizeof(int64_t) * ((size_t)G + 1));
+    const void* ptrs[5] = {src, dst, T_out, t_out, lcc_out};
+    key = fnv(key, ptrs, sizeof(ptrs));
+    key = fnv(key, &tun, sizeof(tun));
+    key = fnv(key, &dev, sizeof(dev));
+    RunEntry* hit = nullptr;
+    if (graph_mode) {
+        std::lock_guard<std::mutex> lock(g_run_mutex);
+        for (auto& r : g_runs)
+            if (r.key == key && r.device == dev) hit = &r;
+    }
+    int status_h = 0;
+    if (hit) {
+        TC_CK(cudaGraphLaunch(hit->exec, stream));
+        count_launch((int)hit->kernels);
+        TC_CK(cudaMemcpyAsync(&status_h, hit->status, sizeof(int), cudaMemcpyDeviceToHost, stream));
+        TC_CK(cudaStreamSynchronize(stream));
+    } else {
+        RunEntry ent;
+        ent.key = key;
+        ent.device = dev;
+        std::vector<int32_t> vb((size_t)G + 1, 0);
+        for (int32_t i = 0; i < G; ++i) vb[i + 1] = vb[i] + n[i];
+        TC_CK(cudaMalloc(&ent.vbase, sizeof(int32_t) * vb.size()));
+        TC_CK(cudaMalloc(&ent.eoff, sizeof(int64_t) * ((size_t)G + 1)));
+        TC_CK(cudaMalloc(&ent.status, sizeof(int)));
+        TC_CK(cudaMemcpy(ent.vbase, vb.data(), sizeof(int32_t) * vb.size(), cudaMemcpyHostToDevice));
+        if (G > 0) TC_CK(cudaMemcpy(ent.eoff, edge_off, sizeof(int64_t) * ((size_t)G + 1), cudaMemcpyHostToDevice));
+        tc_graph* g = nullptr;
+        if ((st = new_graph((int32_t)n_total, cuda_stream, &g)) != TC_OK) return st;
+        g->m_in = m;
+        g->capture = graph_mode;
+        tuning_put(g, &tun);
+        if (graph_mode) TC_CK(cudaStreamBeginCapture(stream, cudaStreamCaptureModeThreadLocal));
+        const uint64_t k0 = launch_total();
+        st = batch_pipeline(g, G, ent.vbase, ent.eoff, src, dst, m, T_out, t_out, lcc_out, ent.status);
+        g->batch_vbase = nullptr;  // owned by the entry
+        destroy(g);
+        ent.kernels = launch_total() - k0;
+        if (graph_mode) {
+            cudaError_t e = cudaStreamEndCapture(stream, &ent.graph);
+            if (st != TC_OK) return st;
+            if (e != cudaSuccess) return cuda_fail("cudaStreamEndCapture", e);
+            TC_CK(cudaGraphInstantiate(&ent.exec, ent.graph, 0));
+            TC_CK(cudaGraphLaunch(ent.exec, stream));
+        } else if (st != TC_OK) {
+            return st;
+        }
+        TC_CK(cudaMemcpyAsync(&status_h, ent.status, sizeof(int), cudaMemcpyDeviceToHost, stream));
+        TC_CK(cudaStreamSynchronize(stream));
+        if (graph_mode) {
+            std::lock_guard<std::mutex> lock(g_run_mutex);
+            g_runs.push_back(ent);
+        } else {
+            cudaFree(ent.vbase);
+            cudaFree(ent.eoff);
+            cudaFree(ent.status);
+        }
+    }
+    if (status_h & ERR_BAD_ID) {
+        snprintf(g_last_error, sizeof(g_last_error), "vertex id outside [0, n_g) in a batch graph");
+        return TC_EINVAL;
+    }
+    if (status_h & ERR_OVERFLOW) return TC_EINTERNAL;
+    return TC_OK;
+}
+
+extern "C" void tc_release_cached_graphs(void) {
+    std::lock_guard<std::mutex> lock(g_run_mutex);
+    for (auto& r : g_runs) {
+        int cur = 0;
+        cudaGetDevice(&cur);
+        cudaSetDevice(r.device);
+        if (r.exec) cudaGraphExecDestroy(r.exec);
+        if (r.graph) cudaGraphDestroy(r.graph);
+        cudaFree(r.vbase);
+        cudaFree(r.eoff);
+        cudaFree(r.status);
+        cudaSetDevice(cur);
+    }
+    g_runs.clear();
 }
 
 }  // extern "C"

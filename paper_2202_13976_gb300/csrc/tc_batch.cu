@@ -60,7 +60,20 @@ __global__ void k_batch_T(int32_t G, const int32_t* __restrict__ vbase, const in
     }
 }
 
+// Status word of a whole batch call: id errors, failed per-graph sums, sum of t not
+// a multiple of 3.
+__global__ void k_run_status(const DevStats* stats, const int* batch_err, int* status) {
+    int s = stats->err | *batch_err;
+    if (stats->sum_t % 3 != 0) s |= ERR_OVERFLOW;
+    *status = s;
+}
+
 }  // namespace
+
+void launch_run_status(const DevStats* stats, const int* batch_err, int* status, const Launch& L) {
+    k_run_status<<<1, 1, 0, L.stream>>>(stats, batch_err, status);
+    count_launch();
+}
 
 void launch_batch_relabel(int32_t G, const int64_t* edge_off, const int32_t* vbase, const int32_t* src,
                           const int32_t* dst, int32_t* usrc, int32_t* udst, int* err, const Launch& L) {

@@ -144,6 +144,7 @@ void launch_finalize(int32_t n, const int32_t* rank, const unsigned long long* t
 // ---- batch (tc_batch.cu) -------------------------------------------------------
 void launch_batch_relabel(int32_t G, const int64_t* edge_off, const int32_t* vbase, const int32_t* src,
                           const int32_t* dst, int32_t* usrc, int32_t* udst, int* err, const Launch& L);
+void launch_run_status(const DevStats* stats, const int* batch_err, int* status, const Launch& L);
 void launch_batch_T(int32_t G, const int32_t* vbase, const int32_t* rank, const unsigned long long* t_rank,
                     unsigned long long* T_out, int* err, const Launch& L);
 

@@ -97,3 +97,76 @@ def test_empty_batch(tc):
     g = tc.Graph.batch(np.zeros(0, np.int32), np.zeros(1, np.int64), np.zeros(0, np.int32), np.zeros(0, np.int32))
     assert len(g.batch_count()) == 0
     g.close()
+
+
+def test_autotune_keeps_results_and_caches(tc):
+    import time
+    n = 1 << 14
+    s, d = graphgen.rmat(14, 16 * n, seed=2)
+    ref = oracle.triangles(n, s, d)
+    g = tc.Graph.from_edges(n, s, d)
+    tun = g.autotune(force=True)
+    assert g.tuning() == tun
+    assert g.count() == ref["T"]
+    t, lc = g.lcc()
+    np.testing.assert_array_equal(t, ref["t"])
+    g.close()
+    g = tc.Graph.from_edges(n, s, d)
+    t0 = time.perf_counter()
+    assert g.autotune() == tun          # same signature: taken from the cache
+    assert time.perf_counter() - t0 < 0.5
+    g.close()
+    bad = dict(tun)
+    bad["strategy"] = dict(tun["strategy"], small="bitmap")
+    g = tc.Graph.from_edges(n, s, d)
+    with pytest.raises(tc.TCError):
+        g.set_tuning(bad)
+    g.close()
+
+
+@pytest.mark.parametrize("graph", [False, True])
+def test_batch_run_matches_oracle_and_replays(tc, graph):
+    import torch
+    graphs = _batch_graphs(60, seed=11)
+    n, off, src, dst = _pack(graphs)
+    nt = int(n.sum())
+    s_d, d_d = torch.from_numpy(src).cuda(), torch.from_numpy(dst).cuda()
+    T = torch.empty(len(n), dtype=torch.int64, device="cuda")
+    t = torch.empty(nt, dtype=torch.int64, device="cuda")
+    lc = torch.empty(nt, dtype=torch.float64, device="cuda")
+    stream = torch.cuda.Stream()
+    tuning = {"strategy": {"small": "auto", "cta": "probe", "hub": "bitmap"},
+              "factor": {"small": 1.0, "cta": 1.0, "hub": 1.0}, "hub_min_degree": 16, "hub_max": 131072,
+              "hub_big_in": 64}
+    vb = np.zeros(len(n) + 1, dtype=np.int64)
+    vb[1:] = np.cumsum(n)
+    refs = [oracle.triangles(ni, si, di) for ni, si, di in graphs]
+    for rep in range(3):
+        T.fill_(-1)
+        t.fill_(-1)
+        tc.tc_batch_run(n, off, s_d, d_d, T, t, lc, tuning=tuning if rep else None, stream=stream, graph=graph)
+        torch.cuda.synchronize()
+        Th = T.cpu().numpy().view(np.uint64)
+        th = t.cpu().numpy().view(np.uint64)
+        lh = lc.cpu().numpy()
+        for i, ref in enumerate(refs):
+            assert Th[i] == ref["T"]
+            np.testing.assert_array_equal(th[vb[i]:vb[i + 1]], ref["t"])
+            np.testing.assert_array_equal(lh[vb[i]:vb[i + 1]].view(np.uint64), ref["lcc"].view(np.uint64))
+    if graph:
+        with pytest.raises(tc.TCError):
+            tc.tc_batch_run(n, off, s_d, d_d, T, graph=True, stream=None)
+        tc.tc_release_cached_graphs()
+
+
+def test_batch_run_reports_bad_ids(tc):
+    import torch
+    n = np.array([3, 3], np.int32)
+    off = np.array([0, 2, 4], np.int64)
+    s = torch.tensor([0, 1, 0, 1], dtype=torch.int32, device="cuda")
+    d = torch.tensor([1, 2, 1, 9], dtype=torch.int32, device="cuda")
+    T = torch.empty(2, dtype=torch.int64, device="cuda")
+    with pytest.raises(tc.TCError) as e:
+        tc.tc_batch_run(n, off, s, d, T, stream=torch.cuda.Stream(), graph=True)
+    assert e.value.status == tc.TC_EINVAL
+    tc.tc_release_cached_graphs()
