@@ -53,8 +53,17 @@ def parse_args():
     p.add_argument("--workload", default="rmat20", choices=sorted(WORKLOAD_TEXT))
     p.add_argument("--e2e-steps", type=int, default=10)
     p.add_argument("--no-cpu-baseline", action="store_true")
-    p.add_argument("--mode", choices=["single", "batch"], default="single",
-                   help="single: one graph per step; batch: the 20,000-graph batch per step")
+    p.add_argument("--mode", choices=["single", "batch", "serve"], default="single",
+                   help="single: one graph per step; batch: the 20,000-graph batch per step; "
+                        "serve: the Poisson request stream through the serving loop")
+    p.add_argument("--serve-seconds", type=float, default=60.0)
+    p.add_argument("--serve-rate", type=float, default=2000.0)
+    p.add_argument("--slots", type=int, default=8)
+    p.add_argument("--budget-gb", type=float, default=120.0)
+    p.add_argument("--serve-deadline", type=float, default=900.0,
+                   help="give up waiting for the backlog after this many seconds")
+    p.add_argument("--serve-verify", type=int, default=24,
+                   help="check this many of the smallest served requests against the oracle")
     p.add_argument("--batch-graphs", type=int, default=20000)
     p.add_argument("--strategy", default=None,
                    help="override as small:name[:factor],cta:name[:factor],hub:name,hubs:mindeg:max")
@@ -456,11 +465,88 @@ def run_batch(args, rank, world, local):
     print(json.dumps(line), flush=True)
 
 
+def run_serve(args, rank, world, local):
+    """Serving: Poisson arrivals submitted at their arrival times; latency from
+    submission to the result on the host; the backlog is drained and reported."""
+    import numpy as np
+    import torch
+
+    import graphgen
+    import paper_2202_13976_gb300 as tc
+    torch.cuda.set_device(local)
+    tc.load()
+    reqs = graphgen.serve_requests(seconds=args.serve_seconds, rate=args.serve_rate, seed=5)
+    offered_pairs = sum(r.workload.m for r in reqs)
+    srv = tc.Server(int(args.budget_gb * (1 << 30)), args.slots)
+    results = {}
+    clocks = Clocks(local)
+    launches0 = tc.tc_launch_count()
+    t0 = time.perf_counter()
+    try:
+        for r in reqs:
+            while True:
+                now = time.perf_counter() - t0
+                if now >= r.arrival:
+                    break
+                time.sleep(min(0.0005, r.arrival - now))
+            srv.submit(r.id, r.workload)
+        submit_end = time.perf_counter() - t0
+        done = srv.wait(len(reqs), max(1.0, args.serve_deadline - submit_end))
+        stats = srv.stats()
+        for x in srv.poll(len(reqs) + 16):
+            results[x["id"]] = x
+    finally:
+        if len(results) == len(reqs):
+            srv.stop()
+    clk = clocks.stop()
+    launches = tc.tc_launch_count() - launches0
+    ok = [x for x in results.values() if x["status"] == 0]
+    lat = np.array([x["end_s"] - x["submit_s"] for x in ok]) * 1000.0
+    first = min(x["submit_s"] for x in ok)
+    last = max(x["end_s"] for x in ok)
+    edges = sum(x["m_simple"] for x in ok)
+    # verification: the smallest requests against the oracle (same generator on the host)
+    verified = 0
+    bad = 0
+    if args.serve_verify > 0:
+        import oracle
+        sys.path.insert(0, os.path.join(ROOT, "tests"))
+        small = sorted(ok, key=lambda x: reqs[x["id"]].workload.m)[: args.serve_verify]
+        for x in small:
+            w = reqs[x["id"]].workload
+            ref = oracle.triangles(w.n, *w.edges())
+            verified += 1
+            bad += int(ref["T"] != x["T"] or ref["m_simple"] != x["m_simple"])
+    if rank != 0:
+        return
+    line = {"metric": "serve p50/p99 latency", "value": float(np.percentile(lat, 50)), "unit": "ms",
+            "p99_ms": float(np.percentile(lat, 99)), "p50_ms": float(np.percentile(lat, 50)),
+            "higher_is_better": False, "n_gpus": world, "steps": 1, "warmup": 0,
+            "ms_per_step": (last - first) * 1000.0, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+            "data": "synthetic, generated on the device per request",
+            "config": {"workload": f"Poisson {args.serve_rate:g} req/s for {args.serve_seconds:g} s, n log-uniform "
+                                   "[1000, 4e6], edge factor U(4, 16), R-MAT 70% / uniform 30%, seed 5",
+                       "requests": len(reqs), "slots": args.slots, "budget_gb": args.budget_gb,
+                       "offered_pairs": offered_pairs,
+                       "offered_pairs_per_s": offered_pairs / args.serve_seconds},
+            "completed": len(ok), "all_completed": bool(done and len(ok) == len(reqs)),
+            "throughput_req_s": len(ok) / (last - first), "throughput_edges_s": edges / (last - first),
+            "submit_phase_s": submit_end, "drain_s": last - submit_end,
+            "saturated": bool((last - first) > 1.2 * args.serve_seconds),
+            "max_queue": stats["max_queue"], "peak_admitted_bytes": stats["peak_bytes"],
+            "oracle_checked": verified, "oracle_mismatches": bad, "gpu_launches": launches, "clocks": clk,
+            "impl": "ours"}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse_args()
     rank, world, local = dist_env()
     if args.impl == "reference":
         run_reference(args, rank, world)
+        return
+    if args.mode == "serve":
+        run_serve(args, rank, world, local)
         return
     if args.mode == "batch":
         if world > 1:

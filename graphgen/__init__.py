@@ -58,6 +58,8 @@ def _load():
                                 ctypes.c_uint32, ctypes.c_uint32, i32p, i32p]
         lib.gg_er.restype = i64
         lib.gg_er.argtypes = [u64, u64, i64, i64, i32p, i32p]
+        lib.gg_er_replace.restype = None
+        lib.gg_er_replace.argtypes = [u64, u64, i64, i64, i64, i32p, i32p]
         _lib = lib
     return _lib
 
@@ -111,6 +113,15 @@ def er(n: int, m: int, seed: int, stream: int = 0) -> tuple[np.ndarray, np.ndarr
     return src[:got], dst[:got]
 
 
+def er_replace(n: int, m: int, seed: int, stream: int = 0) -> tuple[np.ndarray, np.ndarray]:
+    """m uniform pairs with replacement (loops and repeats kept)."""
+    src = np.empty(m, dtype=np.int32)
+    dst = np.empty(m, dtype=np.int32)
+    if m:
+        _load().gg_er_replace(seed, stream, n, 0, m, _i32p(src), _i32p(dst))
+    return src, dst
+
+
 # ---------------------------------------------------------------------------
 # Named workloads.
 
@@ -127,6 +138,8 @@ class Workload:
     def edges(self) -> tuple[np.ndarray, np.ndarray]:
         if self.kind == "rmat":
             return rmat(self.scale, self.m, self.seed, self.stream, n=self.n)
+        if self.kind == "er_replace":
+            return er_replace(self.n, self.m, self.seed, self.stream)
         return er(self.n, self.m, self.seed, self.stream)
 
 
@@ -149,6 +162,49 @@ def workload(name: str) -> Workload:
 def _uniform(x: np.ndarray) -> np.ndarray:
     """Top 53 bits of a draw as a double in [0, 1)."""
     return (x >> np.uint64(11)).astype(np.float64) * (1.0 / 9007199254740992.0)
+
+
+@dataclass(frozen=True)
+class Request:
+    """One request of the serving stream: arrival time (s), graph spec."""
+    id: int
+    arrival: float
+    workload: Workload
+
+
+def serve_requests(seconds: float = 60.0, rate: float = 2000.0, seed: int = 5,
+                   n_range: tuple[int, int] = (1000, 4_000_000), ef_range: tuple[float, float] = (4.0, 16.0),
+                   rmat_share: float = 0.7, limit: int | None = None) -> list[Request]:
+    """The serving stream: Poisson arrivals at `rate` per second for `seconds`;
+    request q has n log-uniform in n_range, edge factor U(ef_range), m = round(ef n)
+    generated pairs, R-MAT with probability rmat_share (scale = ceil(log2 n),
+    endpoints >= n redrawn) else uniform pairs with replacement.  Stream 0 of `seed`
+    drives the arrivals and specs (draws 4q .. 4q+3 for request q); request q's
+    edges use stream q + 1."""
+    out = []
+    lo, hi = math.log(n_range[0]), math.log(n_range[1])
+    t = 0.0
+    q = 0
+    chunk = 4096
+    while True:
+        d = draws(seed, 0, 4 * q, 4 * chunk)
+        u = _uniform(d).reshape(-1, 4)
+        for k in range(chunk):
+            gap = -math.log(1.0 - float(u[k, 0])) / rate
+            t += gap
+            if t >= seconds or (limit is not None and q >= limit):
+                return out
+            n = int(math.floor(math.exp(lo + (hi - lo) * float(u[k, 1]))))
+            n = max(n_range[0], min(n_range[1], n))
+            ef = ef_range[0] + (ef_range[1] - ef_range[0]) * float(u[k, 2])
+            m = int(round(ef * n))
+            if float(u[k, 3]) < rmat_share:
+                scale = max(1, int(math.ceil(math.log2(n))))
+                w = Workload(f"req{q}", "rmat", n, m, seed, q + 1, scale=scale)
+            else:
+                w = Workload(f"req{q}", "er_replace", n, m, seed, q + 1)
+            out.append(Request(q, t, w))
+            q += 1
 
 
 def batch_workloads(G: int = 20000, seed: int = 4) -> list[Workload]:

@@ -22,6 +22,10 @@
  * the redraw attempt.  A pair with an endpoint >= n (n not a power of two) is
  * redrawn with r + 1; after 64 attempts the endpoints are reduced modulo n.
  *
+ * ER with replacement (the serving stream): pair i is draw i split into
+ * u = (hi32 * n) >> 32 and v = (lo32 * n) >> 32; loops and repeats are kept in the
+ * list (the counting library drops them).
+ *
  * ER G(n, m): m distinct unordered pairs {u != v}, uniform without replacement.
  *  - when 4m >= C(n,2) (dense) every pair index p in [0, C(n,2)) (row-major over
  *    u < v) gets the key draw(p); the m pairs with the smallest (key, p) are
@@ -91,6 +95,17 @@ void gg_rmat(uint64_t seed, uint64_t stream, int scale, int64_t n, int64_t e0, i
 #pragma omp parallel for schedule(static)
     for (int64_t k = 0; k < count; ++k)
         rmat_pair(key, e0 + k, scale, n, ta, tab, tabc, &src[k], &dst[k]);
+}
+
+/* ER with replacement: pairs i in [i0, i0 + count). */
+void gg_er_replace(uint64_t seed, uint64_t stream, int64_t n, int64_t i0, int64_t count, int32_t* src, int32_t* dst) {
+    uint64_t key = gg_stream_key(seed, stream);
+#pragma omp parallel for schedule(static)
+    for (int64_t k = 0; k < count; ++k) {
+        uint64_t x = gg_draw(key, (uint64_t)(i0 + k));
+        src[k] = (int32_t)(((x >> 32) * (uint64_t)n) >> 32);
+        dst[k] = (int32_t)(((x & 0xffffffffu) * (uint64_t)n) >> 32);
+    }
 }
 
 typedef struct {

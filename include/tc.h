@@ -271,6 +271,71 @@ tc_status tc_batch_run(int32_t G, const int32_t* n, const int64_t* edge_off, con
 void tc_release_cached_graphs(void);
 
 /*
+ * Device-side generation of the synthetic inputs of the serving stream (an
+ * addition of this library; the paper's graphs come from files).  Writes m pairs
+ * (device memory) of an R-MAT graph (a, b, c) = (0.57, 0.19, 0.19) over n vertices
+ * (scale ceil(log2 n), endpoints >= n redrawn) or m uniform pairs with
+ * replacement, from the counter-based SplitMix64 stream (seed, stream_id); the
+ * host generator of the test suite produces the same pairs.  Stream-ordered.
+ */
+enum { TC_GEN_RMAT = 0, TC_GEN_ER_REPLACE = 1 };
+tc_status tc_generate_edges(int kind, int32_t n, int64_t m, uint64_t seed, uint64_t stream_id, int32_t* src,
+                            int32_t* dst, void* cuda_stream);
+
+/*
+ * Serving (north-star pattern "serving"; the paper has no counterpart): a request
+ * loop that accepts TC/LCC jobs on graphs of different sizes as they arrive.
+ * `slots` worker threads, each with its own CUDA stream on the device current at
+ * start, take the oldest waiting request as soon as they are free and the device
+ * memory budget admits it (estimate 24 m + 112 n bytes + 8 MiB per request), so
+ * requests arriving while others run are admitted as slots and memory free up and
+ * their work overlaps on the device.  A request larger than the whole budget runs
+ * alone.  Each request's graph is generated on the device (tc_generate_edges),
+ * counted through this ABI and released; the result carries T, the number of
+ * distinct edges, order-independent checksums of t[] and LCC[] (sum over v of
+ * SplitMix64-mix(v * 0x9e3779b97f4a7c15 ^ x_v), x_v = t[v] or the bits of LCC[v]),
+ * and timestamps in seconds on the server's steady clock.
+ */
+typedef struct tc_server tc_server;
+typedef struct tc_request {
+    int64_t id;          /* caller's id, returned with the result */
+    int32_t kind;        /* TC_GEN_RMAT or TC_GEN_ER_REPLACE */
+    int32_t n;           /* vertices */
+    int64_t m;           /* generated pairs */
+    uint64_t seed;
+    uint64_t stream_id;
+} tc_request;
+typedef struct tc_result {
+    int64_t id;
+    int32_t status;      /* tc_status of the request */
+    int32_t slot;        /* worker that ran it */
+    uint64_t T;
+    int64_t m_simple;
+    uint64_t t_hash;
+    uint64_t lcc_hash;
+    double submit_s, start_s, end_s;
+    uint64_t bytes;      /* admission estimate */
+} tc_result;
+typedef struct tc_server_stats {
+    int32_t slots;
+    uint64_t budget_bytes;
+    uint64_t submitted, completed, running, queued, max_queue;
+    uint64_t peak_bytes, in_flight_bytes;  /* admitted estimates */
+    double clock_s;
+} tc_server_stats;
+
+tc_status tc_server_start(uint64_t hbm_budget_bytes, int32_t slots, tc_server** out);
+/* Queues a request (non-blocking).  TC_EBUSY after tc_server_stop began. */
+tc_status tc_server_submit(tc_server* s, const tc_request* r);
+/* Moves up to max finished results into out (non-blocking); *count receives how many. */
+tc_status tc_server_poll(tc_server* s, tc_result* out, int32_t max, int32_t* count);
+/* Waits until at least `completed` requests have finished (TC_ETIMEOUT after timeout_s). */
+tc_status tc_server_wait(tc_server* s, int64_t completed, double timeout_s);
+tc_status tc_server_get_stats(tc_server* s, tc_server_stats* out);
+/* Stops accepting, finishes every queued request, joins the workers, frees s. */
+tc_status tc_server_stop(tc_server* s);
+
+/*
  * Count without allocating (an addition of this library; the paper has no
  * counterpart).  For callers that cannot allocate device memory while they run: a
  * program that has handed all free HBM to its own caching allocator, code being

@@ -30,7 +30,33 @@ EXPORTS = ["tc_graph_create_from_edges", "tc_graph_create_from_csr", "tc_count",
            "tc_last_error_detail", "tc_graph_set_strategy", "tc_graph_last_timing",
            "tc_graph_plan_stats", "tc_launch_count", "tc_graph_set_hubs", "tc_count_noalloc",
            "tc_batch_create", "tc_batch_count", "tc_batch_size", "tc_graph_get_tuning",
-           "tc_graph_set_tuning", "tc_graph_autotune", "tc_batch_run", "tc_release_cached_graphs"]
+           "tc_graph_set_tuning", "tc_graph_autotune", "tc_batch_run", "tc_release_cached_graphs",
+           "tc_generate_edges", "tc_server_start", "tc_server_submit", "tc_server_poll", "tc_server_wait",
+           "tc_server_get_stats", "tc_server_stop"]
+TC_GEN_RMAT, TC_GEN_ER_REPLACE = 0, 1
+GEN_KINDS = {"rmat": TC_GEN_RMAT, "er_replace": TC_GEN_ER_REPLACE}
+
+
+class TcRequest(ctypes.Structure):
+    _fields_ = [("id", ctypes.c_int64), ("kind", ctypes.c_int32), ("n", ctypes.c_int32), ("m", ctypes.c_int64),
+                ("seed", ctypes.c_uint64), ("stream_id", ctypes.c_uint64)]
+
+
+class TcResult(ctypes.Structure):
+    _fields_ = [("id", ctypes.c_int64), ("status", ctypes.c_int32), ("slot", ctypes.c_int32),
+                ("T", ctypes.c_uint64), ("m_simple", ctypes.c_int64), ("t_hash", ctypes.c_uint64),
+                ("lcc_hash", ctypes.c_uint64), ("submit_s", ctypes.c_double), ("start_s", ctypes.c_double),
+                ("end_s", ctypes.c_double), ("bytes", ctypes.c_uint64)]
+
+    def to_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class TcServerStats(ctypes.Structure):
+    _fields_ = [("slots", ctypes.c_int32), ("budget_bytes", ctypes.c_uint64), ("submitted", ctypes.c_uint64),
+                ("completed", ctypes.c_uint64), ("running", ctypes.c_uint64), ("queued", ctypes.c_uint64),
+                ("max_queue", ctypes.c_uint64), ("peak_bytes", ctypes.c_uint64),
+                ("in_flight_bytes", ctypes.c_uint64), ("clock_s", ctypes.c_double)]
 TC_RUN_GRAPH = 1
 
 
@@ -131,6 +157,20 @@ def load(path: str | None = None):
     lib.tc_batch_run.argtypes = [i32, P, P, P, P, P, P, P, TP, P, ctypes.c_int]
     lib.tc_release_cached_graphs.restype = None
     lib.tc_release_cached_graphs.argtypes = []
+    lib.tc_generate_edges.restype = st
+    lib.tc_generate_edges.argtypes = [ctypes.c_int, i32, i64, u64, u64, P, P, P]
+    lib.tc_server_start.restype = st
+    lib.tc_server_start.argtypes = [u64, i32, ctypes.POINTER(P)]
+    lib.tc_server_submit.restype = st
+    lib.tc_server_submit.argtypes = [P, ctypes.POINTER(TcRequest)]
+    lib.tc_server_poll.restype = st
+    lib.tc_server_poll.argtypes = [P, ctypes.POINTER(TcResult), i32, ctypes.POINTER(i32)]
+    lib.tc_server_wait.restype = st
+    lib.tc_server_wait.argtypes = [P, i64, ctypes.c_double]
+    lib.tc_server_get_stats.restype = st
+    lib.tc_server_get_stats.argtypes = [P, ctypes.POINTER(TcServerStats)]
+    lib.tc_server_stop.restype = st
+    lib.tc_server_stop.argtypes = [P]
     lib.tc_count_noalloc.restype = st
     lib.tc_count_noalloc.argtypes = [i32, i64, P, P, ctypes.POINTER(u64), P, P, P]
     _lib = lib
@@ -347,6 +387,53 @@ def tc_batch_run(n, edge_off, src, dst, T_out, t_out=None, lcc_out=None, tuning=
 
 def tc_release_cached_graphs() -> None:
     load().tc_release_cached_graphs()
+
+
+def tc_generate_edges(kind, n: int, m: int, seed: int, stream_id: int, src, dst, stream=None) -> None:
+    """Device-side generation into int32 CUDA tensors src/dst of length >= m."""
+    load()
+    kind = GEN_KINDS[kind] if isinstance(kind, str) else kind
+    (ps, pd), k = _ptr_kind(src, dst)
+    if k != TC_MEM_DEVICE:
+        raise ValueError("tc_generate_edges writes device buffers")
+    _check(_lib.tc_generate_edges(kind, n, m, seed, stream_id, ps, pd, _stream_ptr(stream)))
+
+
+class Server:
+    """Serving loop (tc_server_*): requests are graph specs generated on the device."""
+
+    def __init__(self, hbm_budget_bytes: int, slots: int = 4):
+        load()
+        self._h = ctypes.c_void_p()
+        _check(_lib.tc_server_start(int(hbm_budget_bytes), int(slots), ctypes.byref(self._h)))
+
+    def submit(self, rid: int, workload) -> None:
+        """workload: graphgen.Workload of kind "rmat" or "er_replace"."""
+        r = TcRequest(rid, GEN_KINDS[workload.kind], workload.n, workload.m, workload.seed, workload.stream)
+        _check(_lib.tc_server_submit(self._h, ctypes.byref(r)))
+
+    def poll(self, max_results: int = 4096) -> list[dict]:
+        buf = (TcResult * max_results)()
+        cnt = ctypes.c_int32()
+        _check(_lib.tc_server_poll(self._h, buf, max_results, ctypes.byref(cnt)))
+        return [buf[i].to_dict() for i in range(cnt.value)]
+
+    def wait(self, completed: int, timeout_s: float) -> bool:
+        st = _lib.tc_server_wait(self._h, int(completed), float(timeout_s))
+        if st == TC_ETIMEOUT:
+            return False
+        _check(st)
+        return True
+
+    def stats(self) -> dict:
+        s = TcServerStats()
+        _check(_lib.tc_server_get_stats(self._h, ctypes.byref(s)))
+        return {k: getattr(s, k) for k, _ in s._fields_}
+
+    def stop(self) -> None:
+        if self._h:
+            _check(_lib.tc_server_stop(self._h))
+            self._h = ctypes.c_void_p()
 
 
 def tc_launch_count() -> int:

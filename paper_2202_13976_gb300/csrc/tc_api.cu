@@ -79,6 +79,13 @@ tc_status init_device(int dev, DeviceState** out) {
 
 }  // namespace
 
+namespace tcg {
+cudaMemPool_t device_pool(int dev) {
+    DeviceState* D = nullptr;
+    return init_device(dev, &D) == TC_OK ? D->pool : nullptr;
+}
+}  // namespace tcg
+
 struct tc_graph {
     int device = 0;
     cudaStream_t stream = nullptr;

@@ -148,6 +148,14 @@ void launch_run_status(const DevStats* stats, const int* batch_err, int* status,
 void launch_batch_T(int32_t G, const int32_t* vbase, const int32_t* rank, const unsigned long long* t_rank,
                     unsigned long long* T_out, int* err, const Launch& L);
 
+// ---- device generators (tc_gen.cu) and serving (tc_serve.cu, tc_api.cu) ---------
+cudaError_t launch_generate(int kind, int32_t n, int64_t m, unsigned long long seed, unsigned long long stream_id,
+                            int32_t* src, int32_t* dst, const Launch& L);
+// The library's stream-ordered pool of a device (initialising the device state).
+cudaMemPool_t device_pool(int dev);
+// Device memory a serving request is admitted with.
+uint64_t serve_estimate_bytes(int32_t n, int64_t m);
+
 // Kernel launch accounting (tc_launch_count).
 void count_launch(int k = 1);
 uint64_t launch_total();
