@@ -108,9 +108,7 @@ struct tc_graph {
     uint32_t* hub_cur = nullptr;
     int32_t* big_list = nullptr;
     int32_t* med_list = nullptr;
-    int32_t* in_u = nullptr;
-    int32_t* in_b = nullptr;
-    int32_t* in_e = nullptr;
+    int4* in_rec = nullptr;
     void* plan_tmp = nullptr;
     unsigned long long* t_rank = nullptr;
     DevStats* stats = nullptr;
@@ -224,8 +222,7 @@ tc_status build_graph(tc_graph* g, const int32_t* src, const int32_t* dst, int64
         (st = dalloc(g, &g->small_list[2], nn, &keep)) || (st = dalloc(g, &g->cta_list, nn, &keep)) ||
         (st = dalloc(g, &g->hub_cnt, hc + 1, &keep)) || (st = dalloc(g, &g->hub_start, hc + 1, &keep)) ||
         (st = dalloc(g, &g->hub_cur, hc + 1, &keep)) || (st = dalloc(g, &g->big_list, hc + 1, &keep)) ||
-        (st = dalloc(g, &g->med_list, hc + 1, &keep)) || (st = dalloc(g, &g->in_u, (size_t)m, &keep)) ||
-        (st = dalloc(g, &g->in_b, (size_t)m, &keep)) || (st = dalloc(g, &g->in_e, (size_t)m, &keep)) ||
+        (st = dalloc(g, &g->med_list, hc + 1, &keep)) || (st = dalloc(g, &g->in_rec, (size_t)m, &keep)) ||
         (st = dalloc(g, (char**)&g->plan_tmp, scan_tmp_bytes((int64_t)hc + 1), &keep)) ||
         (st = dalloc(g, &g->t_rank, nn, &keep)))
         return st;
@@ -242,7 +239,7 @@ tc_status build_graph(tc_graph* g, const int32_t* src, const int32_t* dst, int64
     if ((st = dalloc(g, &B.dmulti, nn, &scratch)) || (st = dalloc(g, &B.keys, nn, &scratch)) ||
         (st = dalloc(g, &B.keys_alt, nn, &scratch)) || (st = dalloc(g, &B.rowcnt, nn + 1, &scratch)) ||
         (st = dalloc(g, &B.cursor, nn, &scratch)) || (st = dalloc(g, &B.longlist, nn, &scratch)) ||
-        (st = dalloc(g, &B.midlist, nn, &scratch)) ||
+        (st = dalloc(g, &B.midlist, nn, &scratch)) || (st = dalloc(g, &B.dupin, nn, &scratch)) ||
         (st = dalloc(g, &tmp, tmp_bytes, &scratch))) {
         free_list(g, &scratch);
         return st;
@@ -296,9 +293,7 @@ CountBuffers count_buffers(tc_graph* g) {
     C.hub_cur = g->hub_cur;
     C.big_list = g->big_list;
     C.med_list = g->med_list;
-    C.in_u = g->in_u;
-    C.in_b = g->in_b;
-    C.in_e = g->in_e;
+    C.in_rec = g->in_rec;
     C.tmp = g->plan_tmp;
     C.t_rank = g->t_rank;
     C.stats = g->stats;
@@ -473,6 +468,10 @@ tc_status tc_count(tc_graph* g, uint64_t* T_out) {
     if (st != TC_OK) return st;
     DevStats h;
     if ((st = read_stats(g, &h)) != TC_OK) return st;
+    if (h.err & ERR_OVERFLOW) {
+        snprintf(g_last_error, sizeof(g_last_error), "internal count mismatch (overflow guard)");
+        return TC_EINTERNAL;
+    }
     if (h.sum_t % 3 != 0) {
         snprintf(g_last_error, sizeof(g_last_error), "sum of t is not a multiple of 3");
         return TC_EINTERNAL;

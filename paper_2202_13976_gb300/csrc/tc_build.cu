@@ -11,8 +11,9 @@
 //                   counting sort on the source rank
 //  4. segsort       each row is sorted (bitonic network in shared memory or, for very
 //                   long rows, in global memory) and repeated entries are removed;
-//                   the simple-graph degree of every vertex is counted from the
-//                   surviving entries
+//                   the simple-graph degree of every vertex is its distinct
+//                   out-entries plus its in-entries before deduplication minus the
+//                   repeats dropped at it
 // Any strict total order finds each triangle once; the (degree, id) order keeps
 // every oriented row short (d+(u) <= sqrt(2m)).  The degree used for the order is
 // the count of non-loop input pairs at a vertex, which equals the simple degree
@@ -108,10 +109,16 @@ __global__ void k_rank_keys(const uint32_t* __restrict__ dmulti, int32_t n, uint
         keys[i] = ((uint64_t)dmulti[i] << 32) | (uint32_t)i;
 }
 
-__global__ void k_rank_invert(const uint64_t* __restrict__ sorted, int32_t n, int32_t* __restrict__ rank) {
+// rank[id] = position in (degree, id) order; dmulti is rewritten in rank space
+// (dmulti_rank[r] = degree of the vertex of rank r, the high word of its key).
+__global__ void k_rank_invert(const uint64_t* __restrict__ sorted, int32_t n, int32_t* __restrict__ rank,
+                              uint32_t* __restrict__ dmulti) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += stride)
-        rank[(uint32_t)sorted[r]] = (int32_t)r;
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += stride) {
+        const uint64_t key = sorted[r];
+        rank[(uint32_t)key] = (int32_t)r;
+        dmulti[r] = (uint32_t)(key >> 32);
+    }
 }
 
 __global__ void k_orient_count(const int32_t* __restrict__ src, const int32_t* __restrict__ dst, int64_t m,
@@ -135,8 +142,19 @@ __global__ void k_orient_scatter(const int32_t* __restrict__ src, const int32_t*
         int32_t a = rank[u], b = rank[v];
         int32_t s = min(a, b), t = max(a, b);
         int64_t p = rowstart[s] + atomicAdd(&cursor[s], 1u);
-        col[p] = t;
+        if (p < rowstart[s + 1]) col[p] = t;  // always true unless the two passes disagree
     }
+}
+
+// Simple degree in rank space: distinct out-entries + in-entries before
+// deduplication (non-loop pairs at v minus those where v is the source) - repeats
+// dropped at v.  dmulti, rowcnt, rowlen and dupin are all indexed by rank here.
+__global__ void k_degree(int32_t n, const int32_t* __restrict__ rowlen, const uint32_t* __restrict__ dmulti,
+                         const uint32_t* __restrict__ rowcnt, const uint32_t* __restrict__ dupin,
+                         int32_t* __restrict__ deg) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride)
+        deg[v] = rowlen[v] + (int32_t)(dmulti[v] - rowcnt[v]) - (int32_t)dupin[v];
 }
 
 struct WarpSync {
@@ -242,9 +260,9 @@ __device__ __forceinline__ void reg_bitonic(int32_t (&v)[N]) {
 }
 
 // Sorts a row of len <= N entries in registers, writes the distinct entries back
-// to its start and counts each kept entry at its target; returns how many were kept.
+// to its start and counts each dropped repeat at its target; returns how many were kept.
 template <int N>
-__device__ __forceinline__ int sort_row_regs(int32_t* __restrict__ row, int len, int32_t* __restrict__ deg) {
+__device__ __forceinline__ int sort_row_regs(int32_t* __restrict__ row, int len, uint32_t* __restrict__ dupin) {
     int32_t v[N];
 #pragma unroll
     for (int i = 0; i < N; ++i) v[i] = i < len ? row[i] : INT_MAX;
@@ -253,9 +271,11 @@ __device__ __forceinline__ int sort_row_regs(int32_t* __restrict__ row, int len,
     int32_t prev = INT_MIN;
 #pragma unroll
     for (int i = 0; i < N; ++i) {
-        if (i < len && v[i] != prev) {
-            row[kept++] = v[i];
-            atomicAdd(&deg[v[i]], 1);
+        if (i < len) {
+            if (v[i] != prev)
+                row[kept++] = v[i];
+            else
+                atomicAdd(&dupin[v[i]], 1u);
         }
         prev = v[i];
     }
@@ -267,7 +287,7 @@ __device__ __forceinline__ int sort_row_regs(int32_t* __restrict__ row, int len,
 __global__ void __launch_bounds__(256) k_segsort_thread(int32_t n, const int64_t* __restrict__ rowstart,
                                                         const uint32_t* __restrict__ rowcnt, int32_t* __restrict__ col,
                                                         int32_t* __restrict__ rowlen, int2* __restrict__ rowinfo,
-                                                        int32_t* __restrict__ deg, int32_t* __restrict__ midlist,
+                                                        uint32_t* __restrict__ dupin, int32_t* __restrict__ midlist,
                                                         int32_t* __restrict__ longlist, DevStats* stats) {
     unsigned long long kept_total = 0;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -282,10 +302,9 @@ __global__ void __launch_bounds__(256) k_segsort_thread(int32_t n, const int64_t
         if (lng) longlist[pl] = (int32_t)r;
         if (r < n && len <= 16) {
             const int64_t base = rowstart[r];
-            const int kept = len <= 8 ? sort_row_regs<8>(col + base, len, deg) : sort_row_regs<16>(col + base, len, deg);
+            const int kept = len <= 8 ? sort_row_regs<8>(col + base, len, dupin) : sort_row_regs<16>(col + base, len, dupin);
             rowlen[r] = kept;
             rowinfo[r] = make_int2((int)base, kept);
-            if (kept) atomicAdd(&deg[r], kept);
             kept_total += (unsigned long long)kept;
         }
     }
@@ -297,7 +316,7 @@ __global__ void __launch_bounds__(256) k_segsort_thread(int32_t n, const int64_t
 __global__ void __launch_bounds__(SEG_WARPS * 32) k_segsort_warp(const int64_t* __restrict__ rowstart,
                                                                  const uint32_t* __restrict__ rowcnt,
                                                                  int32_t* __restrict__ col, int32_t* __restrict__ rowlen,
-                                                                 int2* __restrict__ rowinfo, int32_t* __restrict__ deg,
+                                                                 int2* __restrict__ rowinfo, uint32_t* __restrict__ dupin,
                                                                  const int32_t* __restrict__ midlist, DevStats* stats) {
     __shared__ int32_t sh[SEG_WARPS][WARP_SORT_MAX];
     const int lane = lane_id(), w = threadIdx.x >> 5;
@@ -318,16 +337,15 @@ __global__ void __launch_bounds__(SEG_WARPS * 32) k_segsort_warp(const int64_t* 
             int i = c + lane;
             bool keep = i < len && (i == 0 || s[i] != s[i - 1]);
             unsigned mk = __ballot_sync(FULL, keep);
-            if (keep) {
+            if (keep)
                 col[base + kept + __popc(mk & lanemask_lt())] = s[i];
-                atomicAdd(&deg[s[i]], 1);
-            }
+            else if (i < len)
+                atomicAdd(&dupin[s[i]], 1u);
             kept += __popc(mk);
         }
         if (lane == 0) {
             rowlen[r] = kept;
             rowinfo[r] = make_int2((int)base, kept);
-            atomicAdd(&deg[r], kept);
             kept_total += (unsigned long long)kept;
         }
         __syncwarp();
@@ -340,7 +358,7 @@ __global__ void __launch_bounds__(SEG_WARPS * 32) k_segsort_warp(const int64_t* 
 __global__ void __launch_bounds__(1024) k_segsort_block(const int64_t* __restrict__ rowstart,
                                                         const uint32_t* __restrict__ rowcnt,
                                                         int32_t* __restrict__ col, int32_t* __restrict__ rowlen,
-                                                        int2* __restrict__ rowinfo, int32_t* __restrict__ deg,
+                                                        int2* __restrict__ rowinfo, uint32_t* __restrict__ dupin,
                                                         const int32_t* __restrict__ longlist,
                                                         DevStats* stats) {
     extern __shared__ int32_t sh[];  // CTA_SORT_MAX entries
@@ -383,10 +401,10 @@ __global__ void __launch_bounds__(1024) k_segsort_block(const int64_t* __restric
             }
             int32_t last = s[min(c + (int)blockDim.x, len) - 1];
             __syncthreads();
-            if (keep) {
+            if (keep)
                 col[base + kept + before + __popc(mk & lanemask_lt())] = x;
-                atomicAdd(&deg[x], 1);
-            }
+            else if (i < len)
+                atomicAdd(&dupin[x], 1u);
             kept += tot;
             if (threadIdx.x == 0) boundary = last;
             __syncthreads();
@@ -394,7 +412,6 @@ __global__ void __launch_bounds__(1024) k_segsort_block(const int64_t* __restric
         if (threadIdx.x == 0) {
             rowlen[r] = kept;
             rowinfo[r] = make_int2((int)base, kept);
-            atomicAdd(&deg[r], kept);
             atomicAdd(&stats->m_simple, (unsigned long long)kept);
         }
         __syncthreads();
@@ -424,14 +441,14 @@ void launch_rank(const BuildBuffers& B, int deg_bits, const Launch& L) {
     k_rank_keys<<<grid_for(B.n, THREADS, L.sms), THREADS, 0, L.stream>>>(B.dmulti, B.n, B.keys); count_launch();
     // the keys start in id order, so a stable sort on the degree bits yields (degree, id)
     uint64_t* sorted = radix_sort_u64(B.keys, B.keys_alt, B.n, 32, 32 + deg_bits, B.tmp, L);
-    k_rank_invert<<<grid_for(B.n, THREADS, L.sms), THREADS, 0, L.stream>>>(sorted, B.n, B.rank); count_launch();
+    k_rank_invert<<<grid_for(B.n, THREADS, L.sms), THREADS, 0, L.stream>>>(sorted, B.n, B.rank, B.dmulti); count_launch();
 }
 
 void launch_orient(const BuildBuffers& B, const Launch& L) {
     if (B.n <= 0) return;
     cudaMemsetAsync(B.rowcnt, 0, sizeof(uint32_t) * (size_t)B.n, L.stream);
     cudaMemsetAsync(B.cursor, 0, sizeof(uint32_t) * (size_t)B.n, L.stream);
-    cudaMemsetAsync(B.deg, 0, sizeof(int32_t) * (size_t)B.n, L.stream);
+    cudaMemsetAsync(B.dupin, 0, sizeof(uint32_t) * (size_t)B.n, L.stream);
     if (B.m > 0) {
         k_orient_count<<<grid_for(B.m, THREADS, L.sms), THREADS, 0, L.stream>>>(B.src, B.dst, B.m, B.n, B.rank,
                                                                               B.rowcnt); count_launch(); }
@@ -440,13 +457,16 @@ void launch_orient(const BuildBuffers& B, const Launch& L) {
         k_orient_scatter<<<grid_for(B.m, THREADS, L.sms), THREADS, 0, L.stream>>>(
             B.src, B.dst, B.m, B.n, B.rank, B.rowstart, B.cursor, B.col); count_launch(); }
     k_segsort_thread<<<grid_for(B.n, THREADS, L.sms), THREADS, 0, L.stream>>>(
-        B.n, B.rowstart, B.rowcnt, B.col, B.rowlen, B.rowinfo, B.deg, B.midlist, B.longlist, B.stats);
+        B.n, B.rowstart, B.rowcnt, B.col, B.rowlen, B.rowinfo, B.dupin, B.midlist, B.longlist, B.stats);
     count_launch();
     k_segsort_warp<<<L.sms * 4, SEG_WARPS * 32, 0, L.stream>>>(B.rowstart, B.rowcnt, B.col, B.rowlen, B.rowinfo,
-                                                              B.deg, B.midlist, B.stats);
+                                                              B.dupin, B.midlist, B.stats);
     count_launch();
     k_segsort_block<<<L.sms * 2, 1024, CTA_SORT_MAX * sizeof(int32_t), L.stream>>>(
-        B.rowstart, B.rowcnt, B.col, B.rowlen, B.rowinfo, B.deg, B.longlist, B.stats);
+        B.rowstart, B.rowcnt, B.col, B.rowlen, B.rowinfo, B.dupin, B.longlist, B.stats);
+    count_launch();
+    k_degree<<<grid_for(B.n, THREADS, L.sms), THREADS, 0, L.stream>>>(B.n, B.rowlen, B.dmulti, B.rowcnt, B.dupin,
+                                                                     B.deg);
     count_launch();
 }
 

@@ -71,6 +71,7 @@ struct BuildBuffers {
     uint32_t* cursor;     // n
     int32_t* longlist;    // n
     int32_t* midlist;     // n
+    uint32_t* dupin;      // n: repeated entries dropped at each target
     void* tmp;            // max(scan_tmp_bytes(n + 1), radix_tmp_bytes(n))
     // outputs (kept by the graph)
     int32_t* rank;        // n: rank of each input id in (degree, id) order
@@ -121,9 +122,7 @@ struct CountBuffers {
     uint32_t* hub_cur;       // hub_cap + 1
     int32_t* big_list;       // hub_cap: big hubs, highest rank first
     int32_t* med_list;       // hub_cap: the other hubs, highest rank first
-    int32_t* in_u;           // m: source vertex of the in-edge
-    int32_t* in_b;           // m: first suffix entry (index into col)
-    int32_t* in_e;           // m: end of the source row (index into col)
+    int4* in_rec;            // m: in-edge {u, first suffix entry, end of N+(u), 0} (indices into col)
     void* tmp;               // scan scratch, scan_tmp_bytes(hub_cap + 1)
     unsigned long long* t_rank;  // n
     DevStats* stats;

@@ -341,13 +341,12 @@ __global__ void k_hub_indeg(int32_t n, int32_t hub_cap, const int32_t* __restric
     }
 }
 
-// Every oriented entry (u -> v) with v a hub becomes an in-edge of v: (u, the index
-// after v in N+(u), the end of N+(u)).  One warp per row.
+// Every oriented entry (u -> v) with v a hub becomes an in-edge record of v:
+// {u, index after v in N+(u), end of N+(u), 0}, one 16-byte store.  One warp per row.
 __global__ void k_hub_scatter(int32_t n, int32_t hub_cap, const int64_t* __restrict__ rowstart,
                               const int32_t* __restrict__ rowlen, const int32_t* __restrict__ col,
                               const int64_t* __restrict__ hub_start, uint32_t* __restrict__ hub_cur,
-                              int32_t* __restrict__ in_u, int32_t* __restrict__ in_b, int32_t* __restrict__ in_e,
-                              DevStats* stats) {
+                              int4* __restrict__ in_rec, DevStats* stats) {
     const int32_t R = n - (int32_t)stats->hub_count;
     const int lane = lane_id();
     const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
@@ -361,9 +360,10 @@ __global__ void k_hub_scatter(int32_t n, int32_t hub_cap, const int64_t* __restr
             if (v >= R) {
                 const int i = v - (n - hub_cap);
                 const int64_t slot = hub_start[i] + atomicAdd(&hub_cur[i], 1u);
-                in_u[slot] = (int32_t)u;
-                in_b[slot] = (int32_t)(base + p + 1);
-                in_e[slot] = (int32_t)(base + du);
+                if (slot < hub_start[i + 1])  // counts and entries disagree only on a bug: never write outside
+                    in_rec[slot] = make_int4((int32_t)u, (int32_t)(base + p + 1), (int32_t)(base + du), 0);
+                else
+                    atomicOr(&stats->err, ERR_OVERFLOW);
             }
         }
     }
@@ -602,16 +602,15 @@ struct ListProbe {
 // entries at a time.  Matches add to cnt[p] (or t[x] when cnt is null) and to the
 // per-in-edge total, which goes to t[u].  Returns the batch total (all lanes).
 template <class Probe>
-__device__ uint32_t hub_batch(int64_t k0, int64_t e1, const int32_t* __restrict__ in_u,
-                              const int32_t* __restrict__ in_b, const int32_t* __restrict__ in_e,
+__device__ uint32_t hub_batch(int64_t k0, int64_t e1, const int4* __restrict__ in_rec,
                               const int32_t* __restrict__ col, int32_t maxv, const Probe& probe, uint32_t* cnt,
                               unsigned long long* __restrict__ t, uint32_t* cw) {
     const int lane = lane_id();
     const int64_t k = k0 + lane;
-    const bool ok = k < e1;
-    int32_t uu = ok ? in_u[k] : 0;
-    int32_t b0 = ok ? in_b[k] : 0;
-    int a = ok ? in_e[k] - b0 : 0;
+    const int4 rec = k < e1 ? in_rec[k] : make_int4(0, 0, 0, 0);
+    int32_t uu = rec.x;
+    int32_t b0 = rec.y;
+    int a = rec.z - rec.y;
     uint32_t total_c = 0;
     unsigned longm = __ballot_sync(FULL, a >= 32);
     while (longm) {
@@ -620,20 +619,32 @@ __device__ uint32_t hub_batch(int64_t k0, int64_t e1, const int32_t* __restrict_
         const int32_t bL = __shfl_sync(FULL, b0, L);
         const int aL = __shfl_sync(FULL, a, L);
         uint32_t c = 0;
-        for (int o0 = 0; o0 < aL; o0 += 32) {
-            const int o = o0 + lane;
-            const int32_t x = o < aL ? col[bL + o] : INT_MAX;
-            if (x <= maxv) {
-                const int p = probe(x);
+        // two entries per lane per round: both loads are in flight before either is used
+        for (int o0 = 0; o0 < aL; o0 += 64) {
+            const int o1 = o0 + lane, o2 = o1 + 32;
+            const int32_t x1 = o1 < aL ? col[bL + o1] : INT_MAX;
+            const int32_t x2 = o2 < aL ? col[bL + o2] : INT_MAX;
+            if (x1 <= maxv) {
+                const int p = probe(x1);
                 if (p >= 0) {
                     if (cnt)
                         atomicAdd(&cnt[p], 1u);
                     else
-                        atomicAdd(&t[x], 1ull);
+                        atomicAdd(&t[x1], 1ull);
                     ++c;
                 }
             }
-            if (__any_sync(FULL, x > maxv)) break;  // the suffix is sorted
+            if (x2 <= maxv) {
+                const int p = probe(x2);
+                if (p >= 0) {
+                    if (cnt)
+                        atomicAdd(&cnt[p], 1u);
+                    else
+                        atomicAdd(&t[x2], 1ull);
+                    ++c;
+                }
+            }
+            if (__any_sync(FULL, x2 > maxv)) break;  // the suffix is sorted
         }
         c = __reduce_add_sync(FULL, c);
         total_c += c;
@@ -713,9 +724,7 @@ __global__ void __launch_bounds__(HUB_THREADS) k_tc_hub(int32_t n, int32_t hub_c
                                                         const int64_t* __restrict__ hub_start,
                                                         const int32_t* __restrict__ big_list,
                                                         const int32_t* __restrict__ med_list,
-                                                        const int32_t* __restrict__ in_u,
-                                                        const int32_t* __restrict__ in_b,
-                                                        const int32_t* __restrict__ in_e,
+                                                        const int4* __restrict__ in_rec,
                                                         unsigned long long* __restrict__ t, DevStats* stats,
                                                         int probe_mode) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -750,11 +759,11 @@ __global__ void __launch_bounds__(HUB_THREADS) k_tc_hub(int32_t n, int32_t hub_c
         if (!probe_mode) {
             const BitmapProbe P{sh.u.big.s.b.bm, sh.u.big.s.b.pre, v};
             for (int64_t bb = e0 + (int64_t)w * 32; bb < e1; bb += HUB_WARPS * 32)
-                vtot += hub_batch(bb, e1, in_u, in_b, in_e, col, maxv, P, cnt, t, sh.cw[w]);
+                vtot += hub_batch(bb, e1, in_rec, col, maxv, P, cnt, t, sh.cw[w]);
         } else {
             const ListProbe P{staged ? sh.u.big.s.list : col + base, dv};
             for (int64_t bb = e0 + (int64_t)w * 32; bb < e1; bb += HUB_WARPS * 32)
-                vtot += hub_batch(bb, e1, in_u, in_b, in_e, col, maxv, P, cnt, t, sh.cw[w]);
+                vtot += hub_batch(bb, e1, in_rec, col, maxv, P, cnt, t, sh.cw[w]);
         }
         if (lane == 0) sh.vt[w] = vtot;
         __syncthreads();
@@ -807,7 +816,7 @@ __global__ void __launch_bounds__(HUB_THREADS) k_tc_hub(int32_t n, int32_t hub_c
         const int32_t maxv = L[dv - 1];
         const ListProbe P{L, dv};
         unsigned long long vtot = 0;
-        for (int64_t bb = e0; bb < e1; bb += 32) vtot += hub_batch(bb, e1, in_u, in_b, in_e, col, maxv, P, cnt, t, sh.cw[w]);
+        for (int64_t bb = e0; bb < e1; bb += 32) vtot += hub_batch(bb, e1, in_rec, col, maxv, P, cnt, t, sh.cw[w]);
         __syncwarp();
         for (int p = lane; p < dv; p += 32) {
             const uint32_t c = cnt[p];
@@ -898,7 +907,7 @@ void launch_plan(const CountBuffers& C, const Strategy& S, const Launch& L) {
         scan_u32_to_i64(C.hub_cnt, C.hub_start, C.hub_cap, C.tmp, L);
         cudaMemsetAsync(C.hub_cur, 0, sizeof(uint32_t) * (size_t)C.hub_cap, L.stream);
         k_hub_scatter<<<grid_for((int64_t)C.n * 32, THREADS, L.sms), THREADS, 0, L.stream>>>(
-            C.n, C.hub_cap, C.rowstart, C.rowlen, C.col, C.hub_start, C.hub_cur, C.in_u, C.in_b, C.in_e, C.stats);
+            C.n, C.hub_cap, C.rowstart, C.rowlen, C.col, C.hub_start, C.hub_cur, C.in_rec, C.stats);
         count_launch();
         // hub_cur is free again: it holds the big flags, hub_cnt (still the in-degrees
         // until here) is overwritten by their exclusive scan
@@ -947,8 +956,8 @@ void launch_intersect(const CountBuffers& C, const Strategy& S, cudaEvent_t* ev,
     if (C.hub_cap > 0) {
         cudaMemsetAsync(&C.stats->hub_next, 0, 2 * sizeof(unsigned), L.stream);
         k_tc_hub<<<L.sms * 5, HUB_THREADS, sizeof(HubShared), L.stream>>>(
-            C.n, C.hub_cap, C.rowstart, C.rowlen, C.col, C.hub_start, C.big_list, C.med_list, C.in_u, C.in_b, C.in_e,
-            C.t_rank, C.stats, S.strat[TC_BUCKET_HUB] == TC_STRAT_PROBE ? 1 : 0);
+            C.n, C.hub_cap, C.rowstart, C.rowlen, C.col, C.hub_start, C.big_list, C.med_list, C.in_rec, C.t_rank,
+            C.stats, S.strat[TC_BUCKET_HUB] == TC_STRAT_PROBE ? 1 : 0);
         count_launch();
     }
     if (ev) cudaEventRecord(ev[PH_END], L.stream);
