@@ -126,6 +126,19 @@ class Clocks:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def aggregate_ranks(total_ms: float, steps: int, units_per_step: int, world: int, device=None):
+    """Slowest rank's time per step and the whole-job throughput: every rank runs its
+    own replica, so the job processes world * units_per_step units per step."""
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        tt = torch.tensor([total_ms], dtype=torch.float64, device=device)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        total_ms = float(tt.item())
+    ms_per_step = total_ms / steps
+    return ms_per_step, world * units_per_step / (ms_per_step / 1000.0)
+
+
 def apply_strategy(g, spec, tc):
     if not spec:
         return
@@ -247,13 +260,7 @@ def run_ours(args, rank, world, local):
         dist.barrier()
     clk = clocks.stop()
     step_ms = [a.elapsed_time(b) for a, b in evs]
-    total_ms = sum(step_ms)
-    if world > 1:
-        tt = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        total_ms = float(tt.item())
-    ms_per_step = total_ms / args.steps
-    value = world * m_simple / (ms_per_step / 1000.0)
+    ms_per_step, value = aggregate_ranks(sum(step_ms), args.steps, m_simple, world, dev)
 
     # dominant intersection kernel and its roofline (algorithmic bytes of the survey's
     # per-edge figure: 4 (d+u + d+v) adjacency bytes + 8 edge bytes + 16 offset bytes)
