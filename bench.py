@@ -226,6 +226,7 @@ def run_ours(args, rank, world, local):
             T = g.count()
             g.lcc(t_out, lcc_out)
             tim = g.timing()
+            tim.update({"build_" + k: v for k, v in g.build_timing().items()})
         finally:
             g.close()
         return T, tim

@@ -187,6 +187,14 @@ tc_status tc_graph_set_hubs(tc_graph* g, int32_t min_degree, int32_t max_hubs);
 tc_status tc_graph_last_timing(const tc_graph* g, float* ms, int count);
 
 /*
+ * Timing of the graph's build in milliseconds (CUDA events): ms[0] ingest and
+ * checks, ms[1] (degree, id) ranks, ms[2] row counts, ms[3] row fill, ms[4] row
+ * sort and deduplication, ms[5] degrees, ms[6] total.  count up to 7.  Errors:
+ * TC_EINVAL when the build was not timed (a batch recorded into a CUDA graph).
+ */
+tc_status tc_graph_build_timing(const tc_graph* g, float* ms, int count);
+
+/*
  * Work accounting of the planned intersection, per bucket (b = TC_BUCKET_*):
  *   edges[b]  oriented edges handled by bucket b
  *   ids[b]    sum over those edges (u, v) of |N+(u)| + |N+(v)|: the adjacency

@@ -32,7 +32,8 @@ EXPORTS = ["tc_graph_create_from_edges", "tc_graph_create_from_csr", "tc_count",
            "tc_batch_create", "tc_batch_count", "tc_batch_size", "tc_graph_get_tuning",
            "tc_graph_set_tuning", "tc_graph_autotune", "tc_batch_run", "tc_release_cached_graphs",
            "tc_generate_edges", "tc_server_start", "tc_server_submit", "tc_server_poll", "tc_server_wait",
-           "tc_server_get_stats", "tc_server_stop"]
+           "tc_server_get_stats", "tc_server_stop", "tc_graph_build_timing"]
+BUILD_PHASES = ["ingest_ms", "rank_ms", "count_ms", "fill_ms", "sort_ms", "degree_ms", "total_ms"]
 TC_GEN_RMAT, TC_GEN_ER_REPLACE = 0, 1
 GEN_KINDS = {"rmat": TC_GEN_RMAT, "er_replace": TC_GEN_ER_REPLACE}
 
@@ -134,6 +135,8 @@ def load(path: str | None = None):
     lib.tc_graph_set_strategy.argtypes = [P, ctypes.c_int, ctypes.c_int, ctypes.c_double]
     lib.tc_graph_last_timing.restype = st
     lib.tc_graph_last_timing.argtypes = [P, ctypes.POINTER(ctypes.c_float), ctypes.c_int]
+    lib.tc_graph_build_timing.restype = st
+    lib.tc_graph_build_timing.argtypes = [P, ctypes.POINTER(ctypes.c_float), ctypes.c_int]
     lib.tc_graph_set_hubs.restype = st
     lib.tc_graph_set_hubs.argtypes = [P, i32, i32]
     lib.tc_graph_plan_stats.restype = st
@@ -296,6 +299,12 @@ def tc_graph_last_timing(g: int) -> dict:
     ms = (ctypes.c_float * len(PHASES))()
     _check(_lib.tc_graph_last_timing(g, ms, len(PHASES)))
     return {k: ms[i] for i, k in enumerate(PHASES)}
+
+
+def tc_graph_build_timing(g: int) -> dict:
+    ms = (ctypes.c_float * len(BUILD_PHASES))()
+    _check(_lib.tc_graph_build_timing(g, ms, len(BUILD_PHASES)))
+    return {k: ms[i] for i, k in enumerate(BUILD_PHASES)}
 
 
 def tc_graph_plan_stats(g: int) -> dict:
@@ -487,6 +496,9 @@ class Graph:
 
     def plan_stats(self) -> dict:
         return tc_graph_plan_stats(self.handle)
+
+    def build_timing(self) -> dict:
+        return tc_graph_build_timing(self.handle)
 
     def tuning(self) -> dict:
         return tc_graph_get_tuning(self.handle)

@@ -118,6 +118,8 @@ struct tc_graph {
     Strategy strat{};
     cudaEvent_t ev[PH_EVENTS] = {};
     bool timed = false;
+    cudaEvent_t bev[BP_EVENTS] = {};  // build phases (not while recording a CUDA graph)
+    bool build_timed = false;
     // batch of graphs counted as one disjoint union (tc_batch_create)
     int32_t batch_G = -1;
     int32_t* batch_vbase = nullptr;   // device, G + 1
@@ -239,7 +241,9 @@ tc_status build_graph(tc_graph* g, const int32_t* src, const int32_t* dst, int64
     if ((st = dalloc(g, &B.dmulti, nn, &scratch)) || (st = dalloc(g, &B.keys, nn, &scratch)) ||
         (st = dalloc(g, &B.keys_alt, nn, &scratch)) || (st = dalloc(g, &B.rowcnt, nn + 1, &scratch)) ||
         (st = dalloc(g, &B.cursor, nn, &scratch)) || (st = dalloc(g, &B.longlist, nn, &scratch)) ||
-        (st = dalloc(g, &B.midlist, nn, &scratch)) || (st = dalloc(g, &B.dupin, nn, &scratch)) ||
+        (st = dalloc(g, &B.midlist, nn, &scratch)) || (st = dalloc(g, &B.midlist2, nn, &scratch)) ||
+        (st = dalloc(g, &B.dupin, nn, &scratch)) ||
+        (st = dalloc(g, &B.bcur, 256, &scratch)) || (st = dalloc(g, &B.pairs, (size_t)m, &scratch)) ||
         (st = dalloc(g, &tmp, tmp_bytes, &scratch))) {
         free_list(g, &scratch);
         return st;
@@ -252,9 +256,17 @@ tc_status build_graph(tc_graph* g, const int32_t* src, const int32_t* dst, int64
     B.col = g->col;
     B.deg = g->deg;
     B.stats = g->stats;
+    cudaEvent_t* bev = nullptr;
+    if (!g->capture) {
+        if (!g->bev[0])
+            for (int i = 0; i < BP_EVENTS; ++i) TC_CK(cudaEventCreate(&g->bev[i]));
+        bev = g->bev;
+        cudaEventRecord(bev[BP_START], g->stream);
+    }
     cudaMemsetAsync(g->stats, 0, sizeof(DevStats), g->stream);
     cudaMemsetAsync(B.dmulti, 0, sizeof(uint32_t) * nn, g->stream);
     launch_canon_degree(B, g->L);
+    if (bev) cudaEventRecord(bev[BP_INGEST], g->stream);
     int deg_bits = bits_for((unsigned)(2 * m < (int64_t)UINT32_MAX ? 2 * m : (int64_t)UINT32_MAX));
     if (checked) {
         DevStats h;
@@ -268,9 +280,18 @@ tc_status build_graph(tc_graph* g, const int32_t* src, const int32_t* dst, int64
             return TC_EINVAL;
         }
         deg_bits = bits_for(h.max_deg);
+        // flat degree distribution (max degree within 64x the mean): fill rows through
+        // buckets; skewed graphs keep the direct scatter, whose hot rows stay in cache
+        const double mean = n > 0 ? 2.0 * (double)m / (double)n : 0.0;
+        B.two_level_fill = m > 0 && (double)h.max_deg <= 64.0 * mean;
     }
     launch_rank(B, deg_bits, g->L);
-    launch_orient(B, g->L);
+    if (bev) cudaEventRecord(bev[BP_RANK], g->stream);
+    launch_orient(B, g->L, bev);
+    if (bev) {
+        cudaEventRecord(bev[BP_END], g->stream);
+        g->build_timed = true;
+    }
     free_list(g, &scratch);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail("build kernels", e);
@@ -347,6 +368,8 @@ void destroy(tc_graph* g) {
     free_list(g, &g->blocks);
     for (int i = 0; i < PH_EVENTS; ++i)
         if (g->ev[i]) cudaEventDestroy(g->ev[i]);
+    for (int i = 0; i < BP_EVENTS; ++i)
+        if (g->bev[i]) cudaEventDestroy(g->bev[i]);
     delete g;
 }
 
@@ -568,6 +591,16 @@ tc_status tc_graph_set_hubs(tc_graph* g, int32_t min_degree, int32_t max_hubs) {
     g->strat.hub_max = max_hubs < HUB_BM_BITS ? max_hubs : HUB_BM_BITS;
     g->planned = false;
     g->counted = false;
+    return TC_OK;
+}
+
+tc_status tc_graph_build_timing(const tc_graph* g, float* ms, int count) {
+    if (!g || !ms || count < 0 || !g->build_timed) return TC_EINVAL;
+    TC_CK(cudaEventSynchronize(g->bev[BP_END]));
+    float v[BP_EVENTS] = {};
+    for (int i = 1; i < BP_EVENTS; ++i) TC_CK(cudaEventElapsedTime(&v[i - 1], g->bev[i - 1], g->bev[i]));
+    TC_CK(cudaEventElapsedTime(&v[BP_EVENTS - 1], g->bev[BP_START], g->bev[BP_END]));
+    for (int i = 0; i < count && i < BP_EVENTS; ++i) ms[i] = v[i];
     return TC_OK;
 }
 

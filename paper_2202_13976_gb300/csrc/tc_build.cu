@@ -28,7 +28,7 @@ namespace tcg {
 namespace {
 
 constexpr int THREADS = 256;
-constexpr int WARP_SORT_MAX = 1024;   // rows up to this length: one warp, shared memory
+constexpr int WARP_SORT_MAX = 1024;   // rows up to this length: one warp, registers
 constexpr int CTA_SORT_MAX = 16384;   // rows up to this length: one block, shared memory
 constexpr int SEG_WARPS = 8;          // warps per block in the warp sorter
 
@@ -143,6 +143,81 @@ __global__ void k_orient_scatter(const int32_t* __restrict__ src, const int32_t*
         int32_t s = min(a, b), t = max(a, b);
         int64_t p = rowstart[s] + atomicAdd(&cursor[s], 1u);
         if (p < rowstart[s + 1]) col[p] = t;  // always true unless the two passes disagree
+    }
+}
+
+// Row fill in two levels, used for graphs with a flat degree distribution (where the
+// direct scatter's random row cursors and writes miss every cache).  Pass 1: each block takes 4096 pairs, sorts them by a
+// coarse bucket (the top PART_BITS bits of the source rank) in shared memory,
+// reserves space per bucket with one atomic, and writes (source, target) into the
+// bucket's segment of tmp -- the segment of col that the bucket's rows will occupy.
+// Pass 2: blocks take fixed-size contiguous chunks of the grouped pairs and move
+// them into their rows; a chunk's rows lie within one or two buckets, so its row
+// cursors and the written part of col form a small window that stays in L2.
+constexpr int PART_BITS = 8;
+constexpr int PART_BUCKETS = 1 << PART_BITS;
+constexpr int PART_ITEMS = 16;
+constexpr int PART_TILE = THREADS * PART_ITEMS;
+
+__global__ void __launch_bounds__(THREADS) k_orient_part(const int32_t* __restrict__ src, const int32_t* __restrict__ dst,
+                                                         int64_t m, int32_t n, const int32_t* __restrict__ rank,
+                                                         int shift, const int64_t* __restrict__ rowstart,
+                                                         uint32_t* __restrict__ bcur, int2* __restrict__ tmp) {
+    __shared__ uint32_t hist[PART_BUCKETS];
+    __shared__ int64_t base[PART_BUCKETS], bend[PART_BUCKETS];
+    for (int64_t t0 = (int64_t)blockIdx.x * PART_TILE; t0 < m; t0 += (int64_t)gridDim.x * PART_TILE) {
+        for (int b = threadIdx.x; b < PART_BUCKETS; b += THREADS) hist[b] = 0;
+        __syncthreads();
+        int32_t sv[PART_ITEMS], tv[PART_ITEMS];
+        uint32_t loc[PART_ITEMS];
+#pragma unroll
+        for (int k = 0; k < PART_ITEMS; ++k) {
+            const int64_t i = t0 + (int64_t)k * THREADS + threadIdx.x;
+            sv[k] = -1;
+            if (i < m) {
+                const int32_t u = src[i], v = dst[i];
+                if (u != v && (uint32_t)u < (uint32_t)n && (uint32_t)v < (uint32_t)n) {
+                    const int32_t a = rank[u], b = rank[v];
+                    sv[k] = min(a, b);
+                    tv[k] = max(a, b);
+                    loc[k] = atomicAdd(&hist[sv[k] >> shift], 1u);
+                }
+            }
+        }
+        __syncthreads();
+        for (int b = threadIdx.x; b < PART_BUCKETS; b += THREADS) {
+            const uint32_t c = hist[b];
+            const int64_t first = (int64_t)b << shift;
+            if (c && first < n) {
+                base[b] = rowstart[first] + atomicAdd(&bcur[b], c);
+                bend[b] = rowstart[min(first + ((int64_t)1 << shift), (int64_t)n)];
+            }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < PART_ITEMS; ++k)
+            if (sv[k] >= 0) {
+                const int b = sv[k] >> shift;
+                const int64_t pos = base[b] + loc[k];
+                if (pos < bend[b]) tmp[pos] = make_int2(sv[k], tv[k]);  // always true unless counts disagree
+            }
+        __syncthreads();
+    }
+}
+
+constexpr int LOCAL_CHUNK = 16384;  // pairs per block in pass 2
+
+__global__ void __launch_bounds__(1024) k_orient_local(int32_t n, const int64_t* __restrict__ rowstart,
+                                                       const int2* __restrict__ tmp, uint32_t* __restrict__ cursor,
+                                                       int32_t* __restrict__ col) {
+    const int64_t total = rowstart[n];  // pairs that survived the checks (self-loops excluded)
+    for (int64_t c0 = (int64_t)blockIdx.x * LOCAL_CHUNK; c0 < total; c0 += (int64_t)gridDim.x * LOCAL_CHUNK) {
+        const int64_t c1 = min(c0 + LOCAL_CHUNK, total);
+        for (int64_t e = c0 + threadIdx.x; e < c1; e += blockDim.x) {
+            const int2 st = tmp[e];
+            const int64_t p = rowstart[st.x] + atomicAdd(&cursor[st.x], 1u);
+            if (p < rowstart[st.x + 1]) col[p] = st.y;  // always true unless the passes disagree
+        }
     }
 }
 
@@ -288,17 +363,20 @@ __global__ void __launch_bounds__(256) k_segsort_thread(int32_t n, const int64_t
                                                         const uint32_t* __restrict__ rowcnt, int32_t* __restrict__ col,
                                                         int32_t* __restrict__ rowlen, int2* __restrict__ rowinfo,
                                                         uint32_t* __restrict__ dupin, int32_t* __restrict__ midlist,
-                                                        int32_t* __restrict__ longlist, DevStats* stats) {
+                                                        int32_t* __restrict__ midlist2, int32_t* __restrict__ longlist,
+                                                        DevStats* stats) {
     unsigned long long kept_total = 0;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     // the loop bound is uniform across a warp, as warp_append needs all 32 lanes
     for (int64_t b = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); b < n; b += stride) {
         const int64_t r = b + lane_id();
         const int len = r < n ? (int)rowcnt[r] : 0;
-        const bool mid = len > 16 && len <= WARP_SORT_MAX, lng = len > WARP_SORT_MAX;
+        const bool mid = len > 16 && len <= 256, mid2 = len > 256 && len <= WARP_SORT_MAX, lng = len > WARP_SORT_MAX;
         const unsigned pm = warp_append(mid, &stats->mid_count);
+        const unsigned pm2 = warp_append(mid2, &stats->mid2_count);
         const unsigned pl = warp_append(lng, &stats->long_count);
         if (mid) midlist[pm] = (int32_t)r;
+        if (mid2) midlist2[pm2] = (int32_t)r;
         if (lng) longlist[pl] = (int32_t)r;
         if (r < n && len <= 16) {
             const int64_t base = rowstart[r];
@@ -312,36 +390,116 @@ __global__ void __launch_bounds__(256) k_segsort_thread(int32_t n, const int64_t
     if (lane_id() == 0 && kept_total) atomicAdd(&stats->m_simple, kept_total);
 }
 
-// One warp per listed row (17 .. WARP_SORT_MAX entries): bitonic network in shared memory.
+// Bitonic network over the 32*K entries a warp holds in registers, lane L holding
+// entries L*K .. L*K + K - 1 (ascending overall when done).  Comparator partners
+// closer than K sit in the same lane; farther partners are exchanged with shfl_xor.
+template <int K>
+__device__ __forceinline__ void warp_reg_sort(int32_t (&v)[K], int lane) {
+    constexpr int N = 32 * K;
+#pragma unroll
+    for (int s = 2; s <= N; s <<= 1) {
+#pragma unroll
+        for (int j = s >> 1; j > 0; j >>= 1) {
+            if (j < K) {
+#pragma unroll
+                for (int r = 0; r < K; ++r) {
+                    if ((r & j) == 0) {
+                        const int e = lane * K + r;
+                        const bool asc = (e & s) == 0;
+                        const int32_t a = v[r], b = v[r | j];
+                        v[r] = asc ? min(a, b) : max(a, b);
+                        v[r | j] = asc ? max(a, b) : min(a, b);
+                    }
+                }
+            } else {
+                const int lm = j / K;
+#pragma unroll
+                for (int r = 0; r < K; ++r) {
+                    const int e = lane * K + r;
+                    const int32_t w = __shfl_xor_sync(FULL, v[r], lm);
+                    const bool asc = (e & s) == 0;
+                    const bool lower = (e & j) == 0;
+                    v[r] = (asc == lower) ? min(v[r], w) : max(v[r], w);
+                }
+            }
+        }
+    }
+}
+
+// Sorts one row of len <= 32 K entries with a warp, writes the distinct entries
+// back to the row's start, counts dropped repeats at their targets; returns the
+// number kept (all lanes).
+template <int K>
+__device__ __forceinline__ int warp_sort_row(int32_t* __restrict__ row, int len, uint32_t* __restrict__ dupin,
+                                             int lane) {
+    int32_t v[K];
+#pragma unroll
+    for (int r = 0; r < K; ++r) {
+        const int e = lane * K + r;
+        v[r] = e < len ? row[e] : INT_MAX;
+    }
+    warp_reg_sort<K>(v, lane);
+    int32_t prev = __shfl_up_sync(FULL, v[K - 1], 1);
+    if (lane == 0) prev = INT_MIN;
+    unsigned keepmask = 0;
+    int nk = 0;
+#pragma unroll
+    for (int r = 0; r < K; ++r) {
+        const int e = lane * K + r;
+        if (e < len) {
+            if (v[r] != prev) {
+                keepmask |= 1u << r;
+                ++nk;
+            } else {
+                atomicAdd(&dupin[v[r]], 1u);
+            }
+        }
+        prev = v[r];
+    }
+    const int incl = warp_inclusive_scan(nk);
+    const int total = __shfl_sync(FULL, incl, 31);
+    __syncwarp();  // every lane has read its entries before any is overwritten
+    int pos = incl - nk;
+#pragma unroll
+    for (int r = 0; r < K; ++r)
+        if (keepmask & (1u << r)) row[pos++] = v[r];
+    return total;
+}
+
+// One warp per listed row, sorted in registers: MAXK = 8 takes the rows of 17..256
+// entries, MAXK = 32 those of 257..1024 (separate kernels keep the register budget
+// of the short classes small).
+template <int MAXK>
 __global__ void __launch_bounds__(SEG_WARPS * 32) k_segsort_warp(const int64_t* __restrict__ rowstart,
                                                                  const uint32_t* __restrict__ rowcnt,
                                                                  int32_t* __restrict__ col, int32_t* __restrict__ rowlen,
                                                                  int2* __restrict__ rowinfo, uint32_t* __restrict__ dupin,
-                                                                 const int32_t* __restrict__ midlist, DevStats* stats) {
-    __shared__ int32_t sh[SEG_WARPS][WARP_SORT_MAX];
+                                                                 const int32_t* __restrict__ list,
+                                                                 const unsigned* __restrict__ count, DevStats* stats) {
     const int lane = lane_id(), w = threadIdx.x >> 5;
-    int32_t* s = sh[w];
-    const unsigned nmid = stats->mid_count;
+    const unsigned nrows = *count;
     const unsigned warps = gridDim.x * SEG_WARPS;
     unsigned long long kept_total = 0;
-    for (unsigned q = blockIdx.x * SEG_WARPS + w; q < nmid; q += warps) {
-        const int32_t r = midlist[q];
+    for (unsigned q = blockIdx.x * SEG_WARPS + w; q < nrows; q += warps) {
+        const int32_t r = list[q];
         const int len = (int)rowcnt[r];
         const int64_t base = rowstart[r];
-        const int P = max(32, next_pow2_int(len));
-        for (int i = lane; i < P; i += 32) s[i] = i < len ? col[base + i] : INT_MAX;
-        __syncwarp();
-        bitonic_sort(s, P, lane, 32, WarpSync());
-        int kept = 0;
-        for (int c = 0; c < len; c += 32) {
-            int i = c + lane;
-            bool keep = i < len && (i == 0 || s[i] != s[i - 1]);
-            unsigned mk = __ballot_sync(FULL, keep);
-            if (keep)
-                col[base + kept + __popc(mk & lanemask_lt())] = s[i];
-            else if (i < len)
-                atomicAdd(&dupin[s[i]], 1u);
-            kept += __popc(mk);
+        int32_t* row = col + base;
+        int kept;
+        if (MAXK <= 8) {
+            if (len <= 32)
+                kept = warp_sort_row<1>(row, len, dupin, lane);
+            else if (len <= 64)
+                kept = warp_sort_row<2>(row, len, dupin, lane);
+            else if (len <= 128)
+                kept = warp_sort_row<4>(row, len, dupin, lane);
+            else
+                kept = warp_sort_row<8>(row, len, dupin, lane);
+        } else {
+            if (len <= 512)
+                kept = warp_sort_row<16>(row, len, dupin, lane);
+            else
+                kept = warp_sort_row<32>(row, len, dupin, lane);
         }
         if (lane == 0) {
             rowlen[r] = kept;
@@ -444,7 +602,7 @@ void launch_rank(const BuildBuffers& B, int deg_bits, const Launch& L) {
     k_rank_invert<<<grid_for(B.n, THREADS, L.sms), THREADS, 0, L.stream>>>(sorted, B.n, B.rank, B.dmulti); count_launch();
 }
 
-void launch_orient(const BuildBuffers& B, const Launch& L) {
+void launch_orient(const BuildBuffers& B, const Launch& L, cudaEvent_t* ev) {
     if (B.n <= 0) return;
     cudaMemsetAsync(B.rowcnt, 0, sizeof(uint32_t) * (size_t)B.n, L.stream);
     cudaMemsetAsync(B.cursor, 0, sizeof(uint32_t) * (size_t)B.n, L.stream);
@@ -453,18 +611,38 @@ void launch_orient(const BuildBuffers& B, const Launch& L) {
         k_orient_count<<<grid_for(B.m, THREADS, L.sms), THREADS, 0, L.stream>>>(B.src, B.dst, B.m, B.n, B.rank,
                                                                               B.rowcnt); count_launch(); }
     scan_u32_to_i64(B.rowcnt, B.rowstart, B.n, B.tmp, L);
-    if (B.m > 0) {
+    if (ev) cudaEventRecord(ev[BP_COUNT], L.stream);
+    if (B.m > 0 && !B.two_level_fill) {
         k_orient_scatter<<<grid_for(B.m, THREADS, L.sms), THREADS, 0, L.stream>>>(
-            B.src, B.dst, B.m, B.n, B.rank, B.rowstart, B.cursor, B.col); count_launch(); }
+            B.src, B.dst, B.m, B.n, B.rank, B.rowstart, B.cursor, B.col);
+        count_launch();
+    } else if (B.m > 0) {
+        int bits = 0;
+        while (bits < 31 && ((int64_t)1 << bits) < (int64_t)B.n) ++bits;
+        const int shift = bits > PART_BITS ? bits - PART_BITS : 0;
+        cudaMemsetAsync(B.bcur, 0, sizeof(uint32_t) * PART_BUCKETS, L.stream);
+        k_orient_part<<<grid_for(B.m, PART_TILE, L.sms, 4), THREADS, 0, L.stream>>>(
+            B.src, B.dst, B.m, B.n, B.rank, shift, B.rowstart, B.bcur, B.pairs);
+        count_launch();
+        k_orient_local<<<grid_for(B.m, LOCAL_CHUNK, L.sms, 2), 1024, 0, L.stream>>>(B.n, B.rowstart, B.pairs,
+                                                                                  B.cursor, B.col);
+        count_launch();
+    }
+    if (ev) cudaEventRecord(ev[BP_FILL], L.stream);
     k_segsort_thread<<<grid_for(B.n, THREADS, L.sms), THREADS, 0, L.stream>>>(
-        B.n, B.rowstart, B.rowcnt, B.col, B.rowlen, B.rowinfo, B.dupin, B.midlist, B.longlist, B.stats);
+        B.n, B.rowstart, B.rowcnt, B.col, B.rowlen, B.rowinfo, B.dupin, B.midlist, B.midlist2, B.longlist, B.stats);
     count_launch();
-    k_segsort_warp<<<L.sms * 4, SEG_WARPS * 32, 0, L.stream>>>(B.rowstart, B.rowcnt, B.col, B.rowlen, B.rowinfo,
-                                                              B.dupin, B.midlist, B.stats);
+    k_segsort_warp<8><<<L.sms * 4, SEG_WARPS * 32, 0, L.stream>>>(B.rowstart, B.rowcnt, B.col, B.rowlen, B.rowinfo,
+                                                                 B.dupin, B.midlist, &B.stats->mid_count, B.stats);
+    count_launch();
+    k_segsort_warp<32><<<L.sms * 2, SEG_WARPS * 32, 0, L.stream>>>(B.rowstart, B.rowcnt, B.col, B.rowlen,
+                                                                  B.rowinfo, B.dupin, B.midlist2,
+                                                                  &B.stats->mid2_count, B.stats);
     count_launch();
     k_segsort_block<<<L.sms * 2, 1024, CTA_SORT_MAX * sizeof(int32_t), L.stream>>>(
         B.rowstart, B.rowcnt, B.col, B.rowlen, B.rowinfo, B.dupin, B.longlist, B.stats);
     count_launch();
+    if (ev) cudaEventRecord(ev[BP_SORT], L.stream);
     k_degree<<<grid_for(B.n, THREADS, L.sms), THREADS, 0, L.stream>>>(B.n, B.rowlen, B.dmulti, B.rowcnt, B.dupin,
                                                                      B.deg);
     count_launch();

@@ -31,8 +31,9 @@ struct DevStats {
     unsigned int hub_next2;        // dynamic work counter of the hub kernel (medium hubs)
     unsigned int hub_candidates;   // vertices whose degree reaches the hub threshold
     unsigned int hub_big;          // hubs processed by whole blocks
-    unsigned int mid_count;        // build: rows sorted by one warp
-    unsigned int pad[2];
+    unsigned int mid_count;        // build: rows of 17..256 entries sorted by one warp
+    unsigned int mid2_count;       // build: rows of 257..1024 entries sorted by one warp
+    unsigned int pad[1];
 };
 static_assert(sizeof(DevStats) == 88, "DevStats layout");
 
@@ -70,8 +71,12 @@ struct BuildBuffers {
     uint32_t* rowcnt;     // n + 1
     uint32_t* cursor;     // n
     int32_t* longlist;    // n
-    int32_t* midlist;     // n
+    int32_t* midlist;     // n: rows of 17..256 entries
+    int32_t* midlist2;    // n: rows of 257..1024 entries
     uint32_t* dupin;      // n: repeated entries dropped at each target
+    uint32_t* bcur;       // 256: bucket cursors of the two-level row fill
+    int2* pairs;          // m: (source rank, target rank) grouped by bucket
+    bool two_level_fill;  // row fill through buckets (flat degree distributions)
     void* tmp;            // max(scan_tmp_bytes(n + 1), radix_tmp_bytes(n))
     // outputs (kept by the graph)
     int32_t* rank;        // n: rank of each input id in (degree, id) order
@@ -83,13 +88,17 @@ struct BuildBuffers {
     DevStats* stats;
 };
 
+// Build phases timed by events (tc_graph_build_timing): ingest, rank, row counts,
+// row fill, row sort + dedup, degrees.
+enum { BP_START = 0, BP_INGEST, BP_RANK, BP_COUNT, BP_FILL, BP_SORT, BP_END, BP_EVENTS };
+
 void launch_check_offsets(const int64_t* offsets, int32_t n, int64_t limit, DevStats* stats,
                           const Launch& L);
 void launch_expand_csr(const int64_t* offsets, int32_t n, int32_t* rows, DevStats* stats,
                        const Launch& L);
 void launch_canon_degree(const BuildBuffers& B, const Launch& L);
 void launch_rank(const BuildBuffers& B, int deg_bits, const Launch& L);
-void launch_orient(const BuildBuffers& B, const Launch& L);
+void launch_orient(const BuildBuffers& B, const Launch& L, cudaEvent_t* ev = nullptr);
 cudaError_t build_init_attributes();
 
 // ---- plan + intersect + finalize (tc_intersect.cu) ---------------------------

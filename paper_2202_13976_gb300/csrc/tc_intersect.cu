@@ -342,7 +342,10 @@ __global__ void k_hub_indeg(int32_t n, int32_t hub_cap, const int32_t* __restric
 }
 
 // Every oriented entry (u -> v) with v a hub becomes an in-edge record of v:
-// {u, index after v in N+(u), end of N+(u), 0}, one 16-byte store.  One warp per row.
+// {u, index after v in N+(u), end of N+(u), 0}, one 16-byte store.  A warp takes 32
+// consecutive rows (one per lane) and walks their hub tails from the end backwards
+// in lockstep; the highest-ranked hubs end almost every row, so lanes that name the
+// same hub in a step reserve their slots with one atomic.
 __global__ void k_hub_scatter(int32_t n, int32_t hub_cap, const int64_t* __restrict__ rowstart,
                               const int32_t* __restrict__ rowlen, const int32_t* __restrict__ col,
                               const int64_t* __restrict__ hub_start, uint32_t* __restrict__ hub_cur,
@@ -350,20 +353,33 @@ __global__ void k_hub_scatter(int32_t n, int32_t hub_cap, const int64_t* __restr
     const int32_t R = n - (int32_t)stats->hub_count;
     const int lane = lane_id();
     const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
-    for (int64_t u = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; u < n; u += warps) {
-        const int du = rowlen[u];
-        if (du == 0) continue;
-        const int64_t base = rowstart[u];
-        if (col[base + du - 1] < R) continue;  // no hub in this row
-        for (int p = lane; p < du; p += 32) {
-            const int32_t v = col[base + p];
-            if (v >= R) {
-                const int i = v - (n - hub_cap);
-                const int64_t slot = hub_start[i] + atomicAdd(&hub_cur[i], 1u);
+    for (int64_t w0 = (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 32; w0 < n; w0 += warps * 32) {
+        const int64_t u = w0 + lane;
+        const int du = u < n ? rowlen[u] : 0;
+        const int64_t base = u < n ? rowstart[u] : 0;
+        int p = du - 1;
+        for (int step = 0;; ++step) {
+            const int32_t x = p >= 0 ? col[base + p] : -1;
+            const bool active = x >= R;
+            if (!__any_sync(FULL, active)) break;
+            // the first steps meet the most contended (highest) hubs: aggregate them;
+            // afterwards every lane reserves its own slot
+            const int key = active && step < 16 ? x : -1 - lane;
+            const unsigned peers = __match_any_sync(FULL, key);
+            const int leader = __ffs(peers) - 1;
+            const int i = x - (n - hub_cap);
+            int64_t slot0 = 0;
+            if (active && lane == leader) slot0 = (int64_t)atomicAdd(&hub_cur[i], (unsigned)__popc(peers));
+            slot0 = __shfl_sync(FULL, slot0, leader);
+            if (active) {
+                const int64_t slot = hub_start[i] + slot0 + __popc(peers & lanemask_lt());
                 if (slot < hub_start[i + 1])  // counts and entries disagree only on a bug: never write outside
                     in_rec[slot] = make_int4((int32_t)u, (int32_t)(base + p + 1), (int32_t)(base + du), 0);
                 else
                     atomicOr(&stats->err, ERR_OVERFLOW);
+                --p;
+            } else {
+                p = -1;
             }
         }
     }
@@ -906,7 +922,7 @@ void launch_plan(const CountBuffers& C, const Strategy& S, const Launch& L) {
         count_launch();
         scan_u32_to_i64(C.hub_cnt, C.hub_start, C.hub_cap, C.tmp, L);
         cudaMemsetAsync(C.hub_cur, 0, sizeof(uint32_t) * (size_t)C.hub_cap, L.stream);
-        k_hub_scatter<<<grid_for((int64_t)C.n * 32, THREADS, L.sms), THREADS, 0, L.stream>>>(
+        k_hub_scatter<<<grid_for(C.n, THREADS, L.sms), THREADS, 0, L.stream>>>(
             C.n, C.hub_cap, C.rowstart, C.rowlen, C.col, C.hub_start, C.hub_cur, C.in_rec, C.stats);
         count_launch();
         // hub_cur is free again: it holds the big flags, hub_cnt (still the in-degrees
