@@ -50,7 +50,8 @@ constexpr int HUB_THREADS = 256;
 constexpr int HUB_WARPS = HUB_THREADS / 32;
 constexpr int HUB_BM_WORDS = HUB_BM_BITS / 32;
 constexpr int HUB_CNT_MAX = 4096;      // hub lists longer than this count matches globally
-constexpr int HUB_WARP_MAX = 448;      // longest N+(v) a single warp stages
+constexpr int HUB_WARP_MAX = 256;      // longest N+(v) a single warp stages
+constexpr int HUB_HASH_MAX = 512;      // its hash table: at least twice as many slots as keys
 
 struct Sink {
     uint32_t* cnt;               // per-position counters (shared), or null
@@ -588,7 +589,7 @@ __global__ void __launch_bounds__(CTA_THREADS) k_tc_cta(int32_t n, const int64_t
 // ---- hub bucket ----------------------------------------------------------------
 // Big hubs (in-degree >= the planner's threshold, or lists too long for one warp) are processed
 // by a whole block over a bitmap of N+(v); the remaining hubs by one warp each over
-// the sorted list N+(v) in shared memory.  One persistent kernel drains the big-hub
+// a hash set of N+(v) in shared memory.  One persistent kernel drains the big-hub
 // queue first, then every warp takes medium hubs independently.
 
 
@@ -600,6 +601,23 @@ struct BitmapProbe {
         const int off = x - v - 1;
         const uint32_t word = bm[off >> 5], bit = 1u << (off & 31);
         return (word & bit) ? (int)pre[off >> 5] + __popc(word & (bit - 1)) : -1;
+    }
+};
+
+// Open-addressing hash set of N+(v) in shared memory (Fibonacci hashing, linear
+// probing, empty slots hold -1).  The table has at least twice as many slots as
+// keys, so a probe meets an empty slot after about two steps at most on average.
+struct HashProbe {
+    const int32_t* keys;
+    unsigned shift, mask;
+    __device__ __forceinline__ int operator()(int32_t x) const {
+        unsigned h = ((unsigned)x * 0x9e3779b1u) >> shift;
+        for (;;) {
+            const int32_t k = keys[h];
+            if (k == x) return (int)h;
+            if (k < 0) return -1;
+            h = (h + 1) & mask;
+        }
     }
 };
 
@@ -725,8 +743,8 @@ struct HubShared {
             uint32_t slice[HUB_BM_WORDS / 32];
         } big;
         struct {  // medium hubs, one per warp
-            int32_t list[HUB_WARPS][HUB_WARP_MAX];
-            uint32_t cnt[HUB_WARPS][HUB_WARP_MAX];
+            int32_t keys[HUB_WARPS][HUB_HASH_MAX];
+            uint32_t cnt[HUB_WARPS][HUB_HASH_MAX];
         } med;
     } u;
     uint32_t cw[HUB_WARPS][32];
@@ -810,9 +828,15 @@ __global__ void __launch_bounds__(HUB_THREADS) k_tc_hub(int32_t n, int32_t hub_c
         }
         __syncthreads();
     }
-    // phase 2: medium hubs, one warp each (no block barriers from here on)
-    int32_t* L = sh.u.med.list[w];
+    // phase 2: medium hubs, one warp each (no block barriers from here on), probed
+    // through a hash set of N+(v); every slot is empty again after each hub
+    int32_t* K = sh.u.med.keys[w];
     uint32_t* cnt = sh.u.med.cnt[w];
+    for (int p = lane; p < HUB_HASH_MAX; p += 32) {
+        K[p] = -1;
+        cnt[p] = 0;
+    }
+    __syncwarp();
     for (;;) {
         unsigned q = 0;
         if (lane == 0) q = atomicAdd(&stats->hub_next2, 1u);
@@ -823,20 +847,33 @@ __global__ void __launch_bounds__(HUB_THREADS) k_tc_hub(int32_t n, int32_t hub_c
         const int64_t e0 = hub_start[hi], e1 = hub_start[hi + 1];
         const int dv = rowlen[v];
         if (dv == 0 || e1 == e0) continue;
-        const int64_t base = rowstart[v];
-        for (int p = lane; p < dv; p += 32) {
-            L[p] = col[base + p];
-            cnt[p] = 0;
+        if (dv > HUB_WARP_MAX) {  // the flags never make such a hub medium: do not overrun the table
+            if (lane == 0) atomicOr(&stats->err, ERR_OVERFLOW);
+            continue;
         }
+        const int64_t base = rowstart[v];
+        int lg = 5;
+        while ((1 << lg) < 2 * dv) ++lg;
+        const unsigned shift = 32u - (unsigned)lg, mask = (1u << lg) - 1u;
+        for (int p = lane; p < dv; p += 32) {
+            const int32_t x = col[base + p];
+            unsigned h = ((unsigned)x * 0x9e3779b1u) >> shift;
+            while (atomicCAS(&K[h], -1, x) != -1) h = (h + 1) & mask;  // keys are distinct
+        }
+        const int32_t maxv = col[base + dv - 1];
         __syncwarp();
-        const int32_t maxv = L[dv - 1];
-        const ListProbe P{L, dv};
+        const HashProbe P{K, shift, mask};
         unsigned long long vtot = 0;
         for (int64_t bb = e0; bb < e1; bb += 32) vtot += hub_batch(bb, e1, in_rec, col, maxv, P, cnt, t, sh.cw[w]);
         __syncwarp();
-        for (int p = lane; p < dv; p += 32) {
-            const uint32_t c = cnt[p];
-            if (c) atomicAdd(&t[L[p]], (unsigned long long)c);
+        for (int p = lane; p <= (int)mask; p += 32) {
+            const int32_t x = K[p];
+            if (x >= 0) {
+                const uint32_t c = cnt[p];
+                if (c) atomicAdd(&t[x], (unsigned long long)c);
+                K[p] = -1;
+                cnt[p] = 0;
+            }
         }
         if (lane == 0 && vtot) atomicAdd(&t[v], vtot);
         __syncwarp();
