@@ -52,6 +52,11 @@ constexpr int HUB_BM_WORDS = HUB_BM_BITS / 32;
 constexpr int HUB_CNT_MAX = 4096;      // hub lists longer than this count matches globally
 constexpr int HUB_WARP_MAX = 256;      // longest N+(v) a single warp stages
 constexpr int HUB_HASH_MAX = 512;      // its hash table: at least twice as many slots as keys
+constexpr int SCAT_STEPS = 4;          // lockstep steps of the hub in-edge scatter in flight together
+constexpr int HUB_LONG = 32;           // suffixes at least this long are read by lane groups
+constexpr int HUB_GROUPS = 4;          // long suffixes one warp reads at a time
+constexpr int HUB_GLANES = 32 / HUB_GROUPS;
+constexpr int HUB_UNROLL = 8;          // entries a lane reads per round of a long suffix
 
 struct Sink {
     uint32_t* cnt;               // per-position counters (shared), or null
@@ -359,29 +364,39 @@ __global__ void k_hub_scatter(int32_t n, int32_t hub_cap, const int64_t* __restr
         const int du = u < n ? rowlen[u] : 0;
         const int64_t base = u < n ? rowstart[u] : 0;
         int p = du - 1;
-        for (int step = 0;; ++step) {
-            const int32_t x = p >= 0 ? col[base + p] : -1;
-            const bool active = x >= R;
-            if (!__any_sync(FULL, active)) break;
-            // the first steps meet the most contended (highest) hubs: aggregate them;
-            // afterwards every lane reserves its own slot
-            const int key = active && step < 16 ? x : -1 - lane;
-            const unsigned peers = __match_any_sync(FULL, key);
-            const int leader = __ffs(peers) - 1;
-            const int i = x - (n - hub_cap);
-            int64_t slot0 = 0;
-            if (active && lane == leader) slot0 = (int64_t)atomicAdd(&hub_cur[i], (unsigned)__popc(peers));
-            slot0 = __shfl_sync(FULL, slot0, leader);
-            if (active) {
-                const int64_t slot = hub_start[i] + slot0 + __popc(peers & lanemask_lt());
-                if (slot < hub_start[i + 1])  // counts and entries disagree only on a bug: never write outside
-                    in_rec[slot] = make_int4((int32_t)u, (int32_t)(base + p + 1), (int32_t)(base + du), 0);
-                else
-                    atomicOr(&stats->err, ERR_OVERFLOW);
-                --p;
-            } else {
-                p = -1;
+        // SCAT_STEPS steps at a time: their loads, then their slot reservations, are
+        // independent and in flight together.  Walking backwards, the hub entries of a
+        // row come first, so a lane's active steps are a prefix.
+        for (int step = 0;; step += SCAT_STEPS) {
+            int32_t x[SCAT_STEPS];
+#pragma unroll
+            for (int j = 0; j < SCAT_STEPS; ++j) x[j] = p - j >= 0 ? col[base + p - j] : -1;
+            if (!__any_sync(FULL, x[0] >= R)) break;
+            unsigned peers[SCAT_STEPS];
+            int64_t slot0[SCAT_STEPS];
+#pragma unroll
+            for (int j = 0; j < SCAT_STEPS; ++j) {
+                const bool active = x[j] >= R;
+                // the first steps meet the most contended (highest) hubs: aggregate them;
+                // afterwards every lane reserves its own slot
+                peers[j] = __match_any_sync(FULL, active && step + j < 16 ? x[j] : -1 - lane);
+                slot0[j] = 0;
+                if (active && lane == __ffs(peers[j]) - 1)
+                    slot0[j] = (int64_t)atomicAdd(&hub_cur[x[j] - (n - hub_cap)], (unsigned)__popc(peers[j]));
             }
+#pragma unroll
+            for (int j = 0; j < SCAT_STEPS; ++j) {
+                slot0[j] = __shfl_sync(FULL, slot0[j], __ffs(peers[j]) - 1);
+                if (x[j] >= R) {
+                    const int i = x[j] - (n - hub_cap);
+                    const int64_t slot = hub_start[i] + slot0[j] + __popc(peers[j] & lanemask_lt());
+                    if (slot < hub_start[i + 1])  // counts and entries disagree only on a bug: never write outside
+                        in_rec[slot] = make_int4((int32_t)u, (int32_t)(base + p - j + 1), (int32_t)(base + du), 0);
+                    else
+                        atomicOr(&stats->err, ERR_OVERFLOW);
+                }
+            }
+            p = x[SCAT_STEPS - 1] >= R ? p - SCAT_STEPS : -1;
         }
     }
 }
@@ -646,45 +661,56 @@ __device__ uint32_t hub_batch(int64_t k0, int64_t e1, const int4* __restrict__ i
     int32_t b0 = rec.y;
     int a = rec.z - rec.y;
     uint32_t total_c = 0;
-    unsigned longm = __ballot_sync(FULL, a >= 32);
+    unsigned longm = __ballot_sync(FULL, a >= HUB_LONG);
+    // HUB_GROUPS long suffixes at a time, one per group of HUB_GLANES lanes, each lane
+    // reading HUB_UNROLL entries per round with all loads in flight before any is used
+    const int g = lane / HUB_GLANES, gl = lane % HUB_GLANES;
+    const unsigned gmask = (HUB_GLANES == 32 ? FULL : ((1u << HUB_GLANES) - 1u)) << (g * HUB_GLANES);
     while (longm) {
-        const int L = __ffs(longm) - 1;
-        longm &= longm - 1;
-        const int32_t bL = __shfl_sync(FULL, b0, L);
-        const int aL = __shfl_sync(FULL, a, L);
-        uint32_t c = 0;
-        // two entries per lane per round: both loads are in flight before either is used
-        for (int o0 = 0; o0 < aL; o0 += 64) {
-            const int o1 = o0 + lane, o2 = o1 + 32;
-            const int32_t x1 = o1 < aL ? col[bL + o1] : INT_MAX;
-            const int32_t x2 = o2 < aL ? col[bL + o2] : INT_MAX;
-            if (x1 <= maxv) {
-                const int p = probe(x1);
-                if (p >= 0) {
-                    if (cnt)
-                        atomicAdd(&cnt[p], 1u);
-                    else
-                        atomicAdd(&t[x1], 1ull);
-                    ++c;
-                }
-            }
-            if (x2 <= maxv) {
-                const int p = probe(x2);
-                if (p >= 0) {
-                    if (cnt)
-                        atomicAdd(&cnt[p], 1u);
-                    else
-                        atomicAdd(&t[x2], 1ull);
-                    ++c;
-                }
-            }
-            if (__any_sync(FULL, x2 > maxv)) break;  // the suffix is sorted
+        int my = -1;  // batch lane holding this group's in-edge
+#pragma unroll
+        for (int j = 0; j < HUB_GROUPS; ++j) {
+            const int f = longm ? __ffs(longm) - 1 : -1;
+            if (j == g) my = f;
+            longm &= longm - 1;  // no-op once empty
         }
-        c = __reduce_add_sync(FULL, c);
-        total_c += c;
-        if (c && lane == L) atomicAdd(&t[uu], (unsigned long long)c);
+        const int src = my < 0 ? 0 : my;
+        const int32_t bL = __shfl_sync(FULL, b0, src);
+        int aL = __shfl_sync(FULL, a, src);
+        const int32_t uL = __shfl_sync(FULL, uu, src);
+        if (my < 0) aL = 0;
+        uint32_t c = 0;
+        for (int o0 = 0;; o0 += HUB_GLANES * HUB_UNROLL) {
+            int32_t x[HUB_UNROLL];
+#pragma unroll
+            for (int j = 0; j < HUB_UNROLL; ++j) {
+                const int o = o0 + j * HUB_GLANES + gl;
+                x[j] = o < aL ? col[bL + o] : INT_MAX;
+            }
+#pragma unroll
+            for (int j = 0; j < HUB_UNROLL; ++j) {
+                if (x[j] <= maxv) {
+                    const int p = probe(x[j]);
+                    if (p >= 0) {
+                        if (cnt)
+                            atomicAdd(&cnt[p], 1u);
+                        else
+                            atomicAdd(&t[x[j]], 1ull);
+                        ++c;
+                    }
+                }
+            }
+            // the suffix is sorted: a group is done once one of its lanes read past maxv
+            // (or past the end of the suffix)
+            if (__ballot_sync(FULL, x[HUB_UNROLL - 1] > maxv) & gmask) aL = 0;
+            if (__all_sync(FULL, aL == 0)) break;
+        }
+#pragma unroll
+        for (int off = HUB_GLANES / 2; off > 0; off >>= 1) c += __shfl_xor_sync(FULL, c, off);
+        if (gl == 0 && my >= 0 && c) atomicAdd(&t[uL], (unsigned long long)c);
+        total_c += __reduce_add_sync(FULL, gl == 0 ? c : 0u);
     }
-    if (a >= 32) a = 0;  // done above
+    if (a >= HUB_LONG) a = 0;  // done above
     const unsigned nz = __ballot_sync(FULL, a > 0);
     const int cz = __popc(nz);
     if (cz == 0) return total_c;
