@@ -59,33 +59,57 @@ __global__ void k_expand_csr(const int64_t* __restrict__ offsets, int32_t n, int
     }
 }
 
-__global__ void k_canon_degree(const int32_t* __restrict__ src, const int32_t* __restrict__ dst,
-                               int64_t m, int32_t n, uint32_t* __restrict__ dmulti, DevStats* stats) {
+// Multigraph degree counts.  Each block keeps the counts of the vertices it meets
+// first in a shared-memory hash table (open addressing, at most DEG_PROBES slots
+// looked at); hub vertices occur often enough to take a slot early, so their many
+// increments stay in shared memory and reach dmulti with one atomic per block.
+// Vertices that find no slot add to dmulti directly.
+constexpr int DEG_SLOTS = 4096;
+constexpr int DEG_PROBES = 4;
+
+__device__ __forceinline__ void deg_add(int32_t x, int32_t* hk, uint32_t* hc, uint32_t* __restrict__ dmulti) {
+    unsigned h = ((unsigned)x * 0x9e3779b1u) >> (32 - 12);
+#pragma unroll
+    for (int k = 0; k < DEG_PROBES; ++k) {
+        int32_t cur = hk[h];
+        if (cur == -1) cur = atomicCAS(&hk[h], -1, x);
+        if (cur == -1 || cur == x) {
+            atomicAdd(&hc[h], 1u);
+            return;
+        }
+        h = (h + 1) & (DEG_SLOTS - 1);
+    }
+    atomicAdd(&dmulti[x], 1u);
+}
+
+__global__ void __launch_bounds__(THREADS) k_canon_degree(const int32_t* __restrict__ src,
+                                                          const int32_t* __restrict__ dst, int64_t m, int32_t n,
+                                                          uint32_t* __restrict__ dmulti, DevStats* stats) {
+    static_assert(DEG_SLOTS == 1 << 12, "hash width");
+    __shared__ int32_t hk[DEG_SLOTS];
+    __shared__ uint32_t hc[DEG_SLOTS];
+    for (int i = threadIdx.x; i < DEG_SLOTS; i += blockDim.x) {
+        hk[i] = -1;
+        hc[i] = 0;
+    }
+    __syncthreads();
     unsigned long long loops = 0;
     int err = 0;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    const int lane = lane_id();
-    // warp-uniform loop: lanes of a warp that name the same vertex add their counts
-    // with one atomic (hub degrees collect most increments)
-    for (int64_t b = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); b < m; b += stride) {
-        const int64_t i = b + lane;
-        int32_t u = -1 - lane, v = -33 - lane;  // private values for lanes without a pair
-        if (i < m) {
-            const int32_t a = src[i], c = dst[i];
-            if ((uint32_t)a >= (uint32_t)n || (uint32_t)c >= (uint32_t)n) {
-                err = ERR_BAD_ID;
-            } else if (a == c) {
-                ++loops;
-            } else {
-                u = a;
-                v = c;
-            }
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += stride) {
+        const int32_t a = src[i], c = dst[i];
+        if ((uint32_t)a >= (uint32_t)n || (uint32_t)c >= (uint32_t)n) {
+            err = ERR_BAD_ID;
+        } else if (a == c) {
+            ++loops;
+        } else {
+            deg_add(a, hk, hc, dmulti);
+            deg_add(c, hk, hc, dmulti);
         }
-        const unsigned pu = __match_any_sync(FULL, u);
-        const unsigned pv = __match_any_sync(FULL, v);
-        if (u >= 0 && lane == __ffs(pu) - 1) atomicAdd(&dmulti[u], (uint32_t)__popc(pu));
-        if (v >= 0 && lane == __ffs(pv) - 1) atomicAdd(&dmulti[v], (uint32_t)__popc(pv));
     }
+    __syncthreads();
+    for (int i = threadIdx.x; i < DEG_SLOTS; i += blockDim.x)
+        if (hc[i]) atomicAdd(&dmulti[hk[i]], hc[i]);
     loops = warp_sum(loops);
     err = __reduce_or_sync(FULL, err);
     if (lane_id() == 0) {
@@ -589,8 +613,9 @@ void launch_expand_csr(const int64_t* offsets, int32_t n, int32_t* rows, DevStat
 
 void launch_canon_degree(const BuildBuffers& B, const Launch& L) {
     if (B.m > 0) {
-        k_canon_degree<<<grid_for(B.m, THREADS, L.sms), THREADS, 0, L.stream>>>(B.src, B.dst, B.m, B.n, B.dmulti,
-                                                                              B.stats); count_launch(); }
+        // 32 KB of shared memory per block: four blocks per SM stay resident
+        k_canon_degree<<<grid_for(B.m, THREADS, L.sms, 4), THREADS, 0, L.stream>>>(B.src, B.dst, B.m, B.n, B.dmulti,
+                                                                                 B.stats); count_launch(); }
     if (B.n > 0) { k_max_deg<<<grid_for(B.n, THREADS, L.sms), THREADS, 0, L.stream>>>(B.dmulti, B.n, B.stats); count_launch(); }
 }
 
