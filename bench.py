@@ -263,8 +263,8 @@ def run_ours(args, rank, world, local):
     step_ms = [a.elapsed_time(b) for a, b in evs]
     ms_per_step, value = aggregate_ranks(sum(step_ms), args.steps, m_simple, world, dev)
 
-    # dominant intersection kernel and its roofline (algorithmic bytes of the survey's
-    # per-edge figure: 4 (d+u + d+v) adjacency bytes + 8 edge bytes + 16 offset bytes)
+    # dominant intersection kernel and its roofline (algorithmic bytes per oriented
+    # edge: 4 (d+u + d+v) adjacency bytes + 8 edge bytes + 16 offset bytes)
     phase = {k: statistics.mean(t[k] for t in timings) for k in timings[0]}
     kernels = {"k_tc_small": ("small_ms", "small"), "k_tc_cta": ("cta_ms", "cta"), "k_tc_hub": ("hub_ms", "hub")}
     name = max(kernels, key=lambda k: phase[kernels[k][0]])

@@ -207,8 +207,8 @@ tc_status tc_graph_build_timing(const tc_graph* g, float* ms, int count);
 tc_status tc_graph_plan_stats(tc_graph* g, int64_t* edges, int64_t* ids);
 
 /*
- * Batches: G independent graphs in one object (north-star pattern "batching";
- * the paper has no counterpart).  Graph g has n[g] vertices with local ids
+ * Batches: G independent graphs in one object (an addition of this library; the
+ * paper has no counterpart).  Graph g has n[g] vertices with local ids
  * [0, n[g]) and the pairs src/dst[edge_off[g] .. edge_off[g+1]).  The batch is
  * counted as one disjoint union: vertex (g, i) becomes union id vbase[g] + i with
  * vbase[g] = n[0] + ... + n[g-1].  t[] and LCC[] from lcc_compute on a batch are
@@ -235,6 +235,9 @@ tc_status tc_batch_size(const tc_graph* g, int32_t* G);
  * Tuning of the intersection: strategy and Eq. 3 factor per bucket, and the hub
  * selection (min_degree, max hubs) and block-versus-warp split of hubs (hubs with
  * in-degree >= hub_big_in get a whole thread block, the others one warp).
+ * hub_core: the highest min(hub_core, hubs, 8192) ranks form a dense core whose
+ * triangles are counted by bit-parallel row intersections (every out-neighbour of a
+ * core vertex lies in the core); 0 turns the core off.  Default 8192.
  */
 typedef struct tc_tuning {
     int32_t strategy[TC_NUM_BUCKETS];
@@ -242,6 +245,7 @@ typedef struct tc_tuning {
     int32_t hub_min_degree;
     int32_t hub_max;
     int32_t hub_big_in;
+    int32_t hub_core;
 } tc_tuning;
 
 tc_status tc_graph_get_tuning(const tc_graph* g, tc_tuning* out);
@@ -291,7 +295,7 @@ tc_status tc_generate_edges(int kind, int32_t n, int64_t m, uint64_t seed, uint6
                             int32_t* dst, void* cuda_stream);
 
 /*
- * Serving (north-star pattern "serving"; the paper has no counterpart): a request
+ * Serving (an addition of this library; the paper has no counterpart): a request
  * loop that accepts TC/LCC jobs on graphs of different sizes as they arrive.
  * `slots` worker threads, each with its own CUDA stream on the device current at
  * start, take the oldest waiting request as soon as they are free and the device

@@ -64,13 +64,15 @@ TC_RUN_GRAPH = 1
 class TcTuning(ctypes.Structure):
     """struct tc_tuning of include/tc.h."""
     _fields_ = [("strategy", ctypes.c_int32 * 3), ("factor", ctypes.c_double * 3),
-                ("hub_min_degree", ctypes.c_int32), ("hub_max", ctypes.c_int32), ("hub_big_in", ctypes.c_int32)]
+                ("hub_min_degree", ctypes.c_int32), ("hub_max", ctypes.c_int32), ("hub_big_in", ctypes.c_int32),
+                ("hub_core", ctypes.c_int32)]
 
     def to_dict(self) -> dict:
         names = {v: k for k, v in STRATEGIES.items()}
         return {"strategy": {b: names[self.strategy[i]] for b, i in BUCKETS.items()},
                 "factor": {b: self.factor[i] for b, i in BUCKETS.items()},
-                "hub_min_degree": self.hub_min_degree, "hub_max": self.hub_max, "hub_big_in": self.hub_big_in}
+                "hub_min_degree": self.hub_min_degree, "hub_max": self.hub_max, "hub_big_in": self.hub_big_in,
+                "hub_core": self.hub_core}
 
     @classmethod
     def from_dict(cls, d: dict) -> "TcTuning":
@@ -82,6 +84,7 @@ class TcTuning(ctypes.Structure):
         t.hub_min_degree = int(d["hub_min_degree"])
         t.hub_max = int(d["hub_max"])
         t.hub_big_in = int(d["hub_big_in"])
+        t.hub_core = int(d.get("hub_core", 8192))
         return t
 TC_NOALLOC_MAX_N, TC_NOALLOC_MAX_M = 16384, 262144
 

@@ -110,6 +110,11 @@ struct tc_graph {
     int32_t* med_list = nullptr;
     int4* in_rec = nullptr;
     void* plan_tmp = nullptr;
+    int32_t core_cap = 0;
+    int32_t core_words = 0;
+    uint32_t* core_bits = nullptr;  // Out rows, In rows, core in-degrees
+    int32_t* core_lohi = nullptr;   // lowest in-neighbour, highest out-neighbour
+
     unsigned long long* t_rank = nullptr;
     DevStats* stats = nullptr;
     std::vector<void*> blocks;
@@ -187,6 +192,7 @@ tc_status new_graph(int32_t n, void* stream, tc_graph** out) {
     g->strat.hub_min_degree = 32;
     g->strat.hub_max = HUB_BM_BITS;
     g->strat.hub_big_in = 256;
+    g->strat.hub_core = CORE_MAX;
     *out = g;
     return TC_OK;
 }
@@ -216,6 +222,9 @@ tc_status build_graph(tc_graph* g, const int32_t* src, const int32_t* dst, int64
     g->m_alloc = m;
     g->hub_cap = n < HUB_BM_BITS ? n : HUB_BM_BITS;
     const size_t hc = (size_t)g->hub_cap;
+    g->core_cap = g->hub_cap < CORE_MAX ? g->hub_cap : CORE_MAX;
+    g->core_words = core_words_for(g->core_cap);
+    const size_t cc = (size_t)g->core_cap;
     if ((st = dalloc(g, &g->stats, 1, &keep)) || (st = dalloc(g, &g->rank, nn, &keep)) ||
         (st = dalloc(g, &g->rowstart, nn + 1, &keep)) || (st = dalloc(g, &g->rowlen, nn, &keep)) ||
         (st = dalloc(g, &g->rowinfo, nn, &keep)) ||
@@ -226,7 +235,9 @@ tc_status build_graph(tc_graph* g, const int32_t* src, const int32_t* dst, int64
         (st = dalloc(g, &g->hub_cur, hc + 1, &keep)) || (st = dalloc(g, &g->big_list, hc + 1, &keep)) ||
         (st = dalloc(g, &g->med_list, hc + 1, &keep)) || (st = dalloc(g, &g->in_rec, (size_t)m, &keep)) ||
         (st = dalloc(g, (char**)&g->plan_tmp, scan_tmp_bytes((int64_t)hc + 1), &keep)) ||
-        (st = dalloc(g, &g->t_rank, nn, &keep)))
+        (st = dalloc(g, &g->t_rank, nn, &keep)) ||
+        (st = dalloc(g, &g->core_bits, 2 * cc * (size_t)g->core_words + cc, &keep)) ||
+        (st = dalloc(g, &g->core_lohi, 2 * cc, &keep)))
         return st;
     std::vector<void*> scratch;
     BuildBuffers B{};
@@ -316,6 +327,14 @@ CountBuffers count_buffers(tc_graph* g) {
     C.med_list = g->med_list;
     C.in_rec = g->in_rec;
     C.tmp = g->plan_tmp;
+    C.core_cap = g->core_cap;
+    C.core_words = g->core_words;
+    const size_t rows = (size_t)g->core_cap * (size_t)g->core_words;
+    C.core_out = g->core_bits;
+    C.core_in = g->core_bits + rows;
+    C.core_cnt = g->core_bits + 2 * rows;
+    C.core_lo = g->core_lohi;
+    C.core_hi = g->core_lohi + g->core_cap;
     C.t_rank = g->t_rank;
     C.stats = g->stats;
     return C;
@@ -786,7 +805,7 @@ static tc_status tuning_check(const tc_tuning* t) {
         if (b == TC_BUCKET_SMALL && (s == TC_STRAT_PROBE || s == TC_STRAT_BITMAP)) return TC_EINVAL;
         if (b == TC_BUCKET_HUB && (s == TC_STRAT_MERGE || s == TC_STRAT_SEARCH)) return TC_EINVAL;
     }
-    if (t->hub_min_degree < 0 || t->hub_max < 0 || t->hub_big_in < 1) return TC_EINVAL;
+    if (t->hub_min_degree < 0 || t->hub_max < 0 || t->hub_big_in < 1 || t->hub_core < 0) return TC_EINVAL;
     return TC_OK;
 }
 
@@ -798,11 +817,12 @@ static void tuning_get(const Strategy& S, tc_tuning* t) {
     t->hub_min_degree = S.hub_min_degree;
     t->hub_max = S.hub_max;
     t->hub_big_in = S.hub_big_in;
+    t->hub_core = S.hub_core;
 }
 
 static void tuning_put(tc_graph* g, const tc_tuning* t) {
     const bool replan = g->strat.hub_min_degree != t->hub_min_degree || g->strat.hub_max != t->hub_max ||
-                        g->strat.hub_big_in != t->hub_big_in;
+                        g->strat.hub_big_in != t->hub_big_in || g->strat.hub_core != t->hub_core;
     for (int b = 0; b < TC_NUM_BUCKETS; ++b) {
         g->strat.strat[b] = t->strategy[b];
         g->strat.factor[b] = (float)t->factor[b];
@@ -810,6 +830,7 @@ static void tuning_put(tc_graph* g, const tc_tuning* t) {
     g->strat.hub_min_degree = t->hub_min_degree;
     g->strat.hub_max = t->hub_max < HUB_BM_BITS ? t->hub_max : HUB_BM_BITS;
     g->strat.hub_big_in = t->hub_big_in;
+    g->strat.hub_core = t->hub_core < CORE_MAX ? t->hub_core : CORE_MAX;
     if (replan) g->planned = false;
     g->counted = false;
 }
@@ -824,6 +845,7 @@ static tc_tuning default_tuning() {
     t.hub_min_degree = 32;
     t.hub_max = HUB_BM_BITS;
     t.hub_big_in = 256;
+    t.hub_core = CORE_MAX;
     return t;
 }
 

@@ -33,7 +33,7 @@ struct DevStats {
     unsigned int hub_big;          // hubs processed by whole blocks
     unsigned int mid_count;        // build: rows of 17..256 entries sorted by one warp
     unsigned int mid2_count;       // build: rows of 257..1024 entries sorted by one warp
-    unsigned int pad[1];
+    unsigned int core_n;           // planner: dense core size (ranks n - core_n .. n-1)
 };
 static_assert(sizeof(DevStats) == 88, "DevStats layout");
 
@@ -110,10 +110,13 @@ struct Strategy {
     int hub_min_degree;   // vertices of degree >= this are hub candidates (<= 0: no hubs)
     int hub_max;          // at most this many hubs (the highest ranks)
     int hub_big_in;       // hubs with at least this in-degree get a whole block (else one warp)
+    int hub_core;         // the highest min(hub_core, hubs, CORE_MAX) ranks form the dense core (0: none)
 };
 
 // Capacity of the hub kernel's shared-memory bitmap (ranks above the hub).
 constexpr int HUB_BM_BITS = 131072;
+// Largest dense core (tc_core.cu): two core_n x core_n bit matrices.
+constexpr int CORE_MAX = 8192;
 
 struct CountBuffers {
     int32_t n;
@@ -133,6 +136,14 @@ struct CountBuffers {
     int32_t* med_list;       // hub_cap: the other hubs, highest rank first
     int4* in_rec;            // m: in-edge {u, first suffix entry, end of N+(u), 0} (indices into col)
     void* tmp;               // scan scratch, scan_tmp_bytes(hub_cap + 1)
+    // dense core (tc_core.cu): bit rows of core_words words for core indices 0 .. core_cap-1
+    int32_t core_cap;        // min(hub_cap, CORE_MAX)
+    int32_t core_words;      // core_words_for(core_cap)
+    uint32_t* core_out;      // core_cap * core_words; followed by core_in and core_cnt
+    uint32_t* core_in;       // core_cap * core_words
+    uint32_t* core_cnt;      // core_cap: in-degree from the core
+    int32_t* core_lo;        // core_cap: lowest core in-neighbour
+    int32_t* core_hi;        // core_cap: highest core out-neighbour (-1: none)
     unsigned long long* t_rank;  // n
     DevStats* stats;
 };
@@ -141,6 +152,10 @@ enum { PH_PLAN = 0, PH_SMALL, PH_CTA, PH_HUB, PH_END, PH_EVENTS };
 
 // Builds the bucket lists and the hub in-edge lists.
 void launch_plan(const CountBuffers& C, const Strategy& S, const Launch& L);
+// Dense core (tc_core.cu): bit matrices after the hub count is known, and the count.
+int core_words_for(int32_t core_cap);
+void launch_core_plan(const CountBuffers& C, const Launch& L);
+void launch_core_count(const CountBuffers& C, const Launch& L);
 cudaError_t intersect_init_attributes();
 // Runs the three bucket kernels; ev (may be null) holds PH_EVENTS events.
 void launch_intersect(const CountBuffers& C, const Strategy& S, cudaEvent_t* ev, const Launch& L);

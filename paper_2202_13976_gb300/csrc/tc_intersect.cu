@@ -329,21 +329,27 @@ __global__ void k_hub_candidates(int32_t n, const int32_t* __restrict__ deg, int
     if (lane_id() == 0 && c) atomicAdd(&stats->hub_candidates, c);
 }
 
-__global__ void k_hub_count(int32_t hub_cap, int hub_max, DevStats* stats) {
+__global__ void k_hub_count(int32_t hub_cap, int hub_max, int core_max, DevStats* stats) {
     unsigned k = stats->hub_candidates;
     k = min(k, (unsigned)hub_max);
     k = min(k, (unsigned)hub_cap);
     stats->hub_count = k;
+    stats->core_n = min(k, (unsigned)core_max);
 }
 
-// In-degree d-(v) = deg(v) - d+(v) of every hub slot (0 for slots below the hubs).
+// In-degree d-(v) = deg(v) - d+(v) of every hub slot (0 for slots below the hubs),
+// less the in-edges from the dense core, which the core count covers.
 __global__ void k_hub_indeg(int32_t n, int32_t hub_cap, const int32_t* __restrict__ deg,
-                            const int32_t* __restrict__ rowlen, uint32_t* __restrict__ cnt, DevStats* stats) {
+                            const int32_t* __restrict__ rowlen, const uint32_t* __restrict__ core_cnt,
+                            uint32_t* __restrict__ cnt, DevStats* stats) {
     const int32_t R = n - (int32_t)stats->hub_count;
+    const int32_t c0 = n - (int32_t)stats->core_n;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < hub_cap; i += stride) {
         const int32_t r = n - hub_cap + (int32_t)i;
-        cnt[i] = r >= R ? (uint32_t)(deg[r] - rowlen[r]) : 0u;
+        uint32_t d = r >= R ? (uint32_t)(deg[r] - rowlen[r]) : 0u;
+        if (r >= c0) d -= core_cnt[r - c0];
+        cnt[i] = d;
     }
 }
 
@@ -357,11 +363,12 @@ __global__ void k_hub_scatter(int32_t n, int32_t hub_cap, const int64_t* __restr
                               const int64_t* __restrict__ hub_start, uint32_t* __restrict__ hub_cur,
                               int4* __restrict__ in_rec, DevStats* stats) {
     const int32_t R = n - (int32_t)stats->hub_count;
+    const int32_t c0 = n - (int32_t)stats->core_n;  // rows of the dense core are counted there
     const int lane = lane_id();
     const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
-    for (int64_t w0 = (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 32; w0 < n; w0 += warps * 32) {
+    for (int64_t w0 = (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 32; w0 < c0; w0 += warps * 32) {
         const int64_t u = w0 + lane;
-        const int du = u < n ? rowlen[u] : 0;
+        const int du = u < c0 ? rowlen[u] : 0;
         const int64_t base = u < n ? rowstart[u] : 0;
         int p = du - 1;
         // SCAT_STEPS steps at a time: their loads, then their slot reservations, are
@@ -977,11 +984,13 @@ void launch_plan(const CountBuffers& C, const Strategy& S, const Launch& L) {
                                                                                  C.stats);
         count_launch();
     }
-    k_hub_count<<<1, 1, 0, L.stream>>>(C.hub_cap, hub_max, C.stats);
+    const int core_max = hubs && C.core_cap > 0 && S.hub_core > 0 ? (S.hub_core < C.core_cap ? S.hub_core : C.core_cap) : 0;
+    k_hub_count<<<1, 1, 0, L.stream>>>(C.hub_cap, hub_max, core_max, C.stats);
     count_launch();
     if (hubs) {
+        if (core_max > 0) launch_core_plan(C, L);
         k_hub_indeg<<<grid_for(C.hub_cap, THREADS, L.sms), THREADS, 0, L.stream>>>(C.n, C.hub_cap, C.deg, C.rowlen,
-                                                                                  C.hub_cnt, C.stats);
+                                                                                  C.core_cnt, C.hub_cnt, C.stats);
         count_launch();
         scan_u32_to_i64(C.hub_cnt, C.hub_start, C.hub_cap, C.tmp, L);
         cudaMemsetAsync(C.hub_cur, 0, sizeof(uint32_t) * (size_t)C.hub_cap, L.stream);
@@ -1033,6 +1042,7 @@ void launch_intersect(const CountBuffers& C, const Strategy& S, cudaEvent_t* ev,
     count_launch();
     if (ev) cudaEventRecord(ev[PH_HUB], L.stream);
     if (C.hub_cap > 0) {
+        if (S.hub_core > 0) launch_core_count(C, L);
         cudaMemsetAsync(&C.stats->hub_next, 0, 2 * sizeof(unsigned), L.stream);
         k_tc_hub<<<L.sms * 5, HUB_THREADS, sizeof(HubShared), L.stream>>>(
             C.n, C.hub_cap, C.rowstart, C.rowlen, C.col, C.hub_start, C.big_list, C.med_list, C.in_rec, C.t_rank,

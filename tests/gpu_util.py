@@ -7,12 +7,13 @@ import numpy as np
 import oracle
 
 
-def gpu_run(tc, n, src, dst, device_io=False, strategies=None, csr=None, stream=None, hubs=None):
+def gpu_run(tc, n, src, dst, device_io=False, strategies=None, csr=None, stream=None, hubs=None, tuning=None):
     """T, t, lcc and input accounting from the CUDA library.
 
     device_io: inputs and outputs as CUDA tensors (TC_MEM_DEVICE), else numpy.
     strategies: {bucket: (strategy, factor)} applied before counting.
     hubs: (min_degree, max_hubs) for the hub bucket.
+    tuning: {field: value} merged into the graph's tuning before counting.
     csr: (offsets, adj) to build from CSR instead of the edge list."""
     import torch
     if csr is not None:
@@ -30,6 +31,10 @@ def gpu_run(tc, n, src, dst, device_io=False, strategies=None, csr=None, stream=
             g.set_strategy(bucket, s, f)
         if hubs is not None:
             g.set_hubs(*hubs)
+        if tuning:
+            t0 = g.tuning()
+            t0.update(tuning)
+            g.set_tuning(t0)
         T = g.count()
         if device_io:
             t = torch.empty(n, dtype=torch.int64, device="cuda")

@@ -77,6 +77,25 @@ def test_hub_strategies_agree(tc, rmat14, hub, hubs):
     assert_matches_oracle(tc, n, s, d, ref=ref, strategies={tc.TC_BUCKET_HUB: hub}, hubs=hubs)
 
 
+# dense core sizes: off, one vertex, a partial word, several words, the default
+CORE_SETTINGS = [0, 1, 33, 200, 8192]
+
+
+@pytest.mark.parametrize("core", CORE_SETTINGS)
+@pytest.mark.parametrize("hubs", HUB_SETTINGS)
+def test_dense_core_sizes_agree(tc, rmat14, core, hubs):
+    n, s, d, ref = rmat14
+    assert_matches_oracle(tc, n, s, d, ref=ref, hubs=hubs, tuning={"hub_core": core})
+
+
+@pytest.mark.parametrize("core", CORE_SETTINGS)
+@pytest.mark.parametrize("make", [lambda: F.complete(90), lambda: F.wheel(40),
+                                  lambda: F.complete_tripartite(3, 5, 40), lambda: F.friendship(7)])
+def test_dense_core_closed_forms(tc, make, core):
+    n, (s, d) = make()
+    assert_matches_oracle(tc, n, s, d, hubs=(1, 131072), tuning={"hub_core": core})
+
+
 def test_strategy_rejects_unsupported_pairs(tc, er4096):
     n, s, d, _ = er4096
     g = tc.Graph.from_edges(n, s, d)
