@@ -59,6 +59,7 @@ __global__ void __launch_bounds__(CORE_THREADS) k_core_build(int32_t n, const in
 __device__ __forceinline__ uint32_t and_popc(const uint32_t* __restrict__ row, const uint32_t (&mine)[CORE_LANE_WORDS],
                                              int first, int w0, int w1) {
     uint32_t c = 0;
+    if (w0 > w1) return 0;  // empty range
 #pragma unroll
     for (int h = 0; h < CORE_LANE_WORDS / 4; ++h) {
         const int q = first + 4 * h;  // word index of this uint4
