@@ -266,7 +266,10 @@ def run_ours(args, rank, world, local):
     # dominant intersection kernel and its roofline (algorithmic bytes per oriented
     # edge: 4 (d+u + d+v) adjacency bytes + 8 edge bytes + 16 offset bytes)
     phase = {k: statistics.mean(t[k] for t in timings) for k in timings[0]}
-    kernels = {"k_tc_small": ("small_ms", "small"), "k_tc_cta": ("cta_ms", "cta"), "k_tc_hub": ("hub_ms", "hub")}
+    # each bucket phase, timed by events around its launches: small = three group
+    # widths, hub = the dense-core count followed by the hub kernel
+    kernels = {"k_tc_small<8>+k_tc_small<16>+k_tc_small<32>": ("small_ms", "small"), "k_tc_cta": ("cta_ms", "cta"),
+               "k_core_count+k_tc_hub": ("hub_ms", "hub")}
     name = max(kernels, key=lambda k: phase[kernels[k][0]])
     kms = phase[kernels[name][0]]
     b = plan[kernels[name][1]]
