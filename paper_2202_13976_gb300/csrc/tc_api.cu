@@ -109,6 +109,7 @@ struct tc_graph {
     int32_t* big_list = nullptr;
     int32_t* med_list = nullptr;
     int4* in_rec = nullptr;
+    int32_t* rowof = nullptr;
     void* plan_tmp = nullptr;
     int32_t core_cap = 0;
     int32_t core_words = 0;
@@ -234,6 +235,7 @@ tc_status build_graph(tc_graph* g, const int32_t* src, const int32_t* dst, int64
         (st = dalloc(g, &g->hub_cnt, hc + 1, &keep)) || (st = dalloc(g, &g->hub_start, hc + 1, &keep)) ||
         (st = dalloc(g, &g->hub_cur, hc + 1, &keep)) || (st = dalloc(g, &g->big_list, hc + 1, &keep)) ||
         (st = dalloc(g, &g->med_list, hc + 1, &keep)) || (st = dalloc(g, &g->in_rec, (size_t)m, &keep)) ||
+        (st = dalloc(g, &g->rowof, (size_t)m, &keep)) ||
         (st = dalloc(g, (char**)&g->plan_tmp, scan_tmp_bytes((int64_t)hc + 1), &keep)) ||
         (st = dalloc(g, &g->t_rank, nn, &keep)) ||
         (st = dalloc(g, &g->core_bits, 2 * cc * (size_t)g->core_words + cc, &keep)) ||
@@ -326,6 +328,8 @@ CountBuffers count_buffers(tc_graph* g) {
     C.big_list = g->big_list;
     C.med_list = g->med_list;
     C.in_rec = g->in_rec;
+    C.rowof = g->rowof;
+    C.m_cap = g->m_alloc;
     C.tmp = g->plan_tmp;
     C.core_cap = g->core_cap;
     C.core_words = g->core_words;

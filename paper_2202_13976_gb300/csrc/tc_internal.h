@@ -135,6 +135,8 @@ struct CountBuffers {
     int32_t* big_list;       // hub_cap: big hubs, highest rank first
     int32_t* med_list;       // hub_cap: the other hubs, highest rank first
     int4* in_rec;            // m: in-edge {u, first suffix entry, end of N+(u), 0} (indices into col)
+    int32_t* rowof;          // m: source row of each entry of the non-core rows
+    int64_t m_cap;           // entries of col (and of in_rec, rowof)
     void* tmp;               // scan scratch, scan_tmp_bytes(hub_cap + 1)
     // dense core (tc_core.cu): bit rows of core_words words for core indices 0 .. core_cap-1
     int32_t core_cap;        // min(hub_cap, CORE_MAX)

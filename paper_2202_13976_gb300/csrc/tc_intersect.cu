@@ -52,7 +52,7 @@ constexpr int HUB_BM_WORDS = HUB_BM_BITS / 32;
 constexpr int HUB_CNT_MAX = 4096;      // hub lists longer than this count matches globally
 constexpr int HUB_WARP_MAX = 256;      // longest N+(v) a single warp stages
 constexpr int HUB_HASH_MAX = 512;      // its hash table: at least twice as many slots as keys
-constexpr int SCAT_STEPS = 4;          // lockstep steps of the hub in-edge scatter in flight together
+constexpr int SCAT_STEPS = 4;          // lockstep steps of the row-walk scatter in flight together
 constexpr int HUB_LONG = 32;           // suffixes at least this long are read by lane groups
 constexpr int HUB_GROUPS = 4;          // long suffixes one warp reads at a time
 constexpr int HUB_GLANES = 32 / HUB_GROUPS;
@@ -353,17 +353,144 @@ __global__ void k_hub_indeg(int32_t n, int32_t hub_cap, const int32_t* __restric
     }
 }
 
-// Every oriented entry (u -> v) with v a hub becomes an in-edge record of v:
-// {u, index after v in N+(u), end of N+(u), 0}, one 16-byte store.  A warp takes 32
-// consecutive rows (one per lane) and walks their hub tails from the end backwards
-// in lockstep; the highest-ranked hubs end almost every row, so lanes that name the
-// same hub in a step reserve their slots with one atomic.
-__global__ void k_hub_scatter(int32_t n, int32_t hub_cap, const int64_t* __restrict__ rowstart,
-                              const int32_t* __restrict__ rowlen, const int32_t* __restrict__ col,
-                              const int64_t* __restrict__ hub_start, uint32_t* __restrict__ hub_cur,
-                              int4* __restrict__ in_rec, DevStats* stats) {
+// The hub in-edge records are written by tiles of entries (k_row_of, k_hub_scatter)
+// when the hub in-edges are at least a quarter of the entries of the non-core rows,
+// else by a walk over the rows' hub tails (k_hub_scatter_rows).  All three kernels
+// are launched and read the choice from the planned counts.
+__device__ __forceinline__ bool scatter_by_tiles(const int64_t* __restrict__ hub_start, int32_t hub_cap,
+                                                 const int64_t* __restrict__ rowstart, int32_t c0) {
+    return 4 * hub_start[hub_cap] >= rowstart[c0];
+}
+
+// Source row of every entry of the non-core rows (whole row capacity, so that the
+// slots left free by deduplication also name a valid row).  A lane writes its own
+// row when it holds at most 32 entries; longer rows are written by the whole warp.
+__global__ void k_row_of(int32_t n, int32_t hub_cap, const int64_t* __restrict__ rowstart,
+                         const int64_t* __restrict__ hub_start, int32_t* __restrict__ rowof, const DevStats* stats) {
+    const int32_t c0 = n - (int32_t)stats->core_n;
+    if (!scatter_by_tiles(hub_start, hub_cap, rowstart, c0)) return;
+    const int lane = lane_id();
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    // the loop bound is uniform across a warp, as the ballot needs all 32 lanes
+    for (int64_t b = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); b < c0; b += stride) {
+        const int64_t u = b + lane;
+        const int64_t a0 = u < c0 ? rowstart[u] : 0, a1 = u < c0 ? rowstart[u + 1] : 0;
+        const bool longrow = a1 - a0 > 32;
+        if (!longrow)
+            for (int64_t p = a0; p < a1; ++p) rowof[p] = (int32_t)u;
+        unsigned lm = __ballot_sync(FULL, longrow);
+        while (lm) {
+            const int r = __ffs(lm) - 1;
+            lm &= lm - 1;
+            const int64_t ar = __shfl_sync(FULL, a0, r), br = __shfl_sync(FULL, a1, r);
+            for (int64_t p = ar + lane; p < br; p += 32) rowof[p] = (int32_t)(b + r);
+        }
+    }
+}
+
+// Every oriented entry (u -> v) of a row outside the dense core with v a hub becomes
+// an in-edge record of v: {u, index after v in N+(u), end of N+(u), 0}, one 16-byte
+// store into v's segment.  Blocks take tiles of SCAT_TILE consecutive entries (16
+// bytes per thread and load), so the work is spread evenly whatever the row lengths;
+// entries in the slots deduplication left free are skipped.  The SCAT_TOP highest
+// hubs, whose cursors every tile would contend for, are served per tile: shared-
+// memory counters give each entry its offset, then one global atomic per hub and
+// tile reserves the tile's run; the other hubs take their slot from a global
+// cursor per entry.  Records of one tile stay together, nearly in source order.
+constexpr int SCAT_THREADS = 256;
+constexpr int SCAT_ITEMS = 8;  // entries per thread and tile (two 16-byte loads)
+constexpr int SCAT_TILE = SCAT_THREADS * SCAT_ITEMS;
+constexpr int SCAT_TOP = 2048;
+
+__global__ void __launch_bounds__(SCAT_THREADS) k_hub_scatter(int32_t n, int32_t hub_cap,
+                                                              const int64_t* __restrict__ rowstart,
+                                                              const int2* __restrict__ rowinfo,
+                                                              const int32_t* __restrict__ col,
+                                                              const int32_t* __restrict__ rowof,
+                                                              const int64_t* __restrict__ hub_start,
+                                                              uint32_t* __restrict__ hub_cur, int4* __restrict__ in_rec,
+                                                              DevStats* stats) {
+    __shared__ uint32_t lcnt[SCAT_TOP];
+    __shared__ int64_t gbase[SCAT_TOP];
     const int32_t R = n - (int32_t)stats->hub_count;
     const int32_t c0 = n - (int32_t)stats->core_n;  // rows of the dense core are counted there
+    const int top = min((int)stats->hub_count, SCAT_TOP);
+    const int32_t T0 = n - top;  // top hubs: ranks T0 .. n-1 (all hubs)
+    const int32_t H0 = n - hub_cap;  // rank of hub slot 0
+    if (!scatter_by_tiles(hub_start, hub_cap, rowstart, c0)) return;
+    const int64_t mend = rowstart[c0];
+    for (int64_t t0 = (int64_t)blockIdx.x * SCAT_TILE; t0 < mend; t0 += (int64_t)gridDim.x * SCAT_TILE) {
+        for (int h = threadIdx.x; h < top; h += SCAT_THREADS) lcnt[h] = 0;
+        __syncthreads();
+        int32_t x[SCAT_ITEMS], u[SCAT_ITEMS], end[SCAT_ITEMS];
+        uint32_t loc[SCAT_ITEMS];
+#pragma unroll
+        for (int k = 0; k < SCAT_ITEMS / 4; ++k) {
+            const int64_t e0 = t0 + ((int64_t)k * SCAT_THREADS + threadIdx.x) * 4;
+            if (e0 + 3 < mend) {
+                const int4 q = *reinterpret_cast<const int4*>(col + e0);
+                x[4 * k] = q.x, x[4 * k + 1] = q.y, x[4 * k + 2] = q.z, x[4 * k + 3] = q.w;
+            } else {
+#pragma unroll
+                for (int j = 0; j < 4; ++j) x[4 * k + j] = e0 + j < mend ? col[e0 + j] : -1;
+            }
+        }
+#pragma unroll
+        for (int e = 0; e < SCAT_ITEMS; ++e) {
+            const int64_t p = t0 + ((int64_t)(e >> 2) * SCAT_THREADS + threadIdx.x) * 4 + (e & 3);
+            if (x[e] >= R) {
+                u[e] = rowof[p];
+                const int2 ri = rowinfo[u[e]];
+                end[e] = ri.x + ri.y;
+                if (p >= end[e]) x[e] = -1;  // a slot freed by deduplication
+            }
+            if (x[e] >= T0) {
+                loc[e] = atomicAdd(&lcnt[x[e] - T0], 1u);
+            } else if (x[e] >= R) {
+                const int i = x[e] - H0;
+                const int64_t slot = hub_start[i] + atomicAdd(&hub_cur[i], 1u);
+                if (slot < hub_start[i + 1])  // counts and entries disagree only on a bug: never write outside
+                    in_rec[slot] = make_int4(u[e], (int32_t)(p + 1), end[e], 0);
+                else
+                    atomicOr(&stats->err, ERR_OVERFLOW);
+            }
+        }
+        __syncthreads();
+        for (int h = threadIdx.x; h < top; h += SCAT_THREADS) {
+            const uint32_t c = lcnt[h];
+            if (c) {
+                const int i = T0 + h - H0;
+                gbase[h] = hub_start[i] + atomicAdd(&hub_cur[i], c);
+            }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int e = 0; e < SCAT_ITEMS; ++e) {
+            if (x[e] < T0) continue;
+            const int64_t p = t0 + ((int64_t)(e >> 2) * SCAT_THREADS + threadIdx.x) * 4 + (e & 3);
+            const int i = x[e] - H0;
+            const int64_t slot = gbase[x[e] - T0] + loc[e];
+            if (slot < hub_start[i + 1])
+                in_rec[slot] = make_int4(u[e], (int32_t)(p + 1), end[e], 0);
+            else
+                atomicOr(&stats->err, ERR_OVERFLOW);
+        }
+        __syncthreads();  // lcnt and gbase are reused by the next tile
+    }
+}
+
+// The same records when hub entries are a small share of the entries (flat degree
+// distributions): a warp takes 32 consecutive rows (one per lane) and walks their
+// hub tails from the end backwards in lockstep, so rows without a hub cost one
+// load; the highest-ranked hubs end almost every row, so lanes that name the same
+// hub in a step reserve their slots with one atomic.
+__global__ void k_hub_scatter_rows(int32_t n, int32_t hub_cap, const int64_t* __restrict__ rowstart,
+                                   const int32_t* __restrict__ rowlen, const int32_t* __restrict__ col,
+                                   const int64_t* __restrict__ hub_start, uint32_t* __restrict__ hub_cur,
+                                   int4* __restrict__ in_rec, DevStats* stats) {
+    const int32_t R = n - (int32_t)stats->hub_count;
+    const int32_t c0 = n - (int32_t)stats->core_n;  // rows of the dense core are counted there
+    if (scatter_by_tiles(hub_start, hub_cap, rowstart, c0)) return;
     const int lane = lane_id();
     const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
     for (int64_t w0 = (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 32; w0 < c0; w0 += warps * 32) {
@@ -994,8 +1121,14 @@ void launch_plan(const CountBuffers& C, const Strategy& S, const Launch& L) {
         count_launch();
         scan_u32_to_i64(C.hub_cnt, C.hub_start, C.hub_cap, C.tmp, L);
         cudaMemsetAsync(C.hub_cur, 0, sizeof(uint32_t) * (size_t)C.hub_cap, L.stream);
-        k_hub_scatter<<<grid_for(C.n, THREADS, L.sms), THREADS, 0, L.stream>>>(
+        k_row_of<<<grid_for((int64_t)C.n, THREADS, L.sms), THREADS, 0, L.stream>>>(C.n, C.hub_cap, C.rowstart,
+                                                                                  C.hub_start, C.rowof, C.stats);
+        count_launch();
+        k_hub_scatter_rows<<<grid_for(C.n, THREADS, L.sms), THREADS, 0, L.stream>>>(
             C.n, C.hub_cap, C.rowstart, C.rowlen, C.col, C.hub_start, C.hub_cur, C.in_rec, C.stats);
+        count_launch();
+        k_hub_scatter<<<grid_for((int64_t)C.m_cap / SCAT_ITEMS + 1, SCAT_THREADS, L.sms), SCAT_THREADS, 0, L.stream>>>(
+            C.n, C.hub_cap, C.rowstart, C.rowinfo, C.col, C.rowof, C.hub_start, C.hub_cur, C.in_rec, C.stats);
         count_launch();
         // hub_cur is free again: it holds the big flags, hub_cnt (still the in-degrees
         // until here) is overwritten by their exclusive scan
