@@ -113,8 +113,8 @@ struct tc_graph {
     void* plan_tmp = nullptr;
     int32_t core_cap = 0;
     int32_t core_words = 0;
-    uint32_t* core_bits = nullptr;  // Out rows, In rows, core in-degrees
-    int32_t* core_lohi = nullptr;   // lowest in-neighbour, highest out-neighbour
+    uint32_t* core_bits = nullptr;  // adjacency rows, core in-degrees
+    int32_t* core_lohi = nullptr;   // lowest and highest neighbour, highest out-neighbour
 
     unsigned long long* t_rank = nullptr;
     DevStats* stats = nullptr;
@@ -192,7 +192,7 @@ tc_status new_graph(int32_t n, void* stream, tc_graph** out) {
     g->strat.strat[TC_BUCKET_CTA] = TC_STRAT_BITMAP;
     g->strat.hub_min_degree = 32;
     g->strat.hub_max = HUB_BM_BITS;
-    g->strat.hub_big_in = 256;
+    g->strat.hub_big_in = 128;
     g->strat.hub_core = CORE_MAX;
     *out = g;
     return TC_OK;
@@ -238,8 +238,8 @@ tc_status build_graph(tc_graph* g, const int32_t* src, const int32_t* dst, int64
         (st = dalloc(g, &g->rowof, (size_t)m, &keep)) ||
         (st = dalloc(g, (char**)&g->plan_tmp, scan_tmp_bytes((int64_t)hc + 1), &keep)) ||
         (st = dalloc(g, &g->t_rank, nn, &keep)) ||
-        (st = dalloc(g, &g->core_bits, 2 * cc * (size_t)g->core_words + cc, &keep)) ||
-        (st = dalloc(g, &g->core_lohi, 2 * cc, &keep)))
+        (st = dalloc(g, &g->core_bits, cc * (size_t)g->core_words + cc, &keep)) ||
+        (st = dalloc(g, &g->core_lohi, 3 * cc, &keep)))
         return st;
     std::vector<void*> scratch;
     BuildBuffers B{};
@@ -334,11 +334,11 @@ CountBuffers count_buffers(tc_graph* g) {
     C.core_cap = g->core_cap;
     C.core_words = g->core_words;
     const size_t rows = (size_t)g->core_cap * (size_t)g->core_words;
-    C.core_out = g->core_bits;
-    C.core_in = g->core_bits + rows;
-    C.core_cnt = g->core_bits + 2 * rows;
+    C.core_z = g->core_bits;
+    C.core_cnt = g->core_bits + rows;
     C.core_lo = g->core_lohi;
     C.core_hi = g->core_lohi + g->core_cap;
+    C.core_hiout = g->core_lohi + 2 * (size_t)g->core_cap;
     C.t_rank = g->t_rank;
     C.stats = g->stats;
     return C;
@@ -848,7 +848,7 @@ static tc_tuning default_tuning() {
     t.strategy[TC_BUCKET_CTA] = TC_STRAT_BITMAP;
     t.hub_min_degree = 32;
     t.hub_max = HUB_BM_BITS;
-    t.hub_big_in = 256;
+    t.hub_big_in = 128;
     t.hub_core = CORE_MAX;
     return t;
 }
@@ -907,7 +907,7 @@ extern "C" tc_status tc_graph_autotune(tc_graph* g, int32_t force, tc_tuning* ou
     }
     float ms[5];
     // 1. hub threshold and block/warp split, default strategies
-    const int hub_cands[][2] = {{32, 256}, {16, 256}, {64, 256}, {128, 256}, {32, 64}, {32, 1024}};
+    const int hub_cands[][2] = {{32, 128}, {16, 128}, {64, 128}, {128, 128}, {32, 64}, {32, 256}, {32, 1024}};
     float best_total = 1e30f;
     for (const auto& hc : hub_cands) {
         tc_tuning t = default_tuning();

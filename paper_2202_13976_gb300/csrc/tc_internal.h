@@ -115,7 +115,7 @@ struct Strategy {
 
 // Capacity of the hub kernel's shared-memory bitmap (ranks above the hub).
 constexpr int HUB_BM_BITS = 131072;
-// Largest dense core (tc_core.cu): two core_n x core_n bit matrices.
+// Largest dense core (tc_core.cu): one core_n x core_n bit matrix.
 constexpr int CORE_MAX = 8192;
 
 struct CountBuffers {
@@ -141,11 +141,11 @@ struct CountBuffers {
     // dense core (tc_core.cu): bit rows of core_words words for core indices 0 .. core_cap-1
     int32_t core_cap;        // min(hub_cap, CORE_MAX)
     int32_t core_words;      // core_words_for(core_cap)
-    uint32_t* core_out;      // core_cap * core_words; followed by core_in and core_cnt
-    uint32_t* core_in;       // core_cap * core_words
+    uint32_t* core_z;        // core_cap * core_words: symmetric adjacency rows; followed by core_cnt
     uint32_t* core_cnt;      // core_cap: in-degree from the core
-    int32_t* core_lo;        // core_cap: lowest core in-neighbour
-    int32_t* core_hi;        // core_cap: highest core out-neighbour (-1: none)
+    int32_t* core_lo;        // core_cap: lowest core neighbour
+    int32_t* core_hi;        // core_cap: highest core neighbour (-1: none)
+    int32_t* core_hiout;     // core_cap: highest core out-neighbour (-1: none)
     unsigned long long* t_rank;  // n
     DevStats* stats;
 };
