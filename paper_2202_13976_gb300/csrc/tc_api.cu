@@ -256,7 +256,10 @@ tc_status build_graph(tc_graph* g, const int32_t* src, const int32_t* dst, int64
         (st = dalloc(g, &B.cursor, nn, &scratch)) || (st = dalloc(g, &B.longlist, nn, &scratch)) ||
         (st = dalloc(g, &B.midlist, nn, &scratch)) || (st = dalloc(g, &B.midlist2, nn, &scratch)) ||
         (st = dalloc(g, &B.dupin, nn, &scratch)) ||
-        (st = dalloc(g, &B.bcur, 256, &scratch)) || (st = dalloc(g, &B.pairs, (size_t)m, &scratch)) ||
+        (st = dalloc(g, &B.bcount, (size_t)BUCKET_MAX + 1, &scratch)) ||
+        (st = dalloc(g, &B.bcur, (size_t)BUCKET_MAX, &scratch)) ||
+        (st = dalloc(g, &B.bstart, (size_t)BUCKET_MAX + 1, &scratch)) ||
+        (st = dalloc(g, &B.pairs, (size_t)m, &scratch)) ||
         (st = dalloc(g, &tmp, tmp_bytes, &scratch))) {
         free_list(g, &scratch);
         return st;
@@ -293,10 +296,9 @@ tc_status build_graph(tc_graph* g, const int32_t* src, const int32_t* dst, int64
             return TC_EINVAL;
         }
         deg_bits = bits_for(h.max_deg);
-        // flat degree distribution (max degree within 64x the mean): fill rows through
-        // buckets; skewed graphs keep the direct scatter, whose hot rows stay in cache
+        // flat degree distribution (max degree within 64x the mean): rows through buckets
         const double mean = n > 0 ? 2.0 * (double)m / (double)n : 0.0;
-        B.two_level_fill = m > 0 && (double)h.max_deg <= 64.0 * mean;
+        B.bucket_fill = m > 0 && (double)h.max_deg <= 64.0 * mean;
     }
     launch_rank(B, deg_bits, g->L);
     if (bev) cudaEventRecord(bev[BP_RANK], g->stream);

@@ -64,6 +64,7 @@ __global__ void k_expand_csr(const int64_t* __restrict__ offsets, int32_t n, int
 // looked at); hub vertices occur often enough to take a slot early, so their many
 // increments stay in shared memory and reach dmulti with one atomic per block.
 // Vertices that find no slot add to dmulti directly.
+constexpr int PAIR_UNROLL = 4;  // pairs per thread and round in the pair passes
 constexpr int DEG_SLOTS = 4096;
 constexpr int DEG_PROBES = 4;
 
@@ -96,15 +97,25 @@ __global__ void __launch_bounds__(THREADS) k_canon_degree(const int32_t* __restr
     unsigned long long loops = 0;
     int err = 0;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += stride) {
-        const int32_t a = src[i], c = dst[i];
-        if ((uint32_t)a >= (uint32_t)n || (uint32_t)c >= (uint32_t)n) {
-            err = ERR_BAD_ID;
-        } else if (a == c) {
-            ++loops;
-        } else {
-            deg_add(a, hk, hc, dmulti);
-            deg_add(c, hk, hc, dmulti);
+    for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i0 < m; i0 += PAIR_UNROLL * stride) {
+        int32_t a[PAIR_UNROLL], c[PAIR_UNROLL];
+#pragma unroll
+        for (int k = 0; k < PAIR_UNROLL; ++k) {
+            const int64_t i = i0 + k * stride;
+            a[k] = i < m ? src[i] : 0;
+            c[k] = i < m ? dst[i] : 0;
+        }
+#pragma unroll
+        for (int k = 0; k < PAIR_UNROLL; ++k) {
+            if (i0 + k * stride >= m) break;
+            if ((uint32_t)a[k] >= (uint32_t)n || (uint32_t)c[k] >= (uint32_t)n) {
+                err = ERR_BAD_ID;
+            } else if (a[k] == c[k]) {
+                ++loops;
+            } else {
+                deg_add(a[k], hk, hc, dmulti);
+                deg_add(c[k], hk, hc, dmulti);
+            }
         }
     }
     __syncthreads();
@@ -145,14 +156,25 @@ __global__ void k_rank_invert(const uint64_t* __restrict__ sorted, int32_t n, in
     }
 }
 
+// Both passes take PAIR_UNROLL pairs per thread and round (pair i0 + k * stride), so
+// that the loads, the rank gathers and the atomics of the pairs are in flight
+// together instead of one dependent chain per pair.
 __global__ void k_orient_count(const int32_t* __restrict__ src, const int32_t* __restrict__ dst, int64_t m,
                                int32_t n, const int32_t* __restrict__ rank, uint32_t* __restrict__ rowcnt) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += stride) {
-        int32_t u = src[i], v = dst[i];
-        if (u == v || (uint32_t)u >= (uint32_t)n || (uint32_t)v >= (uint32_t)n) continue;
-        int32_t a = rank[u], b = rank[v];
-        atomicAdd(&rowcnt[min(a, b)], 1u);
+    for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i0 < m; i0 += PAIR_UNROLL * stride) {
+        int32_t u[PAIR_UNROLL], v[PAIR_UNROLL];
+#pragma unroll
+        for (int k = 0; k < PAIR_UNROLL; ++k) {
+            const int64_t i = i0 + k * stride;
+            u[k] = i < m ? src[i] : 0;
+            v[k] = i < m ? dst[i] : 0;
+        }
+#pragma unroll
+        for (int k = 0; k < PAIR_UNROLL; ++k) {
+            if (u[k] == v[k] || (uint32_t)u[k] >= (uint32_t)n || (uint32_t)v[k] >= (uint32_t)n) continue;
+            atomicAdd(&rowcnt[min(rank[u[k]], rank[v[k]])], 1u);
+        }
     }
 }
 
@@ -160,37 +182,90 @@ __global__ void k_orient_scatter(const int32_t* __restrict__ src, const int32_t*
                                  int32_t n, const int32_t* __restrict__ rank, const int64_t* __restrict__ rowstart,
                                  uint32_t* __restrict__ cursor, int32_t* __restrict__ col) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += stride) {
-        int32_t u = src[i], v = dst[i];
-        if (u == v || (uint32_t)u >= (uint32_t)n || (uint32_t)v >= (uint32_t)n) continue;
-        int32_t a = rank[u], b = rank[v];
-        int32_t s = min(a, b), t = max(a, b);
-        int64_t p = rowstart[s] + atomicAdd(&cursor[s], 1u);
-        if (p < rowstart[s + 1]) col[p] = t;  // always true unless the two passes disagree
+    for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i0 < m; i0 += PAIR_UNROLL * stride) {
+        int32_t s[PAIR_UNROLL], t[PAIR_UNROLL];
+#pragma unroll
+        for (int k = 0; k < PAIR_UNROLL; ++k) {
+            const int64_t i = i0 + k * stride;
+            s[k] = i < m ? src[i] : 0;
+            t[k] = i < m ? dst[i] : 0;
+        }
+#pragma unroll
+        for (int k = 0; k < PAIR_UNROLL; ++k) {
+            const bool ok = s[k] != t[k] && (uint32_t)s[k] < (uint32_t)n && (uint32_t)t[k] < (uint32_t)n;
+            if (ok) {
+                const int32_t a = rank[s[k]], b = rank[t[k]];
+                s[k] = min(a, b);
+                t[k] = max(a, b);
+            } else {
+                s[k] = -1;
+            }
+        }
+        int64_t p[PAIR_UNROLL];
+#pragma unroll
+        for (int k = 0; k < PAIR_UNROLL; ++k)
+            p[k] = s[k] >= 0 ? rowstart[s[k]] + atomicAdd(&cursor[s[k]], 1u) : 0;
+#pragma unroll
+        for (int k = 0; k < PAIR_UNROLL; ++k)
+            if (s[k] >= 0 && p[k] < rowstart[s[k] + 1]) col[p[k]] = t[k];  // always true unless the passes disagree
     }
 }
 
-// Row fill in two levels, used for graphs with a flat degree distribution (where the
-// direct scatter's random row cursors and writes miss every cache).  Pass 1: each block takes 4096 pairs, sorts them by a
-// coarse bucket (the top PART_BITS bits of the source rank) in shared memory,
-// reserves space per bucket with one atomic, and writes (source, target) into the
-// bucket's segment of tmp -- the segment of col that the bucket's rows will occupy.
-// Pass 2: blocks take fixed-size contiguous chunks of the grouped pairs and move
-// them into their rows; a chunk's rows lie within one or two buckets, so its row
-// cursors and the written part of col form a small window that stays in L2.
-constexpr int PART_BITS = 8;
-constexpr int PART_BUCKETS = 1 << PART_BITS;
+// Row counts and row fill by buckets of consecutive source ranks (2^shift rows each,
+// nb buckets), with no per-pair global atomic:
+//  k_bucket_count  counts the pairs of each bucket (shared-memory histogram, one
+//                  global atomic per bucket and block);
+//  k_orient_part   takes PART_TILE pairs per block, groups them by bucket in shared
+//                  memory, reserves each bucket's run with one atomic and writes
+//                  (source, target) into the bucket's segment of `pairs`;
+//  k_bucket_fill   takes one bucket per block: counts its rows in shared memory,
+//                  scans them into rowstart and rowcnt, and moves every pair into its
+//                  row through shared-memory cursors.
+// Used for flat degree distributions when a bucket's rows fit in shared memory
+// (BUCKET_ROWS_MAX) and nb is at most BUCKET_MAX.  Skewed graphs take the direct
+// count and scatter above: their heavy rows would pile onto a few buckets and onto
+// single shared-memory counters, while in the direct scatter they stay in cache.
 constexpr int PART_ITEMS = 16;
 constexpr int PART_TILE = THREADS * PART_ITEMS;
+constexpr int FILL_THREADS = 1024;
+
+__global__ void __launch_bounds__(THREADS) k_bucket_count(const int32_t* __restrict__ src,
+                                                          const int32_t* __restrict__ dst, int64_t m, int32_t n,
+                                                          const int32_t* __restrict__ rank, int shift, int nb,
+                                                          uint32_t* __restrict__ bcount) {
+    extern __shared__ uint32_t hist[];  // nb
+    for (int b = threadIdx.x; b < nb; b += THREADS) hist[b] = 0;
+    __syncthreads();
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i0 < m; i0 += PAIR_UNROLL * stride) {
+        int32_t u[PAIR_UNROLL], v[PAIR_UNROLL];
+#pragma unroll
+        for (int k = 0; k < PAIR_UNROLL; ++k) {
+            const int64_t i = i0 + k * stride;
+            u[k] = i < m ? src[i] : 0;
+            v[k] = i < m ? dst[i] : 0;
+        }
+#pragma unroll
+        for (int k = 0; k < PAIR_UNROLL; ++k) {
+            if (u[k] == v[k] || (uint32_t)u[k] >= (uint32_t)n || (uint32_t)v[k] >= (uint32_t)n) continue;
+            atomicAdd(&hist[min(rank[u[k]], rank[v[k]]) >> shift], 1u);
+        }
+    }
+    __syncthreads();
+    for (int b = threadIdx.x; b < nb; b += THREADS)
+        if (hist[b]) atomicAdd(&bcount[b], hist[b]);
+}
 
 __global__ void __launch_bounds__(THREADS) k_orient_part(const int32_t* __restrict__ src, const int32_t* __restrict__ dst,
                                                          int64_t m, int32_t n, const int32_t* __restrict__ rank,
-                                                         int shift, const int64_t* __restrict__ rowstart,
-                                                         uint32_t* __restrict__ bcur, int2* __restrict__ tmp) {
-    __shared__ uint32_t hist[PART_BUCKETS];
-    __shared__ int64_t base[PART_BUCKETS], bend[PART_BUCKETS];
+                                                         int shift, int nb, const int64_t* __restrict__ bstart,
+                                                         uint32_t* __restrict__ bcur, int2* __restrict__ pairs,
+                                                         DevStats* stats) {
+    extern __shared__ __align__(8) unsigned char part_sh[];
+    int64_t* base = reinterpret_cast<int64_t*>(part_sh);  // nb
+    uint32_t* hist = reinterpret_cast<uint32_t*>(base + nb);  // nb
     for (int64_t t0 = (int64_t)blockIdx.x * PART_TILE; t0 < m; t0 += (int64_t)gridDim.x * PART_TILE) {
-        for (int b = threadIdx.x; b < PART_BUCKETS; b += THREADS) hist[b] = 0;
+        for (int b = threadIdx.x; b < nb; b += THREADS) hist[b] = 0;
         __syncthreads();
         int32_t sv[PART_ITEMS], tv[PART_ITEMS];
         uint32_t loc[PART_ITEMS];
@@ -209,13 +284,9 @@ __global__ void __launch_bounds__(THREADS) k_orient_part(const int32_t* __restri
             }
         }
         __syncthreads();
-        for (int b = threadIdx.x; b < PART_BUCKETS; b += THREADS) {
+        for (int b = threadIdx.x; b < nb; b += THREADS) {
             const uint32_t c = hist[b];
-            const int64_t first = (int64_t)b << shift;
-            if (c && first < n) {
-                base[b] = rowstart[first] + atomicAdd(&bcur[b], c);
-                bend[b] = rowstart[min(first + ((int64_t)1 << shift), (int64_t)n)];
-            }
+            if (c) base[b] = bstart[b] + atomicAdd(&bcur[b], c);
         }
         __syncthreads();
 #pragma unroll
@@ -223,26 +294,69 @@ __global__ void __launch_bounds__(THREADS) k_orient_part(const int32_t* __restri
             if (sv[k] >= 0) {
                 const int b = sv[k] >> shift;
                 const int64_t pos = base[b] + loc[k];
-                if (pos < bend[b]) tmp[pos] = make_int2(sv[k], tv[k]);  // always true unless counts disagree
+                if (pos < bstart[b + 1])  // always true unless the two passes disagree
+                    pairs[pos] = make_int2(sv[k], tv[k]);
+                else
+                    atomicOr(&stats->err, ERR_OVERFLOW);
             }
         __syncthreads();
     }
 }
 
-constexpr int LOCAL_CHUNK = 16384;  // pairs per block in pass 2
-
-__global__ void __launch_bounds__(1024) k_orient_local(int32_t n, const int64_t* __restrict__ rowstart,
-                                                       const int2* __restrict__ tmp, uint32_t* __restrict__ cursor,
-                                                       int32_t* __restrict__ col) {
-    const int64_t total = rowstart[n];  // pairs that survived the checks (self-loops excluded)
-    for (int64_t c0 = (int64_t)blockIdx.x * LOCAL_CHUNK; c0 < total; c0 += (int64_t)gridDim.x * LOCAL_CHUNK) {
-        const int64_t c1 = min(c0 + LOCAL_CHUNK, total);
-        for (int64_t e = c0 + threadIdx.x; e < c1; e += blockDim.x) {
-            const int2 st = tmp[e];
-            const int64_t p = rowstart[st.x] + atomicAdd(&cursor[st.x], 1u);
-            if (p < rowstart[st.x + 1]) col[p] = st.y;  // always true unless the passes disagree
+__global__ void __launch_bounds__(FILL_THREADS) k_bucket_fill(int32_t n, int shift, int nb,
+                                                              const int64_t* __restrict__ bstart,
+                                                              const int2* __restrict__ pairs,
+                                                              int64_t* __restrict__ rowstart,
+                                                              uint32_t* __restrict__ rowcnt, int32_t* __restrict__ col,
+                                                              DevStats* stats) {
+    extern __shared__ uint32_t rc[];  // 2^shift row counters, then row cursors
+    __shared__ uint32_t part[FILL_THREADS / 32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (int b = blockIdx.x; b < nb; b += gridDim.x) {
+        const int32_t r0 = b << shift;
+        const int nr = (int)min((int64_t)1 << shift, (int64_t)n - r0);
+        const int64_t e0 = bstart[b], e1 = bstart[b + 1];
+        for (int i = threadIdx.x; i < nr; i += FILL_THREADS) rc[i] = 0;
+        __syncthreads();
+        for (int64_t e = e0 + threadIdx.x; e < e1; e += FILL_THREADS) {
+            const int r = pairs[e].x - r0;
+            if ((unsigned)r < (unsigned)nr)
+                atomicAdd(&rc[r], 1u);
+            else
+                atomicOr(&stats->err, ERR_OVERFLOW);
         }
+        __syncthreads();
+        // exclusive scan of rc[0, nr): thread k sums rows [k*per, (k+1)*per)
+        const int per = (nr + FILL_THREADS - 1) / FILL_THREADS;
+        const int i0 = min(threadIdx.x * per, nr), i1 = min(i0 + per, nr);
+        uint32_t sum = 0;
+        for (int i = i0; i < i1; ++i) sum += rc[i];
+        const uint32_t inc = warp_inclusive_scan(sum);
+        if (lane == 31) part[w] = inc;
+        __syncthreads();
+        if (w == 0) {
+            const uint32_t pv = lane < FILL_THREADS / 32 ? part[lane] : 0u;
+            const uint32_t pi = warp_inclusive_scan(pv);
+            if (lane < FILL_THREADS / 32) part[lane] = pi - pv;
+        }
+        __syncthreads();
+        uint32_t run = part[w] + inc - sum;
+        for (int i = i0; i < i1; ++i) {
+            const uint32_t c = rc[i];
+            rowstart[r0 + i] = e0 + run;
+            rowcnt[r0 + i] = c;
+            rc[i] = run;
+            run += c;
+        }
+        __syncthreads();
+        for (int64_t e = e0 + threadIdx.x; e < e1; e += FILL_THREADS) {
+            const int2 st = pairs[e];
+            const int r = st.x - r0;
+            if ((unsigned)r < (unsigned)nr) col[e0 + atomicAdd(&rc[r], 1u)] = st.y;
+        }
+        __syncthreads();
     }
+    if (blockIdx.x == 0 && threadIdx.x == 0) rowstart[n] = bstart[nb];
 }
 
 // Simple degree in rank space: distinct out-entries + in-entries before
@@ -627,31 +741,57 @@ void launch_rank(const BuildBuffers& B, int deg_bits, const Launch& L) {
     k_rank_invert<<<grid_for(B.n, THREADS, L.sms), THREADS, 0, L.stream>>>(sorted, B.n, B.rank, B.dmulti); count_launch();
 }
 
+void bucket_shape(int32_t n, int* shift, int* nb) {
+    int bits = 0;
+    while (bits < 31 && ((int64_t)1 << bits) < (int64_t)n) ++bits;
+    int sh = bits - BUCKET_BITS;
+    if (sh < 0) sh = 0;
+    if (((int64_t)1 << sh) > BUCKET_ROWS_MAX) sh = 0;
+    while (((int64_t)1 << sh) < BUCKET_ROWS_MAX && (((int64_t)n + ((int64_t)1 << sh) - 1) >> sh) > BUCKET_MAX) ++sh;
+    const int64_t b = ((int64_t)n + ((int64_t)1 << sh) - 1) >> sh;
+    *shift = sh;
+    *nb = b <= BUCKET_MAX ? (int)b : 0;  // 0: too many rows for the bucket path
+}
+
 void launch_orient(const BuildBuffers& B, const Launch& L, cudaEvent_t* ev) {
     if (B.n <= 0) return;
-    cudaMemsetAsync(B.rowcnt, 0, sizeof(uint32_t) * (size_t)B.n, L.stream);
     cudaMemsetAsync(B.cursor, 0, sizeof(uint32_t) * (size_t)B.n, L.stream);
     cudaMemsetAsync(B.dupin, 0, sizeof(uint32_t) * (size_t)B.n, L.stream);
-    if (B.m > 0) {
-        k_orient_count<<<grid_for(B.m, THREADS, L.sms), THREADS, 0, L.stream>>>(B.src, B.dst, B.m, B.n, B.rank,
-                                                                              B.rowcnt); count_launch(); }
-    scan_u32_to_i64(B.rowcnt, B.rowstart, B.n, B.tmp, L);
-    if (ev) cudaEventRecord(ev[BP_COUNT], L.stream);
-    if (B.m > 0 && !B.two_level_fill) {
-        k_orient_scatter<<<grid_for(B.m, THREADS, L.sms), THREADS, 0, L.stream>>>(
-            B.src, B.dst, B.m, B.n, B.rank, B.rowstart, B.cursor, B.col);
+    int shift = 0, nb = 0;
+    bucket_shape(B.n, &shift, &nb);
+    if (B.bucket_fill && nb > 0) {
+        cudaMemsetAsync(B.bcount, 0, sizeof(uint32_t) * (size_t)nb, L.stream);
+        cudaMemsetAsync(B.bcur, 0, sizeof(uint32_t) * (size_t)nb, L.stream);
+        if (B.m > 0) {
+            k_bucket_count<<<grid_for(B.m, THREADS * PAIR_UNROLL, L.sms, 4), THREADS, sizeof(uint32_t) * nb, L.stream>>>(
+                B.src, B.dst, B.m, B.n, B.rank, shift, nb, B.bcount);
+            count_launch();
+        }
+        scan_u32_to_i64(B.bcount, B.bstart, nb, B.tmp, L);
+        if (ev) cudaEventRecord(ev[BP_COUNT], L.stream);
+        if (B.m > 0) {
+            k_orient_part<<<grid_for(B.m, PART_TILE, L.sms, 4), THREADS, (sizeof(int64_t) + sizeof(uint32_t)) * nb,
+                            L.stream>>>(B.src, B.dst, B.m, B.n, B.rank, shift, nb, B.bstart, B.bcur, B.pairs, B.stats);
+            count_launch();
+        }
+        const int fill_blocks = nb < 4 * L.sms ? nb : 4 * L.sms;
+        k_bucket_fill<<<fill_blocks, FILL_THREADS, sizeof(uint32_t) << shift, L.stream>>>(
+            B.n, shift, nb, B.bstart, B.pairs, B.rowstart, B.rowcnt, B.col, B.stats);
         count_launch();
-    } else if (B.m > 0) {
-        int bits = 0;
-        while (bits < 31 && ((int64_t)1 << bits) < (int64_t)B.n) ++bits;
-        const int shift = bits > PART_BITS ? bits - PART_BITS : 0;
-        cudaMemsetAsync(B.bcur, 0, sizeof(uint32_t) * PART_BUCKETS, L.stream);
-        k_orient_part<<<grid_for(B.m, PART_TILE, L.sms, 4), THREADS, 0, L.stream>>>(
-            B.src, B.dst, B.m, B.n, B.rank, shift, B.rowstart, B.bcur, B.pairs);
-        count_launch();
-        k_orient_local<<<grid_for(B.m, LOCAL_CHUNK, L.sms, 2), 1024, 0, L.stream>>>(B.n, B.rowstart, B.pairs,
-                                                                                  B.cursor, B.col);
-        count_launch();
+    } else {
+        cudaMemsetAsync(B.rowcnt, 0, sizeof(uint32_t) * (size_t)B.n, L.stream);
+        if (B.m > 0) {
+            k_orient_count<<<grid_for(B.m, THREADS, L.sms), THREADS, 0, L.stream>>>(B.src, B.dst, B.m, B.n, B.rank,
+                                                                                  B.rowcnt);
+            count_launch();
+        }
+        scan_u32_to_i64(B.rowcnt, B.rowstart, B.n, B.tmp, L);
+        if (ev) cudaEventRecord(ev[BP_COUNT], L.stream);
+        if (B.m > 0) {
+            k_orient_scatter<<<grid_for(B.m, THREADS, L.sms), THREADS, 0, L.stream>>>(
+                B.src, B.dst, B.m, B.n, B.rank, B.rowstart, B.cursor, B.col);
+            count_launch();
+        }
     }
     if (ev) cudaEventRecord(ev[BP_FILL], L.stream);
     k_segsort_thread<<<grid_for(B.n, THREADS, L.sms), THREADS, 0, L.stream>>>(
@@ -673,10 +813,20 @@ void launch_orient(const BuildBuffers& B, const Launch& L, cudaEvent_t* ev) {
     count_launch();
 }
 
-// 64 KB of dynamic shared memory for the block sorter.
+// Dynamic shared memory: 64 KB for the block sorter, up to BUCKET_ROWS_MAX row
+// counters for the bucket fill and BUCKET_MAX buckets for the partition pass.
 cudaError_t build_init_attributes() {
-    return cudaFuncSetAttribute(k_segsort_block, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                CTA_SORT_MAX * (int)sizeof(int32_t));
+    cudaError_t e = cudaFuncSetAttribute(k_segsort_block, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         CTA_SORT_MAX * (int)sizeof(int32_t));
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(k_bucket_fill, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             BUCKET_ROWS_MAX * (int)sizeof(uint32_t));
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(k_orient_part, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             BUCKET_MAX * (int)(sizeof(int64_t) + sizeof(uint32_t)));
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(k_bucket_count, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                BUCKET_MAX * (int)sizeof(uint32_t));
 }
 
 }  // namespace tcg

@@ -74,9 +74,11 @@ struct BuildBuffers {
     int32_t* midlist;     // n: rows of 17..256 entries
     int32_t* midlist2;    // n: rows of 257..1024 entries
     uint32_t* dupin;      // n: repeated entries dropped at each target
-    uint32_t* bcur;       // 256: bucket cursors of the two-level row fill
+    uint32_t* bcount;     // BUCKET_MAX + 1: pairs per source bucket
+    uint32_t* bcur;       // BUCKET_MAX: bucket cursors of the partition pass
+    int64_t* bstart;      // BUCKET_MAX + 1: first pair of each bucket
     int2* pairs;          // m: (source rank, target rank) grouped by bucket
-    bool two_level_fill;  // row fill through buckets (flat degree distributions)
+    bool bucket_fill;     // rows counted and filled by source buckets (flat degree distributions)
     void* tmp;            // max(scan_tmp_bytes(n + 1), radix_tmp_bytes(n))
     // outputs (kept by the graph)
     int32_t* rank;        // n: rank of each input id in (degree, id) order
@@ -99,6 +101,12 @@ void launch_expand_csr(const int64_t* offsets, int32_t n, int32_t* rows, DevStat
 void launch_canon_degree(const BuildBuffers& B, const Launch& L);
 void launch_rank(const BuildBuffers& B, int deg_bits, const Launch& L);
 void launch_orient(const BuildBuffers& B, const Launch& L, cudaEvent_t* ev = nullptr);
+// Row fill by source buckets: at most BUCKET_MAX buckets of at most BUCKET_ROWS_MAX
+// rows (2^BUCKET_BITS buckets when that fits); nb = 0 selects the direct fill.
+constexpr int BUCKET_BITS = 10;
+constexpr int BUCKET_MAX = 4096;
+constexpr int BUCKET_ROWS_MAX = 32768;
+void bucket_shape(int32_t n, int* shift, int* nb);
 cudaError_t build_init_attributes();
 
 // ---- plan + intersect + finalize (tc_intersect.cu) ---------------------------
