@@ -42,6 +42,7 @@ namespace {
 
 constexpr int THREADS = 256;
 constexpr int SMALL_WARPS = 8;         // warps per block in the small-bucket kernel
+constexpr int SMALL_BLOCKS = 8;        // its resident blocks per SM (the grid is one wave of them)
 constexpr int CTA_THREADS = 256;       // block push kernel
 constexpr int CTA_WARPS = CTA_THREADS / 32;
 constexpr int CTA_LIST_MAX = 2048;     // staged list capacity of the block push kernel
@@ -589,7 +590,7 @@ __global__ void k_plan(int32_t n, const int64_t* __restrict__ rowstart, const in
 // ---- small bucket: groups of G lanes, one lane per edge -----------------------
 
 template <int G>
-__global__ void __launch_bounds__(SMALL_WARPS * 32) k_tc_small(int32_t n, const int64_t* __restrict__ rowstart,
+__global__ void __launch_bounds__(SMALL_WARPS * 32, SMALL_BLOCKS) k_tc_small(int32_t n, const int64_t* __restrict__ rowstart,
                                                                const int32_t* __restrict__ rowlen,
                                                                const int2* __restrict__ rowinfo,
                                                                const int32_t* __restrict__ col,
@@ -607,12 +608,18 @@ __global__ void __launch_bounds__(SMALL_WARPS * 32) k_tc_small(int32_t n, const 
     const unsigned count = stats->small_count[cls];
     const int32_t R = n - (int32_t)stats->hub_count;
     const unsigned groups = gridDim.x * SMALL_WARPS * GPW;
-    for (unsigned q = (blockIdx.x * SMALL_WARPS + w) * GPW + grp; q < count; q += groups) {
-        const int32_t u = list[q];
-        const int du = rowlen[u];
-        const int64_t base = rowstart[u];
+    // the next source and its row are fetched while the current one is counted
+    unsigned q = (blockIdx.x * SMALL_WARPS + w) * GPW + grp;
+    int32_t u = q < count ? list[q] : 0;
+    int2 ru = q < count ? rowinfo[u] : make_int2(0, 0);
+    for (; q < count; q += groups) {
+        const unsigned qn = q + groups;
+        const int32_t un = qn < count ? list[qn] : 0;
+        const int du = ru.y;
+        const int64_t base = ru.x;
         Lu[g] = g < du ? col[base + g] : INT_MAX;
         cnt[g] = 0;
+        const int2 run = qn < count ? rowinfo[un] : make_int2(0, 0);
         __syncwarp(gmask);
         uint32_t c = 0;
         if (g < du - 1) {
@@ -639,6 +646,8 @@ __global__ void __launch_bounds__(SMALL_WARPS * 32) k_tc_small(int32_t n, const 
         if (g < du && cv) atomicAdd(&t[Lu[g]], (unsigned long long)cv);
         if (g == 0 && c) atomicAdd(&t[u], (unsigned long long)c);
         __syncwarp(gmask);
+        u = un;
+        ru = run;
     }
 }
 
@@ -1157,13 +1166,13 @@ void launch_intersect(const CountBuffers& C, const Strategy& S, cudaEvent_t* ev,
     if (ev) cudaEventRecord(ev[PH_SMALL], L.stream);
     const int ss = S.strat[TC_BUCKET_SMALL];
     const float sf = S.factor[TC_BUCKET_SMALL];
-    k_tc_small<8><<<L.sms * 8, SMALL_WARPS * 32, 0, L.stream>>>(C.n, C.rowstart, C.rowlen, C.rowinfo, C.col, C.small_list[0],
+    k_tc_small<8><<<L.sms * SMALL_BLOCKS, SMALL_WARPS * 32, 0, L.stream>>>(C.n, C.rowstart, C.rowlen, C.rowinfo, C.col, C.small_list[0],
                                                                0, C.t_rank, C.stats, ss, sf);
     count_launch();
-    k_tc_small<16><<<L.sms * 8, SMALL_WARPS * 32, 0, L.stream>>>(C.n, C.rowstart, C.rowlen, C.rowinfo, C.col, C.small_list[1],
+    k_tc_small<16><<<L.sms * SMALL_BLOCKS, SMALL_WARPS * 32, 0, L.stream>>>(C.n, C.rowstart, C.rowlen, C.rowinfo, C.col, C.small_list[1],
                                                                 1, C.t_rank, C.stats, ss, sf);
     count_launch();
-    k_tc_small<32><<<L.sms * 8, SMALL_WARPS * 32, 0, L.stream>>>(C.n, C.rowstart, C.rowlen, C.rowinfo, C.col, C.small_list[2],
+    k_tc_small<32><<<L.sms * SMALL_BLOCKS, SMALL_WARPS * 32, 0, L.stream>>>(C.n, C.rowstart, C.rowlen, C.rowinfo, C.col, C.small_list[2],
                                                                 2, C.t_rank, C.stats, ss, sf);
     count_launch();
     if (ev) cudaEventRecord(ev[PH_CTA], L.stream);
