@@ -763,7 +763,7 @@ void launch_orient(const BuildBuffers& B, const Launch& L, cudaEvent_t* ev) {
         cudaMemsetAsync(B.bcount, 0, sizeof(uint32_t) * (size_t)nb, L.stream);
         cudaMemsetAsync(B.bcur, 0, sizeof(uint32_t) * (size_t)nb, L.stream);
         if (B.m > 0) {
-            k_bucket_count<<<grid_for(B.m, THREADS * PAIR_UNROLL, L.sms, 4), THREADS, sizeof(uint32_t) * nb, L.stream>>>(
+            k_bucket_count<<<grid_for(B.m, THREADS * PAIR_UNROLL, L.sms, 8), THREADS, sizeof(uint32_t) * nb, L.stream>>>(
                 B.src, B.dst, B.m, B.n, B.rank, shift, nb, B.bcount);
             count_launch();
         }

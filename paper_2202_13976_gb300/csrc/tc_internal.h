@@ -103,7 +103,7 @@ void launch_rank(const BuildBuffers& B, int deg_bits, const Launch& L);
 void launch_orient(const BuildBuffers& B, const Launch& L, cudaEvent_t* ev = nullptr);
 // Row fill by source buckets: at most BUCKET_MAX buckets of at most BUCKET_ROWS_MAX
 // rows (2^BUCKET_BITS buckets when that fits); nb = 0 selects the direct fill.
-constexpr int BUCKET_BITS = 10;
+constexpr int BUCKET_BITS = 11;
 constexpr int BUCKET_MAX = 4096;
 constexpr int BUCKET_ROWS_MAX = 32768;
 void bucket_shape(int32_t n, int* shift, int* nb);
