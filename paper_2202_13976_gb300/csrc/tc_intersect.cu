@@ -564,26 +564,52 @@ __global__ void k_hub_lists(int32_t n, const uint32_t* __restrict__ big, const u
     }
 }
 
-// Push lists: sources with at least one non-hub target and a non-empty suffix.
-__global__ void k_plan(int32_t n, const int64_t* __restrict__ rowstart, const int32_t* __restrict__ rowlen,
-                       const int32_t* __restrict__ col, int32_t* __restrict__ l8, int32_t* __restrict__ l16,
-                       int32_t* __restrict__ l32, int32_t* __restrict__ lcta, DevStats* stats) {
+// Push lists: sources with at least one non-hub target and a non-empty suffix.  A
+// block classifies PLAN_ITEMS vertices per thread and appends them with one global
+// atomic per list and block (warp ballots, then shared-memory offsets), since one
+// atomic per warp and list serialises on the four list counters.
+constexpr int PLAN_ITEMS = 4;
+
+__global__ void __launch_bounds__(THREADS) k_plan(int32_t n, const int64_t* __restrict__ rowstart,
+                                                  const int32_t* __restrict__ rowlen, const int32_t* __restrict__ col,
+                                                  int32_t* __restrict__ l8, int32_t* __restrict__ l16,
+                                                  int32_t* __restrict__ l32, int32_t* __restrict__ lcta,
+                                                  DevStats* stats) {
+    __shared__ unsigned bcount[4];
+    __shared__ unsigned bbase[4];
     const int32_t R = n - (int32_t)stats->hub_count;
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    // the loop bound is uniform across a warp, as warp_append needs all 32 lanes
-    for (int64_t b = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); b < n; b += stride) {
-        const int64_t u = b + lane_id();
-        int d = u < n ? rowlen[u] : 0;
-        if (d >= 2 && col[rowstart[u]] >= R) d = 0;  // every target is a hub
-        const bool c8 = d >= 2 && d <= 8, c16 = d > 8 && d <= 16, c32 = d > 16 && d <= 32, cc = d > 32;
-        const unsigned p8 = warp_append(c8, &stats->small_count[0]);
-        const unsigned p16 = warp_append(c16, &stats->small_count[1]);
-        const unsigned p32 = warp_append(c32, &stats->small_count[2]);
-        const unsigned pc = warp_append(cc, &stats->cta_count);
-        if (c8) l8[p8] = (int32_t)u;
-        if (c16) l16[p16] = (int32_t)u;
-        if (c32) l32[p32] = (int32_t)u;
-        if (cc) lcta[pc] = (int32_t)u;
+    const int lane = lane_id();
+    unsigned* counters[4] = {&stats->small_count[0], &stats->small_count[1], &stats->small_count[2],
+                             &stats->cta_count};
+    int32_t* lists[4] = {l8, l16, l32, lcta};
+    const int64_t tile = (int64_t)THREADS * PLAN_ITEMS;
+    for (int64_t t0 = (int64_t)blockIdx.x * tile; t0 < n; t0 += (int64_t)gridDim.x * tile) {
+        if (threadIdx.x < 4) bcount[threadIdx.x] = 0;
+        __syncthreads();
+        int cls[PLAN_ITEMS];
+        unsigned off[PLAN_ITEMS];
+#pragma unroll
+        for (int k = 0; k < PLAN_ITEMS; ++k) {
+            const int64_t u = t0 + (int64_t)k * THREADS + threadIdx.x;
+            int d = u < n ? rowlen[u] : 0;
+            if (d >= 2 && col[rowstart[u]] >= R) d = 0;  // every target is a hub
+            cls[k] = d < 2 ? -1 : d <= 8 ? 0 : d <= 16 ? 1 : d <= 32 ? 2 : 3;
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                const unsigned mk = __ballot_sync(FULL, cls[k] == c);
+                unsigned wb = 0;
+                if (mk && lane == 0) wb = atomicAdd(&bcount[c], (unsigned)__popc(mk));
+                wb = __shfl_sync(FULL, wb, 0);
+                if (cls[k] == c) off[k] = wb + __popc(mk & lanemask_lt());
+            }
+        }
+        __syncthreads();
+        if (threadIdx.x < 4) bbase[threadIdx.x] = bcount[threadIdx.x] ? atomicAdd(counters[threadIdx.x], bcount[threadIdx.x]) : 0u;
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < PLAN_ITEMS; ++k)
+            if (cls[k] >= 0) lists[cls[k]][bbase[cls[k]] + off[k]] = (int32_t)(t0 + (int64_t)k * THREADS + threadIdx.x);
+        __syncthreads();
     }
 }
 
@@ -1071,7 +1097,8 @@ __global__ void k_finalize(int32_t n, const int32_t* __restrict__ rank, const un
         if (t_out) t_out[v] = tv;
         if (lcc_out) {
             const long long d = deg[r];
-            lcc_out[v] = d < 2 ? 0.0 : __ddiv_rn((double)(2ull * tv), (double)(d * (d - 1)));
+            // t = 0 gives +0.0 without a double division (FP64 runs at a small fraction of FP32)
+            lcc_out[v] = d < 2 || tv == 0 ? 0.0 : __ddiv_rn((double)(2ull * tv), (double)(d * (d - 1)));
         }
     }
 }
@@ -1149,7 +1176,7 @@ void launch_plan(const CountBuffers& C, const Strategy& S, const Launch& L) {
                                                                                   C.big_list, C.med_list, C.stats);
         count_launch();
     }
-    k_plan<<<grid_for(C.n, THREADS, L.sms), THREADS, 0, L.stream>>>(C.n, C.rowstart, C.rowlen, C.col,
+    k_plan<<<grid_for(C.n, THREADS * PLAN_ITEMS, L.sms), THREADS, 0, L.stream>>>(C.n, C.rowstart, C.rowlen, C.col,
                                                                    C.small_list[0], C.small_list[1],
                                                                    C.small_list[2], C.cta_list, C.stats);
     count_launch();
