@@ -985,14 +985,18 @@ __global__ void __launch_bounds__(HUB_THREADS) k_tc_hub(int32_t n, int32_t hub_c
         }
         uint32_t* cnt = staged ? sh.u.big.cnt : nullptr;
         unsigned long long vtot = 0;
+        // batches of bs in-edges, bs chosen so that every warp gets one when the hub
+        // has fewer than 8 full batches (the block waits for its slowest warp)
+        const int64_t din = e1 - e0;
+        const int bs = din >= HUB_WARPS * 32 ? 32 : max(8, (int)((din + HUB_WARPS - 1) / HUB_WARPS));
         if (!probe_mode) {
             const BitmapProbe P{sh.u.big.s.b.bm, sh.u.big.s.b.pre, v};
-            for (int64_t bb = e0 + (int64_t)w * 32; bb < e1; bb += HUB_WARPS * 32)
-                vtot += hub_batch(bb, e1, in_rec, col, maxv, P, cnt, t, sh.cw[w]);
+            for (int64_t bb = e0 + (int64_t)w * bs; bb < e1; bb += (int64_t)HUB_WARPS * bs)
+                vtot += hub_batch(bb, min(bb + bs, e1), in_rec, col, maxv, P, cnt, t, sh.cw[w]);
         } else {
             const ListProbe P{staged ? sh.u.big.s.list : col + base, dv};
-            for (int64_t bb = e0 + (int64_t)w * 32; bb < e1; bb += HUB_WARPS * 32)
-                vtot += hub_batch(bb, e1, in_rec, col, maxv, P, cnt, t, sh.cw[w]);
+            for (int64_t bb = e0 + (int64_t)w * bs; bb < e1; bb += (int64_t)HUB_WARPS * bs)
+                vtot += hub_batch(bb, min(bb + bs, e1), in_rec, col, maxv, P, cnt, t, sh.cw[w]);
         }
         if (lane == 0) sh.vt[w] = vtot;
         __syncthreads();
