@@ -54,6 +54,7 @@ constexpr int HUB_CNT_MAX = 4096;      // hub lists longer than this count match
 constexpr int HUB_WARP_MAX = 256;      // longest N+(v) a single warp stages
 constexpr int HUB_HASH_MAX = 512;      // its hash table: at least twice as many slots as keys
 constexpr int SCAT_STEPS = 4;          // lockstep steps of the row-walk scatter in flight together
+constexpr int HUB_BATCH = 32;          // in-edges per batch of a big hub
 constexpr int HUB_LONG = 32;           // suffixes at least this long are read by lane groups
 constexpr int HUB_GROUPS = 4;          // long suffixes one warp reads at a time
 constexpr int HUB_GLANES = 32 / HUB_GROUPS;
@@ -945,6 +946,7 @@ struct HubShared {
     uint32_t cw[HUB_WARPS][32];
     unsigned long long vt[HUB_WARPS];
     int q;
+    unsigned bq;  // next batch of the current big hub
 };
 
 __global__ void __launch_bounds__(HUB_THREADS) k_tc_hub(int32_t n, int32_t hub_cap, const int64_t* __restrict__ rowstart,
@@ -962,7 +964,10 @@ __global__ void __launch_bounds__(HUB_THREADS) k_tc_hub(int32_t n, int32_t hub_c
     const unsigned nbig = stats->hub_big, nmed = stats->hub_count - stats->hub_big;
     // phase 1: big hubs, one block each
     for (;;) {
-        if (threadIdx.x == 0) sh.q = (int)atomicAdd(&stats->hub_next, 1u);
+        if (threadIdx.x == 0) {
+            sh.q = (int)atomicAdd(&stats->hub_next, 1u);
+            sh.bq = 0;
+        }
         __syncthreads();
         const int q = sh.q;
         if ((unsigned)q >= nbig) break;
@@ -985,18 +990,30 @@ __global__ void __launch_bounds__(HUB_THREADS) k_tc_hub(int32_t n, int32_t hub_c
         }
         uint32_t* cnt = staged ? sh.u.big.cnt : nullptr;
         unsigned long long vtot = 0;
-        // batches of bs in-edges, bs chosen so that every warp gets one when the hub
-        // has fewer than 8 full batches (the block waits for its slowest warp)
+        // batches of bs in-edges, claimed by the warps from a shared counter (the block
+        // waits for its slowest warp); small hubs use smaller batches so that every
+        // warp gets some
         const int64_t din = e1 - e0;
-        const int bs = din >= HUB_WARPS * 32 ? 32 : max(8, (int)((din + HUB_WARPS - 1) / HUB_WARPS));
+        const int bs = din >= 2 * HUB_WARPS * HUB_BATCH ? HUB_BATCH
+                                                        : max(8, (int)((din + 2 * HUB_WARPS - 1) / (2 * HUB_WARPS)));
         if (!probe_mode) {
             const BitmapProbe P{sh.u.big.s.b.bm, sh.u.big.s.b.pre, v};
-            for (int64_t bb = e0 + (int64_t)w * bs; bb < e1; bb += (int64_t)HUB_WARPS * bs)
+            for (;;) {
+                unsigned k = 0;
+                if (lane == 0) k = atomicAdd(&sh.bq, 1u);
+                const int64_t bb = e0 + (int64_t)__shfl_sync(FULL, k, 0) * bs;
+                if (bb >= e1) break;
                 vtot += hub_batch(bb, min(bb + bs, e1), in_rec, col, maxv, P, cnt, t, sh.cw[w]);
+            }
         } else {
             const ListProbe P{staged ? sh.u.big.s.list : col + base, dv};
-            for (int64_t bb = e0 + (int64_t)w * bs; bb < e1; bb += (int64_t)HUB_WARPS * bs)
+            for (;;) {
+                unsigned k = 0;
+                if (lane == 0) k = atomicAdd(&sh.bq, 1u);
+                const int64_t bb = e0 + (int64_t)__shfl_sync(FULL, k, 0) * bs;
+                if (bb >= e1) break;
                 vtot += hub_batch(bb, min(bb + bs, e1), in_rec, col, maxv, P, cnt, t, sh.cw[w]);
+            }
         }
         if (lane == 0) sh.vt[w] = vtot;
         __syncthreads();
