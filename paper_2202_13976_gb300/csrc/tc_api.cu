@@ -100,7 +100,7 @@ struct tc_graph {
     int2* rowinfo = nullptr;
     int32_t* col = nullptr;
     int32_t* deg = nullptr;
-    int32_t* small_list[3] = {nullptr, nullptr, nullptr};
+    int32_t* small_list[4] = {nullptr, nullptr, nullptr, nullptr};
     int32_t* cta_list = nullptr;
     int32_t hub_cap = 0;
     uint32_t* hub_cnt = nullptr;
@@ -231,7 +231,8 @@ tc_status build_graph(tc_graph* g, const int32_t* src, const int32_t* dst, int64
         (st = dalloc(g, &g->rowinfo, nn, &keep)) ||
         (st = dalloc(g, &g->col, (size_t)m, &keep)) || (st = dalloc(g, &g->deg, nn, &keep)) ||
         (st = dalloc(g, &g->small_list[0], nn, &keep)) || (st = dalloc(g, &g->small_list[1], nn, &keep)) ||
-        (st = dalloc(g, &g->small_list[2], nn, &keep)) || (st = dalloc(g, &g->cta_list, nn, &keep)) ||
+        (st = dalloc(g, &g->small_list[2], nn, &keep)) || (st = dalloc(g, &g->small_list[3], nn, &keep)) ||
+        (st = dalloc(g, &g->cta_list, nn, &keep)) ||
         (st = dalloc(g, &g->hub_cnt, hc + 1, &keep)) || (st = dalloc(g, &g->hub_start, hc + 1, &keep)) ||
         (st = dalloc(g, &g->hub_cur, hc + 1, &keep)) || (st = dalloc(g, &g->big_list, hc + 1, &keep)) ||
         (st = dalloc(g, &g->med_list, hc + 1, &keep)) || (st = dalloc(g, &g->in_rec, (size_t)m, &keep)) ||
@@ -321,7 +322,7 @@ CountBuffers count_buffers(tc_graph* g) {
     C.rowinfo = g->rowinfo;
     C.col = g->col;
     C.deg = g->deg;
-    for (int i = 0; i < 3; ++i) C.small_list[i] = g->small_list[i];
+    for (int i = 0; i < 4; ++i) C.small_list[i] = g->small_list[i];
     C.cta_list = g->cta_list;
     C.hub_cap = g->hub_cap;
     C.hub_cnt = g->hub_cnt;

@@ -23,7 +23,7 @@ struct DevStats {
     unsigned int max_deg;          // largest multigraph degree
     int err;                       // ERR_* flags
     unsigned int long_count;       // build: rows sorted by whole blocks
-    unsigned int small_count[3];   // planner: vertices per small-list class (d+ <= 8, 16, 32)
+    unsigned int small_count[4];   // planner: vertices per small-list class (d+ <= 8, 16, 32, 256)
     unsigned int cta_count;        // planner: vertices with d+ > 32
     unsigned int cta_next;         // dynamic work counter of the block push kernel
     unsigned int hub_count;        // vertices staged as hubs (ranks n - hub_count .. n-1)
@@ -34,8 +34,9 @@ struct DevStats {
     unsigned int mid_count;        // build: rows of 17..256 entries sorted by one warp
     unsigned int mid2_count;       // build: rows of 257..1024 entries sorted by one warp
     unsigned int core_n;           // planner: dense core size (ranks n - core_n .. n-1)
+    unsigned int pad[1];
 };
-static_assert(sizeof(DevStats) == 88, "DevStats layout");
+static_assert(sizeof(DevStats) == 96, "DevStats layout");
 
 struct Launch {
     cudaStream_t stream;
@@ -133,7 +134,7 @@ struct CountBuffers {
     const int2* rowinfo;     // {first index in col, length} per row
     const int32_t* col;
     const int32_t* deg;
-    int32_t* small_list[3];  // n each
+    int32_t* small_list[4];  // n each: d+ <= 8, 16, 32, 256
     int32_t* cta_list;       // n
     // hub in-edges (transpose of the oriented edges that point into the hub ranks)
     int32_t hub_cap;         // min(n, HUB_BM_BITS): slots for ranks n - hub_cap .. n-1

@@ -43,6 +43,7 @@ namespace {
 constexpr int THREADS = 256;
 constexpr int SMALL_WARPS = 8;         // warps per block in the small-bucket kernel
 constexpr int SMALL_BLOCKS = 8;        // its resident blocks per SM (the grid is one wave of them)
+constexpr int SMALL_WIDE_MAX = 256;    // longest N+(u) the warp-per-source kernel stages
 constexpr int CTA_THREADS = 256;       // block push kernel
 constexpr int CTA_WARPS = CTA_THREADS / 32;
 constexpr int CTA_LIST_MAX = 2048;     // staged list capacity of the block push kernel
@@ -570,22 +571,23 @@ __global__ void k_hub_lists(int32_t n, const uint32_t* __restrict__ big, const u
 // atomic per list and block (warp ballots, then shared-memory offsets), since one
 // atomic per warp and list serialises on the four list counters.
 constexpr int PLAN_ITEMS = 4;
+constexpr int PLAN_LISTS = 5;  // d+ classes <= 8, <= 16, <= 32, <= SMALL_WIDE_MAX, larger
 
 __global__ void __launch_bounds__(THREADS) k_plan(int32_t n, const int64_t* __restrict__ rowstart,
                                                   const int32_t* __restrict__ rowlen, const int32_t* __restrict__ col,
                                                   int32_t* __restrict__ l8, int32_t* __restrict__ l16,
-                                                  int32_t* __restrict__ l32, int32_t* __restrict__ lcta,
-                                                  DevStats* stats) {
-    __shared__ unsigned bcount[4];
-    __shared__ unsigned bbase[4];
+                                                  int32_t* __restrict__ l32, int32_t* __restrict__ l256,
+                                                  int32_t* __restrict__ lcta, DevStats* stats) {
+    __shared__ unsigned bcount[PLAN_LISTS];
+    __shared__ unsigned bbase[PLAN_LISTS];
     const int32_t R = n - (int32_t)stats->hub_count;
     const int lane = lane_id();
-    unsigned* counters[4] = {&stats->small_count[0], &stats->small_count[1], &stats->small_count[2],
-                             &stats->cta_count};
-    int32_t* lists[4] = {l8, l16, l32, lcta};
+    unsigned* counters[PLAN_LISTS] = {&stats->small_count[0], &stats->small_count[1], &stats->small_count[2],
+                                      &stats->small_count[3], &stats->cta_count};
+    int32_t* lists[PLAN_LISTS] = {l8, l16, l32, l256, lcta};
     const int64_t tile = (int64_t)THREADS * PLAN_ITEMS;
     for (int64_t t0 = (int64_t)blockIdx.x * tile; t0 < n; t0 += (int64_t)gridDim.x * tile) {
-        if (threadIdx.x < 4) bcount[threadIdx.x] = 0;
+        if (threadIdx.x < PLAN_LISTS) bcount[threadIdx.x] = 0;
         __syncthreads();
         int cls[PLAN_ITEMS];
         unsigned off[PLAN_ITEMS];
@@ -594,9 +596,9 @@ __global__ void __launch_bounds__(THREADS) k_plan(int32_t n, const int64_t* __re
             const int64_t u = t0 + (int64_t)k * THREADS + threadIdx.x;
             int d = u < n ? rowlen[u] : 0;
             if (d >= 2 && col[rowstart[u]] >= R) d = 0;  // every target is a hub
-            cls[k] = d < 2 ? -1 : d <= 8 ? 0 : d <= 16 ? 1 : d <= 32 ? 2 : 3;
+            cls[k] = d < 2 ? -1 : d <= 8 ? 0 : d <= 16 ? 1 : d <= 32 ? 2 : d <= SMALL_WIDE_MAX ? 3 : 4;
 #pragma unroll
-            for (int c = 0; c < 4; ++c) {
+            for (int c = 0; c < PLAN_LISTS; ++c) {
                 const unsigned mk = __ballot_sync(FULL, cls[k] == c);
                 unsigned wb = 0;
                 if (mk && lane == 0) wb = atomicAdd(&bcount[c], (unsigned)__popc(mk));
@@ -605,7 +607,8 @@ __global__ void __launch_bounds__(THREADS) k_plan(int32_t n, const int64_t* __re
             }
         }
         __syncthreads();
-        if (threadIdx.x < 4) bbase[threadIdx.x] = bcount[threadIdx.x] ? atomicAdd(counters[threadIdx.x], bcount[threadIdx.x]) : 0u;
+        if (threadIdx.x < PLAN_LISTS)
+            bbase[threadIdx.x] = bcount[threadIdx.x] ? atomicAdd(counters[threadIdx.x], bcount[threadIdx.x]) : 0u;
         __syncthreads();
 #pragma unroll
         for (int k = 0; k < PLAN_ITEMS; ++k)
@@ -678,14 +681,135 @@ __global__ void __launch_bounds__(SMALL_WARPS * 32, SMALL_BLOCKS) k_tc_small(int
     }
 }
 
+// Sources with 32 < |N+(u)| <= SMALL_WIDE_MAX: a group of SMALL_WIDE_G lanes per
+// source stages N+(u) in shared memory and its lanes take the edges (u, v) with v a
+// non-hub (the first jh entries), one at a time, with the same per-edge choice
+// (Eq. 3) between the batched merge and binary search as the small kernel.  Such
+// sources mostly point to hubs and have few non-hub edges, so a block (or a whole
+// warp) per source would idle.
+constexpr int SMALL_WIDE_G = 16;
+constexpr int SMALL_WIDE_BLOCKS = 6;  // blocks per SM
+constexpr int SMALL_WIDE_GROUPS = SMALL_WARPS * 32 / SMALL_WIDE_G;  // per block
+
+__global__ void __launch_bounds__(SMALL_WARPS * 32) k_tc_small_wide(int32_t n, const int2* __restrict__ rowinfo,
+                                                                   const int32_t* __restrict__ col,
+                                                                   const int32_t* __restrict__ list,
+                                                                   unsigned long long* __restrict__ t,
+                                                                   DevStats* stats, int strategy, float factor) {
+    extern __shared__ __align__(16) unsigned char wide_sh[];
+    constexpr int G = SMALL_WIDE_G;
+    const int lane = lane_id(), w = threadIdx.x >> 5;
+    const int grp = lane / G, g = lane % G;
+    const unsigned gmask = G == 32 ? FULL : (((1u << G) - 1u) << (grp * G));
+    const int gi = w * (32 / G) + grp;  // group index in the block
+    int32_t* Lu = reinterpret_cast<int32_t*>(wide_sh) + gi * SMALL_WIDE_MAX;
+    uint32_t* cnt = reinterpret_cast<uint32_t*>(wide_sh) + (SMALL_WIDE_GROUPS + gi) * SMALL_WIDE_MAX;
+    const unsigned count = stats->small_count[3];
+    const int32_t R = n - (int32_t)stats->hub_count;
+    const unsigned groups = gridDim.x * SMALL_WIDE_GROUPS;
+    for (unsigned q = blockIdx.x * SMALL_WIDE_GROUPS + gi; q < count; q += groups) {
+        const int32_t u = list[q];
+        const int2 ru = rowinfo[u];
+        const int du = ru.y;  // 33 .. SMALL_WIDE_MAX
+        for (int p = g; p < du; p += G) {
+            Lu[p] = col[ru.x + p];
+            cnt[p] = 0;
+        }
+        __syncwarp(gmask);
+        const int jh = min(du - 1, lower_bound(Lu, 0, du, R));  // edges into non-hubs
+        uint32_t c = 0;
+        for (int j = g; j < jh; j += G) {
+            const int32_t v = Lu[j];
+            const int2 ri = rowinfo[v];
+            const int dv = ri.y;
+            if (dv == 0) continue;
+            const int32_t* B = col + ri.x;
+            const int a = du - j - 1;
+            int method = strategy;
+            if (method == TC_STRAT_AUTO)
+                method = eq3_prefers_merge(a, dv, factor) || dv < a ? TC_STRAT_MERGE : TC_STRAT_SEARCH;
+            const uint32_t cj = method == TC_STRAT_MERGE
+                                    ? lane_merge_batched(Lu, j + 1, du, B, dv, cnt)
+                                    : (a <= dv ? lane_search(Lu, j + 1, du, B, dv, cnt)
+                                               : lane_search_rev(Lu, j + 1, du, B, dv, cnt));
+            if (cj) atomicAdd(&cnt[j], cj);
+            c += cj;
+        }
+#pragma unroll
+        for (int o = G / 2; o > 0; o >>= 1) c += __shfl_down_sync(gmask, c, o, G);
+        __syncwarp(gmask);
+        for (int p = g; p < du; p += G) {
+            const uint32_t cv = cnt[p];
+            if (cv) atomicAdd(&t[Lu[p]], (unsigned long long)cv);
+        }
+        if (g == 0 && c) atomicAdd(&t[u], (unsigned long long)c);
+        __syncwarp(gmask);
+    }
+}
+
 // ---- block bucket: |N+(u)| > 32, non-hub targets ------------------------------
+
+// Open-addressing hash set of a staged list in shared memory (Fibonacci hashing, linear
+// probing, empty slots hold -1).  The table has at least twice as many slots as
+// keys, so a probe meets an empty slot after about two steps at most on average.
+struct HashProbe {
+    const int32_t* keys;
+    unsigned shift, mask;
+    __device__ __forceinline__ int operator()(int32_t x) const {
+        unsigned h = ((unsigned)x * 0x9e3779b1u) >> shift;
+        for (;;) {
+            const int32_t k = keys[h];
+            if (k == x) return (int)h;
+            if (k < 0) return -1;
+            h = (h + 1) & mask;
+        }
+    }
+};
+
+// Warp per edge: the entries of B = N+(v) (sorted) are probed in a set of the
+// staged N+(u), two per lane per round, stopping above max N+(u); hits add to the
+// set's per-slot counter.  Returns the edge's count (all lanes).
+template <class Probe>
+__device__ uint32_t edge_probe_set(const Probe& P, int32_t maxu, uint32_t* hcnt, const int32_t* __restrict__ B, int b) {
+    const int lane = lane_id();
+    uint32_t c = 0;
+    for (int k0 = 0; k0 < b; k0 += 64) {
+        const int k1 = k0 + lane, k2 = k1 + 32;
+        const int32_t x1 = k1 < b ? B[k1] : INT_MAX;
+        const int32_t x2 = k2 < b ? B[k2] : INT_MAX;
+        if (x1 <= maxu) {
+            const int p = P(x1);
+            if (p >= 0) {
+                atomicAdd(&hcnt[p], 1u);
+                ++c;
+            }
+        }
+        if (x2 <= maxu) {
+            const int p = P(x2);
+            if (p >= 0) {
+                atomicAdd(&hcnt[p], 1u);
+                ++c;
+            }
+        }
+        if (__any_sync(FULL, x2 > maxu)) break;  // B is sorted
+    }
+    return warp_sum(c);
+}
 
 struct CtaShared {
     int32_t Lu[CTA_LIST_MAX];
     uint32_t cnt[CTA_LIST_MAX];
-    uint32_t bm[BITMAP_WORDS];
-    uint16_t pre[BITMAP_WORDS];
-    uint32_t slice[BITMAP_WORDS / 32];
+    union {
+        struct {  // bitmap of N+(u) over its rank window
+            uint32_t bm[BITMAP_WORDS];
+            uint16_t pre[BITMAP_WORDS];
+            uint32_t slice[BITMAP_WORDS / 32];
+        } b;
+        struct {  // hash set of N+(u) when the window is wider than the bitmap
+            int32_t keys[2 * CTA_LIST_MAX];
+            uint32_t hcnt[2 * CTA_LIST_MAX];
+        } h;
+    } s;
     unsigned long long utot[CTA_WARPS];
     int q;
 };
@@ -723,7 +847,26 @@ __global__ void __launch_bounds__(CTA_THREADS) k_tc_cta(int32_t n, const int64_t
         const int jh = min(du - 1, lower_bound(Lu, 0, du, R));  // edges into non-hubs
         const int span = maxu - u;  // ranks u+1 .. maxu
         const bool bitmap = staged && strategy == TC_STRAT_BITMAP && span <= BITMAP_WORDS * 32;
-        if (bitmap) build_bitmap<CTA_THREADS>(sh.bm, sh.pre, sh.slice, sh.Lu, du, u, (span + 31) >> 5);
+        const bool hashed = staged && strategy == TC_STRAT_BITMAP && !bitmap;
+        if (bitmap) build_bitmap<CTA_THREADS>(sh.s.b.bm, sh.s.b.pre, sh.s.b.slice, sh.Lu, du, u, (span + 31) >> 5);
+        unsigned hshift = 0, hmask = 0;
+        if (hashed) {  // uniform across the block
+            int lg = 6;
+            while ((1 << lg) < 2 * du) ++lg;  // du <= CTA_LIST_MAX: at most 2 * CTA_LIST_MAX slots
+            hmask = (1u << lg) - 1u;
+            hshift = 32u - (unsigned)lg;
+            for (int p = threadIdx.x; p <= (int)hmask; p += CTA_THREADS) {
+                sh.s.h.keys[p] = -1;
+                sh.s.h.hcnt[p] = 0;
+            }
+            __syncthreads();
+            for (int p = threadIdx.x; p < du; p += CTA_THREADS) {
+                const int32_t x = sh.Lu[p];
+                unsigned h = ((unsigned)x * 0x9e3779b1u) >> hshift;
+                while (atomicCAS(&sh.s.h.keys[h], -1, x) != -1) h = (h + 1) & hmask;  // keys are distinct
+            }
+            __syncthreads();
+        }
         Sink S{staged ? sh.cnt : nullptr, t, Lu};
         unsigned long long utot = 0;
         for (int j = w; j < jh; j += CTA_WARPS) {
@@ -734,7 +877,9 @@ __global__ void __launch_bounds__(CTA_THREADS) k_tc_cta(int32_t n, const int64_t
             const int32_t* B = col + ri.x;
             uint32_t c;
             if (bitmap) {
-                c = edge_bitmap(sh.bm, sh.pre, u, maxu, sh.cnt, B, dv);
+                c = edge_bitmap(sh.s.b.bm, sh.s.b.pre, u, maxu, sh.cnt, B, dv);
+            } else if (hashed) {
+                c = edge_probe_set(HashProbe{sh.s.h.keys, hshift, hmask}, maxu, sh.s.h.hcnt, B, dv);
             } else {
                 int method = strategy;
                 if (method == TC_STRAT_AUTO) {
@@ -762,6 +907,13 @@ __global__ void __launch_bounds__(CTA_THREADS) k_tc_cta(int32_t n, const int64_t
                 if (cv) atomicAdd(&t[sh.Lu[p]], (unsigned long long)cv);
             }
         }
+        if (hashed) {
+            for (int p = threadIdx.x; p <= (int)hmask; p += CTA_THREADS) {
+                const int32_t x = sh.s.h.keys[p];
+                const uint32_t cv = sh.s.h.hcnt[p];
+                if (x >= 0 && cv) atomicAdd(&t[x], (unsigned long long)cv);
+            }
+        }
         if (threadIdx.x == 0) {
             unsigned long long s = 0;
             for (int k = 0; k < CTA_WARPS; ++k) s += sh.utot[k];
@@ -786,23 +938,6 @@ struct BitmapProbe {
         const int off = x - v - 1;
         const uint32_t word = bm[off >> 5], bit = 1u << (off & 31);
         return (word & bit) ? (int)pre[off >> 5] + __popc(word & (bit - 1)) : -1;
-    }
-};
-
-// Open-addressing hash set of N+(v) in shared memory (Fibonacci hashing, linear
-// probing, empty slots hold -1).  The table has at least twice as many slots as
-// keys, so a probe meets an empty slot after about two steps at most on average.
-struct HashProbe {
-    const int32_t* keys;
-    unsigned shift, mask;
-    __device__ __forceinline__ int operator()(int32_t x) const {
-        unsigned h = ((unsigned)x * 0x9e3779b1u) >> shift;
-        for (;;) {
-            const int32_t k = keys[h];
-            if (k == x) return (int)h;
-            if (k < 0) return -1;
-            h = (h + 1) & mask;
-        }
     }
 };
 
@@ -1135,7 +1270,8 @@ __global__ void k_plan_stats(int32_t n, const int64_t* __restrict__ rowstart, co
         const int d = rowlen[u];
         for (int k = 0; k < d; ++k) {
             const int32_t v = col[rowstart[u] + k];
-            const int b = v >= R ? TC_BUCKET_HUB : (d < 2 ? TC_NUM_BUCKETS : (d <= 32 ? TC_BUCKET_SMALL : TC_BUCKET_CTA));
+            const int b = v >= R ? TC_BUCKET_HUB
+                                 : (d < 2 ? TC_NUM_BUCKETS : (d <= SMALL_WIDE_MAX ? TC_BUCKET_SMALL : TC_BUCKET_CTA));
             e[b] += 1;
             ids[b] += (unsigned long long)(d + rowlen[v]);
         }
@@ -1199,12 +1335,16 @@ void launch_plan(const CountBuffers& C, const Strategy& S, const Launch& L) {
     }
     k_plan<<<grid_for(C.n, THREADS * PLAN_ITEMS, L.sms), THREADS, 0, L.stream>>>(C.n, C.rowstart, C.rowlen, C.col,
                                                                    C.small_list[0], C.small_list[1],
-                                                                   C.small_list[2], C.cta_list, C.stats);
+                                                                   C.small_list[2], C.small_list[3], C.cta_list,
+                                                                   C.stats);
     count_launch();
 }
 
 cudaError_t intersect_init_attributes() {
     cudaError_t e = cudaFuncSetAttribute(k_tc_cta, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(CtaShared));
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(k_tc_small_wide, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             2 * SMALL_WIDE_GROUPS * SMALL_WIDE_MAX * (int)sizeof(int32_t));
     if (e != cudaSuccess) return e;
     return cudaFuncSetAttribute(k_tc_hub, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(HubShared));
 }
@@ -1222,6 +1362,9 @@ void launch_intersect(const CountBuffers& C, const Strategy& S, cudaEvent_t* ev,
     count_launch();
     k_tc_small<32><<<L.sms * SMALL_BLOCKS, SMALL_WARPS * 32, 0, L.stream>>>(C.n, C.rowstart, C.rowlen, C.rowinfo, C.col, C.small_list[2],
                                                                 2, C.t_rank, C.stats, ss, sf);
+    count_launch();
+    k_tc_small_wide<<<L.sms * SMALL_WIDE_BLOCKS, SMALL_WARPS * 32, 2 * SMALL_WIDE_GROUPS * SMALL_WIDE_MAX * sizeof(int32_t),
+                      L.stream>>>(C.n, C.rowinfo, C.col, C.small_list[3], C.t_rank, C.stats, ss, sf);
     count_launch();
     if (ev) cudaEventRecord(ev[PH_CTA], L.stream);
     cudaMemsetAsync(&C.stats->cta_next, 0, sizeof(unsigned), L.stream);

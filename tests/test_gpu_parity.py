@@ -208,6 +208,23 @@ def test_rmat_several_tiles(tc, scale, ef, seed):
     assert_matches_oracle(tc, n, s, d)
 
 
+@pytest.fixture(scope="module")
+def rmat18():
+    n = 1 << 18
+    s, d = graphgen.rmat(18, 16 * n, seed=9)
+    return n, s, d, oracle.triangles(n, s, d)
+
+
+@pytest.mark.parametrize("hubs", [(32, 0), (32, 500), (32, 131072)])
+def test_block_bucket_wide_windows(tc, rmat18, hubs):
+    """Sources of the block bucket whose rank window (u, max N+(u)] is wider than
+    the 131072-bit bitmap fall back to a hash set of N+(u): R-MAT scale 18 with
+    few or no hubs has many such sources."""
+    n, s, d, ref = rmat18
+    for cta in [("bitmap", 1.0), ("auto", 1.0)]:
+        assert_matches_oracle(tc, n, s, d, ref=ref, hubs=hubs, strategies={tc.TC_BUCKET_CTA: cta})
+
+
 def test_er_ragged_sizes(tc):
     for n, m in [(1000, 7777), (65537, 400001), (3, 3)]:
         s, d = graphgen.er(n, m, seed=n)
