@@ -53,7 +53,7 @@ def parse_args():
     p.add_argument("--workload", default="rmat20", choices=sorted(WORKLOAD_TEXT))
     p.add_argument("--e2e-steps", type=int, default=10)
     p.add_argument("--no-cpu-baseline", action="store_true")
-    p.add_argument("--mode", choices=["single", "batch", "serve"], default="single",
+    p.add_argument("--mode", choices=["single", "batch", "serve", "ablation"], default="single",
                    help="single: one graph per step; batch: the 20,000-graph batch per step; "
                         "serve: the Poisson request stream through the serving loop")
     p.add_argument("--serve-seconds", type=float, default=60.0)
@@ -550,6 +550,69 @@ def run_serve(args, rank, world, local):
     print(json.dumps(line), flush=True)
 
 
+ABLATION = [
+    # (name, strategy spec, tuning overrides): Table II's methods on the GPU path with the
+    # hub pull turned off, then the hub pull without and with the dense core
+    ("ssi: merge (Alg. 2) on every edge, no hubs", "hubs:32:0,small:merge,cta:merge", {}),
+    ("bs: binary search (Alg. 1) on every edge, no hubs", "hubs:32:0,small:search,cta:search", {}),
+    ("hybrid: Eq. 3 per edge, no hubs", "hubs:32:0,small:auto,cta:auto", {}),
+    ("hub pull (bitmap / hash sets), no dense core", None, {"hub_core": 0}),
+    ("default: hub pull + dense core", None, {}),
+]
+
+
+def run_ablation(args, rank, world, local):
+    """Table II on the GPU: the count phase (plan + intersection kernels) of one
+    resident graph under each method; edges/s = simple edges / count time."""
+    import numpy as np
+    import torch
+
+    import graphgen
+    import paper_2202_13976_gb300 as tc
+    torch.cuda.set_device(local)
+    tc.load()
+    w = graphgen.workload(args.workload)
+    s, d = w.edges()
+    g = tc.Graph.from_edges(w.n, torch.from_numpy(s).cuda(), torch.from_numpy(d).cuda())
+    T0 = g.count()
+    m_simple = g.info()["m_simple"]
+    base = g.tuning()
+    rows = []
+    for name, spec, over in ABLATION:
+        g.set_tuning(base)
+        g.set_hubs(base["hub_min_degree"], base["hub_max"])
+        apply_strategy(g, spec, tc)
+        if over:
+            t = g.tuning()
+            t.update(over)
+            g.set_tuning(t)
+        times = []
+        plan_ms = 0.0
+        for k in range(max(args.warmup, 1) + args.steps):
+            assert g.count() == T0
+            tim = g.timing()
+            if k == 0:
+                plan_ms = tim["plan_ms"]  # the first count after a change of settings plans
+            if k >= max(args.warmup, 1):
+                times.append(tim["total_ms"])
+        ms = plan_ms + float(np.median(times))
+        rows.append({"method": name, "count_ms": ms, "plan_ms": plan_ms, "intersect_ms": ms - plan_ms,
+                     "edges_per_s": m_simple / (ms / 1000.0), "tuning": g.tuning()})
+    g.close()
+    if rank != 0:
+        return
+    best = min(rows, key=lambda r: r["count_ms"])
+    line = {"metric": "count-phase edges/sec by intersection method", "value": best["edges_per_s"],
+            "unit": "edges/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": best["count_ms"], "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "int32", "data": "synthetic",
+            "config": {"workload": w.name, "m_simple": m_simple, "T": T0,
+                       "timed": "plan (first count after the settings change) + median of the "
+                                "intersection kernels of later counts, resident graph"},
+            "methods": rows, "impl": "ours"}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse_args()
     rank, world, local = dist_env()
@@ -558,6 +621,9 @@ def main():
         return
     if args.mode == "serve":
         run_serve(args, rank, world, local)
+        return
+    if args.mode == "ablation":
+        run_ablation(args, rank, world, local)
         return
     if args.mode == "batch":
         if world > 1:

@@ -91,6 +91,13 @@ __device__ __forceinline__ bool eq3_prefers_merge(int a, int b, float factor) {
     return (float)l <= factor * (log2f((float)l) - 1.0f) * (float)s;
 }
 
+// Lane-per-edge choice between the batched merge and binary search: Eq. 3, except
+// that an N+(v) of at most 16 entries (two 8-entry loads of the merge) is always
+// merged, since one merge round costs less than the dependent loads of a search.
+__device__ __forceinline__ int small_auto(int a, int dv, float factor) {
+    return dv <= 16 || eq3_prefers_merge(a, dv, factor) || dv < a ? TC_STRAT_MERGE : TC_STRAT_SEARCH;
+}
+
 // ---- warp-cooperative methods (block push kernel) -----------------------------
 
 __device__ uint32_t edge_merge(const Sink& S, int a0, int du, const int32_t* __restrict__ B, int b) {
@@ -660,8 +667,7 @@ __global__ void __launch_bounds__(SMALL_WARPS * 32, SMALL_BLOCKS) k_tc_small(int
                 const int32_t* B = col + ri.x;
                 const int a = du - g - 1;
                 int method = strategy;
-                if (method == TC_STRAT_AUTO)
-                    method = eq3_prefers_merge(a, dv, factor) || dv < a ? TC_STRAT_MERGE : TC_STRAT_SEARCH;
+                if (method == TC_STRAT_AUTO) method = small_auto(a, dv, factor);
                 if (method == TC_STRAT_MERGE)
                     c = lane_merge_batched(Lu, g + 1, du, B, dv, cnt);
                 else
@@ -726,8 +732,7 @@ __global__ void __launch_bounds__(SMALL_WARPS * 32) k_tc_small_wide(int32_t n, c
             const int32_t* B = col + ri.x;
             const int a = du - j - 1;
             int method = strategy;
-            if (method == TC_STRAT_AUTO)
-                method = eq3_prefers_merge(a, dv, factor) || dv < a ? TC_STRAT_MERGE : TC_STRAT_SEARCH;
+            if (method == TC_STRAT_AUTO) method = small_auto(a, dv, factor);
             const uint32_t cj = method == TC_STRAT_MERGE
                                     ? lane_merge_batched(Lu, j + 1, du, B, dv, cnt)
                                     : (a <= dv ? lane_search(Lu, j + 1, du, B, dv, cnt)
