@@ -559,6 +559,7 @@ ABLATION = [
     ("hub pull (bitmap / hash sets), no dense core", None, {"hub_core": 0}),
     ("default: hub pull + dense core", None, {}),
 ]
+VERTEX_FORMULA = "per-vertex formula (Alg. 3, unoriented, symmetric CSR built per call)"
 
 
 def run_ablation(args, rank, world, local):
@@ -598,6 +599,17 @@ def run_ablation(args, rank, world, local):
         ms = plan_ms + float(np.median(times))
         rows.append({"method": name, "count_ms": ms, "plan_ms": plan_ms, "intersect_ms": ms - plan_ms,
                      "edges_per_s": m_simple / (ms / 1000.0), "tuning": g.tuning()})
+    # the paper's unoriented per-vertex formula: whole call (symmetric CSR + count)
+    ts = []
+    for k in range(max(args.warmup, 1) + args.steps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        Tv, _ = g.vertex_formula()
+        ts.append(time.perf_counter() - t0)
+        assert Tv == T0
+    ms = 1000.0 * float(np.median(ts[max(args.warmup, 1):]))
+    rows.append({"method": VERTEX_FORMULA, "count_ms": ms, "edges_per_s": m_simple / (ms / 1000.0),
+                 "timed": "wall clock of the call, t[] copied to the host"})
     g.close()
     if rank != 0:
         return

@@ -101,6 +101,22 @@ tc_status tc_count(tc_graph* g, uint64_t* T_out);
 tc_status lcc_compute(tc_graph* g, uint64_t* t_out, double* lcc_out, int mem_kind);
 
 /*
+ * Per-vertex triangle counts by the paper's unoriented per-vertex formula (Alg. 3
+ * with the Sec. II-C offset): t(v_i) = sum over v_j in adj(v_i) of
+ * |adj(v_i) ∩ {v_k in adj(v_j) : k > j}|, each intersection chosen per pair by Eq. 3
+ * (merge, Alg. 2, or binary search of the shorter list, Alg. 1), every vertex's sum
+ * formed by one warp and written once (no shared accumulation).  The graph's
+ * vertices are relabelled by rank, so "k > j" compares ranks; the symmetric CSR it
+ * needs is built for the call (a radix sort of the transposed oriented entries) and
+ * released after it.  An alternative to tc_count / lcc_compute for comparison and
+ * ablation: same results, far more work on skewed graphs.  t_out[n] (uint64) in the
+ * caller's ids, in mem_kind memory; the stream is synchronised.  *T_out (may be
+ * NULL) receives sum t / 3.  Errors: TC_EINVAL (NULL t_out, bad mem_kind), TC_ENOMEM,
+ * TC_ECUDA, TC_EINTERNAL (sum t is not a multiple of 3).
+ */
+tc_status tc_count_vertex_formula(tc_graph* g, uint64_t* t_out, int mem_kind, uint64_t* T_out);
+
+/*
  * Input accounting: number of distinct undirected edges, self-loops dropped and
  * repeated pairs dropped.  Any pointer may be NULL.  Synchronises the stream.
  */

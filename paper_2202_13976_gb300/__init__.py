@@ -32,7 +32,7 @@ EXPORTS = ["tc_graph_create_from_edges", "tc_graph_create_from_csr", "tc_count",
            "tc_batch_create", "tc_batch_count", "tc_batch_size", "tc_graph_get_tuning",
            "tc_graph_set_tuning", "tc_graph_autotune", "tc_batch_run", "tc_release_cached_graphs",
            "tc_generate_edges", "tc_server_start", "tc_server_submit", "tc_server_poll", "tc_server_wait",
-           "tc_server_get_stats", "tc_server_stop", "tc_graph_build_timing"]
+           "tc_server_get_stats", "tc_server_stop", "tc_graph_build_timing", "tc_count_vertex_formula"]
 BUILD_PHASES = ["ingest_ms", "rank_ms", "count_ms", "fill_ms", "sort_ms", "degree_ms", "total_ms"]
 TC_GEN_RMAT, TC_GEN_ER_REPLACE = 0, 1
 GEN_KINDS = {"rmat": TC_GEN_RMAT, "er_replace": TC_GEN_ER_REPLACE}
@@ -124,6 +124,8 @@ def load(path: str | None = None):
     lib.tc_count.argtypes = [P, ctypes.POINTER(u64)]
     lib.lcc_compute.restype = st
     lib.lcc_compute.argtypes = [P, P, P, ctypes.c_int]
+    lib.tc_count_vertex_formula.restype = st
+    lib.tc_count_vertex_formula.argtypes = [P, P, ctypes.c_int, ctypes.POINTER(u64)]
     lib.tc_graph_info.restype = st
     lib.tc_graph_info.argtypes = [P, ctypes.POINTER(i64), ctypes.POINTER(i64), ctypes.POINTER(i64)]
     lib.tc_graph_size.restype = st
@@ -267,6 +269,21 @@ def lcc_compute(g: int, t_out=None, lcc_out=None):
         _check_dtype(lcc_out, "float64")
     (pt, pl), kind = _ptr_kind(t_out, lcc_out)
     _check(_lib.lcc_compute(g, pt, pl, kind))
+
+
+def tc_count_vertex_formula(g: int, t_out=None):
+    """Per-vertex counts by the paper's unoriented per-vertex formula into t_out
+    (uint64[n] as int64, host numpy or CUDA tensor; a numpy array is allocated when
+    None); returns (T, t_out)."""
+    if t_out is None:
+        import numpy as np
+        n, _ = tc_graph_size(g)
+        t_out = np.empty(n, dtype=np.int64)
+    _check_dtype(t_out, "int64")
+    (pt,), kind = _ptr_kind(t_out)
+    T = ctypes.c_uint64()
+    _check(_lib.tc_count_vertex_formula(g, pt, kind, ctypes.byref(T)))
+    return int(T.value), t_out
 
 
 def tc_graph_info(g: int) -> dict:
@@ -484,6 +501,13 @@ class Graph:
             lcc_out = np.empty(self.n, dtype=np.float64)
         lcc_compute(self.handle, t_out, lcc_out)
         return t_out, lcc_out
+
+    def vertex_formula(self, t_out=None):
+        """(T, t) by the paper's unoriented per-vertex formula (for comparison)."""
+        T, t = tc_count_vertex_formula(self.handle, t_out)
+        if not hasattr(t, "cuda"):
+            t = t.view("uint64")
+        return T, t
 
     def info(self) -> dict:
         return tc_graph_info(self.handle)

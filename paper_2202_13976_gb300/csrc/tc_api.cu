@@ -559,6 +559,62 @@ tc_status lcc_compute(tc_graph* g, uint64_t* t_out, double* lcc_out, int mem_kin
     return TC_OK;
 }
 
+tc_status tc_count_vertex_formula(tc_graph* g, uint64_t* t_out, int mem_kind, uint64_t* T_out) {
+    if (!g || !t_out || (mem_kind != TC_MEM_HOST && mem_kind != TC_MEM_DEVICE)) return TC_EINVAL;
+    DevStats h;
+    tc_status st = read_stats(g, &h);
+    if (st != TC_OK) return st;
+    if (h.err & ERR_BAD_ID) return TC_EINVAL;
+    const size_t nn = (size_t)g->n;
+    VertexFormulaBuffers V{};
+    V.n = g->n;
+    V.m = (int64_t)h.m_simple;
+    V.m_cap = g->m_alloc;
+    V.rowstart = g->rowstart;
+    V.rowlen = g->rowlen;
+    V.rowinfo = g->rowinfo;
+    V.col = g->col;
+    V.deg = g->deg;
+    std::vector<void*> tmp;
+    char* radix_tmp = nullptr;
+    char* scan_tmp = nullptr;
+    unsigned long long* dt = nullptr;
+    unsigned* cs = nullptr;
+    if ((st = dalloc(g, &V.indeg, nn, &tmp)) || (st = dalloc(g, &V.sym_start, nn + 1, &tmp)) ||
+        (st = dalloc(g, &V.instart, nn + 1, &tmp)) || (st = dalloc(g, &V.sym, (size_t)(2 * V.m), &tmp)) ||
+        (st = dalloc(g, &V.keys, (size_t)V.m_cap, &tmp)) || (st = dalloc(g, &V.keys_alt, (size_t)V.m_cap, &tmp)) ||
+        (st = dalloc(g, &radix_tmp, radix_tmp_bytes(V.m_cap), &tmp)) ||
+        (st = dalloc(g, &scan_tmp, scan_tmp_bytes((int64_t)nn + 1), &tmp)) || (st = dalloc(g, &V.t, nn, &tmp)) ||
+        (st = dalloc(g, &cs, 8, &tmp))) {
+        free_list(g, &tmp);
+        return st;
+    }
+    V.radix_tmp = radix_tmp;
+    V.tmp = scan_tmp;
+    V.counter = cs;
+    V.sum = reinterpret_cast<unsigned long long*>(cs + 2);
+    launch_vertex_formula(V, g->L);
+    unsigned long long* out = mem_kind == TC_MEM_DEVICE ? reinterpret_cast<unsigned long long*>(t_out) : nullptr;
+    if (!out && (st = dalloc(g, &dt, nn, &tmp))) {
+        free_list(g, &tmp);
+        return st;
+    }
+    launch_finalize(g->n, g->rank, V.t, g->deg, out ? out : dt, nullptr, g->L);
+    unsigned long long sum = 0;
+    cudaError_t e = cudaMemcpyAsync(&sum, V.sum, sizeof(sum), cudaMemcpyDeviceToHost, g->stream);
+    if (e == cudaSuccess && !out && nn > 0)
+        e = cudaMemcpyAsync(t_out, dt, sizeof(uint64_t) * nn, cudaMemcpyDeviceToHost, g->stream);
+    free_list(g, &tmp);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(g->stream);
+    if (e != cudaSuccess) return cuda_fail("tc_count_vertex_formula", e);
+    if (sum % 3 != 0) {
+        snprintf(g_last_error, sizeof(g_last_error), "sum of t is not a multiple of 3");
+        return TC_EINTERNAL;
+    }
+    if (T_out) *T_out = sum / 3;
+    return TC_OK;
+}
+
 tc_status tc_graph_info(const tc_graph* g, int64_t* m_simple, int64_t* loops_dropped, int64_t* dups_dropped) {
     if (!g) return TC_EINVAL;
     DevStats h;

@@ -226,7 +226,8 @@ __global__ void k_orient_scatter(const int32_t* __restrict__ src, const int32_t*
 // count and scatter above: their heavy rows would pile onto a few buckets and onto
 // single shared-memory counters, while in the direct scatter they stay in cache.
 constexpr int PART_ITEMS = 16;
-constexpr int PART_TILE = THREADS * PART_ITEMS;
+constexpr int PART_THREADS = 1024;  // large tiles: one reservation per bucket and 16384 pairs
+constexpr int PART_TILE = PART_THREADS * PART_ITEMS;
 constexpr int FILL_THREADS = 1024;
 
 __global__ void __launch_bounds__(THREADS) k_bucket_count(const int32_t* __restrict__ src,
@@ -256,7 +257,7 @@ __global__ void __launch_bounds__(THREADS) k_bucket_count(const int32_t* __restr
         if (hist[b]) atomicAdd(&bcount[b], hist[b]);
 }
 
-__global__ void __launch_bounds__(THREADS) k_orient_part(const int32_t* __restrict__ src, const int32_t* __restrict__ dst,
+__global__ void __launch_bounds__(PART_THREADS) k_orient_part(const int32_t* __restrict__ src, const int32_t* __restrict__ dst,
                                                          int64_t m, int32_t n, const int32_t* __restrict__ rank,
                                                          int shift, int nb, const int64_t* __restrict__ bstart,
                                                          uint32_t* __restrict__ bcur, int2* __restrict__ pairs,
@@ -265,13 +266,13 @@ __global__ void __launch_bounds__(THREADS) k_orient_part(const int32_t* __restri
     int64_t* base = reinterpret_cast<int64_t*>(part_sh);  // nb
     uint32_t* hist = reinterpret_cast<uint32_t*>(base + nb);  // nb
     for (int64_t t0 = (int64_t)blockIdx.x * PART_TILE; t0 < m; t0 += (int64_t)gridDim.x * PART_TILE) {
-        for (int b = threadIdx.x; b < nb; b += THREADS) hist[b] = 0;
+        for (int b = threadIdx.x; b < nb; b += PART_THREADS) hist[b] = 0;
         __syncthreads();
         int32_t sv[PART_ITEMS], tv[PART_ITEMS];
         uint32_t loc[PART_ITEMS];
 #pragma unroll
         for (int k = 0; k < PART_ITEMS; ++k) {
-            const int64_t i = t0 + (int64_t)k * THREADS + threadIdx.x;
+            const int64_t i = t0 + (int64_t)k * PART_THREADS + threadIdx.x;
             sv[k] = -1;
             if (i < m) {
                 const int32_t u = src[i], v = dst[i];
@@ -284,7 +285,7 @@ __global__ void __launch_bounds__(THREADS) k_orient_part(const int32_t* __restri
             }
         }
         __syncthreads();
-        for (int b = threadIdx.x; b < nb; b += THREADS) {
+        for (int b = threadIdx.x; b < nb; b += PART_THREADS) {
             const uint32_t c = hist[b];
             if (c) base[b] = bstart[b] + atomicAdd(&bcur[b], c);
         }
@@ -770,7 +771,7 @@ void launch_orient(const BuildBuffers& B, const Launch& L, cudaEvent_t* ev) {
         scan_u32_to_i64(B.bcount, B.bstart, nb, B.tmp, L);
         if (ev) cudaEventRecord(ev[BP_COUNT], L.stream);
         if (B.m > 0) {
-            k_orient_part<<<grid_for(B.m, PART_TILE, L.sms, 4), THREADS, (sizeof(int64_t) + sizeof(uint32_t)) * nb,
+            k_orient_part<<<grid_for(B.m, PART_TILE, L.sms, 1), PART_THREADS, (sizeof(int64_t) + sizeof(uint32_t)) * nb,
                             L.stream>>>(B.src, B.dst, B.m, B.n, B.rank, shift, nb, B.bstart, B.bcur, B.pairs, B.stats);
             count_launch();
         }

@@ -175,6 +175,31 @@ void launch_finalize(int32_t n, const int32_t* rank, const unsigned long long* t
                      const int32_t* deg, unsigned long long* t_out, double* lcc_out,
                      const Launch& L);
 
+// ---- per-vertex formula (tc_vertex.cu) -------------------------------------------
+struct VertexFormulaBuffers {
+    int32_t n;
+    int64_t m;               // oriented entries (distinct edges)
+    int64_t m_cap;           // entries of col, including slots freed by deduplication
+    const int64_t* rowstart;
+    const int32_t* rowlen;
+    const int2* rowinfo;
+    const int32_t* col;
+    const int32_t* deg;      // simple degree (rank space)
+    uint32_t* indeg;         // n
+    int64_t* sym_start;      // n + 1
+    int64_t* instart;        // n + 1
+    int32_t* sym;            // 2 m: symmetric rows, ascending
+    uint64_t* keys;          // m_cap
+    uint64_t* keys_alt;      // m_cap
+    void* radix_tmp;         // radix_tmp_bytes(m_cap)
+    void* tmp;               // scan_tmp_bytes(n + 1)
+    unsigned long long* t;   // n (rank space)
+    unsigned* counter;
+    unsigned long long* sum;
+};
+int vf_key_bits(int32_t n);
+void launch_vertex_formula(const VertexFormulaBuffers& V, const Launch& L);
+
 // ---- batch (tc_batch.cu) -------------------------------------------------------
 void launch_batch_relabel(int32_t G, const int64_t* edge_off, const int32_t* vbase, const int32_t* src,
                           const int32_t* dst, int32_t* usrc, int32_t* udst, int* err, const Launch& L);

@@ -245,3 +245,49 @@ def test_repeated_create_destroy_is_stable(tc, er4096):
     for _ in range(5):
         T, t, _, _ = gpu_run(tc, n, s, d)
         assert T == ref["T"]
+
+
+@pytest.mark.parametrize("make", [
+    lambda: F.complete(34), lambda: F.wheel(40), lambda: F.friendship(7), lambda: F.star(100),
+    lambda: F.complete_tripartite(3, 5, 40), lambda: F.grid(20, 30)])
+def test_vertex_formula_closed_forms(tc, make):
+    """The paper's unoriented per-vertex formula on the GPU gives the oracle's t[]."""
+    n, (s, d) = make()
+    ref = oracle.triangles(n, s, d)
+    g = tc.Graph.from_edges(n, s, d)
+    try:
+        T, t = g.vertex_formula()
+    finally:
+        g.close()
+    assert T == ref["T"]
+    np.testing.assert_array_equal(t, ref["t"])
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_vertex_formula_tiny_random(tc, seed):
+    from tests.test_oracle import _tiny
+    n, s, d = _tiny(seed)
+    ref = oracle.triangles(n, s, d)
+    g = tc.Graph.from_edges(n, s, d)
+    try:
+        T, t = g.vertex_formula()
+    finally:
+        g.close()
+    assert T == ref["T"]
+    np.testing.assert_array_equal(t, ref["t"])
+
+
+def test_vertex_formula_rmat_and_er(tc, rmat14, er4096):
+    import torch
+    for n, s, d, ref in (rmat14, er4096):
+        g = tc.Graph.from_edges(n, s, d)
+        try:
+            T, t = g.vertex_formula()
+            td = torch.empty(n, dtype=torch.int64, device="cuda")
+            T2, _ = g.vertex_formula(td)
+            assert g.count() == T  # the oriented count on the same graph object agrees
+        finally:
+            g.close()
+        assert T == ref["T"] and T2 == ref["T"]
+        np.testing.assert_array_equal(t, ref["t"])
+        np.testing.assert_array_equal(td.cpu().numpy().view(np.uint64), ref["t"])
