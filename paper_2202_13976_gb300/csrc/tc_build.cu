@@ -634,6 +634,8 @@ __global__ void __launch_bounds__(SEG_WARPS * 32) k_segsort_warp(const int64_t* 
                 kept = warp_sort_row<4>(row, len, dupin, lane);
             else
                 kept = warp_sort_row<8>(row, len, dupin, lane);
+        } else if (MAXK <= 16) {
+            kept = warp_sort_row<16>(row, len, dupin, lane);
         } else {
             if (len <= 512)
                 kept = warp_sort_row<16>(row, len, dupin, lane);
@@ -801,9 +803,10 @@ void launch_orient(const BuildBuffers& B, const Launch& L, cudaEvent_t* ev) {
     k_segsort_warp<8><<<L.sms * 4, SEG_WARPS * 32, 0, L.stream>>>(B.rowstart, B.rowcnt, B.col, B.rowlen, B.rowinfo,
                                                                  B.dupin, B.midlist, &B.stats->mid_count, B.stats);
     count_launch();
-    k_segsort_warp<32><<<L.sms * 2, SEG_WARPS * 32, 0, L.stream>>>(B.rowstart, B.rowcnt, B.col, B.rowlen,
-                                                                  B.rowinfo, B.dupin, B.midlist2,
-                                                                  &B.stats->mid2_count, B.stats);
+    k_segsort_warp<WARP_SORT_MAX / 32><<<L.sms * 2, SEG_WARPS * 32, 0, L.stream>>>(B.rowstart, B.rowcnt, B.col,
+                                                                                  B.rowlen, B.rowinfo, B.dupin,
+                                                                                  B.midlist2, &B.stats->mid2_count,
+                                                                                  B.stats);
     count_launch();
     k_segsort_block<<<L.sms * 2, 1024, CTA_SORT_MAX * sizeof(int32_t), L.stream>>>(
         B.rowstart, B.rowcnt, B.col, B.rowlen, B.rowinfo, B.dupin, B.longlist, B.stats);
