@@ -215,7 +215,19 @@ int bits_for(unsigned x) {
 // so that create can fail with TC_EINVAL; otherwise the build never waits on the
 // device (the radix sort takes its degree bits from the bound 2m) and invalid ids
 // are reported by the first call that reads the statistics.
-tc_status build_graph(tc_graph* g, const int32_t* src, const int32_t* dst, int64_t m, bool checked = true) {
+// Host input of build_graph: the pairs are copied in INGEST_PIECES pieces on a side
+// stream and each piece's degree counts start as soon as it has landed, so the copy
+// overlaps the ingest pass.
+struct HostPairs {
+    const int32_t* src;
+    const int32_t* dst;
+    cudaStream_t side;
+    cudaEvent_t landed;
+};
+constexpr int INGEST_PIECES = 8;
+
+tc_status build_graph(tc_graph* g, const int32_t* src, const int32_t* dst, int64_t m, bool checked = true,
+                      const HostPairs* host = nullptr) {
     const int32_t n = g->n;
     const size_t nn = (size_t)n;
     tc_status st;
@@ -282,7 +294,28 @@ tc_status build_graph(tc_graph* g, const int32_t* src, const int32_t* dst, int64
     }
     cudaMemsetAsync(g->stats, 0, sizeof(DevStats), g->stream);
     cudaMemsetAsync(B.dmulti, 0, sizeof(uint32_t) * nn, g->stream);
-    launch_canon_degree(B, g->L);
+    if (host && m > 0) {
+        const int64_t piece = (m + INGEST_PIECES - 1) / INGEST_PIECES;
+        cudaError_t e = cudaSuccess;
+        for (int64_t first = 0; first < m && e == cudaSuccess; first += piece) {
+            const int64_t cnt = first + piece < m ? piece : m - first;
+            e = cudaMemcpyAsync(const_cast<int32_t*>(src) + first, host->src + first, sizeof(int32_t) * (size_t)cnt,
+                                cudaMemcpyHostToDevice, host->side);
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(const_cast<int32_t*>(dst) + first, host->dst + first,
+                                    sizeof(int32_t) * (size_t)cnt, cudaMemcpyHostToDevice, host->side);
+            if (e == cudaSuccess) e = cudaEventRecord(host->landed, host->side);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(g->stream, host->landed, 0);
+            if (e == cudaSuccess) launch_canon_degree_part(B, first, cnt, g->L);
+        }
+        if (e != cudaSuccess) {
+            free_list(g, &scratch);
+            return cuda_fail("host input copy", e);
+        }
+        launch_max_deg(B, g->L);
+    } else {
+        launch_canon_degree(B, g->L);
+    }
     if (bev) cudaEventRecord(bev[BP_INGEST], g->stream);
     int deg_bits = bits_for((unsigned)(2 * m < (int64_t)UINT32_MAX ? 2 * m : (int64_t)UINT32_MAX));
     if (checked) {
@@ -431,16 +464,24 @@ tc_status tc_graph_create_from_edges(int32_t n, int64_t m, const int32_t* src, c
         free_list(g, &tmp);
         return finish_create(g, st, out);
     }
-    if (m > 0) {
-        cudaError_t e = cudaMemcpyAsync(ds, src, sizeof(int32_t) * (size_t)m, cudaMemcpyHostToDevice, g->stream);
-        if (e == cudaSuccess)
-            e = cudaMemcpyAsync(dd, dst, sizeof(int32_t) * (size_t)m, cudaMemcpyHostToDevice, g->stream);
-        if (e != cudaSuccess) {
-            free_list(g, &tmp);
-            return finish_create(g, cuda_fail("cudaMemcpyAsync", e), out);
-        }
-    }
-    st = build_graph(g, ds, dd, m);
+    // the side stream may only touch ds and dd once their allocation is ordered
+    HostPairs hp{src, dst, nullptr, nullptr};
+    cudaEvent_t allocated = nullptr;
+    cudaError_t e = cudaStreamCreateWithFlags(&hp.side, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&hp.landed, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&allocated, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventRecord(allocated, g->stream);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(hp.side, allocated, 0);
+    if (e != cudaSuccess)
+        st = cuda_fail("host input stream", e);
+    else
+        st = build_graph(g, ds, dd, m, true, &hp);
+    // the build read its statistics back on g->stream, which waited for every piece:
+    // the copies are complete; the side stream and events can go
+    if (st != TC_OK) cudaStreamSynchronize(hp.side);
+    if (allocated) cudaEventDestroy(allocated);
+    if (hp.landed) cudaEventDestroy(hp.landed);
+    if (hp.side) cudaStreamDestroy(hp.side);
     free_list(g, &tmp);
     return finish_create(g, st, out);
 }

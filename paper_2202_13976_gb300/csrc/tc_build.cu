@@ -728,12 +728,21 @@ void launch_expand_csr(const int64_t* offsets, int32_t n, int32_t* rows, DevStat
     k_expand_csr<<<grid_for((int64_t)n * 32, THREADS, L.sms), THREADS, 0, L.stream>>>(offsets, n, rows, stats); count_launch();
 }
 
-void launch_canon_degree(const BuildBuffers& B, const Launch& L) {
-    if (B.m > 0) {
-        // 32 KB of shared memory per block: four blocks per SM stay resident
-        k_canon_degree<<<grid_for(B.m, THREADS, L.sms, 4), THREADS, 0, L.stream>>>(B.src, B.dst, B.m, B.n, B.dmulti,
-                                                                                 B.stats); count_launch(); }
+void launch_canon_degree_part(const BuildBuffers& B, int64_t first, int64_t count, const Launch& L) {
+    if (count <= 0) return;
+    // 32 KB of shared memory per block: four blocks per SM stay resident
+    k_canon_degree<<<grid_for(count, THREADS, L.sms, 4), THREADS, 0, L.stream>>>(B.src + first, B.dst + first, count,
+                                                                               B.n, B.dmulti, B.stats);
+    count_launch();
+}
+
+void launch_max_deg(const BuildBuffers& B, const Launch& L) {
     if (B.n > 0) { k_max_deg<<<grid_for(B.n, THREADS, L.sms), THREADS, 0, L.stream>>>(B.dmulti, B.n, B.stats); count_launch(); }
+}
+
+void launch_canon_degree(const BuildBuffers& B, const Launch& L) {
+    launch_canon_degree_part(B, 0, B.m, L);
+    launch_max_deg(B, L);
 }
 
 void launch_rank(const BuildBuffers& B, int deg_bits, const Launch& L) {

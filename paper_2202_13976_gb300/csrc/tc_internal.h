@@ -100,6 +100,10 @@ void launch_check_offsets(const int64_t* offsets, int32_t n, int64_t limit, DevS
 void launch_expand_csr(const int64_t* offsets, int32_t n, int32_t* rows, DevStats* stats,
                        const Launch& L);
 void launch_canon_degree(const BuildBuffers& B, const Launch& L);
+// The same in pieces: the degree counts of pairs [first, first + count), then the
+// maximum degree once all pieces are in.
+void launch_canon_degree_part(const BuildBuffers& B, int64_t first, int64_t count, const Launch& L);
+void launch_max_deg(const BuildBuffers& B, const Launch& L);
 void launch_rank(const BuildBuffers& B, int deg_bits, const Launch& L);
 void launch_orient(const BuildBuffers& B, const Launch& L, cudaEvent_t* ev = nullptr);
 // Row fill by source buckets: at most BUCKET_MAX buckets of at most BUCKET_ROWS_MAX

@@ -53,7 +53,8 @@ constexpr int HUB_WARPS = HUB_THREADS / 32;
 constexpr int HUB_BM_WORDS = HUB_BM_BITS / 32;
 constexpr int HUB_CNT_MAX = 4096;      // hub lists longer than this count matches globally
 constexpr int HUB_WARP_MAX = 256;      // longest N+(v) a single warp stages
-constexpr int HUB_HASH_MAX = 512;      // its hash table: at least twice as many slots as keys
+constexpr int HUB_HASH_LOAD = 2;       // its hash table has at least this many slots per key
+constexpr int HUB_HASH_MAX = HUB_HASH_LOAD * HUB_WARP_MAX;
 constexpr int SCAT_STEPS = 4;          // lockstep steps of the row-walk scatter in flight together
 constexpr int HUB_BATCH = 32;          // in-edges per batch of a big hub
 constexpr int HUB_LONG = 32;           // suffixes at least this long are read by lane groups
@@ -1209,7 +1210,7 @@ __global__ void __launch_bounds__(HUB_THREADS) k_tc_hub(int32_t n, int32_t hub_c
         }
         const int64_t base = rowstart[v];
         int lg = 5;
-        while ((1 << lg) < 2 * dv) ++lg;
+        while ((1 << lg) < HUB_HASH_LOAD * dv) ++lg;
         const unsigned shift = 32u - (unsigned)lg, mask = (1u << lg) - 1u;
         for (int p = lane; p < dv; p += 32) {
             const int32_t x = col[base + p];
