@@ -34,7 +34,7 @@ UNIT = "edges/s"
 # Table II of the paper: R-MAT S20 EF16, hybrid intersection, 0.425 edges per
 # microsecond on a 16-thread Xeon Gold 6154 (context; another machine).
 PAPER_RMAT20_EDGES_PER_S = 0.425e6
-DEVSTATS_BYTES = 88
+DEVSTATS_BYTES = 96  # sizeof(DevStats): the library reads it back after the build and after the count
 FALLBACK_HBM_GBS = 6800.0
 WORKLOAD_TEXT = {
     "rmat20": "R-MAT scale 20, edge factor 16, (a,b,c,d)=(0.57,0.19,0.19,0.05), seed 2",
