@@ -226,8 +226,15 @@ struct HostPairs {
 };
 constexpr int INGEST_PIECES = 8;
 
+// Batches: the graphs' union id offsets and the widths of the rank key fields.
+struct SegInfo {
+    const int32_t* vbase;  // device, G + 1
+    int32_t G;
+    int seg_bits, deg_bits, local_bits;
+};
+
 tc_status build_graph(tc_graph* g, const int32_t* src, const int32_t* dst, int64_t m, bool checked = true,
-                      const HostPairs* host = nullptr) {
+                      const HostPairs* host = nullptr, const SegInfo* seg = nullptr) {
     const int32_t n = g->n;
     const size_t nn = (size_t)n;
     tc_status st;
@@ -260,6 +267,16 @@ tc_status build_graph(tc_graph* g, const int32_t* src, const int32_t* dst, int64
     B.dst = dst;
     B.m = m;
     B.n = n;
+    if (seg) {
+        // graph by graph ranks keep every graph's rows together, so the bucket fill's
+        // buckets hold whole graphs and stay balanced whatever the degrees
+        B.bucket_fill = m > 0;
+        B.seg_vbase = seg->vbase;
+        B.seg_count = seg->G;
+        B.seg_bits = seg->seg_bits;
+        B.seg_deg_bits = seg->deg_bits;
+        B.local_bits = seg->local_bits;
+    }
     size_t tmp_bytes = scan_tmp_bytes((int64_t)nn + 1);
     size_t rt = radix_tmp_bytes((int64_t)nn);
     if (rt > tmp_bytes) tmp_bytes = rt;
@@ -783,8 +800,24 @@ static tc_status batch_host_checks(int32_t G, const int32_t* n, const int64_t* e
 }
 
 // Device pipeline of a batch (no host synchronisation: capturable).
+// Widths of the (graph, degree, local id) rank key of a batch, from the host arrays:
+// a vertex's pair count is at most its graph's pair count.
+static SegInfo batch_seg_info(int32_t G, const int32_t* n, const int64_t* edge_off, const int32_t* vbase_dev) {
+    SegInfo s{vbase_dev, G, 1, 1, 1};
+    int32_t nmax = 1;
+    int64_t mmax = 1;
+    for (int32_t i = 0; i < G; ++i) {
+        if (n[i] > nmax) nmax = n[i];
+        if (edge_off[i + 1] - edge_off[i] > mmax) mmax = edge_off[i + 1] - edge_off[i];
+    }
+    while (s.seg_bits < 31 && ((int64_t)1 << s.seg_bits) < (int64_t)G) ++s.seg_bits;
+    while (s.local_bits < 31 && ((int64_t)1 << s.local_bits) < (int64_t)nmax) ++s.local_bits;
+    while (s.deg_bits < 33 && ((int64_t)1 << s.deg_bits) <= mmax) ++s.deg_bits;
+    return s;
+}
+
 static tc_status batch_build(tc_graph* g, int32_t G, const int32_t* vbase_dev, const int64_t* eoff_dev,
-                             const int32_t* src, const int32_t* dst, int64_t m) {
+                             const int32_t* src, const int32_t* dst, int64_t m, const SegInfo* seg) {
     std::vector<void*> tmp;
     int32_t *us = nullptr, *ud = nullptr;
     tc_status st;
@@ -793,7 +826,7 @@ static tc_status batch_build(tc_graph* g, int32_t G, const int32_t* vbase_dev, c
         return st;
     }
     launch_batch_relabel(G, eoff_dev, vbase_dev, src, dst, us, ud, g->batch_err, g->L);
-    st = build_graph(g, us, ud, m, false);
+    st = build_graph(g, us, ud, m, false, nullptr, seg);
     free_list(g, &tmp);
     return st;
 }
@@ -844,7 +877,8 @@ extern "C" tc_status tc_batch_create(int32_t G, const int32_t* n, const int64_t*
         s_dev = hs;
         d_dev = hd;
     }
-    st = batch_build(g, G, g->batch_vbase, eoff, s_dev, d_dev, m);
+    const SegInfo seg = batch_seg_info(G, n, edge_off, g->batch_vbase);
+    st = batch_build(g, G, g->batch_vbase, eoff, s_dev, d_dev, m, &seg);
     free_list(g, &tmp);
     return finish_create(g, st, out);
 }
@@ -1090,13 +1124,13 @@ static uint64_t fnv(uint64_t h, const void* p, size_t bytes) {
 // The device work of one batch call on g->stream (no host synchronisation).
 static tc_status batch_pipeline(tc_graph* g, int32_t G, int32_t* vbase, const int64_t* eoff, const int32_t* src,
                                 const int32_t* dst, int64_t m, uint64_t* T_out, uint64_t* t_out, double* lcc_out,
-                                int* status) {
+                                int* status, const SegInfo* seg) {
     g->batch_G = G;
     g->batch_vbase = vbase;
     tc_status st;
     if ((st = dalloc(g, &g->batch_err, 1, &g->blocks)) != TC_OK) return st;
     TC_CK(cudaMemsetAsync(g->batch_err, 0, sizeof(int), g->stream));
-    if ((st = batch_build(g, G, vbase, eoff, src, dst, m)) != TC_OK) return st;
+    if ((st = batch_build(g, G, vbase, eoff, src, dst, m, seg)) != TC_OK) return st;
     if ((st = batch_count_device(g, reinterpret_cast<unsigned long long*>(T_out))) != TC_OK) return st;
     if (t_out || lcc_out)
         launch_finalize(g->n, g->rank, g->t_rank, g->deg, reinterpret_cast<unsigned long long*>(t_out), lcc_out, g->L);
@@ -1159,7 +1193,8 @@ extern "C" tc_status tc_batch_run(int32_t G, const int32_t* n, const int64_t* ed
         tuning_put(g, &tun);
         if (graph_mode) TC_CK(cudaStreamBeginCapture(stream, cudaStreamCaptureModeThreadLocal));
         const uint64_t k0 = launch_total();
-        st = batch_pipeline(g, G, ent.vbase, ent.eoff, src, dst, m, T_out, t_out, lcc_out, ent.status);
+        const SegInfo seg = batch_seg_info(G, n, edge_off, ent.vbase);
+        st = batch_pipeline(g, G, ent.vbase, ent.eoff, src, dst, m, T_out, t_out, lcc_out, ent.status, &seg);
         g->batch_vbase = nullptr;  // owned by the entry
         destroy(g);
         ent.kernels = launch_total() - k0;

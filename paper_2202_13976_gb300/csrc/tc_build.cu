@@ -745,8 +745,57 @@ void launch_canon_degree(const BuildBuffers& B, const Launch& L) {
     launch_max_deg(B, L);
 }
 
+// Batches: the graph of every vertex (one warp per graph), then keys
+// (graph, degree, local id) whose stable sort on the graph and degree fields ranks the
+// vertices graph by graph.
+__global__ void k_seg_of(const int32_t* __restrict__ vbase, int32_t G, uint32_t* __restrict__ seg) {
+    const int lane = lane_id();
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t g = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; g < G; g += warps)
+        for (int64_t v = vbase[g] + lane; v < vbase[g + 1]; v += 32) seg[v] = (uint32_t)g;
+}
+
+__global__ void k_rank_keys_seg(const uint32_t* __restrict__ dmulti, const uint32_t* __restrict__ seg,
+                                const int32_t* __restrict__ vbase, int32_t n, int deg_bits, int local_bits,
+                                uint64_t* __restrict__ keys) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        const uint32_t g = seg[i];
+        keys[i] = ((uint64_t)g << (deg_bits + local_bits)) | ((uint64_t)dmulti[i] << local_bits) |
+                  (uint64_t)(i - vbase[g]);
+    }
+}
+
+__global__ void k_rank_invert_seg(const uint64_t* __restrict__ sorted, const int32_t* __restrict__ vbase, int32_t n,
+                                  int deg_bits, int local_bits, int32_t* __restrict__ rank,
+                                  uint32_t* __restrict__ dmulti) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const uint64_t lmask = (1ull << local_bits) - 1, dmask = (1ull << deg_bits) - 1;
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += stride) {
+        const uint64_t key = sorted[r];
+        const int64_t g = (int64_t)(key >> (deg_bits + local_bits));
+        rank[vbase[g] + (int64_t)(key & lmask)] = (int32_t)r;
+        dmulti[r] = (uint32_t)((key >> local_bits) & dmask);
+    }
+}
+
 void launch_rank(const BuildBuffers& B, int deg_bits, const Launch& L) {
     if (B.n <= 0) return;
+    if (B.seg_vbase && B.seg_count > 0 && B.seg_bits + B.seg_deg_bits + B.local_bits <= 64) {
+        uint32_t* seg = B.cursor;  // free until the row fill
+        k_seg_of<<<grid_for((int64_t)B.seg_count * 32, THREADS, L.sms), THREADS, 0, L.stream>>>(B.seg_vbase,
+                                                                                               B.seg_count, seg);
+        count_launch();
+        k_rank_keys_seg<<<grid_for(B.n, THREADS, L.sms), THREADS, 0, L.stream>>>(B.dmulti, seg, B.seg_vbase, B.n,
+                                                                               B.seg_deg_bits, B.local_bits, B.keys);
+        count_launch();
+        uint64_t* sorted = radix_sort_u64(B.keys, B.keys_alt, B.n, B.local_bits,
+                                          B.local_bits + B.seg_deg_bits + B.seg_bits, B.tmp, L);
+        k_rank_invert_seg<<<grid_for(B.n, THREADS, L.sms), THREADS, 0, L.stream>>>(
+            sorted, B.seg_vbase, B.n, B.seg_deg_bits, B.local_bits, B.rank, B.dmulti);
+        count_launch();
+        return;
+    }
     k_rank_keys<<<grid_for(B.n, THREADS, L.sms), THREADS, 0, L.stream>>>(B.dmulti, B.n, B.keys); count_launch();
     // the keys start in id order, so a stable sort on the degree bits yields (degree, id)
     uint64_t* sorted = radix_sort_u64(B.keys, B.keys_alt, B.n, 32, 32 + deg_bits, B.tmp, L);

@@ -80,6 +80,11 @@ struct BuildBuffers {
     int64_t* bstart;      // BUCKET_MAX + 1: first pair of each bucket
     int2* pairs;          // m: (source rank, target rank) grouped by bucket
     bool bucket_fill;     // rows counted and filled by source buckets (flat degree distributions)
+    // batches: vertices are ranked within their own graph (graph, degree, id), so each
+    // graph keeps a contiguous block of ranks and rows; seg_vbase null for one graph
+    const int32_t* seg_vbase;  // G + 1: first union id of every graph
+    int32_t seg_count;         // G
+    int seg_bits, seg_deg_bits, local_bits;  // key fields: graph, degree within a graph, local id
     void* tmp;            // max(scan_tmp_bytes(n + 1), radix_tmp_bytes(n))
     // outputs (kept by the graph)
     int32_t* rank;        // n: rank of each input id in (degree, id) order
@@ -109,7 +114,7 @@ void launch_orient(const BuildBuffers& B, const Launch& L, cudaEvent_t* ev = nul
 // Row fill by source buckets: at most BUCKET_MAX buckets of at most BUCKET_ROWS_MAX
 // rows (2^BUCKET_BITS buckets when that fits); nb = 0 selects the direct fill.
 constexpr int BUCKET_BITS = 11;
-constexpr int BUCKET_MAX = 4096;
+constexpr int BUCKET_MAX = 8192;
 constexpr int BUCKET_ROWS_MAX = 32768;
 void bucket_shape(int32_t n, int* shift, int* nb);
 cudaError_t build_init_attributes();
