@@ -315,7 +315,7 @@ tc_status tc_generate_edges(int kind, int32_t n, int64_t m, uint64_t seed, uint6
  * loop that accepts TC/LCC jobs on graphs of different sizes as they arrive.
  * `slots` worker threads, each with its own CUDA stream on the device current at
  * start, take the oldest waiting request as soon as they are free and the device
- * memory budget admits it (estimate 40 m + 160 n bytes + 16 MiB per request), so
+ * memory budget admits it (estimate 48 m + 160 n bytes + 16 MiB per request), so
  * requests arriving while others run are admitted as slots and memory free up and
  * their work overlaps on the device.  A request larger than the whole budget runs
  * alone.  Each request's graph is generated on the device (tc_generate_edges),

@@ -351,6 +351,10 @@ tc_status build_graph(tc_graph* g, const int32_t* src, const int32_t* dst, int64
         const double mean = n > 0 ? 2.0 * (double)m / (double)n : 0.0;
         B.bucket_fill = m > 0 && (double)h.max_deg <= 64.0 * mean;
     }
+    if (B.bucket_fill && (st = dalloc(g, &B.oriented, (size_t)m, &scratch)) != TC_OK) {
+        free_list(g, &scratch);
+        return st;
+    }
     launch_rank(B, deg_bits, g->L);
     if (bev) cudaEventRecord(bev[BP_RANK], g->stream);
     launch_orient(B, g->L, bev);

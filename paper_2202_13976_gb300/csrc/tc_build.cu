@@ -214,7 +214,8 @@ __global__ void k_orient_scatter(const int32_t* __restrict__ src, const int32_t*
 // Row counts and row fill by buckets of consecutive source ranks (2^shift rows each,
 // nb buckets), with no per-pair global atomic:
 //  k_bucket_count  counts the pairs of each bucket (shared-memory histogram, one
-//                  global atomic per bucket and block);
+//                  global atomic per bucket and block) and keeps every pair's
+//                  (source rank, target rank), read back in input order;
 //  k_orient_part   takes PART_TILE pairs per block, groups them by bucket in shared
 //                  memory, reserves each bucket's run with one atomic and writes
 //                  (source, target) into the bucket's segment of `pairs`;
@@ -233,7 +234,7 @@ constexpr int FILL_THREADS = 1024;
 __global__ void __launch_bounds__(THREADS) k_bucket_count(const int32_t* __restrict__ src,
                                                           const int32_t* __restrict__ dst, int64_t m, int32_t n,
                                                           const int32_t* __restrict__ rank, int shift, int nb,
-                                                          uint32_t* __restrict__ bcount) {
+                                                          uint32_t* __restrict__ bcount, int2* __restrict__ oriented) {
     extern __shared__ uint32_t hist[];  // nb
     for (int b = threadIdx.x; b < nb; b += THREADS) hist[b] = 0;
     __syncthreads();
@@ -248,8 +249,15 @@ __global__ void __launch_bounds__(THREADS) k_bucket_count(const int32_t* __restr
         }
 #pragma unroll
         for (int k = 0; k < PAIR_UNROLL; ++k) {
-            if (u[k] == v[k] || (uint32_t)u[k] >= (uint32_t)n || (uint32_t)v[k] >= (uint32_t)n) continue;
-            atomicAdd(&hist[min(rank[u[k]], rank[v[k]]) >> shift], 1u);
+            const int64_t i = i0 + k * stride;
+            if (i >= m) break;
+            int2 o = make_int2(-1, -1);  // loop or invalid id: no entry
+            if (u[k] != v[k] && (uint32_t)u[k] < (uint32_t)n && (uint32_t)v[k] < (uint32_t)n) {
+                const int32_t a = rank[u[k]], b = rank[v[k]];
+                o = make_int2(min(a, b), max(a, b));
+                atomicAdd(&hist[o.x >> shift], 1u);
+            }
+            oriented[i] = o;  // the partition pass reads these instead of gathering ranks again
         }
     }
     __syncthreads();
@@ -257,8 +265,7 @@ __global__ void __launch_bounds__(THREADS) k_bucket_count(const int32_t* __restr
         if (hist[b]) atomicAdd(&bcount[b], hist[b]);
 }
 
-__global__ void __launch_bounds__(PART_THREADS) k_orient_part(const int32_t* __restrict__ src, const int32_t* __restrict__ dst,
-                                                         int64_t m, int32_t n, const int32_t* __restrict__ rank,
+__global__ void __launch_bounds__(PART_THREADS) k_orient_part(const int2* __restrict__ oriented, int64_t m,
                                                          int shift, int nb, const int64_t* __restrict__ bstart,
                                                          uint32_t* __restrict__ bcur, int2* __restrict__ pairs,
                                                          DevStats* stats) {
@@ -275,13 +282,10 @@ __global__ void __launch_bounds__(PART_THREADS) k_orient_part(const int32_t* __r
             const int64_t i = t0 + (int64_t)k * PART_THREADS + threadIdx.x;
             sv[k] = -1;
             if (i < m) {
-                const int32_t u = src[i], v = dst[i];
-                if (u != v && (uint32_t)u < (uint32_t)n && (uint32_t)v < (uint32_t)n) {
-                    const int32_t a = rank[u], b = rank[v];
-                    sv[k] = min(a, b);
-                    tv[k] = max(a, b);
-                    loc[k] = atomicAdd(&hist[sv[k] >> shift], 1u);
-                }
+                const int2 o = oriented[i];
+                sv[k] = o.x;
+                tv[k] = o.y;
+                if (o.x >= 0) loc[k] = atomicAdd(&hist[o.x >> shift], 1u);
             }
         }
         __syncthreads();
@@ -825,14 +829,14 @@ void launch_orient(const BuildBuffers& B, const Launch& L, cudaEvent_t* ev) {
         cudaMemsetAsync(B.bcur, 0, sizeof(uint32_t) * (size_t)nb, L.stream);
         if (B.m > 0) {
             k_bucket_count<<<grid_for(B.m, THREADS * PAIR_UNROLL, L.sms, 8), THREADS, sizeof(uint32_t) * nb, L.stream>>>(
-                B.src, B.dst, B.m, B.n, B.rank, shift, nb, B.bcount);
+                B.src, B.dst, B.m, B.n, B.rank, shift, nb, B.bcount, B.oriented);
             count_launch();
         }
         scan_u32_to_i64(B.bcount, B.bstart, nb, B.tmp, L);
         if (ev) cudaEventRecord(ev[BP_COUNT], L.stream);
         if (B.m > 0) {
             k_orient_part<<<grid_for(B.m, PART_TILE, L.sms, 1), PART_THREADS, (sizeof(int64_t) + sizeof(uint32_t)) * nb,
-                            L.stream>>>(B.src, B.dst, B.m, B.n, B.rank, shift, nb, B.bstart, B.bcur, B.pairs, B.stats);
+                            L.stream>>>(B.oriented, B.m, shift, nb, B.bstart, B.bcur, B.pairs, B.stats);
             count_launch();
         }
         const int fill_blocks = nb < 4 * L.sms ? nb : 4 * L.sms;

@@ -79,6 +79,7 @@ struct BuildBuffers {
     uint32_t* bcur;       // BUCKET_MAX: bucket cursors of the partition pass
     int64_t* bstart;      // BUCKET_MAX + 1: first pair of each bucket
     int2* pairs;          // m: (source rank, target rank) grouped by bucket
+    int2* oriented;       // m: (source rank, target rank) in input order ((-1, -1): no entry)
     bool bucket_fill;     // rows counted and filled by source buckets (flat degree distributions)
     // batches: vertices are ranked within their own graph (graph, degree, id), so each
     // graph keeps a contiguous block of ranks and rows; seg_vbase null for one graph

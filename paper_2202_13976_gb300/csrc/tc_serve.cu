@@ -57,8 +57,8 @@ double now_s(std::chrono::steady_clock::time_point t0) {
 
 uint64_t serve_estimate_bytes(int32_t n, int64_t m) {
     // peak of one request: its pairs and outputs, the graph (CSR, hub in-edges and
-    // source rows 24 m, per-vertex arrays), the build scratch (pairs 8 m) and the core
-    return (uint64_t)(40 * m + 160 * (int64_t)n) + (16ull << 20);
+    // source rows 24 m, per-vertex arrays), the build scratch (pairs 16 m) and the core
+    return (uint64_t)(48 * m + 160 * (int64_t)n) + (16ull << 20);
 }
 
 }  // namespace tcg

@@ -93,7 +93,7 @@ def test_each_result_is_the_same_alone_and_in_the_mix(tc):
 
 def test_admission_respects_the_budget(tc):
     reqs = _requests(24)
-    est = [40 * r.workload.m + 160 * r.workload.n + (16 << 20) for r in reqs]  # the library's admission estimate
+    est = [48 * r.workload.m + 160 * r.workload.n + (16 << 20) for r in reqs]  # the library's admission estimate
     budget = 2 * max(est)
     srv = tc.Server(budget, 8)
     try:
