@@ -77,6 +77,8 @@ def _load():
             lib.or_tc_vertex.argtypes = [i64, _i64p, _i32p, _i32p, i64, _u64p]
             lib.or_lcc.restype = None
             lib.or_lcc.argtypes = [i64, _i64p, _u64p, _f64p]
+            lib.or_edge_support.restype = i64
+            lib.or_edge_support.argtypes = [i64, _i64p, _i32p, _i32p, _i32p, ctypes.POINTER(ctypes.c_uint32)]
             _lib = lib
     return _lib
 
@@ -199,6 +201,20 @@ def tc_vertex(n: int, offsets, adj, vertices) -> np.ndarray:
     _load().or_tc_vertex(n, _p(offsets, _i64p), _p(adj, _i32p), _p(vertices, _i32p),
                          vertices.size, _p(out, _u64p))
     return out
+
+
+def edge_support(n: int, src, dst):
+    """Per-edge triangle counts of the simple graph: (u, v, support) with one entry per
+    undirected edge, u < v, sorted by (u, v); support = |adj(u) ∩ adj(v)| (Alg. 2)."""
+    offsets, adj, _ = build_csr(n, src, dst)
+    m = int(offsets[-1]) // 2
+    eu = np.empty(max(1, m), dtype=np.int32)
+    ev = np.empty(max(1, m), dtype=np.int32)
+    sup = np.empty(max(1, m), dtype=np.uint32)
+    got = _load().or_edge_support(n, _p(offsets, _i64p), _p(adj, _i32p), _p(eu, _i32p), _p(ev, _i32p),
+                                  sup.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32)))
+    assert got == m
+    return eu[:m], ev[:m], sup[:m]
 
 
 def lcc(n: int, offsets, t) -> np.ndarray:

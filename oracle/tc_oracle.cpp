@@ -203,6 +203,28 @@ void or_tc_vertex(int64_t n, const int64_t* offsets, const int32_t* adj, const i
     }
 }
 
+// Per-edge support: for every undirected edge {u, v} (listed once, u < v, in CSR
+// order) the number of triangles that contain it, |adj(u) ∩ adj(v)| (Alg. 2) -- the
+// entries C(u, v) of the algebraic form C = A·A ∘ A of Sec. VI-B.  Writes eu, ev and
+// support (room for offsets[n] / 2 entries); returns the number of edges written.
+int64_t or_edge_support(int64_t n, const int64_t* offsets, const int32_t* adj, int32_t* eu, int32_t* ev,
+                        uint32_t* support) {
+    int64_t e = 0;
+    for (int64_t u = 0; u < n; ++u) {
+        const int32_t* Au = adj + offsets[u];
+        const int64_t du = offsets[u + 1] - offsets[u];
+        for (int64_t k = 0; k < du; ++k) {
+            const int64_t v = Au[k];
+            if (v <= u) continue;
+            eu[e] = (int32_t)u;
+            ev[e] = (int32_t)v;
+            support[e] = (uint32_t)or_ssi(Au, du, adj + offsets[v], offsets[v + 1] - offsets[v]);
+            ++e;
+        }
+    }
+    return e;
+}
+
 // Eq. 2: LCC(i) = 2 t(i) / (deg(i) (deg(i) - 1)); 0.0 when deg(i) < 2.  Both the
 // numerator and the denominator are exact integers below 2^53, so the single fp64
 // division is correctly rounded.

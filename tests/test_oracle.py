@@ -302,3 +302,44 @@ def test_csr_input_reads_every_entry_as_a_pair():
     adj2 = np.array([2, 1, 2, 0, 1], dtype=np.int32)
     r2 = oracle.triangles_csr(3, off2, adj2)
     assert r2["T"] == 1 and r2["m_simple"] == 3 and r2["dups_dropped"] == 2
+
+
+# --------------------------------------------------------------------------
+# Per-edge support: |adj(u) ∩ adj(v)| for every edge, the entries of A·A ∘ A
+
+@pytest.mark.parametrize("k", [3, 4, 7, 20])
+def test_edge_support_complete_graph(k):
+    n, (s, d) = F.complete(k)
+    u, v, sup = oracle.edge_support(n, s, d)
+    assert len(u) == comb(k, 2)
+    assert (u < v).all()
+    assert (sup == k - 2).all()
+
+
+@pytest.mark.parametrize("make", [lambda: F.star(30), lambda: F.grid(7, 9), lambda: F.complete_bipartite(6, 9),
+                                  lambda: F.cycle(12), lambda: F.random_tree(60, np.random.default_rng(3))])
+def test_edge_support_triangle_free(make):
+    n, (s, d) = make()
+    _, _, sup = oracle.edge_support(n, s, d)
+    assert (sup == 0).all()
+
+
+def test_edge_support_wheel_and_friendship():
+    n, (s, d) = F.wheel(9)  # hub 0, rim 1..8: each spoke lies in 2 triangles, each rim edge in 1
+    u, v, sup = oracle.edge_support(n, s, d)
+    assert (sup[u == 0] == 2).all() and (sup[u != 0] == 1).all()
+    n, (s, d) = F.friendship(5)  # every edge lies in exactly one triangle
+    _, _, sup = oracle.edge_support(n, s, d)
+    assert (sup == 1).all()
+
+
+@pytest.mark.parametrize("seed", range(12))
+def test_edge_support_matches_dense_products(seed):
+    n, s, d = _tiny(seed)
+    A = F.dense_adjacency(n, s, d)
+    u, v, sup = oracle.edge_support(n, s, d)
+    C = (A @ A) * A  # C[i, j] = number of triangles on edge {i, j}
+    assert int(A.sum()) // 2 == len(u)
+    np.testing.assert_array_equal(sup.astype(np.int64), C[u, v])
+    # each triangle has three edges
+    assert int(sup.sum()) == 3 * oracle.triangles(n, s, d)["T"]
