@@ -117,6 +117,18 @@ tc_status lcc_compute(tc_graph* g, uint64_t* t_out, double* lcc_out, int mem_kin
 tc_status tc_count_vertex_formula(tc_graph* g, uint64_t* t_out, int mem_kind, uint64_t* T_out);
 
 /*
+ * Per-edge support (an extension toward k-truss; Sec. VI-B's C = A·A ∘ A read edge
+ * by edge): for every distinct undirected edge {u, v} the number of triangles that
+ * contain it, |adj(u) ∩ adj(v)|.  Writes m_simple entries (tc_graph_info): u_out[k] <
+ * v_out[k] in the caller's ids, support_out[k] (uint32), each edge once, in an order
+ * of the library's choosing (row by row in its internal rank order); all three
+ * arrays in mem_kind memory.  Builds the symmetric rows for the call (as
+ * tc_count_vertex_formula) and releases them; synchronises the stream.  Errors:
+ * TC_EINVAL (NULL output, bad mem_kind), TC_ENOMEM, TC_ECUDA.
+ */
+tc_status tc_edge_support(tc_graph* g, int32_t* u_out, int32_t* v_out, uint32_t* support_out, int mem_kind);
+
+/*
  * Input accounting: number of distinct undirected edges, self-loops dropped and
  * repeated pairs dropped.  Any pointer may be NULL.  Synchronises the stream.
  */

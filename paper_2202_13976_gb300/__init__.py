@@ -32,7 +32,8 @@ EXPORTS = ["tc_graph_create_from_edges", "tc_graph_create_from_csr", "tc_count",
            "tc_batch_create", "tc_batch_count", "tc_batch_size", "tc_graph_get_tuning",
            "tc_graph_set_tuning", "tc_graph_autotune", "tc_batch_run", "tc_release_cached_graphs",
            "tc_generate_edges", "tc_server_start", "tc_server_submit", "tc_server_poll", "tc_server_wait",
-           "tc_server_get_stats", "tc_server_stop", "tc_graph_build_timing", "tc_count_vertex_formula"]
+           "tc_server_get_stats", "tc_server_stop", "tc_graph_build_timing", "tc_count_vertex_formula",
+           "tc_edge_support"]
 BUILD_PHASES = ["ingest_ms", "rank_ms", "count_ms", "fill_ms", "sort_ms", "degree_ms", "total_ms"]
 TC_GEN_RMAT, TC_GEN_ER_REPLACE = 0, 1
 GEN_KINDS = {"rmat": TC_GEN_RMAT, "er_replace": TC_GEN_ER_REPLACE}
@@ -126,6 +127,8 @@ def load(path: str | None = None):
     lib.lcc_compute.argtypes = [P, P, P, ctypes.c_int]
     lib.tc_count_vertex_formula.restype = st
     lib.tc_count_vertex_formula.argtypes = [P, P, ctypes.c_int, ctypes.POINTER(u64)]
+    lib.tc_edge_support.restype = st
+    lib.tc_edge_support.argtypes = [P, P, P, P, ctypes.c_int]
     lib.tc_graph_info.restype = st
     lib.tc_graph_info.argtypes = [P, ctypes.POINTER(i64), ctypes.POINTER(i64), ctypes.POINTER(i64)]
     lib.tc_graph_size.restype = st
@@ -284,6 +287,22 @@ def tc_count_vertex_formula(g: int, t_out=None):
     T = ctypes.c_uint64()
     _check(_lib.tc_count_vertex_formula(g, pt, kind, ctypes.byref(T)))
     return int(T.value), t_out
+
+
+def tc_edge_support(g: int, u_out=None, v_out=None, support_out=None):
+    """Per-edge triangle counts: (u, v, support) arrays of length m_simple (int32,
+    int32, int32 holding the uint32 counts; numpy unless CUDA tensors are passed),
+    u < v in the caller's ids, one entry per distinct edge."""
+    if u_out is None:
+        m = tc_graph_info(g)["m_simple"]
+        u_out = np.empty(m, dtype=np.int32)
+        v_out = np.empty(m, dtype=np.int32)
+        support_out = np.empty(m, dtype=np.int32)
+    for a in (u_out, v_out, support_out):
+        _check_dtype(a, "int32")
+    (pu, pv, ps), kind = _ptr_kind(u_out, v_out, support_out)
+    _check(_lib.tc_edge_support(g, pu, pv, ps, kind))
+    return u_out, v_out, support_out
 
 
 def tc_graph_info(g: int) -> dict:
@@ -508,6 +527,14 @@ class Graph:
         if not hasattr(t, "cuda"):
             t = t.view("uint64")
         return T, t
+
+    def edge_support(self, u_out=None, v_out=None, support_out=None):
+        """(u, v, support) per distinct edge; numpy results come sorted by (u, v)."""
+        u, v, sup = tc_edge_support(self.handle, u_out, v_out, support_out)
+        if not hasattr(u, "cuda"):
+            order = np.lexsort((v, u))
+            u, v, sup = u[order], v[order], sup[order].view(np.uint32)
+        return u, v, sup
 
     def info(self) -> dict:
         return tc_graph_info(self.handle)

@@ -621,6 +621,36 @@ tc_status lcc_compute(tc_graph* g, uint64_t* t_out, double* lcc_out, int mem_kin
     return TC_OK;
 }
 
+// Scratch of the symmetric rows (tc_vertex.cu) for g; pool memory tracked in tmp.
+static tc_status symmetric_buffers(tc_graph* g, const DevStats& h, VertexFormulaBuffers* V, std::vector<void*>* tmp) {
+    const size_t nn = (size_t)g->n;
+    *V = VertexFormulaBuffers{};
+    V->n = g->n;
+    V->m = (int64_t)h.m_simple;
+    V->m_cap = g->m_alloc;
+    V->rowstart = g->rowstart;
+    V->rowlen = g->rowlen;
+    V->rowinfo = g->rowinfo;
+    V->col = g->col;
+    V->deg = g->deg;
+    char* radix_tmp = nullptr;
+    char* scan_tmp = nullptr;
+    unsigned* cs = nullptr;
+    tc_status st;
+    if ((st = dalloc(g, &V->indeg, nn, tmp)) || (st = dalloc(g, &V->sym_start, nn + 1, tmp)) ||
+        (st = dalloc(g, &V->instart, nn + 1, tmp)) || (st = dalloc(g, &V->sym, (size_t)(2 * V->m), tmp)) ||
+        (st = dalloc(g, &V->keys, (size_t)V->m_cap, tmp)) || (st = dalloc(g, &V->keys_alt, (size_t)V->m_cap, tmp)) ||
+        (st = dalloc(g, &radix_tmp, radix_tmp_bytes(V->m_cap), tmp)) ||
+        (st = dalloc(g, &scan_tmp, scan_tmp_bytes((int64_t)nn + 1), tmp)) || (st = dalloc(g, &V->t, nn, tmp)) ||
+        (st = dalloc(g, &cs, 8, tmp)))
+        return st;
+    V->radix_tmp = radix_tmp;
+    V->tmp = scan_tmp;
+    V->counter = cs;
+    V->sum = reinterpret_cast<unsigned long long*>(cs + 2);
+    return TC_OK;
+}
+
 tc_status tc_count_vertex_formula(tc_graph* g, uint64_t* t_out, int mem_kind, uint64_t* T_out) {
     if (!g || !t_out || (mem_kind != TC_MEM_HOST && mem_kind != TC_MEM_DEVICE)) return TC_EINVAL;
     DevStats h;
@@ -628,33 +658,13 @@ tc_status tc_count_vertex_formula(tc_graph* g, uint64_t* t_out, int mem_kind, ui
     if (st != TC_OK) return st;
     if (h.err & ERR_BAD_ID) return TC_EINVAL;
     const size_t nn = (size_t)g->n;
-    VertexFormulaBuffers V{};
-    V.n = g->n;
-    V.m = (int64_t)h.m_simple;
-    V.m_cap = g->m_alloc;
-    V.rowstart = g->rowstart;
-    V.rowlen = g->rowlen;
-    V.rowinfo = g->rowinfo;
-    V.col = g->col;
-    V.deg = g->deg;
+    VertexFormulaBuffers V;
     std::vector<void*> tmp;
-    char* radix_tmp = nullptr;
-    char* scan_tmp = nullptr;
     unsigned long long* dt = nullptr;
-    unsigned* cs = nullptr;
-    if ((st = dalloc(g, &V.indeg, nn, &tmp)) || (st = dalloc(g, &V.sym_start, nn + 1, &tmp)) ||
-        (st = dalloc(g, &V.instart, nn + 1, &tmp)) || (st = dalloc(g, &V.sym, (size_t)(2 * V.m), &tmp)) ||
-        (st = dalloc(g, &V.keys, (size_t)V.m_cap, &tmp)) || (st = dalloc(g, &V.keys_alt, (size_t)V.m_cap, &tmp)) ||
-        (st = dalloc(g, &radix_tmp, radix_tmp_bytes(V.m_cap), &tmp)) ||
-        (st = dalloc(g, &scan_tmp, scan_tmp_bytes((int64_t)nn + 1), &tmp)) || (st = dalloc(g, &V.t, nn, &tmp)) ||
-        (st = dalloc(g, &cs, 8, &tmp))) {
+    if ((st = symmetric_buffers(g, h, &V, &tmp)) != TC_OK) {
         free_list(g, &tmp);
         return st;
     }
-    V.radix_tmp = radix_tmp;
-    V.tmp = scan_tmp;
-    V.counter = cs;
-    V.sum = reinterpret_cast<unsigned long long*>(cs + 2);
     launch_vertex_formula(V, g->L);
     unsigned long long* out = mem_kind == TC_MEM_DEVICE ? reinterpret_cast<unsigned long long*>(t_out) : nullptr;
     if (!out && (st = dalloc(g, &dt, nn, &tmp))) {
@@ -674,6 +684,44 @@ tc_status tc_count_vertex_formula(tc_graph* g, uint64_t* t_out, int mem_kind, ui
         return TC_EINTERNAL;
     }
     if (T_out) *T_out = sum / 3;
+    return TC_OK;
+}
+
+tc_status tc_edge_support(tc_graph* g, int32_t* u_out, int32_t* v_out, uint32_t* support_out, int mem_kind) {
+    if (!g || !u_out || !v_out || !support_out || (mem_kind != TC_MEM_HOST && mem_kind != TC_MEM_DEVICE))
+        return TC_EINVAL;
+    DevStats h;
+    tc_status st = read_stats(g, &h);
+    if (st != TC_OK) return st;
+    if (h.err & ERR_BAD_ID) return TC_EINVAL;
+    const size_t nn = (size_t)g->n, me = (size_t)h.m_simple;
+    VertexFormulaBuffers V;
+    std::vector<void*> tmp;
+    int32_t* id_of = nullptr;
+    int64_t* estart = nullptr;
+    int32_t *du = nullptr, *dv = nullptr;
+    uint32_t* ds = nullptr;
+    if ((st = symmetric_buffers(g, h, &V, &tmp)) || (st = dalloc(g, &id_of, nn, &tmp)) ||
+        (st = dalloc(g, &estart, nn + 1, &tmp))) {
+        free_list(g, &tmp);
+        return st;
+    }
+    const bool dev = mem_kind == TC_MEM_DEVICE;
+    if (!dev && ((st = dalloc(g, &du, me, &tmp)) || (st = dalloc(g, &dv, me, &tmp)) || (st = dalloc(g, &ds, me, &tmp)))) {
+        free_list(g, &tmp);
+        return st;
+    }
+    launch_edge_support(V, g->rank, id_of, estart, dev ? u_out : du, dev ? v_out : dv, dev ? support_out : ds, g->L);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess && !dev && me > 0) {
+        e = cudaMemcpyAsync(u_out, du, sizeof(int32_t) * me, cudaMemcpyDeviceToHost, g->stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(v_out, dv, sizeof(int32_t) * me, cudaMemcpyDeviceToHost, g->stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(support_out, ds, sizeof(uint32_t) * me, cudaMemcpyDeviceToHost, g->stream);
+    }
+    free_list(g, &tmp);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(g->stream);
+    if (e != cudaSuccess) return cuda_fail("tc_edge_support", e);
     return TC_OK;
 }
 

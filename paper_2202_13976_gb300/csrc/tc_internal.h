@@ -208,7 +208,11 @@ struct VertexFormulaBuffers {
     unsigned long long* sum;
 };
 int vf_key_bits(int32_t n);
+void launch_symmetric_rows(const VertexFormulaBuffers& V, const Launch& L);
 void launch_vertex_formula(const VertexFormulaBuffers& V, const Launch& L);
+// Per-edge support over the symmetric rows; id_of (n) and estart (n + 1) are scratch.
+void launch_edge_support(const VertexFormulaBuffers& V, const int32_t* rank, int32_t* id_of, int64_t* estart,
+                         int32_t* eu, int32_t* ev, uint32_t* support, const Launch& L);
 
 // ---- batch (tc_batch.cu) -------------------------------------------------------
 void launch_batch_relabel(int32_t G, const int64_t* edge_off, const int32_t* vbase, const int32_t* src,

@@ -291,3 +291,46 @@ def test_vertex_formula_rmat_and_er(tc, rmat14, er4096):
         assert T == ref["T"] and T2 == ref["T"]
         np.testing.assert_array_equal(t, ref["t"])
         np.testing.assert_array_equal(td.cpu().numpy().view(np.uint64), ref["t"])
+
+
+def _assert_support_matches(tc, n, s, d):
+    ru, rv, rs = oracle.edge_support(n, s, d)
+    g = tc.Graph.from_edges(n, s, d)
+    try:
+        u, v, sup = g.edge_support()
+    finally:
+        g.close()
+    np.testing.assert_array_equal(u, ru)
+    np.testing.assert_array_equal(v, rv)
+    np.testing.assert_array_equal(sup, rs)
+
+
+@pytest.mark.parametrize("make", [
+    lambda: F.complete(34), lambda: F.wheel(40), lambda: F.friendship(7), lambda: F.star(100),
+    lambda: F.complete_tripartite(3, 5, 40), lambda: F.grid(20, 30), lambda: F.cycle(3)])
+def test_edge_support_closed_forms(tc, make):
+    n, (s, d) = make()
+    _assert_support_matches(tc, n, s, d)
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_edge_support_tiny_random(tc, seed):
+    from tests.test_oracle import _tiny
+    n, s, d = _tiny(seed)
+    _assert_support_matches(tc, n, s, d)
+
+
+def test_edge_support_rmat_and_er_device_io(tc, rmat14, er4096):
+    import torch
+    for n, s, d, ref in (rmat14, er4096):
+        _assert_support_matches(tc, n, s, d)
+        g = tc.Graph.from_edges(n, s, d)
+        try:
+            m = g.info()["m_simple"]
+            bufs = [torch.empty(m, dtype=torch.int32, device="cuda") for _ in range(3)]
+            u, v, sup = g.edge_support(*bufs)
+            torch.cuda.synchronize()
+        finally:
+            g.close()
+        assert int(sup.to(torch.int64).sum()) == 3 * ref["T"]
+        assert bool((u < v).all())
