@@ -51,7 +51,8 @@ constexpr int BITMAP_WORDS = 4096;     // its bitmap window: 131072 ranks
 constexpr int HUB_THREADS = 256;
 constexpr int HUB_WARPS = HUB_THREADS / 32;
 constexpr int HUB_BM_WORDS = HUB_BM_BITS / 32;
-constexpr int HUB_CNT_MAX = 4096;      // hub lists longer than this count matches globally
+constexpr int HUB_CNT_MAX = 1024;      // hub lists longer than this count matches globally
+constexpr int HUB_BLOCKS = 6;          // resident blocks of the hub kernel per SM (registers and shared memory)
 constexpr int HUB_WARP_MAX = 256;      // longest N+(v) a single warp stages
 constexpr int HUB_HASH_LOAD = 2;       // its hash table has at least this many slots per key
 constexpr int HUB_HASH_MAX = HUB_HASH_LOAD * HUB_WARP_MAX;
@@ -1383,7 +1384,7 @@ void launch_intersect(const CountBuffers& C, const Strategy& S, cudaEvent_t* ev,
     if (C.hub_cap > 0) {
         if (S.hub_core > 0) launch_core_count(C, L);
         cudaMemsetAsync(&C.stats->hub_next, 0, 2 * sizeof(unsigned), L.stream);
-        k_tc_hub<<<L.sms * 5, HUB_THREADS, sizeof(HubShared), L.stream>>>(
+        k_tc_hub<<<L.sms * HUB_BLOCKS, HUB_THREADS, sizeof(HubShared), L.stream>>>(
             C.n, C.hub_cap, C.rowstart, C.rowlen, C.col, C.hub_start, C.big_list, C.med_list, C.in_rec, C.t_rank,
             C.stats, S.strat[TC_BUCKET_HUB] == TC_STRAT_PROBE ? 1 : 0);
         count_launch();

@@ -334,3 +334,12 @@ def test_edge_support_rmat_and_er_device_io(tc, rmat14, er4096):
             g.close()
         assert int(sup.to(torch.int64).sum()) == 3 * ref["T"]
         assert bool((u < v).all())
+
+
+@pytest.mark.parametrize("core", [0, 8192])
+def test_hub_longer_than_shared_counters(tc, core):
+    """K_1100 with every vertex a hub: big hubs with |N+(v)| up to 1098 exceed the
+    1024 shared-memory counters and count their matches globally (core off), or the
+    whole graph is one dense core (core on)."""
+    n, (s, d) = F.complete(1100)
+    assert_matches_oracle(tc, n, s, d, hubs=(1, 131072), tuning={"hub_core": core})
