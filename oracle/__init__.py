@@ -15,6 +15,7 @@ numpy arrays.  Every function names the passage of the paper it follows:
 - ``tc_oriented``: edge-centric counting of Sec. II-C with Alg. 2.
 - ``tc_vertex``: the paper's per-vertex formula (Alg. 3) with the Eq. 3 hybrid.
 - ``lcc``: Eq. 2.
+- ``build_digraph`` / ``directed_lcc``: directed graphs (Sec. II-A) and Eq. 1.
 
 Parity status: every function is pinned by the ``-m "not gpu"`` tests
 (brute force, closed forms, scipy's sparse product for the algebraic form
@@ -79,6 +80,10 @@ def _load():
             lib.or_lcc.argtypes = [i64, _i64p, _u64p, _f64p]
             lib.or_edge_support.restype = i64
             lib.or_edge_support.argtypes = [i64, _i64p, _i32p, _i32p, _i32p, ctypes.POINTER(ctypes.c_uint32)]
+            lib.or_build_digraph.restype = ctypes.c_int
+            lib.or_build_digraph.argtypes = [i64, i64, _i32p, _i32p, _i64p, _i32p, _i64p]
+            lib.or_directed_lcc.restype = None
+            lib.or_directed_lcc.argtypes = [i64, _i64p, _i32p, _i32p, i64, _u64p, _f64p]
             _lib = lib
     return _lib
 
@@ -215,6 +220,46 @@ def edge_support(n: int, src, dst):
                                   sup.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32)))
     assert got == m
     return eu[:m], ev[:m], sup[:m]
+
+
+def build_digraph(n: int, src, dst):
+    """Directed simple graph (Sec. II-A: e_ij from v_i to v_j, no loops, no repeated
+    pair): (offsets int64[n+1], adj int32[m'], stats) with sorted out-lists.
+
+    stats = {"m_directed", "loops_dropped", "dups_dropped"}.  Raises ValueError on an
+    id outside [0, n)."""
+    src = _c(src, np.int32)
+    dst = _c(dst, np.int32)
+    if src.shape != dst.shape:
+        raise ValueError("src and dst differ in length")
+    m = src.size
+    offsets = np.zeros(n + 1, dtype=np.int64)
+    adj = np.empty(max(1, m), dtype=np.int32)
+    stats = np.zeros(3, dtype=np.int64)
+    rc = _load().or_build_digraph(n, m, _p(src, _i32p), _p(dst, _i32p), _p(offsets, _i64p),
+                                  _p(adj, _i32p), _p(stats, _i64p))
+    if rc != 0:
+        raise ValueError("vertex id outside [0, n)")
+    adj = adj[: offsets[-1]].copy()
+    return offsets, adj, {"m_directed": int(stats[0]), "loops_dropped": int(stats[1]),
+                          "dups_dropped": int(stats[2])}
+
+
+def directed_lcc(n: int, src, dst, vertices=None) -> dict:
+    """Eq. 1 on the directed simple graph of (src[k] -> dst[k]).
+
+    Returns {"c", "lcc", "out_degree", "m_directed", "loops_dropped", "dups_dropped"};
+    c[q] = |{e_jk : v_j, v_k in adj(v_i)}| and lcc[q] = c / (deg+ (deg+ - 1)) for
+    i = vertices[q] (all vertices when ``vertices`` is None)."""
+    offsets, adj, stats = build_digraph(n, src, dst)
+    vertices = np.arange(n, dtype=np.int32) if vertices is None else _c(vertices, np.int32)
+    c = np.zeros(vertices.size, dtype=np.uint64)
+    l = np.zeros(vertices.size, dtype=np.float64)
+    _load().or_directed_lcc(n, _p(offsets, _i64p), _p(adj, _i32p), _p(vertices, _i32p), vertices.size,
+                            _p(c, _u64p), _p(l, _f64p))
+    out = {"c": c, "lcc": l, "out_degree": np.diff(offsets)[vertices]}
+    out.update(stats)
+    return out
 
 
 def lcc(n: int, offsets, t) -> np.ndarray:

@@ -225,6 +225,61 @@ int64_t or_edge_support(int64_t n, const int64_t* offsets, const int32_t* adj, i
     return e;
 }
 
+// Directed graphs (Sec. II-A, II-C): e_ij is the edge from v_i to v_j and adj(v_i) the
+// out-neighbours {v_j : e_ij in E}.  Self-loops are dropped and a repeated (src, dst)
+// pair is one edge; (u, v) and (v, u) are two different edges.  Outputs offsets[n+1]
+// and adj[offsets[n]] (room for m entries), every out-list sorted ascending.  stats[0..2]
+// receive the distinct directed edges, dropped self-loops and dropped repeats.
+// Returns 0, or -1 if an id lies outside [0, n).
+int or_build_digraph(int64_t n, int64_t m, const int32_t* src, const int32_t* dst, int64_t* offsets,
+                     int32_t* adj, int64_t* stats) {
+    std::vector<uint64_t> keys;
+    keys.reserve((size_t)m);
+    int64_t loops = 0;
+    for (int64_t k = 0; k < m; ++k) {
+        int64_t u = src[k], v = dst[k];
+        if (u < 0 || u >= n || v < 0 || v >= n) return -1;
+        if (u == v) {
+            ++loops;
+            continue;
+        }
+        keys.push_back(((uint64_t)u << 32) | (uint64_t)v);
+    }
+    std::sort(keys.begin(), keys.end());
+    keys.erase(std::unique(keys.begin(), keys.end()), keys.end());
+    const int64_t md = (int64_t)keys.size();
+    stats[0] = md;
+    stats[1] = loops;
+    stats[2] = m - loops - md;
+    std::fill(offsets, offsets + n + 1, (int64_t)0);
+    for (uint64_t key : keys) offsets[(key >> 32) + 1] += 1;
+    for (int64_t i = 0; i < n; ++i) offsets[i + 1] += offsets[i];
+    for (int64_t k = 0; k < md; ++k) adj[k] = (int32_t)(keys[(size_t)k] & 0xffffffffu);  // sorted by (src, dst)
+    return 0;
+}
+
+// Eq. 1 (directed LCC) for the listed vertices of a directed CSR:
+//   c(i) = |{e_jk in E : v_j, v_k in adj(v_i)}|, counted as the sum over v_j in adj(v_i)
+//          of |adj(v_i) ∩ adj(v_j)| (Alg. 2), every edge e_jk met once at its tail v_j;
+//   C(i) = c(i) / (deg+(i) (deg+(i) - 1)), 0.0 when deg+(i) < 2.
+// Writes c_out[q] and lcc_out[q] for vertex vertices[q].
+void or_directed_lcc(int64_t n, const int64_t* offsets, const int32_t* adj, const int32_t* vertices, int64_t nv,
+                     uint64_t* c_out, double* lcc_out) {
+    (void)n;
+    for (int64_t q = 0; q < nv; ++q) {
+        const int64_t i = vertices[q];
+        const int32_t* Ai = adj + offsets[i];
+        const int64_t d = offsets[i + 1] - offsets[i];
+        uint64_t c = 0;
+        for (int64_t k = 0; k < d; ++k) {
+            const int64_t j = Ai[k];
+            c += (uint64_t)or_ssi(Ai, d, adj + offsets[j], offsets[j + 1] - offsets[j]);
+        }
+        c_out[q] = c;
+        lcc_out[q] = d < 2 ? 0.0 : (double)c / (double)(d * (d - 1));
+    }
+}
+
 // Eq. 2: LCC(i) = 2 t(i) / (deg(i) (deg(i) - 1)); 0.0 when deg(i) < 2.  Both the
 // numerator and the denominator are exact integers below 2^53, so the single fp64
 // division is correctly rounded.

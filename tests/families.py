@@ -117,3 +117,55 @@ def exact_lcc(t, deg):
         if di >= 2:
             out[i] = float(Fraction(2 * int(ti), int(di) * (int(di) - 1)))
     return out
+
+
+# ---------------------------------------------------------------------------
+# Directed graphs (Eq. 1): e_ij from v_i to v_j, adj(v_i) = out-neighbours.
+
+def dense_digraph(n, src, dst):
+    """0/1 matrix with A[u, v] = 1 for every pair u -> v, u != v (repeats collapse)."""
+    A = np.zeros((n, n), dtype=np.int64)
+    for u, v in zip(src.tolist(), dst.tolist()):
+        if u != v:
+            A[u, v] = 1
+    return A
+
+
+def brute_directed(n, src, dst):
+    """c(i) = number of ordered pairs (j, k), j != k, with i -> j, i -> k and j -> k,
+    by enumerating vertex triples."""
+    A = dense_digraph(n, src, dst)
+    c = np.zeros(n, dtype=np.uint64)
+    for i in range(n):
+        out = [j for j in range(n) if A[i, j]]
+        for j in out:
+            for k in out:
+                if j != k and A[j, k]:
+                    c[i] += 1
+    return c
+
+
+def exact_directed_lcc(c, dout):
+    """Eq. 1 rounded once from the exact rational (0.0 for out-degree < 2)."""
+    out = np.zeros(len(c), dtype=np.float64)
+    for i, (ci, di) in enumerate(zip(c.tolist(), dout.tolist())):
+        if di >= 2:
+            out[i] = float(Fraction(int(ci), int(di) * (int(di) - 1)))
+    return out
+
+
+def transitive_tournament(n):
+    """i -> j for every i < j: out(i) = {i+1, ..., n-1} and every pair j < k of it has j -> k."""
+    return n, as_arrays((i, j) for i in range(n) for j in range(i + 1, n))
+
+
+def complete_digraph(n):
+    return n, as_arrays((i, j) for i in range(n) for j in range(n) if i != j)
+
+
+def directed_wheel(rim, outward=True):
+    """Hub 0 and a rim cycle 1 -> 2 -> ... -> rim -> 1; spokes hub -> rim (outward)
+    or rim -> hub."""
+    spokes = [(0, r) if outward else (r, 0) for r in range(1, rim + 1)]
+    cyc = [(r, r % rim + 1) for r in range(1, rim + 1)]
+    return rim + 1, as_arrays(spokes + cyc)

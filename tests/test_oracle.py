@@ -343,3 +343,128 @@ def test_edge_support_matches_dense_products(seed):
     np.testing.assert_array_equal(sup.astype(np.int64), C[u, v])
     # each triangle has three edges
     assert int(sup.sum()) == 3 * oracle.triangles(n, s, d)["T"]
+
+
+# --------------------------------------------------------------------------
+# Directed LCC (Eq. 1): c(i) = |{e_jk : v_j, v_k in adj(v_i)}| over out-neighbours
+
+def _tiny_directed(seed):
+    """Random digraph with reciprocal pairs, repeats and self-loops."""
+    rng = np.random.default_rng(1000 + seed)
+    n = int(rng.integers(2, 40))
+    k = int(rng.integers(0, 3 * n * n // 4 + 1))
+    s = rng.integers(0, n, size=k).astype(np.int32)
+    d = rng.integers(0, n, size=k).astype(np.int32)
+    if k:
+        pick = rng.integers(0, k, size=k // 4 + 1)
+        s = np.concatenate([s, d[pick], s[pick[: len(pick) // 2]]]).astype(np.int32)  # reversed and repeated
+        d = np.concatenate([d, s[:k][pick], d[pick[: len(pick) // 2]]]).astype(np.int32)
+    return n, s, d
+
+
+@pytest.mark.parametrize("seed", range(40))
+def test_directed_brute_force_tiny(seed):
+    n, s, d = _tiny_directed(seed)
+    r = oracle.directed_lcc(n, s, d)
+    A = F.dense_digraph(n, s, d)
+    np.testing.assert_array_equal(r["c"], F.brute_directed(n, s, d))
+    # algebraic form: c = rowsum((A A) o A), the directed counterpart of Sec. VI-B
+    np.testing.assert_array_equal(r["c"].astype(np.int64), ((A @ A) * A).sum(axis=1))
+    np.testing.assert_array_equal(r["out_degree"], A.sum(axis=1))
+    np.testing.assert_array_equal(r["lcc"], F.exact_directed_lcc(r["c"], A.sum(axis=1)))
+    assert r["m_directed"] == int(A.sum())
+    assert r["loops_dropped"] == int((s == d).sum())
+    assert r["m_directed"] + r["loops_dropped"] + r["dups_dropped"] == len(s)
+
+
+def test_directed_algebraic_form_scipy():
+    n = 4096
+    s, d = graphgen.er_replace(n, 40000, seed=7)
+    keep = s != d
+    A = sp.coo_matrix((np.ones(int(keep.sum()), dtype=np.int64), (s[keep], d[keep])), shape=(n, n)).tocsr()
+    A.data[:] = 1
+    A.sum_duplicates()
+    A = (A > 0).astype(np.int64)
+    want = np.asarray((A @ A).multiply(A).sum(axis=1)).ravel()
+    r = oracle.directed_lcc(n, s, d)
+    np.testing.assert_array_equal(r["c"].astype(np.int64), want)
+    np.testing.assert_array_equal(r["out_degree"], np.asarray(A.sum(axis=1)).ravel())
+
+
+@pytest.mark.parametrize("seed", range(8))
+def test_directed_on_symmetric_input_is_eq2(seed):
+    # Both directions of every edge: adj(v_i) is the undirected neighbourhood, every
+    # triangle edge is counted in both directions, so Eq. 1 = Eq. 2 bit for bit.
+    n, s, d = _tiny(seed)
+    r = oracle.directed_lcc(n, np.concatenate([s, d]), np.concatenate([d, s]))
+    u = run(n, s, d)
+    np.testing.assert_array_equal(r["c"], 2 * u["t"])
+    np.testing.assert_array_equal(r["lcc"], u["lcc"])
+    np.testing.assert_array_equal(r["out_degree"], u["degree"])
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 7, 30])
+def test_directed_transitive_tournament(n):
+    n, (s, d) = F.transitive_tournament(n)
+    r = oracle.directed_lcc(n, s, d)
+    dout = np.arange(n - 1, -1, -1)
+    np.testing.assert_array_equal(r["c"], [comb(int(x), 2) for x in dout])
+    np.testing.assert_array_equal(r["lcc"], np.where(dout >= 2, 0.5, 0.0))
+
+
+@pytest.mark.parametrize("n", [2, 3, 5, 12])
+def test_directed_complete(n):
+    n, (s, d) = F.complete_digraph(n)
+    r = oracle.directed_lcc(n, s, d)
+    assert (r["c"] == (n - 1) * (n - 2)).all()
+    np.testing.assert_array_equal(r["lcc"], np.full(n, 1.0 if n >= 3 else 0.0))
+
+
+@pytest.mark.parametrize("rim", [3, 4, 9, 40])
+def test_directed_wheels(rim):
+    n, (s, d) = F.directed_wheel(rim, outward=True)
+    r = oracle.directed_lcc(n, s, d)
+    assert r["c"][0] == rim and r["lcc"][0] == 1.0 / (rim - 1)  # the rim cycle's rim edges
+    assert (r["c"][1:] == 0).all() and (r["lcc"][1:] == 0.0).all()  # out-degree 1
+    n, (s, d) = F.directed_wheel(rim, outward=False)
+    r = oracle.directed_lcc(n, s, d)
+    assert r["c"][0] == 0 and r["lcc"][0] == 0.0  # the hub has no out-edge
+    assert (r["c"][1:] == 1).all() and (r["lcc"][1:] == 0.5).all()  # r -> {0, r+1}, r+1 -> 0
+
+
+def test_directed_three_vertex_cases():
+    cyc = oracle.directed_lcc(3, np.array([0, 1, 2], np.int32), np.array([1, 2, 0], np.int32))
+    assert (cyc["c"] == 0).all() and (cyc["lcc"] == 0.0).all()
+    ffl = oracle.directed_lcc(3, np.array([0, 0, 1], np.int32), np.array([1, 2, 2], np.int32))
+    np.testing.assert_array_equal(ffl["c"], [1, 0, 0])
+    np.testing.assert_array_equal(ffl["lcc"], [0.5, 0.0, 0.0])
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_directed_invariants(seed):
+    n, s, d = _tiny_directed(seed + 50)
+    r = oracle.directed_lcc(n, s, d)
+    rng = np.random.default_rng(seed)
+    # relabelling permutes the outputs
+    perm = rng.permutation(n).astype(np.int32)
+    rp = oracle.directed_lcc(n, perm[s], perm[d])
+    np.testing.assert_array_equal(rp["c"][perm], r["c"])
+    np.testing.assert_array_equal(rp["lcc"][perm], r["lcc"])
+    # edge order and repeats do not matter
+    order = rng.permutation(len(s))
+    ro = oracle.directed_lcc(n, np.concatenate([s[order], s]), np.concatenate([d[order], d]))
+    np.testing.assert_array_equal(ro["c"], r["c"])
+    # the total counts transitive triples (i -> j, i -> k, j -> k), which reversing
+    # every edge maps onto each other: sum(c) is invariant under reversal
+    rr = oracle.directed_lcc(n, d, s)
+    assert int(rr["c"].sum()) == int(r["c"].sum())
+
+
+def test_directed_sampled_vertices_and_bad_ids():
+    n, s, d = _tiny_directed(3)
+    full = oracle.directed_lcc(n, s, d)
+    pick = np.array([n - 1, 0, n // 2], dtype=np.int32)
+    part = oracle.directed_lcc(n, s, d, vertices=pick)
+    np.testing.assert_array_equal(part["c"], full["c"][pick])
+    with pytest.raises(ValueError):
+        oracle.directed_lcc(3, np.array([0], np.int32), np.array([3], np.int32))
