@@ -53,7 +53,7 @@ def parse_args():
     p.add_argument("--workload", default="rmat20", choices=sorted(WORKLOAD_TEXT))
     p.add_argument("--e2e-steps", type=int, default=10)
     p.add_argument("--no-cpu-baseline", action="store_true")
-    p.add_argument("--mode", choices=["single", "batch", "serve", "ablation"], default="single",
+    p.add_argument("--mode", choices=["single", "batch", "serve", "ablation", "directed"], default="single",
                    help="single: one graph per step; batch: the 20,000-graph batch per step; "
                         "serve: the Poisson request stream through the serving loop")
     p.add_argument("--serve-seconds", type=float, default=60.0)
@@ -625,6 +625,127 @@ def run_ablation(args, rank, world, local):
     print(json.dumps(line), flush=True)
 
 
+def directed_cpu_baseline(n, src, dst, sample_vertices=100000, seed=5):
+    """The oracle's directed LCC on a bounded sample: the digraph build of the whole
+    workload, then Eq. 1 at random vertices; the build is charged in proportion to the
+    sampled vertices' share of the edges."""
+    import numpy as np
+    import oracle
+    oracle.build()
+    t0 = time.perf_counter()
+    off, _, st = oracle.build_digraph(n, src, dst)
+    t_build = time.perf_counter() - t0
+    rng = np.random.default_rng(seed)
+    k = min(n, sample_vertices)
+    pick = rng.choice(n, k, replace=False).astype(np.int32)
+    t0 = time.perf_counter()
+    oracle.directed_lcc(n, src, dst, vertices=pick)
+    t_all = time.perf_counter() - t0  # includes the oracle's own digraph build again
+    t_count = max(t_all - t_build, 1e-9)
+    edges = int(np.diff(off)[pick].sum())
+    share = edges / max(1, st["m_directed"])
+    value = edges / (t_count + share * t_build)
+    return {"value": value, "unit": "edges/s", "cores": 1, "kind": "oracle",
+            "sample": f"digraph build of the whole workload ({t_build:.2f} s) and Eq. 1 at {k} random vertices "
+                      f"({edges} out-edges, {t_count:.2f} s); the build charged by the sample's edge share"}
+
+
+def run_directed(args, rank, world, local):
+    """Directed LCC (Eq. 1) of the workload's pairs read as directed edges src -> dst,
+    through tc_directed_lcc with device buffers; value = distinct directed edges per
+    second of the whole call."""
+    import numpy as np
+    import torch
+
+    import graphgen
+    import paper_2202_13976_gb300 as tc
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    tc.load()
+    w = graphgen.workload(args.workload)
+    src_h, dst_h = w.edges()
+    n, m_in = w.n, len(src_h)
+    stream = torch.cuda.current_stream()
+    src = torch.from_numpy(src_h).to(dev)
+    dst = torch.from_numpy(dst_h).to(dev)
+    c_out = torch.empty(n, dtype=torch.int64, device=dev)
+    l_out = torch.empty(n, dtype=torch.float64, device=dev)
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+
+    def step():
+        return tc.tc_directed_lcc(n, src, dst, c_out, l_out, stream, timed=True)[2]
+
+    for _ in range(max(args.warmup, 3)):
+        st0 = step()
+    torch.cuda.synchronize()
+    clocks = Clocks(local)
+    launches0 = tc.tc_launch_count()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    stats = []
+    for k in range(args.steps):
+        flush.zero_()
+        evs[k][0].record(stream)
+        stats.append(step())
+        evs[k][1].record(stream)
+    torch.cuda.synchronize()
+    launches = tc.tc_launch_count() - launches0
+    clk = clocks.stop()
+    assert all(x["total"] == st0["total"] for x in stats)
+    ms_per_step, value = aggregate_ranks(sum(a.elapsed_time(b) for a, b in evs), args.steps, st0["m_directed"],
+                                         world, dev)
+    phase = {k: statistics.mean(x[k] for x in stats) for k in ("build_ms", "count_ms", "finalize_ms")}
+    # k_dg_count reads 5 bytes per list entry (4 id + 1 direction byte) and 24 bytes per
+    # oriented edge (its key and three row offsets)
+    alg_bytes = 5 * st0["list_entries"] + 24 * st0["m_undirected"]
+    peak, peak_kind = measured_peak()
+    achieved = alg_bytes / (phase["count_ms"] / 1000.0) / 1e9
+    traffic = None
+    try:
+        rec = json.load(open(os.path.join(ROOT, "profiles", "traffic.json"))).get(args.workload + "_directed",
+                                                                                    {}).get("k_dg_count")
+        if rec and rec.get("source_sha256") == tc.source_digest():
+            traffic = rec["dram_bytes_per_launch"]
+    except Exception:
+        traffic = None
+    roofline = {"bound": "hbm", "kernel": "k_dg_count", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": traffic, "peak_source": f"{peak_kind} hbm_gbs",
+                "algorithmic_bytes": alg_bytes, "kernel_ms": phase["count_ms"],
+                "note": "of measured" if peak_kind == "measured" else "of fallback"}
+    # end to end with pinned host buffers, copies inside the call
+    src_p = torch.from_numpy(src_h).pin_memory()
+    dst_p = torch.from_numpy(dst_h).pin_memory()
+    c_p = torch.empty(n, dtype=torch.int64).pin_memory()
+    l_p = torch.empty(n, dtype=torch.float64).pin_memory()
+    s_np, d_np, c_np, l_np = src_p.numpy(), dst_p.numpy(), c_p.numpy().view(np.uint64), l_p.numpy()
+    tc.tc_directed_lcc(n, s_np, d_np, c_np, l_np, stream)
+    e2e_times = []
+    for _ in range(args.e2e_steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        tot = tc.tc_directed_lcc(n, s_np, d_np, c_np, l_np, stream)[2]["total"]
+        e2e_times.append(time.perf_counter() - t0)
+        assert tot == st0["total"]
+    e2e_s = sum(e2e_times) / len(e2e_times)
+    e2e = {"value": world * st0["m_directed"] / e2e_s, "unit": "edges/s", "h2d_bytes_per_step": 8 * m_in,
+           "d2h_bytes_per_step": 16 * n, "ms_per_step": 1000.0 * e2e_s}
+    if rank != 0:
+        return
+    cpu = None if args.no_cpu_baseline else directed_cpu_baseline(n, src_h, dst_h)
+    line = {"metric": "directed edges/sec (Eq. 1 LCC)", "value": value, "unit": "edges/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+            "config": {"workload": args.workload + "_directed",
+                       "graph": WORKLOAD_TEXT[args.workload] + ", pairs read as directed edges src -> dst",
+                       "n": n, "m_generated": m_in, "m_directed": st0["m_directed"],
+                       "m_undirected": st0["m_undirected"], "sum_c": st0["total"],
+                       "list_entries": st0["list_entries"], "l2": "flushed between steps (512 MB write)",
+                       "phase_ms": phase},
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+            "gpu_launches_per_step": launches / args.steps, "clocks": clk, "impl": "ours"}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse_args()
     rank, world, local = dist_env()
@@ -636,6 +757,9 @@ def main():
         return
     if args.mode == "ablation":
         run_ablation(args, rank, world, local)
+        return
+    if args.mode == "directed":
+        run_directed(args, rank, world, local)
         return
     if args.mode == "batch":
         if world > 1:

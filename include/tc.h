@@ -129,6 +129,49 @@ tc_status tc_count_vertex_formula(tc_graph* g, uint64_t* t_out, int mem_kind, ui
 tc_status tc_edge_support(tc_graph* g, int32_t* u_out, int32_t* v_out, uint32_t* support_out, int mem_kind);
 
 /*
+ * Directed local clustering coefficient, Eq. 1 (Sec. II-C), from a directed edge list.
+ * Pair k is the edge e_ij from i = src[k] to j = dst[k] (Sec. II-A); self-loops are
+ * dropped and a repeated (src, dst) pair is one edge, while (u, v) and (v, u) are two
+ * different edges.  With adj(v_i) the out-neighbours of v_i and deg+(i) = |adj(v_i)|:
+ *   c(i) = |{e_jk in E : v_j, v_k in adj(v_i)}|        (ordered pairs j != k)
+ *   C(i) = c(i) / (deg+(i) (deg+(i) - 1)), +0.0 when deg+(i) < 2 or c(i) = 0,
+ * one IEEE fp64 division of the two integers (the correctly rounded ratio while
+ * deg+(i) < 2^26).  On a symmetric input (both directions of every edge) c = 2t and
+ * C is Eq. 2's LCC.
+ *   n, m          vertices (>= 0) and pairs (0 <= m <= 2^31 - 1)
+ *   src, dst      int32[m] in mem_kind memory, read only (the caller keeps them)
+ *   cuda_stream   stream the work is ordered on (NULL: the legacy default stream);
+ *                 the call synchronises it before returning
+ *   c_out         uint64[n] or NULL, in mem_kind memory, caller's ids
+ *   lcc_out       double[n] or NULL, in mem_kind memory, caller's ids
+ *   stats         host struct or NULL, filled on success
+ *   flags         TC_DIRECTED_TIMED: time the phases with CUDA events on the stream
+ *                 and count the list entries the intersections read (stats fields)
+ * Works on the undirected graph underlying the input, oriented by (degree, id) as
+ * tc_count is, with two direction bits per edge; scratch comes from the library's
+ * device pool and is released before the call returns.  Errors: TC_EINVAL (an id
+ * outside [0, n), n < 0, m out of range, NULL src/dst with m > 0, bad mem_kind or
+ * flags; the outputs are then left untouched), TC_ENOMEM, TC_ECUDA.
+ */
+enum { TC_DIRECTED_TIMED = 1 };
+
+typedef struct tc_directed_stats {
+    int64_t m_directed;      /* distinct directed edges after dropping loops and repeats */
+    int64_t m_undirected;    /* edges of the underlying undirected graph */
+    int64_t loops_dropped;   /* self-loops in the input */
+    uint64_t total;          /* sum over i of c(i) */
+    uint64_t list_entries;   /* TC_DIRECTED_TIMED: sum over oriented edges (u, v) of d+(u) + d+(v) */
+    float build_ms;          /* TC_DIRECTED_TIMED: keys, ranks and oriented rows (input copy excluded) */
+    float count_ms;          /* TC_DIRECTED_TIMED: the intersection kernel */
+    float finalize_ms;       /* TC_DIRECTED_TIMED: c and C in the caller's ids */
+    float pad;
+} tc_directed_stats;
+
+tc_status tc_directed_lcc(int32_t n, int64_t m, const int32_t* src, const int32_t* dst, int mem_kind,
+                          void* cuda_stream, uint64_t* c_out, double* lcc_out, tc_directed_stats* stats,
+                          int flags);
+
+/*
  * Input accounting: number of distinct undirected edges, self-loops dropped and
  * repeated pairs dropped.  Any pointer may be NULL.  Synchronises the stream.
  */

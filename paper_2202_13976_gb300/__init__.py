@@ -33,7 +33,7 @@ EXPORTS = ["tc_graph_create_from_edges", "tc_graph_create_from_csr", "tc_count",
            "tc_graph_set_tuning", "tc_graph_autotune", "tc_batch_run", "tc_release_cached_graphs",
            "tc_generate_edges", "tc_server_start", "tc_server_submit", "tc_server_poll", "tc_server_wait",
            "tc_server_get_stats", "tc_server_stop", "tc_graph_build_timing", "tc_count_vertex_formula",
-           "tc_edge_support"]
+           "tc_edge_support", "tc_directed_lcc"]
 BUILD_PHASES = ["ingest_ms", "rank_ms", "count_ms", "fill_ms", "sort_ms", "degree_ms", "total_ms"]
 TC_GEN_RMAT, TC_GEN_ER_REPLACE = 0, 1
 GEN_KINDS = {"rmat": TC_GEN_RMAT, "er_replace": TC_GEN_ER_REPLACE}
@@ -52,6 +52,18 @@ class TcResult(ctypes.Structure):
 
     def to_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+TC_DIRECTED_TIMED = 1
+
+
+class TcDirectedStats(ctypes.Structure):
+    _fields_ = [("m_directed", ctypes.c_int64), ("m_undirected", ctypes.c_int64), ("loops_dropped", ctypes.c_int64),
+                ("total", ctypes.c_uint64), ("list_entries", ctypes.c_uint64), ("build_ms", ctypes.c_float),
+                ("count_ms", ctypes.c_float), ("finalize_ms", ctypes.c_float), ("pad", ctypes.c_float)]
+
+    def to_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_ if k != "pad"}
 
 
 class TcServerStats(ctypes.Structure):
@@ -129,6 +141,9 @@ def load(path: str | None = None):
     lib.tc_count_vertex_formula.argtypes = [P, P, ctypes.c_int, ctypes.POINTER(u64)]
     lib.tc_edge_support.restype = st
     lib.tc_edge_support.argtypes = [P, P, P, P, ctypes.c_int]
+    lib.tc_directed_lcc.restype = st
+    lib.tc_directed_lcc.argtypes = [i32, i64, P, P, ctypes.c_int, P, P, P, ctypes.POINTER(TcDirectedStats),
+                                    ctypes.c_int]
     lib.tc_graph_info.restype = st
     lib.tc_graph_info.argtypes = [P, ctypes.POINTER(i64), ctypes.POINTER(i64), ctypes.POINTER(i64)]
     lib.tc_graph_size.restype = st
@@ -303,6 +318,37 @@ def tc_edge_support(g: int, u_out=None, v_out=None, support_out=None):
     (pu, pv, ps), kind = _ptr_kind(u_out, v_out, support_out)
     _check(_lib.tc_edge_support(g, pu, pv, ps, kind))
     return u_out, v_out, support_out
+
+
+def tc_directed_lcc(n: int, src, dst, c_out=None, lcc_out=None, stream=None, timed=False):
+    """Directed LCC (Eq. 1) of the pairs src[k] -> dst[k] (int32; numpy on the host or
+    CUDA tensors): fills c_out (uint64[n] as int64) and lcc_out (float64[n]), allocated
+    like the inputs when None; returns (c_out, lcc_out, stats dict).  timed: phase
+    times from CUDA events and the list entries the count reads."""
+    load()
+    if len(src) != len(dst):
+        raise ValueError("src and dst differ in length")
+    _check_dtype(src, "int32")
+    _check_dtype(dst, "int32")
+    if c_out is None or lcc_out is None:
+        if _is_device(src):
+            import torch
+            if c_out is None:
+                c_out = torch.empty(n, dtype=torch.int64, device=src.device)
+            if lcc_out is None:
+                lcc_out = torch.empty(n, dtype=torch.float64, device=src.device)
+        else:
+            if c_out is None:
+                c_out = np.empty(n, dtype=np.uint64)
+            if lcc_out is None:
+                lcc_out = np.empty(n, dtype=np.float64)
+    _check_dtype(c_out, "int64")
+    _check_dtype(lcc_out, "float64")
+    (ps, pd, pc, pl), kind = _ptr_kind(src, dst, c_out, lcc_out)
+    st = TcDirectedStats()
+    _check(_lib.tc_directed_lcc(n, len(src), ps, pd, kind, _stream_ptr(stream), pc, pl, ctypes.byref(st),
+                                TC_DIRECTED_TIMED if timed else 0))
+    return c_out, lcc_out, st.to_dict()
 
 
 def tc_graph_info(g: int) -> dict:

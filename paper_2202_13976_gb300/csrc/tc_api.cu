@@ -80,6 +80,8 @@ tc_status init_device(int dev, DeviceState** out) {
 }  // namespace
 
 namespace tcg {
+void set_last_error(const char* where, cudaError_t e) { set_error(where, e); }
+
 cudaMemPool_t device_pool(int dev) {
     DeviceState* D = nullptr;
     return init_device(dev, &D) == TC_OK ? D->pool : nullptr;

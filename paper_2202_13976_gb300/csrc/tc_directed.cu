@@ -1,0 +1,530 @@
+// Directed local clustering coefficient (Eq. 1, Sec. II-C).
+//
+// For a directed simple graph (e_ij from v_i to v_j, Sec. II-A) with adj(v_i) the
+// out-neighbours of v_i, Eq. 1 counts
+//   c(i) = |{e_jk in E : v_j, v_k in adj(v_i)}|,   C(i) = c(i) / (deg+(i) (deg+(i) - 1)).
+// Every pair counted in c(i) closes a triangle {i, j, k} of the undirected graph U
+// that underlies G, so the count runs on U with the undirected path's orientation
+// (rank = (degree in U, id); every triangle met once, at the edge joining its two
+// lowest ranks, Sec. II-C's offset).  Each edge of U carries two direction bits
+// relative to rank order: bit 0 = lower -> higher exists in G, bit 1 = higher -> lower.
+// A triangle u < v < w (ranks) found at the oriented edge (u, v) adds to each corner
+// x, with y and z the other two corners, the number of its ordered pairs:
+//   [x -> y] [x -> z] ([y -> z] + [z -> y]).
+//
+// Phases (all on the device; one host synchronisation after phase 1 reads the error
+// flag and the size of U):
+//  1. pairs -> keys (min id, max id, direction), radix sorted; a run of keys with the
+//     same (min, max) is one edge of U whose bits are the OR of its directions;
+//     out-degrees (distinct tails) and degrees in U are counted from the runs;
+//  2. rank by (degree in U, id): stable radix sort of the degree field;
+//  3. oriented keys (lower rank, higher rank, bits in rank order) radix sorted, which
+//     lays the oriented rows out in order; row starts by binary search;
+//  4. count: a thread per oriented entry (u, v), highest ranks first: N+(u) after v
+//     against N+(v), by a merge (Alg. 2) or a binary search of the shorter list
+//     (Alg. 1), as Eq. 3 decides, the direction bits read at the matched positions;
+//  5. c and C per input id, and the sum of c.
+#include <cuda_runtime.h>
+
+#include <climits>
+#include <cstdio>
+#include <cstring>
+#include <vector>
+
+#include "tc_device.cuh"
+#include "tc_internal.h"
+
+namespace tcg {
+namespace {
+
+constexpr int DG_THREADS = 256;
+constexpr uint64_t DG_NONE = ~0ull;  // key of a dropped pair: sorts after every edge
+
+struct DgStats {
+    unsigned long long loops;       // self-loops dropped
+    unsigned long long m_directed;  // distinct directed edges
+    unsigned long long sum_c;       // sum over i of c(i)
+    unsigned long long entries;     // list entries read by the count (timed calls)
+    int err;                        // an id outside [0, n)
+    int pad;
+};
+
+int key_bits(int32_t n) {
+    int b = 1;
+    while (b < 31 && ((int64_t)1 << b) < (int64_t)n) ++b;
+    return b;
+}
+
+// Phase 1a: key = (min << (b + 1)) | (max << 1) | (src > dst) per pair; loops and
+// bad ids get DG_NONE.
+__global__ void k_dg_keys(int64_t m, const int32_t* __restrict__ src, const int32_t* __restrict__ dst, int32_t n,
+                          int b, uint64_t* __restrict__ keys, DgStats* st) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    unsigned long long loops = 0;
+    int err = 0;
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < m; k += stride) {
+        const int32_t a = src[k], c = dst[k];
+        uint64_t key = DG_NONE;
+        if ((uint32_t)a >= (uint32_t)n || (uint32_t)c >= (uint32_t)n) {
+            err = 1;
+        } else if (a == c) {
+            ++loops;
+        } else {
+            const uint64_t lo = (uint32_t)min(a, c), hi = (uint32_t)max(a, c);
+            key = (lo << (b + 1)) | (hi << 1) | (uint64_t)(a > c);
+        }
+        keys[k] = key;
+    }
+    loops = warp_sum(loops);
+    err = __any_sync(FULL, err);
+    if (lane_id() == 0) {
+        if (loops) atomicAdd(&st->loops, loops);
+        if (err) atomicOr(&st->err, 1);
+    }
+}
+
+// Phase 1b: head[k] = 1 where a run of equal (min, max) starts; distinct directed
+// edges counted and their tails' out-degrees incremented.  Warps walk aligned chunks
+// so that every lane takes part in the match below.
+__global__ void k_dg_heads(int64_t m, const uint64_t* __restrict__ keys, int b, uint32_t* __restrict__ head,
+                           uint32_t* __restrict__ dout, DgStats* st) {
+    const int lane = lane_id();
+    const int64_t warp0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t wstride = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const uint64_t mask = (1ull << b) - 1;
+    unsigned long long distinct = 0;
+    for (int64_t base = warp0 * 32; base < m; base += wstride * 32) {
+        const int64_t k = base + lane;
+        const uint64_t key = k < m ? keys[k] : DG_NONE;
+        const uint64_t prev = k > 0 && k < m ? keys[k - 1] : DG_NONE;
+        const bool valid = key != DG_NONE;
+        const bool h = valid && (k == 0 || (key >> 1) != (prev >> 1));
+        const bool d = valid && (k == 0 || key != prev);
+        if (k < m) head[k] = h ? 1u : 0u;
+        distinct += d;
+        // tail of the directed edge: min for direction 0, max for direction 1
+        const int32_t tail = d ? (int32_t)((key & 1) ? (key >> 1) & mask : key >> (b + 1)) : -1;
+        const unsigned same = __match_any_sync(FULL, tail);
+        if (tail >= 0 && lane == __ffs(same) - 1) atomicAdd(&dout[tail], (unsigned)__popc(same));
+    }
+    distinct = warp_sum(distinct);
+    if (lane == 0 && distinct) atomicAdd(&st->m_directed, distinct);
+}
+
+// Phase 1c: edge e = idx[k] + head[k] - 1 of U gets its ends at the run's head and
+// the direction bit of the last key of every group of equal keys; degrees in U are
+// counted at the heads (the min ends aggregated per warp: the keys are sorted by min).
+__global__ void k_dg_unique(int64_t m, const uint64_t* __restrict__ keys, int b, const uint32_t* __restrict__ head,
+                            const uint32_t* __restrict__ idx, int32_t* __restrict__ ulo, int32_t* __restrict__ uhi,
+                            uint32_t* __restrict__ flags, uint32_t* __restrict__ deg) {
+    const int lane = lane_id();
+    const int64_t warp0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t wstride = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const uint64_t mask = (1ull << b) - 1;
+    for (int64_t base = warp0 * 32; base < m; base += wstride * 32) {
+        const int64_t k = base + lane;
+        const uint64_t key = k < m ? keys[k] : DG_NONE;
+        const bool valid = key != DG_NONE;
+        int32_t lo = -1;
+        if (valid) {
+            const uint32_t h = head[k];
+            const int64_t e = (int64_t)idx[k] + h - 1;
+            const int32_t hi = (int32_t)((key >> 1) & mask);
+            lo = (int32_t)(key >> (b + 1));
+            if (k + 1 == m || keys[k + 1] != key) atomicOr(&flags[e], 1u << (key & 1));
+            if (h) {
+                ulo[e] = lo;
+                uhi[e] = hi;
+                atomicAdd(&deg[hi], 1u);
+            } else {
+                lo = -1;
+            }
+        }
+        const unsigned same = __match_any_sync(FULL, lo);
+        if (lo >= 0 && lane == __ffs(same) - 1) atomicAdd(&deg[lo], (unsigned)__popc(same));
+    }
+}
+
+// Phase 2: vkey = (degree << b) | id; a stable sort of the degree field alone gives
+// (degree, id) order because the keys start in id order.
+__global__ void k_dg_rank_keys(int32_t n, const uint32_t* __restrict__ deg, int b, uint64_t* __restrict__ vkeys) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride)
+        vkeys[v] = ((uint64_t)deg[v] << b) | (uint64_t)v;
+}
+
+__global__ void k_dg_rank(int32_t n, const uint64_t* __restrict__ vkeys, int b, int32_t* __restrict__ rank) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const uint64_t mask = (1ull << b) - 1;
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += stride)
+        rank[vkeys[p] & mask] = (int32_t)p;
+}
+
+// Phase 3a: okey = (lower rank << (b + 2)) | (higher rank << 2) | bits in rank order.
+__global__ void k_dg_orient(int64_t mu, const int32_t* __restrict__ ulo, const int32_t* __restrict__ uhi,
+                            const uint32_t* __restrict__ flags, const int32_t* __restrict__ rank, int b,
+                            uint64_t* __restrict__ okeys) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < mu; e += stride) {
+        const int32_t rx = rank[ulo[e]], ry = rank[uhi[e]];
+        const uint32_t f = flags[e];  // bit 0: min id -> max id, bit 1: max id -> min id
+        const bool keep = rx < ry;
+        const uint64_t a = (uint32_t)(keep ? rx : ry), c = (uint32_t)(keep ? ry : rx);
+        const uint32_t of = keep ? f : ((f & 1u) << 1) | (f >> 1);
+        okeys[e] = (a << (b + 2)) | (c << 2) | of;
+    }
+}
+
+// Phase 3b: the sorted keys become the rows: col (higher rank) and dirf (bits).
+__global__ void k_dg_rows(int64_t mu, const uint64_t* __restrict__ okeys, int b, int32_t* __restrict__ col,
+                          uint8_t* __restrict__ dirf) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const uint64_t mask = (1ull << b) - 1;
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < mu; k += stride) {
+        const uint64_t key = okeys[k];
+        col[k] = (int32_t)((key >> 2) & mask);
+        dirf[k] = (uint8_t)(key & 3);
+    }
+}
+
+// rowstart[a] = first sorted entry whose lower rank is >= a (a = 0 .. n).
+__global__ void k_dg_rowstart(int32_t n, int64_t mu, const uint64_t* __restrict__ okeys, int b,
+                              int64_t* __restrict__ rowstart) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t a = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; a <= n; a += stride) {
+        int64_t lo = 0, hi = mu;
+        while (lo < hi) {
+            const int64_t mid = (lo + hi) >> 1;
+            if ((int64_t)(okeys[mid] >> (b + 2)) < a)
+                lo = mid + 1;
+            else
+                hi = mid;
+        }
+        rowstart[a] = lo;
+    }
+}
+
+// One matched corner w of the triangle (u, v, w): fa = bits of (u, w), fb = bits of
+// (v, w), fuv = bits of (u, v), all in rank order (u < v < w).
+struct DgAcc {
+    uint32_t uv, vu, pop_uv;
+    unsigned long long cu, cv;
+    __device__ __forceinline__ void match(uint32_t fa, uint32_t fb, int32_t w, unsigned long long* __restrict__ c) {
+        if (uv & fa & 1u) cu += __popc(fb);                   // [u->v][u->w]([v->w] + [w->v])
+        if (vu & fb & 1u) cv += __popc(fa);                   // [v->u][v->w]([u->w] + [w->u])
+        if ((fa >> 1) & (fb >> 1)) atomicAdd(&c[w], (unsigned long long)pop_uv);  // [w->u][w->v]([u->v] + [v->u])
+    }
+};
+
+// Phase 4: a thread per oriented entry, from the last (highest ranks) down.
+__global__ void __launch_bounds__(DG_THREADS) k_dg_count(int64_t mu, const uint64_t* __restrict__ okeys, int b,
+                                                         const int64_t* __restrict__ rowstart,
+                                                         const int32_t* __restrict__ col,
+                                                         const uint8_t* __restrict__ dirf,
+                                                         unsigned long long* __restrict__ c) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const uint64_t mask = (1ull << b) - 1;
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < mu; q += stride) {
+        const int64_t k = mu - 1 - q;
+        const uint64_t key = okeys[k];
+        const int32_t u = (int32_t)(key >> (b + 2)), v = (int32_t)((key >> 2) & mask);
+        DgAcc acc;
+        const uint32_t fuv = (uint32_t)(key & 3);
+        acc.uv = fuv & 1u;
+        acc.vu = fuv >> 1;
+        acc.pop_uv = __popc(fuv);
+        acc.cu = 0;
+        acc.cv = 0;
+        const int64_t r1 = rowstart[u + 1];
+        const int32_t* A = col + k + 1;
+        const uint8_t* FA = dirf + k + 1;
+        const int a = (int)(r1 - k - 1);
+        const int64_t s0 = rowstart[v];
+        const int32_t* B = col + s0;
+        const uint8_t* FB = dirf + s0;
+        const int bl = (int)(rowstart[v + 1] - s0);
+        if (a > 0 && bl > 0) {
+            const int s = min(a, bl), l = max(a, bl);
+            if (l <= 16 || (float)l <= (log2f((float)l) - 1.0f) * (float)s) {  // Eq. 3: merge
+                int i = 0, j = 0;
+                while (i < a && j < bl) {
+                    const int32_t x = A[i], y = B[j];
+                    if (x == y) acc.match(FA[i], FB[j], x, c);
+                    i += x <= y;
+                    j += y <= x;
+                }
+            } else if (a <= bl) {  // keys from the suffix of N+(u), looked up in N+(v)
+                int lo = 0;
+                for (int i = 0; i < a && lo < bl; ++i) {
+                    const int32_t x = A[i];
+                    lo = lower_bound(B, lo, bl, x);
+                    if (lo < bl && B[lo] == x) acc.match(FA[i], FB[lo], x, c);
+                }
+            } else {  // keys from N+(v), looked up in the suffix of N+(u)
+                int lo = 0;
+                for (int j = 0; j < bl && lo < a; ++j) {
+                    const int32_t y = B[j];
+                    lo = lower_bound(A, lo, a, y);
+                    if (lo < a && A[lo] == y) acc.match(FA[lo], FB[j], y, c);
+                }
+            }
+        }
+        if (acc.cu) atomicAdd(&c[u], acc.cu);
+        if (acc.cv) atomicAdd(&c[v], acc.cv);
+    }
+}
+
+// Sum over oriented entries (u, v) of d+(u) + d+(v): the list entries the count reads.
+__global__ void k_dg_list_entries(int64_t mu, const uint64_t* __restrict__ okeys, int b,
+                                  const int64_t* __restrict__ rowstart, DgStats* st) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const uint64_t mask = (1ull << b) - 1;
+    unsigned long long s = 0;
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < mu; k += stride) {
+        const uint64_t key = okeys[k];
+        const int64_t u = (int64_t)(key >> (b + 2)), v = (int64_t)((key >> 2) & mask);
+        s += (unsigned long long)(rowstart[u + 1] - rowstart[u] + rowstart[v + 1] - rowstart[v]);
+    }
+    s = warp_sum(s);
+    if (lane_id() == 0 && s) atomicAdd(&st->entries, s);
+}
+
+// Phase 5: outputs in input ids and the sum of c.
+__global__ void k_dg_finalize(int32_t n, const int32_t* __restrict__ rank, const unsigned long long* __restrict__ c_rank,
+                              const uint32_t* __restrict__ dout, unsigned long long* __restrict__ c_out,
+                              double* __restrict__ lcc_out, DgStats* st) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    unsigned long long sum = 0;
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride) {
+        const unsigned long long cv = c_rank[rank[v]];
+        sum += cv;
+        if (c_out) c_out[v] = cv;
+        if (lcc_out) {
+            const long long d = dout[v];
+            lcc_out[v] = d < 2 || cv == 0 ? 0.0 : __ddiv_rn((double)cv, (double)(d * (d - 1)));
+        }
+    }
+    sum = warp_sum(sum);
+    if (lane_id() == 0 && sum) atomicAdd(&st->sum_c, sum);
+}
+
+// Pool allocations of one call, released (stream-ordered) when it ends.
+struct Arena {
+    cudaMemPool_t pool;
+    cudaStream_t stream;
+    std::vector<void*> list;
+    bool failed = false;
+    template <typename T>
+    T* get(size_t count) {
+        size_t bytes = count * sizeof(T);
+        if (bytes == 0) bytes = 16;
+        bytes = (bytes + 255) & ~(size_t)255;
+        void* p = nullptr;
+        if (failed) return nullptr;
+        if (cudaMallocFromPoolAsync(&p, bytes, pool, stream) != cudaSuccess) {
+            cudaGetLastError();
+            failed = true;
+            return nullptr;
+        }
+        list.push_back(p);
+        return static_cast<T*>(p);
+    }
+    ~Arena() {
+        for (void* p : list) cudaFreeAsync(p, stream);
+    }
+};
+
+// CUDA events around the phases of a timed call (none otherwise).
+struct Events {
+    cudaEvent_t e[4] = {};
+    bool on = false, ok = true;
+    explicit Events(bool timed) : on(timed) {
+        for (int k = 0; on && k < 4; ++k)
+            if (cudaEventCreate(&e[k]) != cudaSuccess) {
+                cudaGetLastError();
+                ok = false;
+                on = false;
+            }
+    }
+    void record(int k, cudaStream_t s) {
+        if (on) cudaEventRecord(e[k], s);
+    }
+    float ms(int a, int b) const {
+        float t = 0.0f;
+        if (on && cudaEventElapsedTime(&t, e[a], e[b]) != cudaSuccess) {
+            cudaGetLastError();
+            t = 0.0f;
+        }
+        return t;
+    }
+    ~Events() {
+        for (int k = 0; k < 4; ++k)
+            if (e[k]) cudaEventDestroy(e[k]);
+    }
+};
+
+tc_status fail(const char* where, cudaError_t e) {
+    set_last_error(where, e);
+    return TC_ECUDA;
+}
+
+}  // namespace
+}  // namespace tcg
+
+using namespace tcg;
+
+extern "C" tc_status tc_directed_lcc(int32_t n, int64_t m, const int32_t* src, const int32_t* dst, int mem_kind,
+                                     void* cuda_stream, uint64_t* c_out, double* lcc_out, tc_directed_stats* stats,
+                                     int flags) {
+    if (n < 0 || m < 0 || m > INT32_MAX || (m > 0 && (!src || !dst)) ||
+        (mem_kind != TC_MEM_HOST && mem_kind != TC_MEM_DEVICE) || (flags & ~TC_DIRECTED_TIMED))
+        return TC_EINVAL;
+    const bool timed = (flags & TC_DIRECTED_TIMED) != 0;
+    const bool host = mem_kind == TC_MEM_HOST;
+    cudaStream_t stream = static_cast<cudaStream_t>(cuda_stream);
+    int dev = 0, sms = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return fail("tc_directed_lcc: device", e);
+    cudaMemPool_t pool = device_pool(dev);
+    if (!pool) return TC_ECUDA;
+    const Launch L{stream, sms};
+    const size_t nn = (size_t)n, mm = (size_t)m;
+    Arena A{pool, stream};
+
+    if (m == 0) {  // no edge: every count and coefficient is zero
+        if (host) {
+            if (c_out) memset(c_out, 0, sizeof(uint64_t) * nn);
+            if (lcc_out) memset(lcc_out, 0, sizeof(double) * nn);
+        } else {
+            if (c_out && nn) e = cudaMemsetAsync(c_out, 0, sizeof(uint64_t) * nn, stream);
+            if (e == cudaSuccess && lcc_out && nn) e = cudaMemsetAsync(lcc_out, 0, sizeof(double) * nn, stream);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+            if (e != cudaSuccess) return fail("tc_directed_lcc", e);
+        }
+        if (stats) *stats = tc_directed_stats{};
+        return TC_OK;
+    }
+
+    const int b = key_bits(n);
+    const int32_t* dsrc = src;
+    const int32_t* ddst = dst;
+    if (host) {
+        int32_t* s = A.get<int32_t>(mm);
+        int32_t* d = A.get<int32_t>(mm);
+        if (A.failed) return TC_ENOMEM;
+        e = cudaMemcpyAsync(s, src, sizeof(int32_t) * mm, cudaMemcpyHostToDevice, stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(d, dst, sizeof(int32_t) * mm, cudaMemcpyHostToDevice, stream);
+        if (e != cudaSuccess) return fail("tc_directed_lcc: copy in", e);
+        dsrc = s;
+        ddst = d;
+    }
+    const int64_t big = m > (int64_t)n + 1 ? m : (int64_t)n + 1;
+    uint64_t* keys = A.get<uint64_t>(mm);
+    uint64_t* alt = A.get<uint64_t>(mm);
+    void* radix_tmp = A.get<char>(radix_tmp_bytes(big));
+    void* scan_tmp = A.get<char>(scan_tmp_bytes(big + 1));
+    uint32_t* head = A.get<uint32_t>(mm + 1);
+    uint32_t* idx = A.get<uint32_t>(mm + 1);
+    uint32_t* ebits = A.get<uint32_t>(mm);
+    int32_t* ulo = A.get<int32_t>(mm);
+    int32_t* uhi = A.get<int32_t>(mm);
+    uint32_t* deg = A.get<uint32_t>(nn);
+    uint32_t* dout = A.get<uint32_t>(nn);
+    DgStats* st = A.get<DgStats>(1);
+    if (A.failed) return TC_ENOMEM;
+    DgStats hst_v{};
+    uint32_t hmu_v = 0;
+    DgStats* hst = &hst_v;  // host copies are read only after the stream is synchronised
+    uint32_t* hmu = &hmu_v;
+
+    Events ev(timed);
+    if (!ev.ok) return fail("tc_directed_lcc: events", cudaErrorMemoryAllocation);
+    ev.record(0, stream);
+    cudaMemsetAsync(st, 0, sizeof(DgStats), stream);
+    cudaMemsetAsync(ebits, 0, sizeof(uint32_t) * mm, stream);
+    cudaMemsetAsync(deg, 0, sizeof(uint32_t) * nn, stream);
+    cudaMemsetAsync(dout, 0, sizeof(uint32_t) * nn, stream);
+    // phase 1
+    k_dg_keys<<<grid_for(m, DG_THREADS, sms), DG_THREADS, 0, stream>>>(m, dsrc, ddst, n, b, keys, st);
+    count_launch();
+    uint64_t* sorted = radix_sort_u64(keys, alt, m, 0, 2 * b + 1, radix_tmp, L);
+    k_dg_heads<<<grid_for(m, DG_THREADS, sms), DG_THREADS, 0, stream>>>(m, sorted, b, head, dout, st);
+    count_launch();
+    scan_u32_to_u32(head, idx, m, scan_tmp, L);
+    k_dg_unique<<<grid_for(m, DG_THREADS, sms), DG_THREADS, 0, stream>>>(m, sorted, b, head, idx, ulo, uhi, ebits,
+                                                                          deg);
+    count_launch();
+    e = cudaMemcpyAsync(hst, st, sizeof(DgStats), cudaMemcpyDeviceToHost, stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(hmu, idx + m, sizeof(uint32_t), cudaMemcpyDeviceToHost, stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+    if (e != cudaSuccess) return fail("tc_directed_lcc: phase 1", e);
+    if (hst->err) return TC_EINVAL;
+    const int64_t mu = (int64_t)*hmu;
+    const unsigned long long md = hst->m_directed, loops = hst->loops;
+
+    // phase 2: ranks (the key buffers of phase 1 are free again)
+    uint64_t* vkeys = A.get<uint64_t>(nn);
+    uint64_t* valt = A.get<uint64_t>(nn);
+    int32_t* rank = A.get<int32_t>(nn);
+    int64_t* rowstart = A.get<int64_t>(nn + 1);
+    int32_t* col = A.get<int32_t>((size_t)mu);
+    uint8_t* dirf = A.get<uint8_t>((size_t)mu);
+    unsigned long long* c_rank = A.get<unsigned long long>(nn);
+    unsigned long long* dc = nullptr;
+    double* dl = nullptr;
+    if (host && c_out) dc = A.get<unsigned long long>(nn);
+    if (host && lcc_out) dl = A.get<double>(nn);
+    if (A.failed) return TC_ENOMEM;
+    k_dg_rank_keys<<<grid_for(n, DG_THREADS, sms), DG_THREADS, 0, stream>>>(n, deg, b, vkeys);
+    count_launch();
+    uint64_t* vsorted = radix_sort_u64(vkeys, valt, n, b, 2 * b, radix_tmp, L);
+    k_dg_rank<<<grid_for(n, DG_THREADS, sms), DG_THREADS, 0, stream>>>(n, vsorted, b, rank);
+    count_launch();
+    // phase 3: oriented rows
+    k_dg_orient<<<grid_for(mu, DG_THREADS, sms), DG_THREADS, 0, stream>>>(mu, ulo, uhi, ebits, rank, b, keys);
+    count_launch();
+    uint64_t* osorted = radix_sort_u64(keys, alt, mu, 2, 2 * b + 2, radix_tmp, L);
+    k_dg_rows<<<grid_for(mu, DG_THREADS, sms), DG_THREADS, 0, stream>>>(mu, osorted, b, col, dirf);
+    count_launch();
+    k_dg_rowstart<<<grid_for((int64_t)n + 1, DG_THREADS, sms), DG_THREADS, 0, stream>>>(n, mu, osorted, b, rowstart);
+    count_launch();
+    // phase 4: count
+    cudaMemsetAsync(c_rank, 0, sizeof(unsigned long long) * nn, stream);
+    if (timed) {
+        k_dg_list_entries<<<grid_for(mu, DG_THREADS, sms), DG_THREADS, 0, stream>>>(mu, osorted, b, rowstart, st);
+        count_launch();
+    }
+    ev.record(1, stream);
+    k_dg_count<<<grid_for(mu, DG_THREADS, sms), DG_THREADS, 0, stream>>>(mu, osorted, b, rowstart, col, dirf,
+                                                                          c_rank);
+    count_launch();
+    ev.record(2, stream);
+    // phase 5
+    k_dg_finalize<<<grid_for(n, DG_THREADS, sms), DG_THREADS, 0, stream>>>(
+        n, rank, c_rank, dout, host ? dc : reinterpret_cast<unsigned long long*>(c_out), host ? dl : lcc_out, st);
+    count_launch();
+    ev.record(3, stream);
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaMemcpyAsync(hst, st, sizeof(DgStats), cudaMemcpyDeviceToHost, stream);
+    if (e == cudaSuccess && host && c_out && nn)
+        e = cudaMemcpyAsync(c_out, dc, sizeof(uint64_t) * nn, cudaMemcpyDeviceToHost, stream);
+    if (e == cudaSuccess && host && lcc_out && nn)
+        e = cudaMemcpyAsync(lcc_out, dl, sizeof(double) * nn, cudaMemcpyDeviceToHost, stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+    if (e != cudaSuccess) return fail("tc_directed_lcc", e);
+    if (stats) {
+        *stats = tc_directed_stats{};
+        stats->m_directed = (int64_t)md;
+        stats->m_undirected = mu;
+        stats->loops_dropped = (int64_t)loops;
+        stats->total = hst->sum_c;
+        stats->list_entries = hst->entries;
+        if (timed) {
+            stats->build_ms = ev.ms(0, 1);
+            stats->count_ms = ev.ms(1, 2);
+            stats->finalize_ms = ev.ms(2, 3);
+        }
+    }
+    return TC_OK;
+}

@@ -229,6 +229,9 @@ cudaMemPool_t device_pool(int dev);
 // Device memory a serving request is admitted with.
 uint64_t serve_estimate_bytes(int32_t n, int64_t m);
 
+// Records "where: CUDA error text" for tc_last_error_detail on this thread.
+void set_last_error(const char* where, cudaError_t e);
+
 // Kernel launch accounting (tc_launch_count).
 void count_launch(int k = 1);
 uint64_t launch_total();
