@@ -20,9 +20,12 @@
 //  2. rank by (degree in U, id): stable radix sort of the degree field;
 //  3. oriented keys (lower rank, higher rank, bits in rank order) radix sorted, which
 //     lays the oriented rows out in order; row starts by binary search;
-//  4. count: a thread per oriented entry (u, v), highest ranks first: N+(u) after v
-//     against N+(v), by a merge (Alg. 2) or a binary search of the shorter list
-//     (Alg. 1), as Eq. 3 decides, the direction bits read at the matched positions;
+//  4. count, pull: vertices with many in-edges (hubs) stage N+(v) as a 2-bit map of
+//     direction bits in shared memory, and every in-edge (u -> v) streams N+(u) after v
+//     against it (the in-edges come from a stable sort of the entries by target);
+//     count, push: a thread per other oriented entry (u, v), highest ranks first: N+(u)
+//     after v against N+(v), by a merge (Alg. 2) or a binary search of the shorter
+//     list (Alg. 1), as Eq. 3 decides, the direction bits read at the matched positions;
 //  5. c and C per input id, and the sum of c.
 #include <cuda_runtime.h>
 
@@ -39,6 +42,11 @@ namespace {
 
 constexpr int DG_THREADS = 256;
 constexpr uint64_t DG_NONE = ~0ull;  // key of a dropped pair: sorts after every edge
+constexpr int DGH_WINDOW = 131072;   // ranks above a hub covered by its 2-bit map (32 KB)
+constexpr int DGH_MIN_IN = 32;       // in-edges that make a vertex a hub
+constexpr int DGH_BLOCKS = 5;        // resident hub blocks per SM (40.1 KB shared memory each)
+constexpr int DGH_UNROLL = 8;        // suffix loads in flight per lane of the hub kernel
+constexpr int DGH_TOP = 1024;        // highest ranks whose c the hub kernel sums in shared memory
 
 struct DgStats {
     unsigned long long loops;       // self-loops dropped
@@ -216,11 +224,177 @@ struct DgAcc {
     }
 };
 
-// Phase 4: a thread per oriented entry, from the last (highest ranks) down.
+// Phase 4, pull: the in-edges (u -> v) of a vertex v, in rank order; ikey = (v << 31) | k
+// for the entry k of (u, v) in col, so that a stable sort of the v field lists every
+// vertex's in-edges together, in entry order.
+__global__ void k_dg_in_keys(int64_t mu, const int32_t* __restrict__ col, uint64_t* __restrict__ ikeys) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < mu; k += stride)
+        ikeys[k] = ((uint64_t)(uint32_t)col[k] << 31) | (uint64_t)k;
+}
+
+// instart[a] = first sorted in-key whose target is >= a (a = 0 .. n).
+__global__ void k_dg_instart(int32_t n, int64_t mu, const uint64_t* __restrict__ ikeys,
+                             int64_t* __restrict__ instart) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t a = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; a <= n; a += stride) {
+        int64_t lo = 0, hi = mu;
+        while (lo < hi) {
+            const int64_t mid = (lo + hi) >> 1;
+            if ((int64_t)(ikeys[mid] >> 31) < a)
+                lo = mid + 1;
+            else
+                hi = mid;
+        }
+        instart[a] = lo;
+    }
+}
+
+// Hubs: at least DGH_MIN_IN in-edges, a non-empty N+(v) and a rank window
+// (v, max N+(v)] that the shared 2-bit map covers.  hubflag is indexed by q = n-1-v so
+// that the scanned list runs from the highest rank down.
+__global__ void k_dg_hub_flags(int32_t n, const int64_t* __restrict__ rowstart, const int32_t* __restrict__ col,
+                               const int64_t* __restrict__ instart, uint32_t* __restrict__ hubflag,
+                               uint8_t* __restrict__ ishub) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride) {
+        const int64_t r0 = rowstart[v], r1 = rowstart[v + 1];
+        const bool hub = instart[v + 1] - instart[v] >= DGH_MIN_IN && r1 > r0 && col[r1 - 1] - v <= DGH_WINDOW;
+        ishub[v] = hub ? 1 : 0;
+        hubflag[n - 1 - v] = hub ? 1u : 0u;
+    }
+}
+
+__global__ void k_dg_hub_list(int32_t n, const uint32_t* __restrict__ hubflag, const uint32_t* __restrict__ hubpos,
+                              int32_t* __restrict__ hubs) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += stride)
+        if (hubflag[q]) hubs[hubpos[q]] = n - 1 - (int32_t)q;
+}
+
+// In-edge records of the hubs: rec[i] = {u, first entry after v in N+(u), end of
+// N+(u), bits of (u, v)} for the sorted in-key i of (u -> v).
+__global__ void k_dg_in_rec(int64_t mu, const uint64_t* __restrict__ ikeys, const uint64_t* __restrict__ okeys, int b,
+                            const int64_t* __restrict__ rowstart, const uint8_t* __restrict__ ishub,
+                            int4* __restrict__ rec) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const uint64_t kmask = (1ull << 31) - 1;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < mu; i += stride) {
+        const uint64_t ik = ikeys[i];
+        if (!ishub[ik >> 31]) continue;
+        const int64_t k = (int64_t)(ik & kmask);
+        const uint64_t key = okeys[k];
+        const int32_t u = (int32_t)(key >> (b + 2));
+        rec[i] = make_int4(u, (int)(k + 1), (int)rowstart[u + 1], (int)(key & 3));
+    }
+}
+
+// One block per hub v (claimed from the list, highest rank first).  N+(v) is staged as
+// a 2-bit map over the window (v, max N+(v)]: position w - v - 1 holds the direction
+// bits of (v, w), 0 when w is not an out-neighbour.  Groups of 8 lanes take the
+// in-edges (u -> v); each streams N+(u) after v (stopping above max N+(v)) and probes
+// the map: a non-zero code fb is a triangle u < v < w with fa = bits of (u, w) read
+// beside w, fuv = bits of (u, v).  The map is cleared once per block; each hub resets
+// only the words its own entries set, so a hub costs O(|N+(v)|) on top of its in-edges'
+// suffixes, not O(window).  Matches that add to one of the DGH_TOP highest ranks (the
+// vertices most in-edges lead to) are summed in shared memory and flushed once per
+// block; the others add to c[] directly.
+__global__ void __launch_bounds__(DG_THREADS, DGH_BLOCKS) k_dg_hub(int32_t n, const uint32_t* __restrict__ nh_ptr,
+                                                       const int32_t* __restrict__ hubs,
+                                                       const int64_t* __restrict__ rowstart,
+                                                       const int32_t* __restrict__ col,
+                                                       const uint8_t* __restrict__ dirf,
+                                                       const int4* __restrict__ rec,
+                                                       const int64_t* __restrict__ instart,
+                                                       unsigned long long* __restrict__ c,
+                                                       unsigned* __restrict__ counter) {
+    __shared__ uint32_t map[DGH_WINDOW / 16];
+    __shared__ unsigned long long top[DGH_TOP];  // c of ranks n - DGH_TOP .. n - 1, this block's share
+    __shared__ unsigned long long cv_w[DG_THREADS / 32];
+    __shared__ unsigned next;
+    const int lane = lane_id(), warp = threadIdx.x >> 5;
+    const int grp = lane >> 3, gl = lane & 7;
+    const unsigned nh = *nh_ptr;
+    const int32_t top0 = n - DGH_TOP;
+    for (int i = threadIdx.x; i < DGH_WINDOW / 16; i += DG_THREADS) map[i] = 0;  // once; each hub clears its own
+    for (int i = threadIdx.x; i < DGH_TOP; i += DG_THREADS) top[i] = 0;
+    for (;;) {
+        if (threadIdx.x == 0) next = atomicAdd(counter, 1u);
+        __syncthreads();  // the previous hub is finished and cleared by every thread
+        const unsigned q = next;
+        if (q >= nh) break;
+        const int32_t v = hubs[q];
+        const int64_t s0 = rowstart[v];
+        const int dv = (int)(rowstart[v + 1] - s0);
+        const int32_t hi = col[s0 + dv - 1];  // dv > 0 for every hub
+        for (int j = threadIdx.x; j < dv; j += DG_THREADS) {
+            const int off = col[s0 + j] - v - 1;
+            atomicOr(&map[off >> 4], (uint32_t)dirf[s0 + j] << (2 * (off & 15)));
+        }
+        __syncthreads();
+        unsigned long long cv = 0;
+        const int64_t i0 = instart[v], i1 = instart[v + 1];
+        for (int64_t base = i0 + (int64_t)warp * 4; base < i1; base += DG_THREADS / 8) {  // uniform per warp
+            const int64_t i = base + grp;
+            unsigned long long cu = 0;
+            int4 r = make_int4(-1, 0, 0, 0);
+            if (i < i1) r = rec[i];
+            const uint32_t fuv = (uint32_t)r.w;
+            // the group's lanes take positions sb + gl + 8 j, DGH_UNROLL loads in flight
+            for (int p0 = r.y + gl; p0 < r.z; p0 += 8 * DGH_UNROLL) {
+                int32_t w[DGH_UNROLL];
+                uint32_t fa[DGH_UNROLL];
+#pragma unroll
+                for (int j = 0; j < DGH_UNROLL; ++j) {
+                    const int p = p0 + 8 * j;
+                    w[j] = p < r.z ? col[p] : INT_MAX;
+                    fa[j] = p < r.z ? dirf[p] : 0u;
+                }
+#pragma unroll
+                for (int j = 0; j < DGH_UNROLL; ++j) {
+                    if (w[j] > hi) break;  // the row is sorted: nothing further lies in the window
+                    const int off = w[j] - v - 1;
+                    const uint32_t fb = (map[off >> 4] >> (2 * (off & 15))) & 3u;
+                    if (fb) {
+                        if (fuv & fa[j] & 1u) cu += __popc(fb);         // [u->v][u->w]([v->w] + [w->v])
+                        if ((fuv >> 1) & fb & 1u) cv += __popc(fa[j]);  // [v->u][v->w]([u->w] + [w->u])
+                        if ((fa[j] >> 1) & (fb >> 1)) {                 // [w->u][w->v]([u->v] + [v->u])
+                            const unsigned long long x = (unsigned long long)__popc(fuv);
+                            if (w[j] >= top0)
+                                atomicAdd(&top[w[j] - top0], x);
+                            else
+                                atomicAdd(&c[w[j]], x);
+                        }
+                    }
+                }
+                if (w[DGH_UNROLL - 1] > hi) break;
+            }
+            cu += __shfl_xor_sync(FULL, cu, 1);
+            cu += __shfl_xor_sync(FULL, cu, 2);
+            cu += __shfl_xor_sync(FULL, cu, 4);
+            if (gl == 0 && cu) atomicAdd(&c[r.x], cu);
+        }
+        cv = warp_sum(cv);
+        if (lane == 0) cv_w[warp] = cv;
+        __syncthreads();  // every probe of this hub is done
+        if (threadIdx.x == 0) {
+            unsigned long long sv = 0;
+            for (int k = 0; k < DG_THREADS / 32; ++k) sv += cv_w[k];
+            if (sv) atomicAdd(&c[v], sv);
+        }
+        for (int j = threadIdx.x; j < dv; j += DG_THREADS) map[(col[s0 + j] - v - 1) >> 4] = 0;
+    }
+    for (int i = threadIdx.x; i < DGH_TOP; i += DG_THREADS)  // after the final barrier of the loop
+        if (top0 + i >= 0 && top[i]) atomicAdd(&c[top0 + i], top[i]);
+}
+
+// Phase 4, push: a thread per oriented entry whose target is not a hub, from the last
+// (highest ranks) down.
 __global__ void __launch_bounds__(DG_THREADS) k_dg_count(int64_t mu, const uint64_t* __restrict__ okeys, int b,
                                                          const int64_t* __restrict__ rowstart,
                                                          const int32_t* __restrict__ col,
                                                          const uint8_t* __restrict__ dirf,
+                                                         const uint8_t* __restrict__ ishub,
                                                          unsigned long long* __restrict__ c) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     const uint64_t mask = (1ull << b) - 1;
@@ -228,6 +402,7 @@ __global__ void __launch_bounds__(DG_THREADS) k_dg_count(int64_t mu, const uint6
         const int64_t k = mu - 1 - q;
         const uint64_t key = okeys[k];
         const int32_t u = (int32_t)(key >> (b + 2)), v = (int32_t)((key >> 2) & mask);
+        if (ishub[v]) continue;  // pulled by k_dg_hub
         DgAcc acc;
         const uint32_t fuv = (uint32_t)(key & 3);
         acc.uv = fuv & 1u;
@@ -489,14 +664,43 @@ extern "C" tc_status tc_directed_lcc(int32_t n, int64_t m, const int32_t* src, c
     count_launch();
     k_dg_rowstart<<<grid_for((int64_t)n + 1, DG_THREADS, sms), DG_THREADS, 0, stream>>>(n, mu, osorted, b, rowstart);
     count_launch();
+    // in-edge lists and hubs (the phase-1 buffer that does not hold osorted is free)
+    uint64_t* ikeys = osorted == keys ? alt : keys;
+    uint64_t* ialt = A.get<uint64_t>((size_t)mu);
+    int64_t* instart = A.get<int64_t>(nn + 1);
+    uint32_t* hubflag = A.get<uint32_t>(nn + 1);
+    uint32_t* hubpos = A.get<uint32_t>(nn + 1);
+    int32_t* hubs = A.get<int32_t>(nn);
+    uint8_t* ishub = A.get<uint8_t>(nn);
+    unsigned* counter = A.get<unsigned>(1);
+    int4* rec = A.get<int4>((size_t)mu);
+    if (A.failed) return TC_ENOMEM;
+    k_dg_in_keys<<<grid_for(mu, DG_THREADS, sms), DG_THREADS, 0, stream>>>(mu, col, ikeys);
+    count_launch();
+    uint64_t* isorted = radix_sort_u64(ikeys, ialt, mu, 31, 31 + b, radix_tmp, L);
+    k_dg_instart<<<grid_for((int64_t)n + 1, DG_THREADS, sms), DG_THREADS, 0, stream>>>(n, mu, isorted, instart);
+    count_launch();
+    k_dg_hub_flags<<<grid_for(n, DG_THREADS, sms), DG_THREADS, 0, stream>>>(n, rowstart, col, instart, hubflag,
+                                                                             ishub);
+    count_launch();
+    scan_u32_to_u32(hubflag, hubpos, n, scan_tmp, L);
+    k_dg_hub_list<<<grid_for(n, DG_THREADS, sms), DG_THREADS, 0, stream>>>(n, hubflag, hubpos, hubs);
+    count_launch();
+    k_dg_in_rec<<<grid_for(mu, DG_THREADS, sms), DG_THREADS, 0, stream>>>(mu, isorted, osorted, b, rowstart, ishub,
+                                                                           rec);
+    count_launch();
     // phase 4: count
     cudaMemsetAsync(c_rank, 0, sizeof(unsigned long long) * nn, stream);
+    cudaMemsetAsync(counter, 0, sizeof(unsigned), stream);
     if (timed) {
         k_dg_list_entries<<<grid_for(mu, DG_THREADS, sms), DG_THREADS, 0, stream>>>(mu, osorted, b, rowstart, st);
         count_launch();
     }
     ev.record(1, stream);
-    k_dg_count<<<grid_for(mu, DG_THREADS, sms), DG_THREADS, 0, stream>>>(mu, osorted, b, rowstart, col, dirf,
+    k_dg_hub<<<sms * DGH_BLOCKS, DG_THREADS, 0, stream>>>(n, hubpos + n, hubs, rowstart, col, dirf, rec, instart,
+                                                          c_rank, counter);
+    count_launch();
+    k_dg_count<<<grid_for(mu, DG_THREADS, sms), DG_THREADS, 0, stream>>>(mu, osorted, b, rowstart, col, dirf, ishub,
                                                                           c_rank);
     count_launch();
     ev.record(2, stream);
