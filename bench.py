@@ -280,7 +280,7 @@ def run_ours(args, rank, world, local):
     tpath = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         rec = json.load(open(tpath)).get(args.workload, {}).get(name)
-        if rec and rec.get("source_sha256") == tc.source_digest():
+        if rec and rec.get("source_sha256") == tc.source_digest(kernels[name][1] if name != "k_tc_cta" else None):
             traffic = rec["dram_bytes_per_launch"]
     except Exception:
         traffic = None
@@ -694,20 +694,20 @@ def run_directed(args, rank, world, local):
     ms_per_step, value = aggregate_ranks(sum(a.elapsed_time(b) for a, b in evs), args.steps, st0["m_directed"],
                                          world, dev)
     phase = {k: statistics.mean(x[k] for x in stats) for k in ("build_ms", "count_ms", "finalize_ms")}
-    # k_dg_count reads 5 bytes per list entry (4 id + 1 direction byte) and 24 bytes per
-    # oriented edge (its key and three row offsets)
+    # the count phase (k_dg_hub, then k_dg_count) reads 5 bytes per list entry (4 id + 1
+    # direction byte) and 24 bytes per oriented edge (its key and three row offsets)
     alg_bytes = 5 * st0["list_entries"] + 24 * st0["m_undirected"]
     peak, peak_kind = measured_peak()
     achieved = alg_bytes / (phase["count_ms"] / 1000.0) / 1e9
     traffic = None
     try:
         rec = json.load(open(os.path.join(ROOT, "profiles", "traffic.json"))).get(args.workload + "_directed",
-                                                                                    {}).get("k_dg_count")
-        if rec and rec.get("source_sha256") == tc.source_digest():
+                                                                                    {}).get("k_dg_hub+k_dg_count")
+        if rec and rec.get("source_sha256") == tc.source_digest("directed"):
             traffic = rec["dram_bytes_per_launch"]
     except Exception:
         traffic = None
-    roofline = {"bound": "hbm", "kernel": "k_dg_count", "achieved": achieved, "peak": peak, "unit": "GB/s",
+    roofline = {"bound": "hbm", "kernel": "k_dg_hub+k_dg_count", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": traffic, "peak_source": f"{peak_kind} hbm_gbs",
                 "algorithmic_bytes": alg_bytes, "kernel_ms": phase["count_ms"],
                 "note": "of measured" if peak_kind == "measured" else "of fallback"}

@@ -38,11 +38,23 @@ def _inputs() -> list[str]:
         [os.path.join(ROOT, "include", "tc.h")]
 
 
-def source_digest() -> str:
-    """sha256 over the library sources (identifies the kernels a profile was taken on)."""
+# Source files that define the kernels of each measured phase: a DRAM-traffic record
+# taken on them stays valid while these files are unchanged (the device headers hold
+# the kernels' constants and helpers; include/tc.h only declares the C ABI).
+KERNEL_SOURCES = {
+    "hub": ["tc_intersect.cu", "tc_core.cu", "tc_device.cuh", "tc_internal.h"],
+    "small": ["tc_intersect.cu", "tc_device.cuh", "tc_internal.h"],
+    "directed": ["tc_directed.cu", "tc_device.cuh", "tc_internal.h"],
+}
+
+
+def source_digest(phase: str | None = None) -> str:
+    """sha256 over the library sources, or over the files that define one measured
+    phase's kernels (KERNEL_SOURCES): identifies the kernels a profile was taken on."""
     import hashlib
     h = hashlib.sha256()
-    for p in sorted(_inputs()):
+    files = _inputs() if phase is None else [os.path.join(CSRC, f) for f in KERNEL_SOURCES[phase]]
+    for p in sorted(files):
         h.update(os.path.basename(p).encode())
         with open(p, "rb") as f:
             h.update(f.read())
