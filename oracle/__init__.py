@@ -16,6 +16,9 @@ numpy arrays.  Every function names the passage of the paper it follows:
 - ``tc_vertex``: the paper's per-vertex formula (Alg. 3) with the Eq. 3 hybrid.
 - ``lcc``: Eq. 2.
 - ``build_digraph`` / ``directed_lcc``: directed graphs (Sec. II-A) and Eq. 1.
+- ``remote_reads`` / ``cache_lru`` / ``cache_score`` / ``remote_cache``: the remote
+  reads of the 1D-partitioned algorithm (Sec. IV-A, Alg. 4) and the simulated caches
+  of Sec. IV-B (LRU, degree score).
 
 Parity status: every function is pinned by the ``-m "not gpu"`` tests
 (brute force, closed forms, scipy's sparse product for the algebraic form
@@ -82,6 +85,12 @@ def _load():
             lib.or_edge_support.argtypes = [i64, _i64p, _i32p, _i32p, _i32p, ctypes.POINTER(ctypes.c_uint32)]
             lib.or_build_digraph.restype = ctypes.c_int
             lib.or_build_digraph.argtypes = [i64, i64, _i32p, _i32p, _i64p, _i32p, _i64p]
+            lib.or_remote_reads.restype = i64
+            lib.or_remote_reads.argtypes = [i64, _i64p, _i32p, i64, _i32p, _i32p]
+            lib.or_cache_lru.restype = ctypes.c_uint64
+            lib.or_cache_lru.argtypes = [i64, _i32p, _u64p, ctypes.c_uint64, _u64p]
+            lib.or_cache_score.restype = ctypes.c_uint64
+            lib.or_cache_score.argtypes = [i64, _i32p, _u64p, _i64p, ctypes.c_uint64, _u64p]
             lib.or_directed_lcc.restype = None
             lib.or_directed_lcc.argtypes = [i64, _i64p, _i32p, _i32p, i64, _u64p, _f64p]
             _lib = lib
@@ -260,6 +269,85 @@ def directed_lcc(n: int, src, dst, vertices=None) -> dict:
     out = {"c": c, "lcc": l, "out_degree": np.diff(offsets)[vertices]}
     out.update(stats)
     return out
+
+
+def remote_reads(n: int, offsets, adj, parts: int):
+    """Alg. 4 over a 1D partition into ``parts`` processes (process k owns ids
+    [k n / p, (k+1) n / p)): (item int32[N], process int32[N]) of every remote read of an
+    adjacency list, processes in order, each walking its vertices and their sorted
+    adjacency lists in id order."""
+    offsets = _c(offsets, np.int64)
+    adj = _c(adj, np.int32)
+    cap = max(1, adj.size)
+    items = np.empty(cap, dtype=np.int32)
+    part = np.empty(cap, dtype=np.int32)
+    N = _load().or_remote_reads(n, _p(offsets, _i64p), _p(adj, _i32p), parts, _p(items, _i32p), _p(part, _i32p))
+    return items[:N].copy(), part[:N].copy()
+
+
+def cache_lru(items, size_of, capacity: int):
+    """Sec. IV-B, LRU cache of ``capacity`` bytes over one process's reads; entry sizes
+    size_of[item] bytes.  Returns (hits, hit bytes)."""
+    items = _c(items, np.int32)
+    size_of = _c(size_of, np.uint64)
+    hb = ctypes.c_uint64()
+    h = _load().or_cache_lru(items.size, _p(items, _i32p), _p(size_of, _u64p), int(capacity), ctypes.byref(hb))
+    return int(h), int(hb.value)
+
+
+def cache_score(items, size_of, degree, capacity: int):
+    """Sec. IV-B, degree-score cache (victim = lowest (degree, id); a miss is admitted
+    only above every entry evicted so far).  Returns (hits, hit bytes)."""
+    items = _c(items, np.int32)
+    size_of = _c(size_of, np.uint64)
+    degree = _c(degree, np.int64)
+    hb = ctypes.c_uint64()
+    h = _load().or_cache_score(items.size, _p(items, _i32p), _p(size_of, _u64p), _p(degree, _i64p), int(capacity),
+                               ctypes.byref(hb))
+    return int(h), int(hb.value)
+
+
+OFFSET_ENTRY_BYTES = 16  # a (start, end) pair of 64-bit offsets
+
+
+def remote_cache(n: int, src, dst, parts: int, capacities) -> dict:
+    """The remote reads of Alg. 4 on the simple graph of (src, dst) and the four
+    simulated caches of Sec. IV-B at every capacity (bytes).
+
+    Returns {"reads", "top_reads", "distinct", "read_bytes": int64[parts],
+    "hits", "hit_bytes": uint64[4, parts, len(capacities)]} with cache index 0 =
+    adjacency lists / LRU, 1 = adjacency lists / degree score, 2 = offsets / LRU,
+    3 = offsets / degree score; an adjacency entry holds 4 deg(v_j) bytes, an offsets
+    entry 16.  top_reads counts the reads of the ceil(n / 10) vertices of highest
+    (degree, id)."""
+    offsets, adj, _ = build_csr(n, src, dst)
+    deg = np.diff(offsets)
+    items, part = remote_reads(n, offsets, adj, parts)
+    caps = [int(c) for c in capacities]
+    order = sorted(range(n), key=lambda v: (int(deg[v]), v), reverse=True)
+    top = np.zeros(n, dtype=bool)
+    top[order[: (n + 9) // 10]] = True
+    size_adj = (4 * deg).astype(np.uint64)
+    size_off = np.full(n, OFFSET_ENTRY_BYTES, dtype=np.uint64)
+    hits = np.zeros((4, parts, len(caps)), dtype=np.uint64)
+    hit_bytes = np.zeros((4, parts, len(caps)), dtype=np.uint64)
+    reads = np.zeros(parts, dtype=np.int64)
+    top_reads = np.zeros(parts, dtype=np.int64)
+    distinct = np.zeros(parts, dtype=np.int64)
+    read_bytes = np.zeros(parts, dtype=np.int64)
+    for k in range(parts):
+        it = items[part == k]
+        reads[k] = it.size
+        top_reads[k] = int(top[it].sum())
+        distinct[k] = np.unique(it).size
+        read_bytes[k] = int(size_adj[it].sum())
+        for c, cap in enumerate(caps):
+            hits[0, k, c], hit_bytes[0, k, c] = cache_lru(it, size_adj, cap)
+            hits[1, k, c], hit_bytes[1, k, c] = cache_score(it, size_adj, deg, cap)
+            hits[2, k, c], hit_bytes[2, k, c] = cache_lru(it, size_off, cap)
+            hits[3, k, c], hit_bytes[3, k, c] = cache_score(it, size_off, deg, cap)
+    return {"reads": reads, "top_reads": top_reads, "distinct": distinct, "read_bytes": read_bytes,
+            "hits": hits, "hit_bytes": hit_bytes}
 
 
 def lcc(n: int, offsets, t) -> np.ndarray:

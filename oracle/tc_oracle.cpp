@@ -21,6 +21,10 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdint>
+#include <list>
+#include <set>
+#include <unordered_map>
+#include <utility>
 #include <vector>
 
 extern "C" {
@@ -278,6 +282,103 @@ void or_directed_lcc(int64_t n, const int64_t* offsets, const int32_t* adj, cons
         c_out[q] = c;
         lcc_out[q] = d < 2 ? 0.0 : (double)c / (double)(d * (d - 1));
     }
+}
+
+// ---------------------------------------------------------------------------
+// Remote reads of the distributed algorithm (Sec. IV-A, Alg. 4) and their caches
+// (Sec. IV-B).  1D partition: process k owns the ids [floor(k n / p), floor((k+1) n / p)).
+// Process k walks its vertices v_i in id order and, for every v_j in adj(v_i) (sorted,
+// Sec. II-B), reads adj(v_j) remotely when v_j belongs to another process.
+
+// The read stream over a sorted symmetric CSR: item_out[t] = v_j and part_out[t] = k
+// for every remote read, processes in order; returns the number of reads.
+int64_t or_remote_reads(int64_t n, const int64_t* offsets, const int32_t* adj, int64_t parts, int32_t* item_out,
+                        int32_t* part_out) {
+    int64_t t = 0;
+    for (int64_t k = 0; k < parts; ++k) {
+        const int64_t lo = k * n / parts, hi = (k + 1) * n / parts;
+        for (int64_t i = lo; i < hi; ++i)
+            for (int64_t e = offsets[i]; e < offsets[i + 1]; ++e) {
+                const int64_t j = adj[e];
+                if (j < lo || j >= hi) {
+                    item_out[t] = (int32_t)j;
+                    part_out[t] = (int32_t)k;
+                    ++t;
+                }
+            }
+    }
+    return t;
+}
+
+// LRU cache of `capacity` bytes over one process's reads (items[0..count), entry
+// sizes size_of[item] bytes): a hit moves the entry to the front; a miss inserts it at
+// the front and evicts from the back until the entries fit (an entry larger than the
+// cache evicts everything, itself included).  Returns the hits; *hit_bytes gets their
+// bytes.
+uint64_t or_cache_lru(int64_t count, const int32_t* items, const uint64_t* size_of, uint64_t capacity,
+                      uint64_t* hit_bytes) {
+    std::list<int32_t> order;  // front = most recent
+    std::unordered_map<int32_t, std::list<int32_t>::iterator> where;
+    uint64_t used = 0, hits = 0, hb = 0;
+    for (int64_t t = 0; t < count; ++t) {
+        const int32_t x = items[t];
+        auto it = where.find(x);
+        if (it != where.end()) {
+            ++hits;
+            hb += size_of[x];
+            order.splice(order.begin(), order, it->second);
+            continue;
+        }
+        order.push_front(x);
+        where[x] = order.begin();
+        used += size_of[x];
+        while (used > capacity) {
+            const int32_t z = order.back();
+            order.pop_back();
+            where.erase(z);
+            used -= size_of[z];
+        }
+    }
+    *hit_bytes = hb;
+    return hits;
+}
+
+// Degree-score cache (Sec. IV-B, application-defined scores): the victim is the entry
+// of the lowest score, score = (degree, id), and a missing entry is admitted only if
+// its score beats every entry evicted so far (so the cache always holds the
+// highest-scored entries read so far that fit as a prefix in score order).  Returns
+// the hits; *hit_bytes gets their bytes.
+uint64_t or_cache_score(int64_t count, const int32_t* items, const uint64_t* size_of, const int64_t* degree,
+                        uint64_t capacity, uint64_t* hit_bytes) {
+    typedef std::pair<int64_t, int32_t> Score;  // (degree, id)
+    std::set<Score> cache;
+    std::unordered_map<int32_t, bool> in;
+    bool evicted_any = false;
+    Score best_evicted(0, 0);
+    uint64_t used = 0, hits = 0, hb = 0;
+    for (int64_t t = 0; t < count; ++t) {
+        const int32_t x = items[t];
+        const Score sx(degree[x], x);
+        if (in.count(x) && in[x]) {
+            ++hits;
+            hb += size_of[x];
+            continue;
+        }
+        if (evicted_any && !(best_evicted < sx)) continue;  // not admitted
+        cache.insert(sx);
+        in[x] = true;
+        used += size_of[x];
+        while (used > capacity) {
+            const Score z = *cache.begin();
+            cache.erase(cache.begin());
+            in[z.second] = false;
+            used -= size_of[z.second];
+            if (!evicted_any || best_evicted < z) best_evicted = z;
+            evicted_any = true;
+        }
+    }
+    *hit_bytes = hb;
+    return hits;
 }
 
 // Eq. 2: LCC(i) = 2 t(i) / (deg(i) (deg(i) - 1)); 0.0 when deg(i) < 2.  Both the

@@ -468,3 +468,150 @@ def test_directed_sampled_vertices_and_bad_ids():
     np.testing.assert_array_equal(part["c"], full["c"][pick])
     with pytest.raises(ValueError):
         oracle.directed_lcc(3, np.array([0], np.int32), np.array([3], np.int32))
+
+
+# --------------------------------------------------------------------------
+# Remote reads of the 1D-partitioned algorithm (Alg. 4) and their caches (Sec. IV-B)
+
+def _brute_lru_hits(items, size_of, cap):
+    """LRU by its stack property: a read hits iff the item was read before and its size
+    plus the sizes of the distinct other items read since then fit in the cache."""
+    hits = hb = 0
+    last = {}
+    for t, x in enumerate(items):
+        if x in last:
+            seen = set(items[last[x] + 1: t]) - {x}
+            if size_of[x] + sum(size_of[y] for y in seen) <= cap:
+                hits += 1
+                hb += size_of[x]
+        last[x] = t
+    return hits, hb
+
+
+def _brute_score_hits(items, size_of, degree, cap):
+    """Degree score as a priority prefix: a read hits iff the item was read before and
+    the items read before with a score (degree, id) at least its own fit in the cache."""
+    hits = hb = 0
+    seen = set()
+    for x in items:
+        if x in seen:
+            above = [y for y in seen if (degree[y], y) >= (degree[x], x)]
+            if sum(size_of[y] for y in above) <= cap:
+                hits += 1
+                hb += size_of[x]
+        seen.add(x)
+    return hits, hb
+
+
+def test_cache_hand_examples():
+    # LRU, unit entries, 2 slots: A B A C B -> only the second A hits (C evicts B)
+    assert oracle.cache_lru([0, 1, 0, 2, 1], [1, 1, 1], 2) == (1, 1)
+    assert oracle.cache_lru([0, 1, 0, 2, 1], [1, 1, 1], 3) == (2, 2)
+    assert oracle.cache_lru([0, 0, 0], [5], 4) == (0, 0)  # larger than the cache: never held
+    # bytes: sizes 3, 2, 2 in 5 bytes: A B C A -> C evicts A (3 + 2 + 2 > 5), A misses
+    assert oracle.cache_lru([0, 1, 2, 0], [3, 2, 2], 5) == (0, 0)
+    assert oracle.cache_lru([0, 1, 2, 1, 2], [3, 2, 2], 5) == (2, 4)
+    # score, one slot, degrees 3 > 2 > 1: 0 stays, 1 is evicted at once, then neither 2
+    # (below the evicted 1) nor 1 again is admitted
+    assert oracle.cache_score([0, 1, 0, 2, 1], [1, 1, 1], [3, 2, 1], 1) == (1, 1)
+    # a low-score entry read many times loses its slot to a high-score one for good
+    assert oracle.cache_score([2, 2, 0, 2, 2], [1, 1, 1], [3, 2, 1], 1) == (1, 1)
+    assert oracle.cache_lru([2, 2, 0, 2, 2], [1, 1, 1], 1) == (2, 2)
+
+
+@pytest.mark.parametrize("seed", range(40))
+def test_cache_policies_match_their_stack_characterisation(seed):
+    rng = np.random.default_rng(seed)
+    k = int(rng.integers(1, 12))
+    items = rng.integers(0, k, size=int(rng.integers(0, 60))).astype(np.int32)
+    unit = seed % 3 == 0
+    size_of = np.ones(k, np.uint64) if unit else rng.integers(1, 9, size=k).astype(np.uint64)
+    degree = rng.integers(0, 5, size=k).astype(np.int64)
+    s = [int(x) for x in size_of]
+    d = [int(x) for x in degree]
+    lst = [int(x) for x in items]
+    prev_h = (0, 0)
+    for cap in range(0, 2 + int(size_of.sum())):
+        got = oracle.cache_lru(items, size_of, cap)
+        assert got == _brute_lru_hits(lst, s, cap)
+        assert got[0] >= prev_h[0]  # inclusion: a larger cache never hits less
+        prev_h = got
+        assert oracle.cache_score(items, size_of, degree, cap) == _brute_score_hits(lst, s, d, cap)
+    # a cache holding everything misses only the first read of each item
+    big = int(size_of.sum())
+    assert oracle.cache_lru(items, size_of, big)[0] == len(lst) - len(set(lst))
+    assert oracle.cache_score(items, size_of, degree, big)[0] == len(lst) - len(set(lst))
+    assert oracle.cache_lru(items, size_of, 0) == (0, 0)
+
+
+def _cut_reads(n, s, d, parts):
+    """Remote reads counted from the edges: an edge whose ends lie in different
+    processes is read once from each end."""
+    A = F.dense_adjacency(n, s, d)
+    own = np.array([((i + 1) * parts - 1) // n for i in range(n)])
+    per = np.zeros(parts, np.int64)
+    for i in range(n):
+        for j in range(n):
+            if A[i, j] and own[i] != own[j]:
+                per[own[i]] += 1
+    return per, own, A
+
+
+@pytest.mark.parametrize("seed,parts", [(s, p) for s in range(10) for p in (1, 2, 3, 4, 8)])
+def test_remote_reads_match_the_cut(seed, parts):
+    n, s, d = _tiny(seed)
+    offsets, adj, _ = oracle.build_csr(n, s, d)
+    items, part = oracle.remote_reads(n, offsets, adj, parts)
+    per, own, A = _cut_reads(n, s, d, parts)
+    np.testing.assert_array_equal(np.bincount(part, minlength=parts), per)
+    assert (own[items] != part).all()
+    # order: each process walks its vertices and their sorted lists in id order
+    rows = np.repeat(np.arange(n), np.diff(offsets))
+    remote = own[rows] != own[adj]
+    np.testing.assert_array_equal(items, adj[remote])
+
+
+@pytest.mark.parametrize("n,parts", [(8, 2), (12, 3), (16, 4), (9, 1)])
+def test_remote_reads_complete_graph(n, parts):
+    nn, (s, d) = F.complete(n)
+    r = oracle.remote_cache(nn, s, d, parts, [0, 10 ** 9])
+    # every vertex reads the n - n/p vertices of the other processes
+    assert (r["reads"] == (n // parts) * (n - n // parts)).all()
+    assert (r["distinct"] == n - n // parts).all()
+    # unbounded caches miss only the first read of each remote list
+    assert (r["hits"][:, :, 1] == (r["reads"] - r["distinct"])[None, :]).all()
+    assert (r["hits"][:, :, 0] == 0).all()
+    assert (r["read_bytes"] == 4 * (n - 1) * r["reads"]).all()
+
+
+def test_remote_reads_star_top_share():
+    nn, (s, d) = F.star(99)  # hub 0 and 99 leaves; two processes of 50
+    r = oracle.remote_cache(nn, s, d, 2, [4 * 99, 4 * 99 - 1])
+    # process 0 (hub + 49 leaves) reads the 50 leaves of process 1; they read the hub
+    np.testing.assert_array_equal(r["reads"], [50, 50])
+    np.testing.assert_array_equal(r["distinct"], [50, 1])
+    # the top 10 by (degree, id): the hub and leaves 99..91
+    np.testing.assert_array_equal(r["top_reads"], [9, 50])
+    # process 1 reads the hub's 396-byte list 50 times: 49 hits iff it fits
+    assert r["hits"][0, 1, 0] == 49 and r["hits"][0, 1, 1] == 0
+    assert r["hits"][1, 1, 0] == 49 and r["hits"][1, 1, 1] == 0
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_remote_cache_brute_force(seed):
+    n, s, d = _tiny(seed + 20)
+    parts = 2 + seed % 3
+    offsets, adj, _ = oracle.build_csr(n, s, d)
+    deg = [int(x) for x in np.diff(offsets)]
+    caps = [0, 4, 16, 40, 100, 400]
+    r = oracle.remote_cache(n, s, d, parts, caps)
+    items, part = oracle.remote_reads(n, offsets, adj, parts)
+    for k in range(parts):
+        it = [int(x) for x in items[part == k]]
+        for c, cap in enumerate(caps):
+            assert tuple(int(x) for x in (r["hits"][0, k, c], r["hit_bytes"][0, k, c])) == \
+                _brute_lru_hits(it, [4 * x for x in deg], cap)
+            assert tuple(int(x) for x in (r["hits"][1, k, c], r["hit_bytes"][1, k, c])) == \
+                _brute_score_hits(it, [4 * x for x in deg], deg, cap)
+            assert int(r["hits"][2, k, c]) == _brute_lru_hits(it, [16] * n, cap)[0]
+            assert int(r["hits"][3, k, c]) == _brute_score_hits(it, [16] * n, deg, cap)[0]
