@@ -53,7 +53,7 @@ def parse_args():
     p.add_argument("--workload", default="rmat20", choices=sorted(WORKLOAD_TEXT))
     p.add_argument("--e2e-steps", type=int, default=10)
     p.add_argument("--no-cpu-baseline", action="store_true")
-    p.add_argument("--mode", choices=["single", "batch", "serve", "ablation", "directed"], default="single",
+    p.add_argument("--mode", choices=["single", "batch", "serve", "ablation", "directed", "cache"], default="single",
                    help="single: one graph per step; batch: the 20,000-graph batch per step; "
                         "serve: the Poisson request stream through the serving loop")
     p.add_argument("--serve-seconds", type=float, default=60.0)
@@ -746,6 +746,81 @@ def run_directed(args, rank, world, local):
     print(json.dumps(line), flush=True)
 
 
+def run_cache(args, rank, world, local):
+    """Remote reads of the 1D-partitioned algorithm on the workload split over two
+    processes (the configuration of the paper's cache-size study) and the four caches
+    at 100 capacities each, through tc_remote_cache on a resident graph; value = remote
+    reads evaluated per second (each at all 400 cache configurations)."""
+    import numpy as np
+    import torch
+
+    import graphgen
+    import paper_2202_13976_gb300 as tc
+    torch.cuda.set_device(local)
+    tc.load()
+    parts = 2
+    w = graphgen.workload(args.workload)
+    s_h, d_h = w.edges()
+    n = w.n
+    # simple degrees on the host (outside the timed region) for the cache sizes
+    a, b = np.minimum(s_h, d_h).astype(np.int64), np.maximum(s_h, d_h).astype(np.int64)
+    keep = a != b
+    e = np.unique((a[keep] << 32) | b[keep])
+    deg = np.bincount(np.concatenate([e >> 32, e & 0xffffffff]), minlength=n)
+    bounds = [k * n // parts for k in range(parts + 1)]
+    nonlocal_bytes = [4 * int(deg.sum() - deg[bounds[k]:bounds[k + 1]].sum()) for k in range(parts)]
+    graph_bytes = 4 * int(deg.sum())
+    caps = sorted(set(int(x) for x in np.geomspace(1024, graph_bytes, 100)))
+    g = tc.Graph.from_edges(n, torch.from_numpy(s_h).cuda(), torch.from_numpy(d_h).cuda())
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream()
+    for _ in range(max(args.warmup, 3)):
+        r = g.remote_cache(parts, caps)
+    torch.cuda.synchronize()
+    clocks = Clocks(local)
+    launches0 = tc.tc_launch_count()
+    ms = []
+    for _ in range(args.steps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        r2 = g.remote_cache(parts, caps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms.append(e0.elapsed_time(e1))
+        assert (r2["hits"] == r["hits"]).all()
+    launches = tc.tc_launch_count() - launches0
+    clk = clocks.stop()
+    g.close()
+    N = int(r["reads"].sum())
+    ms_per_step = statistics.mean(ms)
+    # the paper's score comparison: C_adj at 25% of each process's non-local partition
+    score_cmp = []
+    for k in range(parts):
+        c = max(i for i, x in enumerate(caps) if x <= nonlocal_bytes[k] // 4)
+        lru, sc = int(r["hits"][0, k, c]), int(r["hits"][1, k, c])
+        score_cmp.append({"process": k, "capacity_bytes": caps[c], "reads": int(r["reads"][k]),
+                          "hits_lru": lru, "hits_score": sc,
+                          "bytes_lru": int(r["hit_bytes"][0, k, c]), "bytes_score": int(r["hit_bytes"][1, k, c])})
+    curve = {kind: [[caps[c], int(r["hits"][i, :, c].sum())] for c in range(0, len(caps), 11)]
+             for i, kind in enumerate(tc.CACHE_KINDS)}
+    if rank != 0:
+        return
+    line = {"metric": "remote reads evaluated/sec (4 caches x 100 sizes)", "value": N / (ms_per_step / 1000.0),
+            "unit": "reads/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "int64", "data": "synthetic",
+            "config": {"workload": args.workload + "_cache_p2", "graph": WORKLOAD_TEXT[args.workload],
+                       "processes": parts, "capacities": len(caps), "reads": r["reads"].tolist(),
+                       "distinct": r["distinct"].tolist(), "top_decile_reads": r["top_reads"].tolist(),
+                       "read_bytes": r["read_bytes"].tolist(), "nonlocal_bytes": nonlocal_bytes,
+                       "l2": "flushed between steps (512 MB write)"},
+            "score_vs_lru_at_25pct_nonlocal": score_cmp, "hits_curve_sample": curve,
+            "gpu_launches": launches, "gpu_launches_per_step": launches / args.steps, "clocks": clk,
+            "impl": "ours"}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse_args()
     rank, world, local = dist_env()
@@ -760,6 +835,9 @@ def main():
         return
     if args.mode == "directed":
         run_directed(args, rank, world, local)
+        return
+    if args.mode == "cache":
+        run_cache(args, rank, world, local)
         return
     if args.mode == "batch":
         if world > 1:

@@ -129,6 +129,40 @@ tc_status tc_count_vertex_formula(tc_graph* g, uint64_t* t_out, int mem_kind, ui
 tc_status tc_edge_support(tc_graph* g, int32_t* u_out, int32_t* v_out, uint32_t* support_out, int mem_kind);
 
 /*
+ * Remote adjacency reads of the distributed algorithm (Sec. IV-A, Alg. 4) and the
+ * caches of Sec. IV-B, for every cache size in one call.  The graph's ids are split
+ * into `parts` processes (1D partition: process k owns [floor(k n / parts),
+ * floor((k+1) n / parts))); process k walks its vertices v_i in id order and every v_j
+ * of the sorted list adj(v_i), and reads adj(v_j) remotely (after its offsets) when
+ * v_j belongs to another process.  Four caches are evaluated per process, each at
+ * every capacity (bytes) of capacity_bytes[0..ncap), which must be non-decreasing:
+ *   TC_CACHE_ADJ_LRU, TC_CACHE_ADJ_SCORE   adjacency lists, an entry of 4 deg(v_j) bytes
+ *   TC_CACHE_OFF_LRU, TC_CACHE_OFF_SCORE   offsets, an entry of 16 bytes
+ * LRU: a miss inserts the entry as the most recent and evicts the least recent until
+ * the entries fit (an entry larger than the cache is never held).  SCORE
+ * (application-defined scores): the victim is the entry of the lowest (degree, id)
+ * and a miss is admitted only if its score beats every entry evicted so far.
+ *   hits, hit_bytes   host uint64[TC_CACHE_KINDS][parts][ncap] or NULL: the reads that
+ *                     hit (and their bytes) per cache, process and capacity
+ *   part_stats        host tc_remote_part[parts] or NULL
+ * The graph's stream is synchronised.  Errors: TC_EINVAL (NULL graph, parts < 1 or >
+ * n, ncap < 0, NULL or decreasing capacities, a graph built from bad ids), TC_ENOMEM,
+ * TC_ECUDA.
+ */
+enum { TC_CACHE_ADJ_LRU = 0, TC_CACHE_ADJ_SCORE = 1, TC_CACHE_OFF_LRU = 2, TC_CACHE_OFF_SCORE = 3,
+       TC_CACHE_KINDS = 4 };
+
+typedef struct tc_remote_part {
+    int64_t reads;       /* remote reads of adjacency lists */
+    int64_t top_reads;   /* of them, reads of the ceil(n / 10) vertices of highest (degree, id) */
+    int64_t distinct;    /* distinct remote vertices read: the first-read misses of every cache */
+    int64_t read_bytes;  /* bytes of the adjacency lists read, 4 deg(v_j) each */
+} tc_remote_part;
+
+tc_status tc_remote_cache(tc_graph* g, int32_t parts, int32_t ncap, const uint64_t* capacity_bytes, uint64_t* hits,
+                          uint64_t* hit_bytes, tc_remote_part* part_stats);
+
+/*
  * Directed local clustering coefficient, Eq. 1 (Sec. II-C), from a directed edge list.
  * Pair k is the edge e_ij from i = src[k] to j = dst[k] (Sec. II-A); self-loops are
  * dropped and a repeated (src, dst) pair is one edge, while (u, v) and (v, u) are two

@@ -33,7 +33,7 @@ EXPORTS = ["tc_graph_create_from_edges", "tc_graph_create_from_csr", "tc_count",
            "tc_graph_set_tuning", "tc_graph_autotune", "tc_batch_run", "tc_release_cached_graphs",
            "tc_generate_edges", "tc_server_start", "tc_server_submit", "tc_server_poll", "tc_server_wait",
            "tc_server_get_stats", "tc_server_stop", "tc_graph_build_timing", "tc_count_vertex_formula",
-           "tc_edge_support", "tc_directed_lcc"]
+           "tc_edge_support", "tc_directed_lcc", "tc_remote_cache"]
 BUILD_PHASES = ["ingest_ms", "rank_ms", "count_ms", "fill_ms", "sort_ms", "degree_ms", "total_ms"]
 TC_GEN_RMAT, TC_GEN_ER_REPLACE = 0, 1
 GEN_KINDS = {"rmat": TC_GEN_RMAT, "er_replace": TC_GEN_ER_REPLACE}
@@ -141,6 +141,8 @@ def load(path: str | None = None):
     lib.tc_count_vertex_formula.argtypes = [P, P, ctypes.c_int, ctypes.POINTER(u64)]
     lib.tc_edge_support.restype = st
     lib.tc_edge_support.argtypes = [P, P, P, P, ctypes.c_int]
+    lib.tc_remote_cache.restype = st
+    lib.tc_remote_cache.argtypes = [P, i32, i32, P, P, P, P]
     lib.tc_directed_lcc.restype = st
     lib.tc_directed_lcc.argtypes = [i32, i64, P, P, ctypes.c_int, P, P, P, ctypes.POINTER(TcDirectedStats),
                                     ctypes.c_int]
@@ -318,6 +320,25 @@ def tc_edge_support(g: int, u_out=None, v_out=None, support_out=None):
     (pu, pv, ps), kind = _ptr_kind(u_out, v_out, support_out)
     _check(_lib.tc_edge_support(g, pu, pv, ps, kind))
     return u_out, v_out, support_out
+
+
+CACHE_KINDS = ["adj_lru", "adj_score", "off_lru", "off_score"]
+
+
+def tc_remote_cache(g: int, parts: int, capacities) -> dict:
+    """Remote reads of a 1D partition into ``parts`` processes and the four caches at
+    every capacity (bytes, non-decreasing): {"hits", "hit_bytes": uint64[4, parts, ncap]
+    (index order CACHE_KINDS), "reads", "top_reads", "distinct", "read_bytes":
+    int64[parts]}."""
+    caps = np.ascontiguousarray(np.asarray(capacities, dtype=np.uint64))
+    ncap = caps.size
+    hits = np.zeros((4, parts, ncap), dtype=np.uint64)
+    hb = np.zeros((4, parts, ncap), dtype=np.uint64)
+    ps = np.zeros((parts, 4), dtype=np.int64)
+    _check(_lib.tc_remote_cache(g, parts, ncap, caps.ctypes.data if ncap else None, hits.ctypes.data,
+                                hb.ctypes.data, ps.ctypes.data))
+    return {"hits": hits, "hit_bytes": hb, "reads": ps[:, 0].copy(), "top_reads": ps[:, 1].copy(),
+            "distinct": ps[:, 2].copy(), "read_bytes": ps[:, 3].copy()}
 
 
 def tc_directed_lcc(n: int, src, dst, c_out=None, lcc_out=None, stream=None, timed=False):
@@ -581,6 +602,10 @@ class Graph:
             order = np.lexsort((v, u))
             u, v, sup = u[order], v[order], sup[order].view(np.uint32)
         return u, v, sup
+
+    def remote_cache(self, parts: int, capacities) -> dict:
+        """Remote reads of a 1D partition and the caches of Sec. IV-B (tc_remote_cache)."""
+        return tc_remote_cache(self.handle, parts, capacities)
 
     def info(self) -> dict:
         return tc_graph_info(self.handle)

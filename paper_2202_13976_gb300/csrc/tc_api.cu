@@ -727,6 +727,119 @@ tc_status tc_edge_support(tc_graph* g, int32_t* u_out, int32_t* v_out, uint32_t*
     return TC_OK;
 }
 
+tc_status tc_remote_cache(tc_graph* g, int32_t parts, int32_t ncap, const uint64_t* capacity_bytes, uint64_t* hits,
+                          uint64_t* hit_bytes, tc_remote_part* part_stats) {
+    if (!g || parts < 1 || (g->n > 0 && parts > g->n) || (g->n == 0 && parts != 1) || ncap < 0 ||
+        (ncap > 0 && !capacity_bytes))
+        return TC_EINVAL;
+    for (int32_t c = 1; c < ncap; ++c)
+        if (capacity_bytes[c] < capacity_bytes[c - 1]) return TC_EINVAL;
+    DevStats h;
+    tc_status st = read_stats(g, &h);
+    if (st != TC_OK) return st;
+    if (h.err & ERR_BAD_ID) return TC_EINVAL;
+    const size_t cells = (size_t)TC_CACHE_KINDS * (size_t)parts * (size_t)ncap;
+    if (hits) memset(hits, 0, sizeof(uint64_t) * cells);
+    if (hit_bytes) memset(hit_bytes, 0, sizeof(uint64_t) * cells);
+    if (part_stats) memset(part_stats, 0, sizeof(tc_remote_part) * (size_t)parts);
+    const int64_t ms = (int64_t)h.m_simple;
+    if (g->n == 0 || ms == 0) return TC_OK;
+    const size_t nn = (size_t)g->n;
+    RemoteCacheBuffers R{};
+    R.n = g->n;
+    R.parts = parts;
+    R.ncap = ncap;
+    R.ms2 = 2 * ms;
+    R.rank = g->rank;
+    R.rowstart = g->rowstart;
+    R.rowlen = g->rowlen;
+    R.col = g->col;
+    R.deg = g->deg;
+    const int64_t big = R.ms2 > (int64_t)nn ? R.ms2 : (int64_t)nn;
+    std::vector<void*> tmp;
+    char *rtmp = nullptr, *stmp = nullptr;
+    uint64_t* dcaps = nullptr;
+    if ((st = dalloc(g, &R.id_of, nn, &tmp)) || (st = dalloc(g, &R.sdeg, nn, &tmp)) ||
+        (st = dalloc(g, &R.prank, nn, &tmp)) || (st = dalloc(g, &R.vkeys, nn, &tmp)) ||
+        (st = dalloc(g, &R.vkeys_alt, nn, &tmp)) || (st = dalloc(g, &R.estart, nn + 1, &tmp)) ||
+        (st = dalloc(g, &R.keys, (size_t)R.ms2, &tmp)) || (st = dalloc(g, &R.keys_alt, (size_t)R.ms2, &tmp)) ||
+        (st = dalloc(g, &R.flag, (size_t)R.ms2, &tmp)) || (st = dalloc(g, &R.pos, (size_t)R.ms2 + 1, &tmp)) ||
+        (st = dalloc(g, &R.item, (size_t)R.ms2, &tmp)) || (st = dalloc(g, &R.part, (size_t)R.ms2, &tmp)) ||
+        (st = dalloc(g, &R.pc, (size_t)parts, &tmp)) || (st = dalloc(g, &rtmp, radix_tmp_bytes(big), &tmp)) ||
+        (st = dalloc(g, &stmp, scan_tmp_bytes(big + 1), &tmp)) || (st = dalloc(g, &dcaps, (size_t)ncap, &tmp)) ||
+        (st = dalloc(g, &R.cnt, cells, &tmp)) || (st = dalloc(g, &R.byt, cells, &tmp))) {
+        free_list(g, &tmp);
+        return st;
+    }
+    R.radix_tmp = rtmp;
+    R.scan_tmp = stmp;
+    R.caps = dcaps;
+    cudaError_t e = cudaSuccess;
+    if (ncap > 0) e = cudaMemcpyAsync(dcaps, capacity_bytes, sizeof(uint64_t) * (size_t)ncap, cudaMemcpyHostToDevice,
+                                      g->stream);
+    cudaMemsetAsync(R.pc, 0, sizeof(PartCounters) * (size_t)parts, g->stream);
+    cudaMemsetAsync(R.cnt, 0, sizeof(unsigned long long) * cells, g->stream);
+    cudaMemsetAsync(R.byt, 0, sizeof(unsigned long long) * cells, g->stream);
+    launch_rc_stream(R, g->L);
+    uint32_t N32 = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&N32, R.pos + R.ms2, sizeof(uint32_t), cudaMemcpyDeviceToHost, g->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(g->stream);
+    if (e != cudaSuccess) {
+        free_list(g, &tmp);
+        return cuda_fail("tc_remote_cache: reads", e);
+    }
+    const int64_t N = (int64_t)N32;
+    if (N > 0) {
+        const size_t n1 = (size_t)N;
+        if ((st = dalloc(g, &R.prev, n1, &tmp)) || (st = dalloc(g, &R.pstart, (size_t)parts + 1, &tmp)) ||
+            (st = dalloc(g, &R.key_lru, n1, &tmp)) || (st = dalloc(g, &R.key_score, n1, &tmp)) ||
+            (st = dalloc(g, &R.wdeg, n1, &tmp)) || (st = dalloc(g, &R.wone, n1, &tmp)) ||
+            (st = dalloc(g, &R.q_lru, n1, &tmp)) || (st = dalloc(g, &R.th_lru, n1, &tmp)) ||
+            (st = dalloc(g, &R.q_score, 2 * n1, &tmp)) || (st = dalloc(g, &R.th_score, 2 * n1, &tmp)) ||
+            (st = dalloc(g, &R.e0deg, n1 + 1, &tmp)) || (st = dalloc(g, &R.lk[0], n1, &tmp)) ||
+            (st = dalloc(g, &R.lk[1], n1, &tmp)) || (st = dalloc(g, &R.la[0], n1, &tmp)) ||
+            (st = dalloc(g, &R.la[1], n1, &tmp)) || (st = dalloc(g, &R.lb[0], n1, &tmp)) ||
+            (st = dalloc(g, &R.lb[1], n1, &tmp)) || (st = dalloc(g, &R.ea, n1 + 1, &tmp)) ||
+            (st = dalloc(g, &R.eb, n1 + 1, &tmp)) || (st = dalloc(g, &R.f_lru_deg, n1, &tmp)) ||
+            (st = dalloc(g, &R.f_lru_one, n1, &tmp)) || (st = dalloc(g, &R.f_sc_deg, 2 * n1, &tmp)) ||
+            (st = dalloc(g, &R.f_sc_one, 2 * n1, &tmp))) {
+            free_list(g, &tmp);
+            return st;
+        }
+        launch_rc_caches(R, N, g->L);
+    }
+    std::vector<unsigned long long> hc(cells), hb(cells);
+    std::vector<PartCounters> hp((size_t)parts);
+    e = cudaGetLastError();
+    if (e == cudaSuccess && cells)
+        e = cudaMemcpyAsync(hc.data(), R.cnt, sizeof(unsigned long long) * cells, cudaMemcpyDeviceToHost, g->stream);
+    if (e == cudaSuccess && cells)
+        e = cudaMemcpyAsync(hb.data(), R.byt, sizeof(unsigned long long) * cells, cudaMemcpyDeviceToHost, g->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(hp.data(), R.pc, sizeof(PartCounters) * (size_t)parts, cudaMemcpyDeviceToHost, g->stream);
+    free_list(g, &tmp);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(g->stream);
+    if (e != cudaSuccess) return cuda_fail("tc_remote_cache", e);
+    // a read that fits capacity c fits every larger one: hits are prefix sums over c
+    for (size_t row = 0; ncap > 0 && row < (size_t)TC_CACHE_KINDS * (size_t)parts; ++row) {
+        uint64_t sc = 0, sb = 0;
+        for (int32_t c = 0; c < ncap; ++c) {
+            sc += hc[row * (size_t)ncap + (size_t)c];
+            sb += hb[row * (size_t)ncap + (size_t)c];
+            if (hits) hits[row * (size_t)ncap + (size_t)c] = sc;
+            if (hit_bytes) hit_bytes[row * (size_t)ncap + (size_t)c] = sb;
+        }
+    }
+    if (part_stats)
+        for (int32_t k = 0; k < parts; ++k) {
+            part_stats[k].reads = (int64_t)hp[(size_t)k].reads;
+            part_stats[k].top_reads = (int64_t)hp[(size_t)k].top_reads;
+            part_stats[k].distinct = (int64_t)hp[(size_t)k].distinct;
+            part_stats[k].read_bytes = (int64_t)hp[(size_t)k].read_bytes;
+        }
+    return TC_OK;
+}
+
 tc_status tc_graph_info(const tc_graph* g, int64_t* m_simple, int64_t* loops_dropped, int64_t* dups_dropped) {
     if (!g) return TC_EINVAL;
     DevStats h;

@@ -1,0 +1,449 @@
+// Remote adjacency reads of the distributed algorithm (Sec. IV-A, Alg. 4) and the
+// caches of Sec. IV-B, evaluated for many cache sizes at once.
+//
+// 1D partition: process k owns the ids [floor(k n / p), floor((k+1) n / p)).  Process k
+// walks its vertices v_i in id order and every v_j of the sorted list adj(v_i); when
+// v_j belongs to another process it reads adj(v_j) remotely (4 deg(v_j) bytes) after
+// reading the offsets of v_j (one 16-byte entry).  Two caches sit in front of the two
+// remote windows (adjacency lists, offsets), each under two policies:
+//  - LRU: a miss inserts the entry as the most recent and evicts the least recent
+//    until the entries fit.  Whatever the size, the cache holds the longest run of
+//    most recently read entries that fits, so the read at time t of x hits a cache of
+//    K bytes iff x was read before (at p = prev(t)) and
+//      D(t) = size(x) + sum of the sizes of the distinct entries read in (p, t) <= K.
+//    The distinct entries of (p, t) are the reads t' in (p, t) with prev(t') < p, so
+//      D(t) = size(x) + F(t, p) - S(p),  F(t, p) = sum over t' < t with prev(t') < p,
+//    S(p) = sum over t' <= p (every such t' has prev(t') < p);
+//  - degree score: the victim is the entry of the lowest (degree, id) and a miss is
+//    admitted only above every entry evicted so far, so the cache holds the
+//    highest-scored entries read so far that fit as a prefix in score order: the read
+//    of x hits iff x was read before and the entries first read before t with a score
+//    at least x's fit:  Q(t) = sum over first reads t' in [start of the process, t)
+//    with score(t') >= score(x) <= K.
+// F and Q are sums over points (t', key(t')) dominated by a query (t, threshold):
+// answered for all reads together by a merge-sort tree over time, level by level
+// (level l holds the keys sorted within aligned blocks of 2^l reads, with prefix sums
+// of the weights); [0, t) splits into one block per set bit of t.
+#include <cuda_runtime.h>
+
+#include <climits>
+#include <cstring>
+#include <vector>
+
+#include "tc_device.cuh"
+#include "tc_internal.h"
+
+namespace tcg {
+namespace {
+
+constexpr int RC_THREADS = 256;
+constexpr uint32_t RC_NEVER = 0xffffffffu;  // a key no threshold counts
+
+__host__ __device__ __forceinline__ int32_t owner_of(int64_t i, int64_t n, int64_t parts) {
+    return (int32_t)(((i + 1) * parts - 1) / n);
+}
+
+__global__ void k_rc_id_of(int32_t n, const int32_t* __restrict__ rank, int32_t* __restrict__ id_of) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride) id_of[rank[v]] = (int32_t)v;
+}
+
+// Simple degree per id, and score keys (degree << b) | id: a stable sort of the degree
+// field orders the ids by (degree, id); prank[id] = position.
+__global__ void k_rc_score_keys(int32_t n, const int32_t* __restrict__ rank, const int32_t* __restrict__ deg_rank,
+                                int b, uint32_t* __restrict__ sdeg, uint64_t* __restrict__ vkeys) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride) {
+        const uint32_t d = (uint32_t)deg_rank[rank[v]];
+        sdeg[v] = d;
+        vkeys[v] = ((uint64_t)d << b) | (uint64_t)v;
+    }
+}
+
+__global__ void k_rc_prank(int32_t n, const uint64_t* __restrict__ vsorted, int b, int32_t* __restrict__ prank) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const uint64_t mask = (1ull << b) - 1;
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += stride)
+        prank[vsorted[p] & mask] = (int32_t)p;
+}
+
+// Both directions of every oriented entry as id keys (i << b) | j, at 2 (estart[r] + p).
+__global__ void k_rc_sym_keys(int32_t n, const int64_t* __restrict__ rowstart, const int32_t* __restrict__ rowlen,
+                              const int32_t* __restrict__ col, const int64_t* __restrict__ estart,
+                              const int32_t* __restrict__ id_of, int b, uint64_t* __restrict__ keys) {
+    const int lane = lane_id();
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t r = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; r < n; r += warps) {
+        const int d = rowlen[r];
+        const int64_t a0 = rowstart[r], e0 = estart[r];
+        const uint64_t iu = (uint32_t)id_of[r];
+        for (int p = lane; p < d; p += 32) {
+            const uint64_t iv = (uint32_t)id_of[col[a0 + p]];
+            keys[2 * (e0 + p)] = (iu << b) | iv;
+            keys[2 * (e0 + p) + 1] = (iv << b) | iu;
+        }
+    }
+}
+
+// flag[s] = 1 for a symmetric entry (i, j) whose ends lie in different processes.
+__global__ void k_rc_remote_flags(int64_t ms2, const uint64_t* __restrict__ sym, int b, int32_t n, int32_t parts,
+                                  uint32_t* __restrict__ flag) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const uint64_t mask = (1ull << b) - 1;
+    for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < ms2; s += stride) {
+        const uint64_t key = sym[s];
+        flag[s] = owner_of((int64_t)(key >> b), n, parts) != owner_of((int64_t)(key & mask), n, parts) ? 1u : 0u;
+    }
+}
+
+// Adds v to field[k] once per group of lanes that share k (k < 0: nothing); every lane
+// of the warp calls it.
+__device__ __forceinline__ void part_add3(int32_t k, unsigned long long v0, unsigned long long v1,
+                                          unsigned long long v2, unsigned long long* f0, unsigned long long* f1,
+                                          unsigned long long* f2) {
+    unsigned pending = __ballot_sync(FULL, k >= 0);
+    while (pending) {
+        const int leader = __ffs(pending) - 1;
+        const int32_t kl = __shfl_sync(FULL, k, leader);
+        const bool mine = k == kl;
+        const unsigned long long s0 = warp_sum(mine ? v0 : 0ull);
+        const unsigned long long s1 = warp_sum(mine ? v1 : 0ull);
+        const unsigned long long s2 = warp_sum(mine ? v2 : 0ull);
+        if (lane_id() == leader) {
+            if (s0 && f0) atomicAdd(f0 + 4 * kl, s0);
+            if (s1 && f1) atomicAdd(f1 + 4 * kl, s1);
+            if (s2 && f2) atomicAdd(f2 + 4 * kl, s2);
+        }
+        pending &= ~__ballot_sync(FULL, mine);
+    }
+}
+
+// The read stream: item[t] = v_j, part[t] = process of v_i, in (i, j) order; per-process
+// reads, reads of the top decile (score rank >= n - ceil(n / 10)) and bytes.
+__global__ void k_rc_stream(int64_t ms2, const uint64_t* __restrict__ sym, int b, int32_t n, int32_t parts,
+                            const uint32_t* __restrict__ flag, const uint32_t* __restrict__ pos,
+                            const int32_t* __restrict__ prank, const uint32_t* __restrict__ sdeg,
+                            int32_t* __restrict__ item, int32_t* __restrict__ part, PartCounters* __restrict__ pc) {
+    const int lane = lane_id();
+    const int64_t warp0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t wstride = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const uint64_t mask = (1ull << b) - 1;
+    const int32_t top_rank = n - (int32_t)(((int64_t)n + 9) / 10);  // ranks >= this: the top decile
+    for (int64_t base = warp0 * 32; base < ms2; base += wstride * 32) {  // uniform per warp
+        const int64_t s = base + lane;
+        int32_t k = -1;
+        unsigned long long top = 0, bytes = 0;
+        if (s < ms2 && flag[s]) {
+            const uint64_t key = sym[s];
+            const int32_t i = (int32_t)(key >> b), j = (int32_t)(key & mask);
+            const int64_t t = pos[s];
+            k = owner_of(i, n, parts);
+            item[t] = j;
+            part[t] = k;
+            top = prank[j] >= top_rank ? 1 : 0;
+            bytes = 4ull * (unsigned long long)sdeg[j];
+        }
+        part_add3(k, 1ull, top, bytes, &pc->reads, &pc->top_reads, &pc->read_bytes);
+    }
+}
+
+// Reuse keys (item << 32) | t: a stable sort of the item field lists every item's
+// reads in time order.
+__global__ void k_rc_item_keys(int64_t N, const int32_t* __restrict__ item, uint64_t* __restrict__ keys) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < N; t += stride)
+        keys[t] = ((uint64_t)(uint32_t)item[t] << 32) | (uint64_t)t;
+}
+
+// prev[t] = the previous read of the same item by the same process (-1: first read).
+// The processes' reads are contiguous in time, so it is the item's previous read when
+// that read belongs to the same process.
+__global__ void k_rc_prev(int64_t N, const uint64_t* __restrict__ sorted, const int32_t* __restrict__ part,
+                          int64_t* __restrict__ prev) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < N; s += stride) {
+        const uint64_t key = sorted[s];
+        const int64_t t = (int64_t)(key & 0xffffffffull);
+        int64_t p = -1;
+        if (s > 0) {
+            const uint64_t q = sorted[s - 1];
+            const int64_t tq = (int64_t)(q & 0xffffffffull);
+            if ((q >> 32) == (key >> 32) && part[tq] == part[t]) p = tq;
+        }
+        prev[t] = p;
+    }
+}
+
+// Inputs of the two dominance sums and their queries:
+//  LRU:   key = prev + 1, weights (deg, 1); query (t, prev(t) + 1) for every read.
+//  score: key = n - 1 - score rank for a first read (RC_NEVER otherwise), weights
+//         (deg, 1); queries (t, n - score rank(x)) and (start of the process, same).
+__global__ void k_rc_inputs(int64_t N, int32_t n, const int32_t* __restrict__ item, const int32_t* __restrict__ part,
+                            const int64_t* __restrict__ prev, const int64_t* __restrict__ pstart,
+                            const int32_t* __restrict__ prank, const uint32_t* __restrict__ sdeg,
+                            uint32_t* __restrict__ key_lru, uint32_t* __restrict__ key_score,
+                            uint32_t* __restrict__ wdeg, uint32_t* __restrict__ wone,
+                            int64_t* __restrict__ q_lru, uint32_t* __restrict__ th_lru,
+                            int64_t* __restrict__ q_score, uint32_t* __restrict__ th_score,
+                            PartCounters* __restrict__ pc) {
+    const int lane = lane_id();
+    const int64_t warp0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t wstride = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t base = warp0 * 32; base < N; base += wstride * 32) {  // uniform per warp
+        const int64_t t = base + lane;
+        int32_t first_k = -1;
+        if (t < N) {
+            const int32_t x = item[t];
+            const int32_t r = prank[x];
+            const int64_t p = prev[t];
+            key_lru[t] = (uint32_t)(p + 1);
+            key_score[t] = p < 0 ? (uint32_t)(n - 1 - r) : RC_NEVER;
+            wdeg[t] = sdeg[x];
+            wone[t] = 1u;
+            q_lru[t] = t;
+            th_lru[t] = (uint32_t)(p + 1);
+            q_score[2 * t] = t;
+            q_score[2 * t + 1] = pstart[part[t]];
+            th_score[2 * t] = th_score[2 * t + 1] = (uint32_t)(n - r);
+            if (p < 0) first_k = part[t];
+        }
+        part_add3(first_k, 1ull, 0ull, 0ull, &pc->distinct, nullptr, nullptr);
+    }
+}
+
+// pstart[k] = first read of process k (k = 0 .. parts).
+__global__ void k_rc_pstart(int64_t N, int32_t parts, const int32_t* __restrict__ part, int64_t* __restrict__ pstart) {
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k <= parts; k += (int64_t)gridDim.x * blockDim.x) {
+        int64_t lo = 0, hi = N;
+        while (lo < hi) {
+            const int64_t mid = (lo + hi) >> 1;
+            if (part[mid] < k)
+                lo = mid + 1;
+            else
+                hi = mid;
+        }
+        pstart[k] = lo;
+    }
+}
+
+// Level l -> l + 1 of the merge-sort tree: the two sorted halves of each block of
+// 2^(l+1) reads are merged (stable: the left half first among equal keys).
+__global__ void k_rc_merge(int64_t N, int l, const uint32_t* __restrict__ key, const uint32_t* __restrict__ wa,
+                           const uint32_t* __restrict__ wb, uint32_t* __restrict__ key2, uint32_t* __restrict__ wa2,
+                           uint32_t* __restrict__ wb2) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int64_t B = (int64_t)1 << l;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += stride) {
+        const int64_t base = (i >> (l + 1)) << (l + 1);
+        const bool left = i - base < B;
+        const uint32_t x = key[i];
+        int64_t lo, hi;
+        if (left) {  // count the right half's keys < x
+            lo = base + B;
+            hi = min(base + 2 * B, N);
+            const int64_t r0 = lo;
+            while (lo < hi) {
+                const int64_t mid = (lo + hi) >> 1;
+                if (key[mid] < x)
+                    lo = mid + 1;
+                else
+                    hi = mid;
+            }
+            const int64_t out = base + (i - base) + (lo - r0);
+            key2[out] = x;
+            wa2[out] = wa[i];
+            wb2[out] = wb[i];
+        } else {  // count the left half's keys <= x
+            lo = base;
+            hi = base + B;
+            while (lo < hi) {
+                const int64_t mid = (lo + hi) >> 1;
+                if (key[mid] <= x)
+                    lo = mid + 1;
+                else
+                    hi = mid;
+            }
+            const int64_t out = base + (i - base - B) + (lo - base);
+            key2[out] = x;
+            wa2[out] = wa[i];
+            wb2[out] = wb[i];
+        }
+    }
+}
+
+// Queries at level l: for a query (q, th) with bit l of q set, the block
+// [(q >> (l+1)) << (l+1), + 2^l) of level l adds the weights of its keys < th.
+__global__ void k_rc_query(int64_t M, int l, const int64_t* __restrict__ q, const uint32_t* __restrict__ th,
+                           const uint32_t* __restrict__ key, const int64_t* __restrict__ ea,
+                           const int64_t* __restrict__ eb, int64_t* __restrict__ sa, int64_t* __restrict__ sb) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < M; i += stride) {
+        const int64_t qi = q[i];
+        if (!((qi >> l) & 1)) continue;
+        const int64_t start = (qi >> (l + 1)) << (l + 1);
+        int64_t lo = start, hi = start + ((int64_t)1 << l);
+        const uint32_t x = th[i];
+        while (lo < hi) {
+            const int64_t mid = (lo + hi) >> 1;
+            if (key[mid] < x)
+                lo = mid + 1;
+            else
+                hi = mid;
+        }
+        sa[i] += ea[lo] - ea[start];
+        sb[i] += eb[lo] - eb[start];
+    }
+}
+
+// Hits per (cache, process, first capacity that holds the read).
+__global__ void k_rc_hist(int64_t N, int32_t parts, int ncap, const uint64_t* __restrict__ caps,
+                          const int32_t* __restrict__ part, const int64_t* __restrict__ prev,
+                          const uint32_t* __restrict__ wdeg, const int64_t* __restrict__ pstart,
+                          const int64_t* __restrict__ e0deg, const int64_t* __restrict__ f_lru_deg,
+                          const int64_t* __restrict__ f_lru_one, const int64_t* __restrict__ f_sc_deg,
+                          const int64_t* __restrict__ f_sc_one, unsigned long long* __restrict__ cnt,
+                          unsigned long long* __restrict__ byt) {
+    extern __shared__ unsigned long long sh[];
+    const int cells = 4 * parts * ncap;
+    const bool local = cells <= RC_HIST_SHARED;
+    unsigned long long* scnt = sh;
+    unsigned long long* sbyt = sh + (local ? cells : 0);
+    if (local)
+        for (int i = threadIdx.x; i < 2 * cells; i += blockDim.x) sh[i] = 0;
+    __syncthreads();
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < N; t += stride) {
+        const int64_t p = prev[t];
+        if (p < 0) continue;  // a first read misses every cache
+        const int k = part[t];
+        const uint64_t d = wdeg[t];  // deg(v_j)
+        uint64_t need[4], size[4];
+        need[0] = 4 * (d + (uint64_t)(f_lru_deg[t] - e0deg[p + 1]));      // adjacency, LRU
+        need[1] = 4 * (uint64_t)(f_sc_deg[2 * t] - f_sc_deg[2 * t + 1]);  // adjacency, score
+        need[2] = 16 * (1 + (uint64_t)(f_lru_one[t] - (p + 1)));           // offsets, LRU
+        need[3] = 16 * (uint64_t)(f_sc_one[2 * t] - f_sc_one[2 * t + 1]);  // offsets, score
+        size[0] = size[1] = 4 * d;
+        size[2] = size[3] = 16;
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            int lo = 0, hi = ncap;  // first capacity >= need
+            while (lo < hi) {
+                const int mid = (lo + hi) >> 1;
+                if (caps[mid] < need[c])
+                    lo = mid + 1;
+                else
+                    hi = mid;
+            }
+            if (lo == ncap) continue;
+            const int cell = (c * parts + k) * ncap + lo;
+            if (local) {
+                atomicAdd(&scnt[cell], 1ull);
+                atomicAdd(&sbyt[cell], (unsigned long long)size[c]);
+            } else {
+                atomicAdd(&cnt[cell], 1ull);
+                atomicAdd(&byt[cell], (unsigned long long)size[c]);
+            }
+        }
+    }
+    if (local) {
+        __syncthreads();
+        for (int i = threadIdx.x; i < cells; i += blockDim.x) {
+            if (scnt[i]) atomicAdd(&cnt[i], scnt[i]);
+            if (sbyt[i]) atomicAdd(&byt[i], sbyt[i]);
+        }
+    }
+}
+
+}  // namespace
+
+int rc_key_bits(int32_t n) {
+    int b = 1;
+    while (b < 31 && ((int64_t)1 << b) < (int64_t)n) ++b;
+    return b;
+}
+
+void launch_rc_stream(const RemoteCacheBuffers& R, const Launch& L) {
+    const int sms = L.sms;
+    const int b = rc_key_bits(R.n);
+    k_rc_id_of<<<grid_for(R.n, RC_THREADS, sms), RC_THREADS, 0, L.stream>>>(R.n, R.rank, R.id_of);
+    count_launch();
+    k_rc_score_keys<<<grid_for(R.n, RC_THREADS, sms), RC_THREADS, 0, L.stream>>>(R.n, R.rank, R.deg, b, R.sdeg,
+                                                                                 R.vkeys);
+    count_launch();
+    uint64_t* vs = radix_sort_u64(R.vkeys, R.vkeys_alt, R.n, b, 2 * b, R.radix_tmp, L);
+    k_rc_prank<<<grid_for(R.n, RC_THREADS, sms), RC_THREADS, 0, L.stream>>>(R.n, vs, b, R.prank);
+    count_launch();
+    scan_u32_to_i64(reinterpret_cast<const uint32_t*>(R.rowlen), R.estart, R.n, R.scan_tmp, L);
+    k_rc_sym_keys<<<grid_for((int64_t)R.n * 32, RC_THREADS, sms), RC_THREADS, 0, L.stream>>>(
+        R.n, R.rowstart, R.rowlen, R.col, R.estart, R.id_of, b, R.keys);
+    count_launch();
+    uint64_t* sym = radix_sort_u64(R.keys, R.keys_alt, R.ms2, 0, 2 * b, R.radix_tmp, L);
+    k_rc_remote_flags<<<grid_for(R.ms2, RC_THREADS, sms), RC_THREADS, 0, L.stream>>>(R.ms2, sym, b, R.n, R.parts,
+                                                                                     R.flag);
+    count_launch();
+    scan_u32_to_u32(R.flag, R.pos, R.ms2, R.scan_tmp, L);
+    k_rc_stream<<<grid_for(R.ms2, RC_THREADS, sms), RC_THREADS, 0, L.stream>>>(
+        R.ms2, sym, b, R.n, R.parts, R.flag, R.pos, R.prank, R.sdeg, R.item, R.part, R.pc);
+    count_launch();
+}
+
+void launch_rc_caches(const RemoteCacheBuffers& R, int64_t N, const Launch& L) {
+    const int sms = L.sms;
+    const int b = rc_key_bits(R.n);
+    // previous reads
+    k_rc_item_keys<<<grid_for(N, RC_THREADS, sms), RC_THREADS, 0, L.stream>>>(N, R.item, R.keys);
+    count_launch();
+    uint64_t* byitem = radix_sort_u64(R.keys, R.keys_alt, N, 32, 32 + b, R.radix_tmp, L);
+    k_rc_prev<<<grid_for(N, RC_THREADS, sms), RC_THREADS, 0, L.stream>>>(N, byitem, R.part, R.prev);
+    count_launch();
+    k_rc_pstart<<<1, RC_THREADS, 0, L.stream>>>(N, R.parts, R.part, R.pstart);
+    count_launch();
+    k_rc_inputs<<<grid_for(N, RC_THREADS, sms), RC_THREADS, 0, L.stream>>>(
+        N, R.n, R.item, R.part, R.prev, R.pstart, R.prank, R.sdeg, R.key_lru, R.key_score, R.wdeg, R.wone, R.q_lru,
+        R.th_lru, R.q_score, R.th_score, R.pc);
+    count_launch();
+    // S(p): prefix sums of the weights in time order (level 0)
+    scan_u32_to_i64(R.wdeg, R.e0deg, N, R.scan_tmp, L);
+    // the two merge-sort trees, one after the other, in the same level buffers
+    for (int tree = 0; tree < 2; ++tree) {
+        uint32_t* key = R.lk[0];
+        uint32_t* wa = R.la[0];
+        uint32_t* wb = R.lb[0];
+        uint32_t* key2 = R.lk[1];
+        uint32_t* wa2 = R.la[1];
+        uint32_t* wb2 = R.lb[1];
+        cudaMemcpyAsync(key, tree == 0 ? R.key_lru : R.key_score, sizeof(uint32_t) * (size_t)N,
+                        cudaMemcpyDeviceToDevice, L.stream);
+        cudaMemcpyAsync(wa, R.wdeg, sizeof(uint32_t) * (size_t)N, cudaMemcpyDeviceToDevice, L.stream);
+        cudaMemcpyAsync(wb, R.wone, sizeof(uint32_t) * (size_t)N, cudaMemcpyDeviceToDevice, L.stream);
+        const int64_t M = tree == 0 ? N : 2 * N;
+        int64_t* sa = tree == 0 ? R.f_lru_deg : R.f_sc_deg;
+        int64_t* sb = tree == 0 ? R.f_lru_one : R.f_sc_one;
+        cudaMemsetAsync(sa, 0, sizeof(int64_t) * (size_t)M, L.stream);
+        cudaMemsetAsync(sb, 0, sizeof(int64_t) * (size_t)M, L.stream);
+        for (int l = 0; ((int64_t)1 << l) <= N; ++l) {
+            scan_u32_to_i64(wa, R.ea, N, R.scan_tmp, L);
+            scan_u32_to_i64(wb, R.eb, N, R.scan_tmp, L);
+            k_rc_query<<<grid_for(M, RC_THREADS, sms), RC_THREADS, 0, L.stream>>>(
+                M, l, tree == 0 ? R.q_lru : R.q_score, tree == 0 ? R.th_lru : R.th_score, key, R.ea, R.eb, sa, sb);
+            count_launch();
+            if (((int64_t)1 << (l + 1)) <= N) {
+                k_rc_merge<<<grid_for(N, RC_THREADS, sms), RC_THREADS, 0, L.stream>>>(N, l, key, wa, wb, key2, wa2,
+                                                                                      wb2);
+                count_launch();
+                uint32_t* t;
+                t = key, key = key2, key2 = t;
+                t = wa, wa = wa2, wa2 = t;
+                t = wb, wb = wb2, wb2 = t;
+            }
+        }
+    }
+    const int cells = 4 * R.parts * R.ncap;
+    const size_t shmem = cells <= RC_HIST_SHARED ? 2 * sizeof(unsigned long long) * (size_t)cells : 0;
+    k_rc_hist<<<grid_for(N, RC_THREADS, sms, 4), RC_THREADS, shmem, L.stream>>>(
+        N, R.parts, R.ncap, R.caps, R.part, R.prev, R.wdeg, R.pstart, R.e0deg, R.f_lru_deg, R.f_lru_one, R.f_sc_deg,
+        R.f_sc_one, R.cnt, R.byt);
+    count_launch();
+}
+
+}  // namespace tcg

@@ -214,6 +214,62 @@ void launch_vertex_formula(const VertexFormulaBuffers& V, const Launch& L);
 void launch_edge_support(const VertexFormulaBuffers& V, const int32_t* rank, int32_t* id_of, int64_t* estart,
                          int32_t* eu, int32_t* ev, uint32_t* support, const Launch& L);
 
+// ---- remote reads and caches of the 1D partition (tc_cache.cu) -------------------
+struct PartCounters {  // per process; four 64-bit fields, nothing else (indexed as such)
+    unsigned long long reads, top_reads, distinct, read_bytes;
+};
+static_assert(sizeof(PartCounters) == 32, "PartCounters layout");
+
+// Cells of the shared-memory hit histogram (4 caches x processes x capacities).
+constexpr int RC_HIST_SHARED = 3072;
+
+struct RemoteCacheBuffers {
+    int32_t n, parts, ncap;
+    int64_t ms2;                 // symmetric entries (2 m)
+    const int32_t* rank;         // graph: id -> rank
+    const int64_t* rowstart;     // graph: oriented rows (rank space)
+    const int32_t* rowlen;
+    const int32_t* col;
+    const int32_t* deg;          // graph: simple degree (rank space)
+    const uint64_t* caps;        // ncap capacities in bytes, ascending (device)
+    // stream phase
+    int32_t* id_of;              // n
+    uint32_t* sdeg;              // n: simple degree per id
+    int32_t* prank;              // n: position in (degree, id) order
+    uint64_t* vkeys;             // n
+    uint64_t* vkeys_alt;         // n
+    int64_t* estart;             // n + 1
+    uint64_t* keys;              // ms2 (later: N item keys)
+    uint64_t* keys_alt;          // ms2
+    uint32_t* flag;              // ms2
+    uint32_t* pos;               // ms2 + 1
+    int32_t* item;               // ms2 (N used)
+    int32_t* part;               // ms2 (N used)
+    PartCounters* pc;            // parts
+    void* radix_tmp;             // radix_tmp_bytes(max(ms2, n))
+    void* scan_tmp;              // scan_tmp_bytes(max(ms2, n) + 1)
+    // cache phase (N reads)
+    int64_t* prev;               // N
+    int64_t* pstart;             // parts + 1
+    uint32_t *key_lru, *key_score, *wdeg, *wone;  // N each
+    int64_t* q_lru;              // N
+    uint32_t* th_lru;            // N
+    int64_t* q_score;            // 2 N
+    uint32_t* th_score;          // 2 N
+    int64_t* e0deg;              // N + 1
+    uint32_t* lk[2];             // N each: level keys (two buffers)
+    uint32_t* la[2];             // N each: level weights deg
+    uint32_t* lb[2];             // N each: level weights 1
+    int64_t *ea, *eb;            // N + 1 each
+    int64_t *f_lru_deg, *f_lru_one;  // N each
+    int64_t *f_sc_deg, *f_sc_one;    // 2 N each
+    unsigned long long *cnt, *byt;   // 4 * parts * ncap each
+};
+int rc_key_bits(int32_t n);
+// The read stream (N = pos[ms2] reads), then, once N is known, the caches.
+void launch_rc_stream(const RemoteCacheBuffers& R, const Launch& L);
+void launch_rc_caches(const RemoteCacheBuffers& R, int64_t N, const Launch& L);
+
 // ---- batch (tc_batch.cu) -------------------------------------------------------
 void launch_batch_relabel(int32_t G, const int64_t* edge_off, const int32_t* vbase, const int32_t* src,
                           const int32_t* dst, int32_t* usrc, int32_t* udst, int* err, const Launch& L);
