@@ -806,6 +806,20 @@ def run_cache(args, rank, world, local):
              for i, kind in enumerate(tc.CACHE_KINDS)}
     if rank != 0:
         return
+    cpu = None
+    if not args.no_cpu_baseline:
+        import oracle
+        oracle.build()
+        few = [caps[len(caps) // 3], caps[2 * len(caps) // 3]]
+        t0 = time.perf_counter()
+        ref = oracle.remote_cache(n, s_h, d_h, parts, few)
+        dt = time.perf_counter() - t0
+        ok = all(int(ref["hits"][i, k, j]) == int(r["hits"][i, k, caps.index(c)])
+                 for i in range(4) for k in range(parts) for j, c in enumerate(few))
+        cpu = {"value": N / (dt * len(caps) / len(few)), "unit": "reads/s", "cores": 1, "kind": "oracle",
+               "sample": f"the oracle's direct simulation of the 4 caches at {len(few)} of the {len(caps)} sizes "
+                         f"({dt:.1f} s, graph build included), scaled to all {len(caps)} sizes",
+               "parity_hits": ok}
     line = {"metric": "remote reads evaluated/sec (4 caches x 100 sizes)", "value": N / (ms_per_step / 1000.0),
             "unit": "reads/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -815,7 +829,7 @@ def run_cache(args, rank, world, local):
                        "distinct": r["distinct"].tolist(), "top_decile_reads": r["top_reads"].tolist(),
                        "read_bytes": r["read_bytes"].tolist(), "nonlocal_bytes": nonlocal_bytes,
                        "l2": "flushed between steps (512 MB write)"},
-            "score_vs_lru_at_25pct_nonlocal": score_cmp, "hits_curve_sample": curve,
+            "score_vs_lru_at_25pct_nonlocal": score_cmp, "hits_curve_sample": curve, "cpu_baseline": cpu,
             "gpu_launches": launches, "gpu_launches_per_step": launches / args.steps, "clocks": clk,
             "impl": "ours"}
     print(json.dumps(line), flush=True)

@@ -175,14 +175,14 @@ __global__ void k_rc_prev(int64_t N, const uint64_t* __restrict__ sorted, const 
 }
 
 // Inputs of the two dominance sums and their queries:
-//  LRU:   key = prev + 1, weights (deg, 1); query (t, prev(t) + 1) for every read.
-//  score: key = n - 1 - score rank for a first read (RC_NEVER otherwise), weights
-//         (deg, 1); queries (t, n - score rank(x)) and (start of the process, same).
+//  LRU:   key = prev + 1, weights deg and 1; query (t, prev(t) + 1) for every read.
+//  score: key = n - 1 - score rank for a first read (RC_NEVER otherwise), weights deg
+//         and 1; queries (t, n - score rank(x)) and (start of the process, same).
 __global__ void k_rc_inputs(int64_t N, int32_t n, const int32_t* __restrict__ item, const int32_t* __restrict__ part,
                             const int64_t* __restrict__ prev, const int64_t* __restrict__ pstart,
                             const int32_t* __restrict__ prank, const uint32_t* __restrict__ sdeg,
                             uint32_t* __restrict__ key_lru, uint32_t* __restrict__ key_score,
-                            uint32_t* __restrict__ wdeg, uint32_t* __restrict__ wone,
+                            uint32_t* __restrict__ wdeg,
                             int64_t* __restrict__ q_lru, uint32_t* __restrict__ th_lru,
                             int64_t* __restrict__ q_score, uint32_t* __restrict__ th_score,
                             PartCounters* __restrict__ pc) {
@@ -199,7 +199,6 @@ __global__ void k_rc_inputs(int64_t N, int32_t n, const int32_t* __restrict__ it
             key_lru[t] = (uint32_t)(p + 1);
             key_score[t] = p < 0 ? (uint32_t)(n - 1 - r) : RC_NEVER;
             wdeg[t] = sdeg[x];
-            wone[t] = 1u;
             q_lru[t] = t;
             th_lru[t] = (uint32_t)(p + 1);
             q_score[2 * t] = t;
@@ -229,8 +228,7 @@ __global__ void k_rc_pstart(int64_t N, int32_t parts, const int32_t* __restrict_
 // Level l -> l + 1 of the merge-sort tree: the two sorted halves of each block of
 // 2^(l+1) reads are merged (stable: the left half first among equal keys).
 __global__ void k_rc_merge(int64_t N, int l, const uint32_t* __restrict__ key, const uint32_t* __restrict__ wa,
-                           const uint32_t* __restrict__ wb, uint32_t* __restrict__ key2, uint32_t* __restrict__ wa2,
-                           uint32_t* __restrict__ wb2) {
+                           uint32_t* __restrict__ key2, uint32_t* __restrict__ wa2) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     const int64_t B = (int64_t)1 << l;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += stride) {
@@ -252,7 +250,6 @@ __global__ void k_rc_merge(int64_t N, int l, const uint32_t* __restrict__ key, c
             const int64_t out = base + (i - base) + (lo - r0);
             key2[out] = x;
             wa2[out] = wa[i];
-            wb2[out] = wb[i];
         } else {  // count the left half's keys <= x
             lo = base;
             hi = base + B;
@@ -266,16 +263,16 @@ __global__ void k_rc_merge(int64_t N, int l, const uint32_t* __restrict__ key, c
             const int64_t out = base + (i - base - B) + (lo - base);
             key2[out] = x;
             wa2[out] = wa[i];
-            wb2[out] = wb[i];
         }
     }
 }
 
 // Queries at level l: for a query (q, th) with bit l of q set, the block
-// [(q >> (l+1)) << (l+1), + 2^l) of level l adds the weights of its keys < th.
+// [(q >> (l+1)) << (l+1), + 2^l) of level l adds the weights of its keys < th (sa) and
+// their number (sb: the unit weights, whose prefix sums are the positions).
 __global__ void k_rc_query(int64_t M, int l, const int64_t* __restrict__ q, const uint32_t* __restrict__ th,
                            const uint32_t* __restrict__ key, const int64_t* __restrict__ ea,
-                           const int64_t* __restrict__ eb, int64_t* __restrict__ sa, int64_t* __restrict__ sb) {
+                           int64_t* __restrict__ sa, int64_t* __restrict__ sb) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < M; i += stride) {
         const int64_t qi = q[i];
@@ -291,7 +288,7 @@ __global__ void k_rc_query(int64_t M, int l, const int64_t* __restrict__ q, cons
                 hi = mid;
         }
         sa[i] += ea[lo] - ea[start];
-        sb[i] += eb[lo] - eb[start];
+        sb[i] += lo - start;
     }
 }
 
@@ -399,7 +396,7 @@ void launch_rc_caches(const RemoteCacheBuffers& R, int64_t N, const Launch& L) {
     k_rc_pstart<<<1, RC_THREADS, 0, L.stream>>>(N, R.parts, R.part, R.pstart);
     count_launch();
     k_rc_inputs<<<grid_for(N, RC_THREADS, sms), RC_THREADS, 0, L.stream>>>(
-        N, R.n, R.item, R.part, R.prev, R.pstart, R.prank, R.sdeg, R.key_lru, R.key_score, R.wdeg, R.wone, R.q_lru,
+        N, R.n, R.item, R.part, R.prev, R.pstart, R.prank, R.sdeg, R.key_lru, R.key_score, R.wdeg, R.q_lru,
         R.th_lru, R.q_score, R.th_score, R.pc);
     count_launch();
     // S(p): prefix sums of the weights in time order (level 0)
@@ -408,14 +405,11 @@ void launch_rc_caches(const RemoteCacheBuffers& R, int64_t N, const Launch& L) {
     for (int tree = 0; tree < 2; ++tree) {
         uint32_t* key = R.lk[0];
         uint32_t* wa = R.la[0];
-        uint32_t* wb = R.lb[0];
         uint32_t* key2 = R.lk[1];
         uint32_t* wa2 = R.la[1];
-        uint32_t* wb2 = R.lb[1];
         cudaMemcpyAsync(key, tree == 0 ? R.key_lru : R.key_score, sizeof(uint32_t) * (size_t)N,
                         cudaMemcpyDeviceToDevice, L.stream);
         cudaMemcpyAsync(wa, R.wdeg, sizeof(uint32_t) * (size_t)N, cudaMemcpyDeviceToDevice, L.stream);
-        cudaMemcpyAsync(wb, R.wone, sizeof(uint32_t) * (size_t)N, cudaMemcpyDeviceToDevice, L.stream);
         const int64_t M = tree == 0 ? N : 2 * N;
         int64_t* sa = tree == 0 ? R.f_lru_deg : R.f_sc_deg;
         int64_t* sb = tree == 0 ? R.f_lru_one : R.f_sc_one;
@@ -423,18 +417,15 @@ void launch_rc_caches(const RemoteCacheBuffers& R, int64_t N, const Launch& L) {
         cudaMemsetAsync(sb, 0, sizeof(int64_t) * (size_t)M, L.stream);
         for (int l = 0; ((int64_t)1 << l) <= N; ++l) {
             scan_u32_to_i64(wa, R.ea, N, R.scan_tmp, L);
-            scan_u32_to_i64(wb, R.eb, N, R.scan_tmp, L);
             k_rc_query<<<grid_for(M, RC_THREADS, sms), RC_THREADS, 0, L.stream>>>(
-                M, l, tree == 0 ? R.q_lru : R.q_score, tree == 0 ? R.th_lru : R.th_score, key, R.ea, R.eb, sa, sb);
+                M, l, tree == 0 ? R.q_lru : R.q_score, tree == 0 ? R.th_lru : R.th_score, key, R.ea, sa, sb);
             count_launch();
             if (((int64_t)1 << (l + 1)) <= N) {
-                k_rc_merge<<<grid_for(N, RC_THREADS, sms), RC_THREADS, 0, L.stream>>>(N, l, key, wa, wb, key2, wa2,
-                                                                                      wb2);
+                k_rc_merge<<<grid_for(N, RC_THREADS, sms), RC_THREADS, 0, L.stream>>>(N, l, key, wa, key2, wa2);
                 count_launch();
                 uint32_t* t;
                 t = key, key = key2, key2 = t;
                 t = wa, wa = wa2, wa2 = t;
-                t = wb, wb = wb2, wb2 = t;
             }
         }
     }

@@ -251,7 +251,7 @@ struct RemoteCacheBuffers {
     // cache phase (N reads)
     int64_t* prev;               // N
     int64_t* pstart;             // parts + 1
-    uint32_t *key_lru, *key_score, *wdeg, *wone;  // N each
+    uint32_t *key_lru, *key_score, *wdeg;  // N each
     int64_t* q_lru;              // N
     uint32_t* th_lru;            // N
     int64_t* q_score;            // 2 N
@@ -259,8 +259,7 @@ struct RemoteCacheBuffers {
     int64_t* e0deg;              // N + 1
     uint32_t* lk[2];             // N each: level keys (two buffers)
     uint32_t* la[2];             // N each: level weights deg
-    uint32_t* lb[2];             // N each: level weights 1
-    int64_t *ea, *eb;            // N + 1 each
+    int64_t* ea;                 // N + 1: prefix sums of a level's weights
     int64_t *f_lru_deg, *f_lru_one;  // N each
     int64_t *f_sc_deg, *f_sc_one;    // 2 N each
     unsigned long long *cnt, *byt;   // 4 * parts * ncap each
