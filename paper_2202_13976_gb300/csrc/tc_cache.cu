@@ -23,7 +23,8 @@
 // F and Q are sums over points (t', key(t')) dominated by a query (t, threshold):
 // answered for all reads together by a merge-sort tree over time, level by level
 // (level l holds the keys sorted within aligned blocks of 2^l reads, with prefix sums
-// of the weights); [0, t) splits into one block per set bit of t.
+// of the weights); [0, t) splits into one block per set bit of t, the blocks of the
+// five lowest bits read directly.
 #include <cuda_runtime.h>
 
 #include <climits>
@@ -38,6 +39,7 @@ namespace {
 
 constexpr int RC_THREADS = 256;
 constexpr uint32_t RC_NEVER = 0xffffffffu;  // a key no threshold counts
+constexpr int RC_LOW = 5;                   // tree levels below this are read directly
 
 __host__ __device__ __forceinline__ int32_t owner_of(int64_t i, int64_t n, int64_t parts) {
     return (int32_t)(((i + 1) * parts - 1) / n);
@@ -267,6 +269,50 @@ __global__ void k_rc_merge(int64_t N, int l, const uint32_t* __restrict__ key, c
     }
 }
 
+// The low bits of every query: [q & ~31, q) read directly in time order (the tree
+// starts at level RC_LOW); initialises the sums.
+__global__ void k_rc_query_low(int64_t M, const int64_t* __restrict__ q, const uint32_t* __restrict__ th,
+                               const uint32_t* __restrict__ key0, const uint32_t* __restrict__ w0,
+                               int64_t* __restrict__ sa, int64_t* __restrict__ sb) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < M; i += stride) {
+        const int64_t qi = q[i];
+        const uint32_t x = th[i];
+        int64_t a = 0, c = 0;
+        for (int64_t t = qi & ~(int64_t)((1 << RC_LOW) - 1); t < qi; ++t)
+            if (key0[t] < x) {
+                a += w0[t];
+                ++c;
+            }
+        sa[i] = a;
+        sb[i] = c;
+    }
+}
+
+// Level RC_LOW of the tree: each aligned block of 32 reads sorted by key, one warp per
+// block (the order among equal keys does not matter to the sums).
+__global__ void k_rc_sort32(int64_t N, const uint32_t* __restrict__ key0, const uint32_t* __restrict__ w0,
+                            uint32_t* __restrict__ key, uint32_t* __restrict__ wa) {
+    static_assert(RC_LOW == 5, "one warp per block of 2^RC_LOW reads");
+    const int lane = lane_id();
+    const int64_t warp0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t wstride = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t base = warp0 * 32; base < N; base += wstride * 32) {  // uniform per warp
+        const int64_t t = base + lane;
+        const uint32_t x = t < N ? key0[t] : 0xffffffffu;
+        int r = 0;
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+            const uint32_t y = __shfl_sync(FULL, x, j);
+            r += (y < x) || (y == x && j < lane);
+        }
+        if (t < N) {
+            key[base + r] = x;
+            wa[base + r] = w0[t];
+        }
+    }
+}
+
 // Queries at level l: for a query (q, th) with bit l of q set, the block
 // [(q >> (l+1)) << (l+1), + 2^l) of level l adds the weights of its keys < th (sa) and
 // their number (sb: the unit weights, whose prefix sums are the positions).
@@ -407,18 +453,19 @@ void launch_rc_caches(const RemoteCacheBuffers& R, int64_t N, const Launch& L) {
         uint32_t* wa = R.la[0];
         uint32_t* key2 = R.lk[1];
         uint32_t* wa2 = R.la[1];
-        cudaMemcpyAsync(key, tree == 0 ? R.key_lru : R.key_score, sizeof(uint32_t) * (size_t)N,
-                        cudaMemcpyDeviceToDevice, L.stream);
-        cudaMemcpyAsync(wa, R.wdeg, sizeof(uint32_t) * (size_t)N, cudaMemcpyDeviceToDevice, L.stream);
+        const uint32_t* key0 = tree == 0 ? R.key_lru : R.key_score;
         const int64_t M = tree == 0 ? N : 2 * N;
+        const int64_t* q = tree == 0 ? R.q_lru : R.q_score;
+        const uint32_t* th = tree == 0 ? R.th_lru : R.th_score;
         int64_t* sa = tree == 0 ? R.f_lru_deg : R.f_sc_deg;
         int64_t* sb = tree == 0 ? R.f_lru_one : R.f_sc_one;
-        cudaMemsetAsync(sa, 0, sizeof(int64_t) * (size_t)M, L.stream);
-        cudaMemsetAsync(sb, 0, sizeof(int64_t) * (size_t)M, L.stream);
-        for (int l = 0; ((int64_t)1 << l) <= N; ++l) {
+        k_rc_query_low<<<grid_for(M, RC_THREADS, sms), RC_THREADS, 0, L.stream>>>(M, q, th, key0, R.wdeg, sa, sb);
+        count_launch();
+        k_rc_sort32<<<grid_for(N, RC_THREADS, sms), RC_THREADS, 0, L.stream>>>(N, key0, R.wdeg, key, wa);
+        count_launch();
+        for (int l = RC_LOW; ((int64_t)1 << l) <= N; ++l) {
             scan_u32_to_i64(wa, R.ea, N, R.scan_tmp, L);
-            k_rc_query<<<grid_for(M, RC_THREADS, sms), RC_THREADS, 0, L.stream>>>(
-                M, l, tree == 0 ? R.q_lru : R.q_score, tree == 0 ? R.th_lru : R.th_score, key, R.ea, sa, sb);
+            k_rc_query<<<grid_for(M, RC_THREADS, sms), RC_THREADS, 0, L.stream>>>(M, l, q, th, key, R.ea, sa, sb);
             count_launch();
             if (((int64_t)1 << (l + 1)) <= N) {
                 k_rc_merge<<<grid_for(N, RC_THREADS, sms), RC_THREADS, 0, L.stream>>>(N, l, key, wa, key2, wa2);

@@ -14,12 +14,13 @@
 //
 // Phases (all on the device; one host synchronisation after phase 1 reads the error
 // flag and the size of U):
-//  1. pairs -> keys (min id, max id, direction), radix sorted; a run of keys with the
-//     same (min, max) is one edge of U whose bits are the OR of its directions;
-//     out-degrees (distinct tails) and degrees in U are counted from the runs;
+//  1. pairs -> keys (min id, max id, direction), radix sorted on (min, max); a run of
+//     keys with the same (min, max) is one edge of U whose bits are the OR of its
+//     directions; degrees in U are counted from the runs;
 //  2. rank by (degree in U, id): stable radix sort of the degree field;
 //  3. oriented keys (lower rank, higher rank, bits in rank order) radix sorted, which
-//     lays the oriented rows out in order; row starts by binary search;
+//     lays the oriented rows out in order (distinct directed edges and out-degrees
+//     counted from the bits on the way); row starts by binary search;
 //  4. count, pull: vertices with many in-edges (hubs) stage N+(v) as a 2-bit map of
 //     direction bits in shared memory, and every in-edge (u -> v) streams N+(u) after v
 //     against it (the in-edges come from a stable sort of the entries by target);
@@ -91,37 +92,20 @@ __global__ void k_dg_keys(int64_t m, const int32_t* __restrict__ src, const int3
     }
 }
 
-// Phase 1b: head[k] = 1 where a run of equal (min, max) starts; distinct directed
-// edges counted and their tails' out-degrees incremented.  Warps walk aligned chunks
-// so that every lane takes part in the match below.
-__global__ void k_dg_heads(int64_t m, const uint64_t* __restrict__ keys, int b, uint32_t* __restrict__ head,
-                           uint32_t* __restrict__ dout, DgStats* st) {
-    const int lane = lane_id();
-    const int64_t warp0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int64_t wstride = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    const uint64_t mask = (1ull << b) - 1;
-    unsigned long long distinct = 0;
-    for (int64_t base = warp0 * 32; base < m; base += wstride * 32) {
-        const int64_t k = base + lane;
-        const uint64_t key = k < m ? keys[k] : DG_NONE;
-        const uint64_t prev = k > 0 && k < m ? keys[k - 1] : DG_NONE;
-        const bool valid = key != DG_NONE;
-        const bool h = valid && (k == 0 || (key >> 1) != (prev >> 1));
-        const bool d = valid && (k == 0 || key != prev);
-        if (k < m) head[k] = h ? 1u : 0u;
-        distinct += d;
-        // tail of the directed edge: min for direction 0, max for direction 1
-        const int32_t tail = d ? (int32_t)((key & 1) ? (key >> 1) & mask : key >> (b + 1)) : -1;
-        const unsigned same = __match_any_sync(FULL, tail);
-        if (tail >= 0 && lane == __ffs(same) - 1) atomicAdd(&dout[tail], (unsigned)__popc(same));
+// Phase 1b: head[k] = 1 where a run of equal (min, max) starts.  The sort leaves the
+// direction bit out, so the keys of one run stay in input order.
+__global__ void k_dg_heads(int64_t m, const uint64_t* __restrict__ keys, uint32_t* __restrict__ head) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < m; k += stride) {
+        const uint64_t key = keys[k];
+        head[k] = key != DG_NONE && (k == 0 || (key >> 1) != (keys[k - 1] >> 1)) ? 1u : 0u;
     }
-    distinct = warp_sum(distinct);
-    if (lane == 0 && distinct) atomicAdd(&st->m_directed, distinct);
 }
 
-// Phase 1c: edge e = idx[k] + head[k] - 1 of U gets its ends at the run's head and
-// the direction bit of the last key of every group of equal keys; degrees in U are
-// counted at the heads (the min ends aggregated per warp: the keys are sorted by min).
+// Phase 1c: edge e = idx[k] + head[k] - 1 of U gets its ends at the run's head and the
+// direction bit of the last key of every group of equal adjacent keys (together they
+// give the OR over the run); degrees in U are counted at the heads (the min ends
+// aggregated per warp: the keys are sorted by min).
 __global__ void k_dg_unique(int64_t m, const uint64_t* __restrict__ keys, int b, const uint32_t* __restrict__ head,
                             const uint32_t* __restrict__ idx, int32_t* __restrict__ ulo, int32_t* __restrict__ uhi,
                             uint32_t* __restrict__ flags, uint32_t* __restrict__ deg) {
@@ -168,19 +152,36 @@ __global__ void k_dg_rank(int32_t n, const uint64_t* __restrict__ vkeys, int b, 
         rank[vkeys[p] & mask] = (int32_t)p;
 }
 
-// Phase 3a: okey = (lower rank << (b + 2)) | (higher rank << 2) | bits in rank order.
+// Phase 3a: okey = (lower rank << (b + 2)) | (higher rank << 2) | bits in rank order;
+// each bit of an edge of U is one distinct directed edge, counted with its tail's
+// out-degree (the min ends aggregated per warp: the edges are sorted by min).
 __global__ void k_dg_orient(int64_t mu, const int32_t* __restrict__ ulo, const int32_t* __restrict__ uhi,
                             const uint32_t* __restrict__ flags, const int32_t* __restrict__ rank, int b,
-                            uint64_t* __restrict__ okeys) {
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < mu; e += stride) {
-        const int32_t rx = rank[ulo[e]], ry = rank[uhi[e]];
-        const uint32_t f = flags[e];  // bit 0: min id -> max id, bit 1: max id -> min id
-        const bool keep = rx < ry;
-        const uint64_t a = (uint32_t)(keep ? rx : ry), c = (uint32_t)(keep ? ry : rx);
-        const uint32_t of = keep ? f : ((f & 1u) << 1) | (f >> 1);
-        okeys[e] = (a << (b + 2)) | (c << 2) | of;
+                            uint64_t* __restrict__ okeys, uint32_t* __restrict__ dout, DgStats* st) {
+    const int lane = lane_id();
+    const int64_t warp0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t wstride = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    unsigned long long distinct = 0;
+    for (int64_t base = warp0 * 32; base < mu; base += wstride * 32) {  // uniform per warp
+        const int64_t e = base + lane;
+        int32_t lo_tail = -1;
+        if (e < mu) {
+            const int32_t x = ulo[e], y = uhi[e];
+            const int32_t rx = rank[x], ry = rank[y];
+            const uint32_t f = flags[e];  // bit 0: min id -> max id, bit 1: max id -> min id
+            const bool keep = rx < ry;
+            const uint64_t a = (uint32_t)(keep ? rx : ry), c = (uint32_t)(keep ? ry : rx);
+            const uint32_t of = keep ? f : ((f & 1u) << 1) | (f >> 1);
+            okeys[e] = (a << (b + 2)) | (c << 2) | of;
+            distinct += __popc(f);
+            if (f & 1u) lo_tail = x;
+            if (f & 2u) atomicAdd(&dout[y], 1u);
+        }
+        const unsigned same = __match_any_sync(FULL, lo_tail);
+        if (lo_tail >= 0 && lane == __ffs(same) - 1) atomicAdd(&dout[lo_tail], (unsigned)__popc(same));
     }
+    distinct = warp_sum(distinct);
+    if (lane == 0 && distinct) atomicAdd(&st->m_directed, distinct);
 }
 
 // Phase 3b: the sorted keys become the rows: col (higher rank) and dirf (bits).
@@ -623,8 +624,8 @@ extern "C" tc_status tc_directed_lcc(int32_t n, int64_t m, const int32_t* src, c
     // phase 1
     k_dg_keys<<<grid_for(m, DG_THREADS, sms), DG_THREADS, 0, stream>>>(m, dsrc, ddst, n, b, keys, st);
     count_launch();
-    uint64_t* sorted = radix_sort_u64(keys, alt, m, 0, 2 * b + 1, radix_tmp, L);
-    k_dg_heads<<<grid_for(m, DG_THREADS, sms), DG_THREADS, 0, stream>>>(m, sorted, b, head, dout, st);
+    uint64_t* sorted = radix_sort_u64(keys, alt, m, 1, 2 * b + 1, radix_tmp, L);
+    k_dg_heads<<<grid_for(m, DG_THREADS, sms), DG_THREADS, 0, stream>>>(m, sorted, head);
     count_launch();
     scan_u32_to_u32(head, idx, m, scan_tmp, L);
     k_dg_unique<<<grid_for(m, DG_THREADS, sms), DG_THREADS, 0, stream>>>(m, sorted, b, head, idx, ulo, uhi, ebits,
@@ -636,7 +637,7 @@ extern "C" tc_status tc_directed_lcc(int32_t n, int64_t m, const int32_t* src, c
     if (e != cudaSuccess) return fail("tc_directed_lcc: phase 1", e);
     if (hst->err) return TC_EINVAL;
     const int64_t mu = (int64_t)*hmu;
-    const unsigned long long md = hst->m_directed, loops = hst->loops;
+    const unsigned long long loops = hst->loops;
 
     // phase 2: ranks (the key buffers of phase 1 are free again)
     uint64_t* vkeys = A.get<uint64_t>(nn);
@@ -657,7 +658,8 @@ extern "C" tc_status tc_directed_lcc(int32_t n, int64_t m, const int32_t* src, c
     k_dg_rank<<<grid_for(n, DG_THREADS, sms), DG_THREADS, 0, stream>>>(n, vsorted, b, rank);
     count_launch();
     // phase 3: oriented rows
-    k_dg_orient<<<grid_for(mu, DG_THREADS, sms), DG_THREADS, 0, stream>>>(mu, ulo, uhi, ebits, rank, b, keys);
+    k_dg_orient<<<grid_for(mu, DG_THREADS, sms), DG_THREADS, 0, stream>>>(mu, ulo, uhi, ebits, rank, b, keys, dout,
+                                                                           st);
     count_launch();
     uint64_t* osorted = radix_sort_u64(keys, alt, mu, 2, 2 * b + 2, radix_tmp, L);
     k_dg_rows<<<grid_for(mu, DG_THREADS, sms), DG_THREADS, 0, stream>>>(mu, osorted, b, col, dirf);
@@ -719,7 +721,7 @@ extern "C" tc_status tc_directed_lcc(int32_t n, int64_t m, const int32_t* src, c
     if (e != cudaSuccess) return fail("tc_directed_lcc", e);
     if (stats) {
         *stats = tc_directed_stats{};
-        stats->m_directed = (int64_t)md;
+        stats->m_directed = (int64_t)hst->m_directed;
         stats->m_undirected = mu;
         stats->loops_dropped = (int64_t)loops;
         stats->total = hst->sum_c;
