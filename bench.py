@@ -150,6 +150,16 @@ def apply_strategy(g, spec, tc):
         g.set_strategy(tc.BUCKETS[bucket], name, float(rest[0]) if rest else 1.0)
 
 
+def step_spread(step_ms):
+    """The paper's timing rule (Sec. V-A): the median of the runs and whether the 95%
+    confidence interval of the mean lies within 5% of it."""
+    med = statistics.median(step_ms)
+    if len(step_ms) < 2:
+        return {"median_ms": med, "ci95_ms": None, "within_5pct": None}
+    half = 1.96 * statistics.stdev(step_ms) / len(step_ms) ** 0.5
+    return {"median_ms": med, "ci95_ms": half, "within_5pct": half <= 0.05 * med}
+
+
 def cpu_baseline(workload, src, dst):
     """The oracle as it stands, whole pipeline on the same workload, host cores."""
     import oracle
@@ -339,6 +349,7 @@ def run_ours(args, rank, world, local):
                    "parallelism": f"replicas x{world}" if world > 1 else "1 GPU",
                    "strategy": args.strategy or "default",
                    "phase_ms": phase,
+                   "step_spread": step_spread(step_ms),
                    "plan": plan,
                    "vs_baseline_ref": "Table II, R-MAT S20 EF16, hybrid, 0.425 edges/us, 16-thread Xeon Gold 6154"},
         "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
