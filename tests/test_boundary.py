@@ -58,6 +58,15 @@ def test_argument_errors_before_device_work(tc):
     assert lib.tc_graph_set_strategy(None, 0, 0, 1.0) == tc.TC_EINVAL
     assert lib.tc_graph_set_hubs(None, 32, 10) == tc.TC_EINVAL
     assert lib.tc_graph_last_timing(None, None, 0) == tc.TC_EINVAL
+    # directed LCC: negative sizes, missing pairs, bad mem_kind or flags
+    assert lib.tc_directed_lcc(-1, 0, None, None, 0, None, None, None, None, 0) == tc.TC_EINVAL
+    assert lib.tc_directed_lcc(4, -1, None, None, 0, None, None, None, None, 0) == tc.TC_EINVAL
+    assert lib.tc_directed_lcc(4, 1, None, None, 0, None, None, None, None, 0) == tc.TC_EINVAL
+    assert lib.tc_directed_lcc(4, 0, None, None, 7, None, None, None, None, 0) == tc.TC_EINVAL
+    assert lib.tc_directed_lcc(4, 0, None, None, 0, None, None, None, None, 8) == tc.TC_EINVAL
+    assert lib.tc_directed_lcc(4, 1 << 40, None, None, 0, None, None, None, None, 0) == tc.TC_EINVAL
+    # remote-read caches: no graph
+    assert lib.tc_remote_cache(None, 2, 0, None, None, None, None) == tc.TC_EINVAL
     lib.tc_graph_destroy(None)
 
 
