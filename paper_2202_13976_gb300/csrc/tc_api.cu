@@ -796,9 +796,10 @@ tc_status tc_remote_cache(tc_graph* g, int32_t parts, int32_t ncap, const uint64
             (st = dalloc(g, &R.wdeg, n1, &tmp)) ||
             (st = dalloc(g, &R.q_lru, n1, &tmp)) || (st = dalloc(g, &R.th_lru, n1, &tmp)) ||
             (st = dalloc(g, &R.q_score, 2 * n1, &tmp)) || (st = dalloc(g, &R.th_score, 2 * n1, &tmp)) ||
-            (st = dalloc(g, &R.e0deg, n1 + 1, &tmp)) || (st = dalloc(g, &R.lk[0], n1, &tmp)) ||
-            (st = dalloc(g, &R.lk[1], n1, &tmp)) || (st = dalloc(g, &R.la[0], n1, &tmp)) ||
-            (st = dalloc(g, &R.la[1], n1, &tmp)) || (st = dalloc(g, &R.ea, n1 + 1, &tmp)) ||
+            (st = dalloc(g, &R.e0deg, n1 + 1, &tmp)) ||
+            (st = dalloc(g, &R.lk, (size_t)rc_levels(N) * n1, &tmp)) ||
+            (st = dalloc(g, &R.le, (size_t)rc_levels(N) * (n1 + 1), &tmp)) || (st = dalloc(g, &R.la[0], n1, &tmp)) ||
+            (st = dalloc(g, &R.la[1], n1, &tmp)) ||
             (st = dalloc(g, &R.f_lru_deg, n1, &tmp)) ||
             (st = dalloc(g, &R.f_lru_one, n1, &tmp)) || (st = dalloc(g, &R.f_sc_deg, 2 * n1, &tmp)) ||
             (st = dalloc(g, &R.f_sc_one, 2 * n1, &tmp))) {

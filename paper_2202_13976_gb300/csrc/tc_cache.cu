@@ -24,7 +24,8 @@
 // answered for all reads together by a merge-sort tree over time, level by level
 // (level l holds the keys sorted within aligned blocks of 2^l reads, with prefix sums
 // of the weights); [0, t) splits into one block per set bit of t, the blocks of the
-// five lowest bits read directly.
+// five lowest bits read directly.  All levels are kept (12 bytes per read and level),
+// so a query walks them in one thread with its sums in registers.
 #include <cuda_runtime.h>
 
 #include <climits>
@@ -269,26 +270,6 @@ __global__ void k_rc_merge(int64_t N, int l, const uint32_t* __restrict__ key, c
     }
 }
 
-// The low bits of every query: [q & ~31, q) read directly in time order (the tree
-// starts at level RC_LOW); initialises the sums.
-__global__ void k_rc_query_low(int64_t M, const int64_t* __restrict__ q, const uint32_t* __restrict__ th,
-                               const uint32_t* __restrict__ key0, const uint32_t* __restrict__ w0,
-                               int64_t* __restrict__ sa, int64_t* __restrict__ sb) {
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < M; i += stride) {
-        const int64_t qi = q[i];
-        const uint32_t x = th[i];
-        int64_t a = 0, c = 0;
-        for (int64_t t = qi & ~(int64_t)((1 << RC_LOW) - 1); t < qi; ++t)
-            if (key0[t] < x) {
-                a += w0[t];
-                ++c;
-            }
-        sa[i] = a;
-        sb[i] = c;
-    }
-}
-
 // Level RC_LOW of the tree: each aligned block of 32 reads sorted by key, one warp per
 // block (the order among equal keys does not matter to the sums).
 __global__ void k_rc_sort32(int64_t N, const uint32_t* __restrict__ key0, const uint32_t* __restrict__ w0,
@@ -313,28 +294,42 @@ __global__ void k_rc_sort32(int64_t N, const uint32_t* __restrict__ key0, const 
     }
 }
 
-// Queries at level l: for a query (q, th) with bit l of q set, the block
-// [(q >> (l+1)) << (l+1), + 2^l) of level l adds the weights of its keys < th (sa) and
-// their number (sb: the unit weights, whose prefix sums are the positions).
-__global__ void k_rc_query(int64_t M, int l, const int64_t* __restrict__ q, const uint32_t* __restrict__ th,
-                           const uint32_t* __restrict__ key, const int64_t* __restrict__ ea,
+// Every query in one thread: the reads [q & ~31, q) directly in time order, then for
+// every level l >= RC_LOW with bit l of q set, the block [(q >> (l+1)) << (l+1), + 2^l)
+// of level l adds the entry sizes of its keys < th (sa) and their number (sb).
+__global__ void k_rc_query(int64_t M, const int64_t* __restrict__ q, const uint32_t* __restrict__ th,
+                           const uint32_t* __restrict__ key0, const uint32_t* __restrict__ w0, int64_t N, int nlev,
+                           const uint32_t* __restrict__ lk, const int64_t* __restrict__ le,
                            int64_t* __restrict__ sa, int64_t* __restrict__ sb) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < M; i += stride) {
         const int64_t qi = q[i];
-        if (!((qi >> l) & 1)) continue;
-        const int64_t start = (qi >> (l + 1)) << (l + 1);
-        int64_t lo = start, hi = start + ((int64_t)1 << l);
         const uint32_t x = th[i];
-        while (lo < hi) {
-            const int64_t mid = (lo + hi) >> 1;
-            if (key[mid] < x)
-                lo = mid + 1;
-            else
-                hi = mid;
+        int64_t a = 0, c = 0;
+        for (int64_t t = qi & ~(int64_t)((1 << RC_LOW) - 1); t < qi; ++t)
+            if (key0[t] < x) {
+                a += w0[t];
+                ++c;
+            }
+        for (int j = 0; j < nlev; ++j) {
+            const int l = RC_LOW + j;
+            if (!((qi >> l) & 1)) continue;
+            const int64_t start = (qi >> (l + 1)) << (l + 1);
+            const uint32_t* K = lk + (int64_t)j * N;
+            int64_t lo = start, hi = start + ((int64_t)1 << l);
+            while (lo < hi) {
+                const int64_t mid = (lo + hi) >> 1;
+                if (K[mid] < x)
+                    lo = mid + 1;
+                else
+                    hi = mid;
+            }
+            const int64_t* E = le + (int64_t)j * (N + 1);
+            a += E[lo] - E[start];
+            c += lo - start;
         }
-        sa[i] += ea[lo] - ea[start];
-        sb[i] += lo - start;
+        sa[i] = a;
+        sb[i] = c;
     }
 }
 
@@ -399,6 +394,12 @@ __global__ void k_rc_hist(int64_t N, int32_t parts, int ncap, const uint64_t* __
 
 }  // namespace
 
+int rc_levels(int64_t N) {
+    int k = 0;
+    while (((int64_t)1 << (RC_LOW + k)) <= N) ++k;
+    return k;
+}
+
 int rc_key_bits(int32_t n) {
     int b = 1;
     while (b < 31 && ((int64_t)1 << b) < (int64_t)n) ++b;
@@ -447,34 +448,29 @@ void launch_rc_caches(const RemoteCacheBuffers& R, int64_t N, const Launch& L) {
     count_launch();
     // S(p): prefix sums of the weights in time order (level 0)
     scan_u32_to_i64(R.wdeg, R.e0deg, N, R.scan_tmp, L);
-    // the two merge-sort trees, one after the other, in the same level buffers
+    // the two merge-sort trees, one after the other, in the same level buffers: every
+    // level is built and kept, then each query walks them all in one thread
+    const int nlev = rc_levels(N);
     for (int tree = 0; tree < 2; ++tree) {
-        uint32_t* key = R.lk[0];
-        uint32_t* wa = R.la[0];
-        uint32_t* key2 = R.lk[1];
-        uint32_t* wa2 = R.la[1];
         const uint32_t* key0 = tree == 0 ? R.key_lru : R.key_score;
         const int64_t M = tree == 0 ? N : 2 * N;
-        const int64_t* q = tree == 0 ? R.q_lru : R.q_score;
-        const uint32_t* th = tree == 0 ? R.th_lru : R.th_score;
-        int64_t* sa = tree == 0 ? R.f_lru_deg : R.f_sc_deg;
-        int64_t* sb = tree == 0 ? R.f_lru_one : R.f_sc_one;
-        k_rc_query_low<<<grid_for(M, RC_THREADS, sms), RC_THREADS, 0, L.stream>>>(M, q, th, key0, R.wdeg, sa, sb);
-        count_launch();
-        k_rc_sort32<<<grid_for(N, RC_THREADS, sms), RC_THREADS, 0, L.stream>>>(N, key0, R.wdeg, key, wa);
-        count_launch();
-        for (int l = RC_LOW; ((int64_t)1 << l) <= N; ++l) {
-            scan_u32_to_i64(wa, R.ea, N, R.scan_tmp, L);
-            k_rc_query<<<grid_for(M, RC_THREADS, sms), RC_THREADS, 0, L.stream>>>(M, l, q, th, key, R.ea, sa, sb);
+        if (nlev > 0) {
+            k_rc_sort32<<<grid_for(N, RC_THREADS, sms), RC_THREADS, 0, L.stream>>>(N, key0, R.wdeg, R.lk, R.la[0]);
             count_launch();
-            if (((int64_t)1 << (l + 1)) <= N) {
-                k_rc_merge<<<grid_for(N, RC_THREADS, sms), RC_THREADS, 0, L.stream>>>(N, l, key, wa, key2, wa2);
+        }
+        for (int j = 0; j < nlev; ++j) {
+            uint32_t* wa = R.la[j & 1];
+            scan_u32_to_i64(wa, R.le + (int64_t)j * (N + 1), N, R.scan_tmp, L);
+            if (j + 1 < nlev) {
+                k_rc_merge<<<grid_for(N, RC_THREADS, sms), RC_THREADS, 0, L.stream>>>(
+                    N, RC_LOW + j, R.lk + (int64_t)j * N, wa, R.lk + (int64_t)(j + 1) * N, R.la[(j + 1) & 1]);
                 count_launch();
-                uint32_t* t;
-                t = key, key = key2, key2 = t;
-                t = wa, wa = wa2, wa2 = t;
             }
         }
+        k_rc_query<<<grid_for(M, RC_THREADS, sms), RC_THREADS, 0, L.stream>>>(
+            M, tree == 0 ? R.q_lru : R.q_score, tree == 0 ? R.th_lru : R.th_score, key0, R.wdeg, N, nlev, R.lk, R.le,
+            tree == 0 ? R.f_lru_deg : R.f_sc_deg, tree == 0 ? R.f_lru_one : R.f_sc_one);
+        count_launch();
     }
     const int cells = 4 * R.parts * R.ncap;
     const size_t shmem = cells <= RC_HIST_SHARED ? 2 * sizeof(unsigned long long) * (size_t)cells : 0;

@@ -257,14 +257,16 @@ struct RemoteCacheBuffers {
     int64_t* q_score;            // 2 N
     uint32_t* th_score;          // 2 N
     int64_t* e0deg;              // N + 1
-    uint32_t* lk[2];             // N each: level keys (two buffers)
-    uint32_t* la[2];             // N each: level weights deg
-    int64_t* ea;                 // N + 1: prefix sums of a level's weights
+    uint32_t* lk;                // rc_levels(N) * N: the tree's keys, level RC_LOW + j at j * N
+    int64_t* le;                 // rc_levels(N) * (N + 1): prefix sums of each level's entry sizes
+    uint32_t* la[2];             // N each: entry sizes of the current and the next level
     int64_t *f_lru_deg, *f_lru_one;  // N each
     int64_t *f_sc_deg, *f_sc_one;    // 2 N each
     unsigned long long *cnt, *byt;   // 4 * parts * ncap each
 };
 int rc_key_bits(int32_t n);
+// Levels of the merge-sort tree kept for N reads (levels 5 .. floor(log2 N)).
+int rc_levels(int64_t N);
 // The read stream (N = pos[ms2] reads), then, once N is known, the caches.
 void launch_rc_stream(const RemoteCacheBuffers& R, const Launch& L);
 void launch_rc_caches(const RemoteCacheBuffers& R, int64_t N, const Launch& L);
