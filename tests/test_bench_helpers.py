@@ -1,0 +1,43 @@
+"""Host-side helpers of the benchmark (no GPU): the timing-rule summary, the peak
+lookup and the sampled CPU baseline of the directed mode."""
+from __future__ import annotations
+
+import numpy as np
+
+import bench
+import graphgen
+
+
+def test_step_spread_follows_the_timing_rule():
+    s = bench.step_spread([3.9, 3.88, 3.87, 3.91])
+    assert s["median_ms"] == (3.88 + 3.9) / 2
+    assert 0 < s["ci95_ms"] < 0.05 * s["median_ms"] and s["within_5pct"]
+    wide = bench.step_spread([1.0, 3.0, 1.0, 3.0])
+    assert wide["within_5pct"] is False
+    one = bench.step_spread([2.0])
+    assert one == {"median_ms": 2.0, "ci95_ms": None, "within_5pct": None}
+
+
+def test_measured_peak_is_positive():
+    peak, kind = bench.measured_peak()
+    assert peak > 0 and kind in ("measured", "fallback")
+
+
+def test_directed_cpu_baseline_samples_the_oracle():
+    n = 1 << 10
+    s, d = graphgen.rmat(10, 8 * n, seed=3)
+    cpu = bench.directed_cpu_baseline(n, s, d, sample_vertices=200, seed=1)
+    assert cpu["kind"] == "oracle" and cpu["unit"] == "edges/s" and cpu["value"] > 0
+    assert "200 random vertices" in cpu["sample"]
+
+
+def test_bench_defaults_are_one_gpu_and_minutes():
+    import sys
+    argv = sys.argv
+    try:
+        sys.argv = ["bench.py"]
+        a = bench.parse_args()
+    finally:
+        sys.argv = argv
+    assert a.gpus == 1 and a.impl == "ours" and a.mode == "single" and a.workload == "rmat20"
+    assert a.warmup >= 3 and 1 <= a.steps <= 200
