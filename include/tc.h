@@ -206,19 +206,26 @@ tc_status tc_directed_lcc(int32_t n, int64_t m, const int32_t* src, const int32_
                           int flags);
 
 /*
- * Input accounting: number of distinct undirected edges, self-loops dropped and
- * repeated pairs dropped.  Any pointer may be NULL.  Synchronises the stream.
+ * Input accounting (Sec. II-A: the input is read as a simple graph, so self-loops
+ * and repeated pairs leave it): number of distinct undirected edges |E|, self-loops
+ * dropped and repeated pairs dropped.  Any pointer may be NULL.  Synchronises the
+ * stream.  Errors: TC_EINVAL for a NULL graph; TC_ECUDA.
  */
 tc_status tc_graph_info(const tc_graph* g, int64_t* m_simple, int64_t* loops_dropped,
                         int64_t* dups_dropped);
 
-/* Number of vertices and of oriented edges (= distinct undirected edges). */
+/* Number of vertices |V| and of oriented edges (Sec. II-C orients every edge of E
+ * once, so this is |E|).  Errors: TC_EINVAL for a NULL graph; TC_ECUDA. */
 tc_status tc_graph_size(const tc_graph* g, int32_t* n, int64_t* m_oriented);
 
-/* Release the graph's device memory (back to the library's device pool). NULL is a no-op. */
+/* Release the graph's device memory (back to the library's device pool).  NULL is
+ * a no-op.  The paper defines no such call: it is this library's ownership rule
+ * (the graph object owns the device CSR of Sec. II-B that tc_graph_create_* built). */
 void tc_graph_destroy(tc_graph* g);
 
-/* Static, NUL-terminated description of a status code. */
+/* Static, NUL-terminated description of a status code (no counterpart in the
+ * paper: the status codes are this library's error reporting).  Unknown codes give
+ * "unknown tc_status". */
 const char* tc_status_str(tc_status s);
 
 /* Detail of the last failure on the calling host thread (CUDA error text or the
@@ -455,9 +462,8 @@ tc_status tc_server_stop(tc_server* s);
 /*
  * Count without allocating (an addition of this library; the paper has no
  * counterpart).  For callers that cannot allocate device memory while they run: a
- * program that has handed all free HBM to its own caching allocator, code being
- * recorded into a CUDA stream capture (where cudaMalloc is not allowed), or
- * real-time code that forbids allocation after start-up.
+ * program that has handed all free HBM to its own caching allocator, or real-time
+ * code that forbids allocation after start-up.
  *
  * Computes the same T, t[] and LCC[] as tc_graph_create_from_edges + tc_count +
  * lcc_compute for a small graph, in one kernel launch whose intermediate arrays
@@ -469,12 +475,16 @@ tc_status tc_server_stop(tc_server* s);
  *   T_out       host scalar, receives T
  *   t_out       n uint64 in device memory, or NULL
  *   lcc_out     n fp64 in device memory, or NULL
- *   cuda_stream a cudaStream_t (as void*), or NULL; the call synchronises it
+ *   cuda_stream a cudaStream_t (as void*), or NULL; the call copies its status words
+ *               to the host and synchronises this stream before it returns
  * The first call on a device looks up the device address of the array (once per
  * device, with that device current); make that first call before any stream
- * capture begins.  All calls share the array and it keeps the previous call's
- * contents (the kernel clears what it needs): calls whose work overlaps on the GPU
- * (other streams or host threads) race on it and must be ordered by the caller.
+ * capture begins.  With lazy module loading (the CUDA default) that first call is
+ * also when the runtime loads this library's device code and places the array on
+ * the device, so make it at start-up, before the free memory is handed to another
+ * allocator.  All calls share the array and it keeps the previous call's contents
+ * (the kernel clears what it needs): calls whose work overlaps on the GPU (other
+ * streams or host threads) race on it and must be ordered by the caller.
  * Errors: TC_EINVAL for sizes beyond the limits, NULL pointers or an id outside
  * [0, n); TC_ECUDA; TC_EINTERNAL.
  */

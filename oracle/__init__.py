@@ -206,6 +206,47 @@ def tc_oriented(n: int, off_plus, adj_plus, threads: int = 1) -> np.ndarray:
     return np.sum(parts, axis=0, dtype=np.uint64)
 
 
+def tc_oriented_ranges(n: int, off_plus, adj_plus, ranges, threads: int = 1) -> np.ndarray:
+    """The Sec. II-C oriented count restricted to the source vertices of the listed
+    half-open ranges [u0, u1) -> partial t uint64[n] (every triangle whose lowest
+    oriented edge starts in a listed range adds to its three corners); the ranges are
+    shared among ``threads`` threads, each summing into its own array."""
+    off_plus = _c(off_plus, np.int64)
+    adj_plus = _c(adj_plus, np.int32)
+    lib = _load()
+    jobs = [(int(a), int(b)) for a, b in ranges]
+    parts = []
+    jl = threading.Lock()
+
+    def worker():
+        t = np.zeros(n, dtype=np.uint64)
+        while True:
+            with jl:
+                if not jobs:
+                    break
+                u0, u1 = jobs.pop()
+            lib.or_tc_oriented(n, _p(off_plus, _i64p), _p(adj_plus, _i32p), _p(t, _u64p), u0, u1)
+        parts.append(t)
+
+    ths = [threading.Thread(target=worker) for _ in range(max(1, threads))]
+    for th in ths:
+        th.start()
+    for th in ths:
+        th.join()
+    return np.sum(parts, axis=0, dtype=np.uint64)
+
+
+def work_ranges(off_plus, pieces: int):
+    """``pieces`` half-open source ranges of roughly equal oriented-count work
+    (d+(u)^2 + d+(u) + 1 per source u), covering [0, n)."""
+    d = np.diff(_c(off_plus, np.int64)).astype(np.float64)
+    n = d.size
+    w = np.cumsum(d * d + d + 1.0)
+    cuts = np.searchsorted(w, np.linspace(0, w[-1], pieces + 1)[1:-1]) if n else []
+    bounds = [0] + [int(c) for c in cuts] + [n]
+    return [(a, b) for a, b in zip(bounds[:-1], bounds[1:]) if b > a]
+
+
 def tc_vertex(n: int, offsets, adj, vertices) -> np.ndarray:
     """Alg. 3 per-vertex formula (symmetric CSR, Eq. 3 hybrid) for the listed vertices."""
     offsets = _c(offsets, np.int64)

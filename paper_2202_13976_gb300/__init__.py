@@ -287,6 +287,10 @@ def lcc_compute(g: int, t_out=None, lcc_out=None):
         _check_dtype(t_out, "int64")
     if lcc_out is not None:
         _check_dtype(lcc_out, "float64")
+    if t_out is not None or lcc_out is not None:
+        n, _ = tc_graph_size(g)
+        _check_room(t_out, n, "t_out")
+        _check_room(lcc_out, n, "lcc_out")
     (pt, pl), kind = _ptr_kind(t_out, lcc_out)
     _check(_lib.lcc_compute(g, pt, pl, kind))
 
@@ -423,18 +427,38 @@ def tc_graph_plan_stats(g: int) -> dict:
     return {names[b]: {"edges": e[b], "ids": i[b]} for b in range(nb)}
 
 
+def _numel(a) -> int:
+    return int(a.numel()) if hasattr(a, "numel") and callable(a.numel) else int(np.asarray(a).size)
+
+
+def _check_room(a, n: int, what: str):
+    """Refuses an output buffer with fewer than n elements (the library writes n)."""
+    if a is not None and _numel(a) < n:
+        raise ValueError(f"{what} holds {_numel(a)} elements, the graph has {n} vertices")
+
+
 def tc_count_noalloc(n: int, src, dst, t_out=None, lcc_out=None, stream=None) -> int:
     """T of a small graph without any allocation by the library (CUDA tensors only);
-    fills t_out (int64/uint64 [n]) and lcc_out (float64 [n]) when given."""
+    fills t_out (int64/uint64 [n]) and lcc_out (float64 [n]) when given.  Every
+    buffer is checked (device, dtype, length) before the call, since the kernel reads
+    len(src) pairs from both lists and writes n entries into each output."""
     load()
     for a in (src, dst, t_out, lcc_out):
         if a is not None and not _is_device(a):
             raise ValueError("tc_count_noalloc takes device buffers")
+    if _numel(src) != _numel(dst):
+        raise ValueError("src and dst differ in length")
     _check_dtype(src, "int32")
     _check_dtype(dst, "int32")
+    if t_out is not None:
+        _check_dtype(t_out, "int64")
+    if lcc_out is not None:
+        _check_dtype(lcc_out, "float64")
+    _check_room(t_out, n, "t_out")
+    _check_room(lcc_out, n, "lcc_out")
     (ps, pd, pt, pl), _ = _ptr_kind(src, dst, t_out, lcc_out)
     T = ctypes.c_uint64()
-    _check(_lib.tc_count_noalloc(n, len(src), ps, pd, ctypes.byref(T), pt, pl, _stream_ptr(stream)))
+    _check(_lib.tc_count_noalloc(n, _numel(src), ps, pd, ctypes.byref(T), pt, pl, _stream_ptr(stream)))
     return int(T.value)
 
 

@@ -3,12 +3,14 @@
 // allocates no memory at all.
 //
 // Who needs it: code that must not allocate device memory while it runs, for
-// example a caller that has handed all free HBM to its own caching allocator, a
-// caller recording work into a CUDA stream capture (where cudaMalloc is not
-// permitted), or real-time code that forbids allocation after start-up.
+// example a caller that has handed all free HBM to its own caching allocator, or
+// real-time code that forbids allocation after start-up.  The call reads its status
+// words back to the host and synchronises the caller's stream before it returns.
 //
 // The scratch array below is reserved on every GPU that loads the library for as
-// long as the process lives (TC_NOALLOC_SCRATCH_BYTES).  All calls share it and it
+// long as the process lives (TC_NOALLOC_SCRATCH_BYTES); with lazy module loading the
+// runtime places it during the first call on each device, so that call belongs at
+// start-up, before the free memory is handed to another allocator.  All calls share it and it
 // keeps the previous call's contents; the kernel clears what it needs before use.
 // Calls whose work overlaps on the GPU (two streams, or two host threads) race on
 // it and give wrong results: the caller must order them.

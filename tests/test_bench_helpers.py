@@ -39,5 +39,29 @@ def test_bench_defaults_are_one_gpu_and_minutes():
         a = bench.parse_args()
     finally:
         sys.argv = argv
-    assert a.gpus == 1 and a.impl == "ours" and a.mode == "single" and a.workload == "rmat20"
+    assert a.gpus == 1 and a.impl == "ours" and a.mode == "single" and a.workload == "rmat23"
     assert a.warmup >= 3 and 1 <= a.steps <= 200
+
+
+def test_roofline_record_reports_the_dram_fraction():
+    peak, _ = bench.measured_peak()
+    r = bench.roofline_record("k", alg_bytes=10 * 10 ** 9, kernel_ms=1.0, traffic=2 * 10 ** 9)
+    assert abs(r["achieved"] - 10000.0) < 1e-6 and abs(r["frac"] - 10000.0 / peak) < 1e-9
+    assert abs(r["dram_achieved"] - 2000.0) < 1e-6 and abs(r["dram_frac"] - 2000.0 / peak) < 1e-9
+    none = bench.roofline_record("k", alg_bytes=1, kernel_ms=1.0, traffic=None)
+    assert none["dram_frac"] is None and none["traffic"] is None
+
+
+def test_reference_sample_ranges_cover_the_sources_once():
+    import oracle
+    n = 1 << 11
+    s, d = graphgen.rmat(11, 8 * n, seed=4)
+    off, adj, _ = oracle.build_csr(n, s, d)
+    op, ap = oracle.orient(n, off, adj)
+    ranges = oracle.work_ranges(op, 64 * bench.REF_SAMPLES)
+    assert ranges[0][0] == 0 and ranges[-1][1] == n
+    assert all(a < b for a, b in ranges) and all(ranges[i][1] == ranges[i + 1][0] for i in range(len(ranges) - 1))
+    # the eight samples together give the full count
+    total = sum(oracle.tc_oriented_ranges(n, op, ap, ranges[k::bench.REF_SAMPLES], threads=2)
+                for k in range(bench.REF_SAMPLES))
+    np.testing.assert_array_equal(total, oracle.tc_oriented(n, op, ap))

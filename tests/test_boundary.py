@@ -87,3 +87,47 @@ def test_binding_rejects_wrong_dtypes(tc):
     import numpy as np
     with pytest.raises(TypeError):
         tc.tc_graph_create_from_edges(4, np.zeros(2, np.int64), np.zeros(2, np.int64))
+
+
+class _FakeDeviceBuffer:
+    """Stands in for a CUDA tensor in the binding's checks: they must reject it
+    before any call into the library, so its pointer is never read."""
+
+    is_cuda = True
+
+    def __init__(self, dtype, n):
+        self.dtype = dtype
+        self._n = n
+
+    def numel(self):
+        return self._n
+
+    def is_contiguous(self):
+        return True
+
+    def data_ptr(self):
+        raise AssertionError("the binding passed a rejected buffer to the library")
+
+
+@pytest.mark.parametrize("case", ["short_dst", "float_lcc", "short_t", "short_lcc", "int32_t_out", "host_src"])
+def test_noalloc_binding_rejects_bad_buffers_before_the_call(tc, case):
+    import numpy as np
+    n, m = 100, 50
+    src = _FakeDeviceBuffer("torch.int32", m)
+    dst = _FakeDeviceBuffer("torch.int32", m)
+    t = _FakeDeviceBuffer("torch.int64", n)
+    lc = _FakeDeviceBuffer("torch.float64", n)
+    if case == "short_dst":
+        dst = _FakeDeviceBuffer("torch.int32", m - 1)
+    elif case == "float_lcc":
+        lc = _FakeDeviceBuffer("torch.float32", n)
+    elif case == "short_t":
+        t = _FakeDeviceBuffer("torch.int64", n - 1)
+    elif case == "short_lcc":
+        lc = _FakeDeviceBuffer("torch.float64", n - 1)
+    elif case == "int32_t_out":
+        t = _FakeDeviceBuffer("torch.int32", n)
+    elif case == "host_src":
+        src = np.zeros(m, np.int32)
+    with pytest.raises((ValueError, TypeError)):
+        tc.tc_count_noalloc(n, src, dst, t, lc)

@@ -1,8 +1,8 @@
 """The no-allocation entry point (tc_count_noalloc) against the regular one.
 
 tc_count_noalloc serves callers that cannot allocate device memory while they run
-(all free memory already handed to their own allocator, work being recorded into
-a stream capture, real-time code).  It keeps its intermediate arrays in one fixed
+(all free memory already handed to their own allocator, real-time code that
+forbids allocation after start-up).  It keeps its intermediate arrays in one fixed
 device array inside the library, so consecutive calls share that array: each case
 below is run twice in a row and both results must equal those of the regular
 entry point (tc_graph_create_from_edges, tc_count, lcc_compute) exactly, the
@@ -86,3 +86,41 @@ def test_noalloc_rejects_sizes_beyond_the_limit(tc):
     # still usable afterwards
     n, (s, d) = F.complete(12)
     assert tc.tc_count_noalloc(n, torch.from_numpy(s).cuda(), torch.from_numpy(d).cuda()) == 220
+
+
+def test_noalloc_second_call_takes_no_device_memory(tc):
+    """After a first call (which may load the library's device code on this device),
+    a further call leaves the device's free memory unchanged."""
+    import torch
+    nn, s, d = CASES[1][3], CASES[1][1], CASES[1][2]
+    src = torch.from_numpy(s).cuda()
+    dst = torch.from_numpy(d).cuda()
+    t = torch.empty(nn, dtype=torch.int64, device="cuda")
+    lc = torch.empty(nn, dtype=torch.float64, device="cuda")
+    T0 = tc.tc_count_noalloc(nn, src, dst, t, lc)
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    T1 = tc.tc_count_noalloc(nn, src, dst, t, lc)
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert T1 == T0
+    assert free1 == free0
+
+
+def test_noalloc_on_a_side_stream(tc):
+    """The same results when the call runs on a stream other than the default one."""
+    import torch
+    _, s, d, n = CASES[0]
+    T0, t0, l0 = _regular(tc, n, s, d)
+    side = torch.cuda.Stream()
+    with torch.cuda.stream(side):
+        src = torch.from_numpy(s).cuda()
+        dst = torch.from_numpy(d).cuda()
+        t = torch.full((n,), -1, dtype=torch.int64, device="cuda")
+        lc = torch.full((n,), -1.0, dtype=torch.float64, device="cuda")
+    for _ in range(2):
+        T = tc.tc_count_noalloc(n, src, dst, t, lc, stream=side)
+        side.synchronize()
+        assert T == T0
+        np.testing.assert_array_equal(t.cpu().numpy().view(np.uint64), t0)
+        np.testing.assert_array_equal(lc.cpu().numpy().view(np.uint64), l0.view(np.uint64))
