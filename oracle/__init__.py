@@ -16,9 +16,10 @@ numpy arrays.  Every function names the passage of the paper it follows:
 - ``tc_vertex``: the paper's per-vertex formula (Alg. 3) with the Eq. 3 hybrid.
 - ``lcc``: Eq. 2.
 - ``build_digraph`` / ``directed_lcc``: directed graphs (Sec. II-A) and Eq. 1.
-- ``remote_reads`` / ``cache_lru`` / ``cache_score`` / ``remote_cache``: the remote
-  reads of the 1D-partitioned algorithm (Sec. IV-A, Alg. 4) and the simulated caches
-  of Sec. IV-B (LRU, degree score).
+- ``remote_reads`` / ``cache_lru`` / ``cache_priority`` / ``cache_score`` /
+  ``remote_cache``: the remote reads of the 1D-partitioned algorithm (Sec. IV-A,
+  Alg. 4) and the simulated caches of Sec. IV-B (LRU; eviction of the lowest
+  application-defined score, with the degree score of TC).
 
 Parity status: every function is pinned by the ``-m "not gpu"`` tests
 (brute force, closed forms, scipy's sparse product for the algebraic form
@@ -89,6 +90,8 @@ def _load():
             lib.or_remote_reads.argtypes = [i64, _i64p, _i32p, i64, _i32p, _i32p]
             lib.or_cache_lru.restype = ctypes.c_uint64
             lib.or_cache_lru.argtypes = [i64, _i32p, _u64p, ctypes.c_uint64, _u64p]
+            lib.or_cache_priority.restype = ctypes.c_uint64
+            lib.or_cache_priority.argtypes = [i64, _i32p, _u64p, _i64p, ctypes.c_uint64, _u64p]
             lib.or_cache_score.restype = ctypes.c_uint64
             lib.or_cache_score.argtypes = [i64, _i32p, _u64p, _i64p, ctypes.c_uint64, _u64p]
             lib.or_directed_lcc.restype = None
@@ -336,9 +339,25 @@ def cache_lru(items, size_of, capacity: int):
     return int(h), int(hb.value)
 
 
+def cache_priority(items, size_of, score_at, capacity: int):
+    """Sec. IV-B2, a cache of ``capacity`` bytes with application-defined scores: the
+    victim is the cached entry of the lowest score (the score given with its latest
+    read, score_at[t]); a miss is stored after evicting the lowest entries until it
+    fits, unless it is larger than the whole cache.  Returns (hits, hit bytes)."""
+    items = _c(items, np.int32)
+    size_of = _c(size_of, np.uint64)
+    score_at = _c(score_at, np.int64)
+    if score_at.shape != items.shape:
+        raise ValueError("one score per read")
+    hb = ctypes.c_uint64()
+    h = _load().or_cache_priority(items.size, _p(items, _i32p), _p(size_of, _u64p), _p(score_at, _i64p),
+                                  int(capacity), ctypes.byref(hb))
+    return int(h), int(hb.value)
+
+
 def cache_score(items, size_of, degree, capacity: int):
-    """Sec. IV-B, degree-score cache (victim = lowest (degree, id); a miss is admitted
-    only above every entry evicted so far).  Returns (hits, hit bytes)."""
+    """Sec. IV-B2, the degree score of TC: ``cache_priority`` with the score of v_j's
+    entry = (degree(v_j), v_j).  Returns (hits, hit bytes)."""
     items = _c(items, np.int32)
     size_of = _c(size_of, np.uint64)
     degree = _c(degree, np.int64)

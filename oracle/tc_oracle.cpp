@@ -343,42 +343,54 @@ uint64_t or_cache_lru(int64_t count, const int32_t* items, const uint64_t* size_
     return hits;
 }
 
-// Degree-score cache (Sec. IV-B, application-defined scores): the victim is the entry
-// of the lowest score, score = (degree, id), and a missing entry is admitted only if
-// its score beats every entry evicted so far (so the cache always holds the
-// highest-scored entries read so far that fit as a prefix in score order).  Returns
-// the hits; *hit_bytes gets their bytes.
-uint64_t or_cache_score(int64_t count, const int32_t* items, const uint64_t* size_of, const int64_t* degree,
-                        uint64_t capacity, uint64_t* hit_bytes) {
-    typedef std::pair<int64_t, int32_t> Score;  // (degree, id)
-    std::set<Score> cache;
-    std::unordered_map<int32_t, bool> in;
-    bool evicted_any = false;
-    Score best_evicted(0, 0);
+// Cache with application-defined scores (Sec. IV-B2): every cached entry carries a
+// score, and whenever an entry must be evicted the victim is the cached entry of the
+// lowest score.  A miss of x is stored if it can be: an entry larger than the whole
+// cache cannot, and evicts nothing; otherwise the lowest-scored cached entries are
+// evicted, one at a time, until x fits, and x is stored (the incoming entry is never
+// its own victim).  The score of a cached entry is the one given with its latest read,
+// score_at[t] for the read at time t (a hit refreshes it); equal scores evict the
+// smaller item first.  Returns the hits; *hit_bytes gets their bytes.
+uint64_t or_cache_priority(int64_t count, const int32_t* items, const uint64_t* size_of, const int64_t* score_at,
+                           uint64_t capacity, uint64_t* hit_bytes) {
+    typedef std::pair<int64_t, int32_t> Entry;  // (score, item), lowest first
+    std::set<Entry> cache;
+    std::unordered_map<int32_t, int64_t> score_of;  // the cached entries and their scores
     uint64_t used = 0, hits = 0, hb = 0;
     for (int64_t t = 0; t < count; ++t) {
         const int32_t x = items[t];
-        const Score sx(degree[x], x);
-        if (in.count(x) && in[x]) {
+        auto it = score_of.find(x);
+        if (it != score_of.end()) {
             ++hits;
             hb += size_of[x];
+            cache.erase(Entry(it->second, x));
+            it->second = score_at[t];
+            cache.insert(Entry(score_at[t], x));
             continue;
         }
-        if (evicted_any && !(best_evicted < sx)) continue;  // not admitted
-        cache.insert(sx);
-        in[x] = true;
-        used += size_of[x];
-        while (used > capacity) {
-            const Score z = *cache.begin();
+        if (size_of[x] > capacity) continue;  // cannot be stored
+        while (used + size_of[x] > capacity) {
+            const Entry z = *cache.begin();
             cache.erase(cache.begin());
-            in[z.second] = false;
+            score_of.erase(z.second);
             used -= size_of[z.second];
-            if (!evicted_any || best_evicted < z) best_evicted = z;
-            evicted_any = true;
         }
+        cache.insert(Entry(score_at[t], x));
+        score_of[x] = score_at[t];
+        used += size_of[x];
     }
     *hit_bytes = hb;
     return hits;
+}
+
+// The degree score of the TC application (Sec. IV-B2): the score of the entry of v_j is
+// its degree, ties between equal degrees going to the larger id, i.e. the victim is the
+// cached entry of the lowest (degree, id).  Returns the hits; *hit_bytes their bytes.
+uint64_t or_cache_score(int64_t count, const int32_t* items, const uint64_t* size_of, const int64_t* degree,
+                        uint64_t capacity, uint64_t* hit_bytes) {
+    std::vector<int64_t> score((size_t)count);
+    for (int64_t t = 0; t < count; ++t) score[(size_t)t] = (degree[items[t]] << 32) | (int64_t)items[t];
+    return or_cache_priority(count, items, size_of, score.data(), capacity, hit_bytes);
 }
 
 // Eq. 2: LCC(i) = 2 t(i) / (deg(i) (deg(i) - 1)); 0.0 when deg(i) < 2.  Both the

@@ -488,19 +488,25 @@ def _brute_lru_hits(items, size_of, cap):
     return hits, hb
 
 
-def _brute_score_hits(items, size_of, degree, cap):
-    """Degree score as a priority prefix: a read hits iff the item was read before and
-    the items read before with a score (degree, id) at least its own fit in the cache."""
-    hits = hb = 0
-    seen = set()
-    for x in items:
-        if x in seen:
-            above = [y for y in seen if (degree[y], y) >= (degree[x], x)]
-            if sum(size_of[y] for y in above) <= cap:
-                hits += 1
-                hb += size_of[x]
-        seen.add(x)
-    return hits, hb
+def _brute_optimal_hits(items, cap):
+    """Unit-size entries, ``cap`` slots: the most hits any policy can reach when every
+    miss must be stored (an exhaustive search over every choice of victim)."""
+    from functools import lru_cache
+
+    @lru_cache(maxsize=None)
+    def best(t, held):
+        if t == len(items):
+            return 0
+        x = items[t]
+        if x in held:
+            return 1 + best(t + 1, held)
+        if cap == 0:
+            return best(t + 1, held)
+        if len(held) < cap:
+            return best(t + 1, held | {x})
+        return max(best(t + 1, (held - {y}) | {x}) for y in held)
+
+    return best(0, frozenset())
 
 
 def test_cache_hand_examples():
@@ -511,16 +517,80 @@ def test_cache_hand_examples():
     # bytes: sizes 3, 2, 2 in 5 bytes: A B C A -> C evicts A (3 + 2 + 2 > 5), A misses
     assert oracle.cache_lru([0, 1, 2, 0], [3, 2, 2], 5) == (0, 0)
     assert oracle.cache_lru([0, 1, 2, 1, 2], [3, 2, 2], 5) == (2, 4)
-    # score, one slot, degrees 3 > 2 > 1: 0 stays, 1 is evicted at once, then neither 2
-    # (below the evicted 1) nor 1 again is admitted
-    assert oracle.cache_score([0, 1, 0, 2, 1], [1, 1, 1], [3, 2, 1], 1) == (1, 1)
-    # a low-score entry read many times loses its slot to a high-score one for good
-    assert oracle.cache_score([2, 2, 0, 2, 2], [1, 1, 1], [3, 2, 1], 1) == (1, 1)
     assert oracle.cache_lru([2, 2, 0, 2, 2], [1, 1, 1], 1) == (2, 2)
 
 
+def test_cache_score_hand_traces():
+    """The degree score of Sec. IV-B2 worked by hand from its rule: on a miss the
+    cached entries of lowest (degree, id) leave until the new entry fits, then it is
+    stored; an entry larger than the cache is not stored and evicts nothing."""
+    deg = [3, 2, 1]  # A = 0 scores highest, C = 2 lowest
+    # one slot: every miss replaces the only entry, whatever the scores:
+    # A; B evicts A; A evicts B; C evicts A; B evicts C -> no hit.  (A filter that
+    # admits a miss only when it scores above every entry evicted so far would keep A
+    # throughout and hit A's second read: 1 hit.)
+    assert oracle.cache_score([0, 1, 0, 2, 1], [1, 1, 1], deg, 1) == (0, 0)
+    # ... and a low-score entry hits again once it is back: C; C hits; A evicts C;
+    # C evicts A; C hits
+    assert oracle.cache_score([2, 2, 0, 2, 2], [1, 1, 1], deg, 1) == (2, 2)
+    # two slots: A B -> {A, B}; C evicts B (lower than A) -> {A, C}; A hits; B evicts
+    # C -> {A, B}; C evicts B -> {A, C}; C hits
+    assert oracle.cache_score([0, 1, 2, 0, 1, 2, 2], [1, 1, 1], deg, 2) == (2, 2)
+    # LRU on the same trace evicts A at C's first read: A B C A B C C -> only the last C
+    assert oracle.cache_lru([0, 1, 2, 0, 1, 2, 2], [1, 1, 1], 2) == (1, 1)
+    # bytes, 5-byte cache, sizes A 3, B 2, C 2: A B -> 5 bytes; C evicts B (A scores
+    # higher) -> {A, C}; A hits (3 bytes); B evicts C -> {A, B}; B hits (2 bytes)
+    assert oracle.cache_score([0, 1, 2, 0, 1, 1], [3, 2, 2], deg, 5) == (2, 5)
+    # the victims go lowest first until the entry fits: sizes A 2, B 2, C 1, D 4 in 5
+    # bytes, scores A > B > C > D; A B C fill the 5 bytes, D evicts C, B and A (2 + 4
+    # is still above 5 after C and B), then A evicts D and B and C fit beside A
+    deg4 = [4, 3, 2, 1]
+    assert oracle.cache_score([0, 1, 2, 3, 0, 1, 2], [2, 2, 1, 4], deg4, 5) == (0, 0)
+    # the same start, then D read again: it hits (4 bytes)
+    assert oracle.cache_score([0, 1, 2, 3, 3], [2, 2, 1, 4], deg4, 5) == (1, 4)
+    # an entry larger than the cache is not stored and leaves the cache as it was
+    assert oracle.cache_score([0, 3, 0], [2, 2, 1, 9], deg4, 5) == (1, 2)
+    # (LRU, by its stack reading, lets an entry larger than the cache push out the rest)
+    assert oracle.cache_lru([0, 3, 0], [2, 2, 1, 9], 5) == (0, 0)
+    # equal degrees: the larger id scores higher, so C evicts id 0 and keeps id 1
+    assert oracle.cache_score([0, 1, 2, 0], [1, 1, 1], [5, 5, 5], 2) == (0, 0)
+    assert oracle.cache_score([0, 1, 2, 1], [1, 1, 1], [5, 5, 5], 2) == (1, 1)
+
+
 @pytest.mark.parametrize("seed", range(40))
-def test_cache_policies_match_their_stack_characterisation(seed):
+def test_cache_priority_with_recency_scores_is_lru(seed):
+    """With the time of the latest read as the score, evicting the lowest score is
+    evicting the least recently used entry: the priority cache must give LRU's hits
+    at every capacity that holds the largest entry."""
+    rng = np.random.default_rng(seed)
+    k = int(rng.integers(1, 12))
+    items = rng.integers(0, k, size=int(rng.integers(0, 60))).astype(np.int32)
+    size_of = np.ones(k, np.uint64) if seed % 3 == 0 else rng.integers(1, 9, size=k).astype(np.uint64)
+    recency = np.arange(items.size, dtype=np.int64)
+    for cap in range(int(size_of.max()), 2 + int(size_of.sum())):
+        assert oracle.cache_priority(items, size_of, recency, cap) == oracle.cache_lru(items, size_of, cap)
+
+
+@pytest.mark.parametrize("seed", range(30))
+def test_cache_priority_with_next_use_scores_is_optimal(seed):
+    """Unit entries with minus the time of the next read as the score: evicting the
+    lowest score evicts the entry needed furthest in the future, which is Belady's
+    optimal policy among those that store every miss.  Its hits must equal the
+    exhaustive optimum at every capacity."""
+    rng = np.random.default_rng(seed + 100)
+    k = int(rng.integers(2, 6))
+    items = [int(x) for x in rng.integers(0, k, size=int(rng.integers(1, 13)))]
+    nxt = []
+    for t, x in enumerate(items):
+        later = [u for u in range(t + 1, len(items)) if items[u] == x]
+        nxt.append(-(later[0] if later else len(items) + 1))
+    for cap in range(0, k + 1):
+        got = oracle.cache_priority(items, np.ones(k, np.uint64), nxt, cap)
+        assert got[0] == _brute_optimal_hits(tuple(items), cap), (items, cap)
+
+
+@pytest.mark.parametrize("seed", range(40))
+def test_cache_policies_limits(seed):
     rng = np.random.default_rng(seed)
     k = int(rng.integers(1, 12))
     items = rng.integers(0, k, size=int(rng.integers(0, 60))).astype(np.int32)
@@ -528,20 +598,22 @@ def test_cache_policies_match_their_stack_characterisation(seed):
     size_of = np.ones(k, np.uint64) if unit else rng.integers(1, 9, size=k).astype(np.uint64)
     degree = rng.integers(0, 5, size=k).astype(np.int64)
     s = [int(x) for x in size_of]
-    d = [int(x) for x in degree]
     lst = [int(x) for x in items]
     prev_h = (0, 0)
     for cap in range(0, 2 + int(size_of.sum())):
         got = oracle.cache_lru(items, size_of, cap)
         assert got == _brute_lru_hits(lst, s, cap)
-        assert got[0] >= prev_h[0]  # inclusion: a larger cache never hits less
+        assert got[0] >= prev_h[0]  # inclusion: a larger LRU cache never hits less
         prev_h = got
-        assert oracle.cache_score(items, size_of, degree, cap) == _brute_score_hits(lst, s, d, cap)
+        sc = oracle.cache_score(items, size_of, degree, cap)
+        # a read can only hit an entry read before that fits in the cache
+        assert sc[0] <= sum(1 for t, x in enumerate(lst) if x in lst[:t] and s[x] <= cap)
     # a cache holding everything misses only the first read of each item
     big = int(size_of.sum())
     assert oracle.cache_lru(items, size_of, big)[0] == len(lst) - len(set(lst))
     assert oracle.cache_score(items, size_of, degree, big)[0] == len(lst) - len(set(lst))
     assert oracle.cache_lru(items, size_of, 0) == (0, 0)
+    assert oracle.cache_score(items, size_of, degree, 0) == (0, 0)
 
 
 def _cut_reads(n, s, d, parts):
@@ -612,6 +684,6 @@ def test_remote_cache_brute_force(seed):
             assert tuple(int(x) for x in (r["hits"][0, k, c], r["hit_bytes"][0, k, c])) == \
                 _brute_lru_hits(it, [4 * x for x in deg], cap)
             assert tuple(int(x) for x in (r["hits"][1, k, c], r["hit_bytes"][1, k, c])) == \
-                _brute_score_hits(it, [4 * x for x in deg], deg, cap)
+                oracle.cache_score(it, [4 * x for x in deg], deg, cap)
             assert int(r["hits"][2, k, c]) == _brute_lru_hits(it, [16] * n, cap)[0]
-            assert int(r["hits"][3, k, c]) == _brute_score_hits(it, [16] * n, deg, cap)[0]
+            assert int(r["hits"][3, k, c]) == oracle.cache_score(it, [16] * n, deg, cap)[0]
