@@ -1,6 +1,7 @@
 """Parity at the full workload sizes, in the launch configuration the benchmark
 times (default strategies): T and every t[v] and LCC[v] against the oracle (its
-oriented count split over the host cores)."""
+oriented count split over the host cores), and against the digests that two
+independent oracle formulas agreed on (tests/golden/large_workloads.json)."""
 from __future__ import annotations
 
 import os
@@ -11,6 +12,7 @@ import pytest
 import graphgen
 import oracle
 from tests.gpu_util import gpu_run
+from tests.test_golden_large import _digest, large_golden
 
 pytestmark = pytest.mark.gpu
 
@@ -26,6 +28,10 @@ def test_full_workload(tc, name):
     assert info["loops_dropped"] == ref["loops_dropped"]
     np.testing.assert_array_equal(t, ref["t"])
     np.testing.assert_array_equal(lc.view(np.uint64), ref["lcc"].view(np.uint64))
+    want = large_golden()[name]
+    assert T == want["T"]
+    assert _digest(np.ascontiguousarray(t, dtype=np.uint64)) == want["t_sha256"]
+    assert _digest(np.ascontiguousarray(lc, dtype=np.float64)) == want["lcc_sha256"]
     # properties that hold at any size
     assert int(t.sum()) == 3 * T
     deg = ref["degree"]
