@@ -65,6 +65,9 @@ def parse_args():
                    help="give up waiting for the backlog after this many seconds")
     p.add_argument("--serve-verify", type=int, default=24,
                    help="check this many of the smallest served requests against the oracle")
+    p.add_argument("--serve-compare-seconds", type=float, default=5.0,
+                   help="the first this many seconds of the stream are also run closed-loop through the "
+                        "server and one request at a time through the plain per-graph path (0: skip)")
     p.add_argument("--batch-graphs", type=int, default=20000)
     p.add_argument("--strategy", default=None,
                    help="override as small:name[:factor],cta:name[:factor],hub:name,hubs:mindeg:max")
@@ -532,6 +535,48 @@ def run_batch(args, rank, world, local):
     print(json.dumps(line), flush=True)
 
 
+def serve_compare(tc, reqs, slots, budget_bytes, timeout_s=600.0):
+    """Capacity of the serving loop against the plain per-graph path on the same
+    requests: (a) every request queued at once on the server (closed loop), (b) one
+    request after another through tc_request_run on one stream.  Both report T, the
+    distinct edges and the checksums of t[] and LCC[] per request, which must agree."""
+    import torch
+    stream = torch.cuda.Stream()
+    warm = reqs[: min(8, len(reqs))]
+    for r in warm:
+        tc.tc_request_run(r.id, r.workload, stream)
+    srv = tc.Server(budget_bytes, slots)
+    for r in warm:
+        srv.submit(r.id, r.workload)
+    srv.wait(len(warm), timeout_s)
+    srv.poll(len(warm) + 16)
+    t0 = time.perf_counter()
+    for r in reqs:
+        srv.submit(r.id, r.workload)
+    done = srv.wait(len(warm) + len(reqs), timeout_s)
+    served_s = time.perf_counter() - t0
+    stats = srv.stats()
+    served = {}
+    while len(served) < len(reqs):
+        got = srv.poll(len(reqs) + 16)
+        if not got:
+            break
+        for x in got:
+            served[x["id"]] = x
+    srv.stop()
+    t0 = time.perf_counter()
+    plain = {r.id: tc.tc_request_run(r.id, r.workload, stream) for r in reqs}
+    plain_s = time.perf_counter() - t0
+    keys = ("status", "T", "m_simple", "t_hash", "lcc_hash")
+    same = done and all(r.id in served and all(served[r.id][k] == plain[r.id][k] for k in keys) for r in reqs)
+    edges = sum(x["m_simple"] for x in plain.values())
+    return {"requests": len(reqs), "slots": slots, "served_s": served_s, "plain_s": plain_s,
+            "served_req_s": len(reqs) / served_s, "plain_req_s": len(reqs) / plain_s,
+            "served_edges_s": edges / served_s, "plain_edges_s": edges / plain_s,
+            "speedup_vs_plain": plain_s / served_s, "identical_results": bool(same),
+            "peak_admitted_bytes": stats["peak_bytes"]}
+
+
 def run_serve(args, rank, world, local):
     """Serving: Poisson arrivals submitted at their arrival times; latency from
     submission to the result on the host; the backlog is drained and reported."""
@@ -569,6 +614,11 @@ def run_serve(args, rank, world, local):
     launches = tc.tc_launch_count() - launches0
     ok = [x for x in results.values() if x["status"] == 0]
     lat = np.array([x["end_s"] - x["submit_s"] for x in ok]) * 1000.0
+    compare = None
+    if args.serve_compare_seconds > 0:
+        window = [r for r in reqs if r.arrival < args.serve_compare_seconds]
+        compare = serve_compare(tc, window, args.slots, int(args.budget_gb * (1 << 30)))
+        compare["window_s"] = args.serve_compare_seconds
     first = min(x["submit_s"] for x in ok)
     last = max(x["end_s"] for x in ok)
     edges = sum(x["m_simple"] for x in ok)
@@ -601,8 +651,8 @@ def run_serve(args, rank, world, local):
             "submit_phase_s": submit_end, "drain_s": last - submit_end,
             "saturated": bool((last - first) > 1.2 * args.serve_seconds),
             "max_queue": stats["max_queue"], "peak_admitted_bytes": stats["peak_bytes"],
-            "oracle_checked": verified, "oracle_mismatches": bad, "gpu_launches": launches, "clocks": clk,
-            "impl": "ours"}
+            "oracle_checked": verified, "oracle_mismatches": bad, "vs_plain_per_graph": compare,
+            "gpu_launches": launches, "clocks": clk, "impl": "ours"}
     print(json.dumps(line), flush=True)
 
 

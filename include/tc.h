@@ -140,8 +140,10 @@ tc_status tc_edge_support(tc_graph* g, int32_t* u_out, int32_t* v_out, uint32_t*
  *   TC_CACHE_OFF_LRU, TC_CACHE_OFF_SCORE   offsets, an entry of 16 bytes
  * LRU: a miss inserts the entry as the most recent and evicts the least recent until
  * the entries fit (an entry larger than the cache is never held).  SCORE
- * (application-defined scores): the victim is the entry of the lowest (degree, id)
- * and a miss is admitted only if its score beats every entry evicted so far.
+ * (application-defined scores, Sec. IV-B2): whenever an entry must be evicted the
+ * victim is the cached entry of the lowest (degree, id); a miss is stored after
+ * evicting the lowest entries until it fits, unless it is larger than the whole
+ * cache (then it is not stored and nothing is evicted).
  *   hits, hit_bytes   host uint64[TC_CACHE_KINDS][parts][ncap] or NULL: the reads that
  *                     hit (and their bytes) per cache, process and capacity
  *   part_stats        host tc_remote_part[parts] or NULL
@@ -458,6 +460,16 @@ tc_status tc_server_wait(tc_server* s, int64_t completed, double timeout_s);
 tc_status tc_server_get_stats(tc_server* s, tc_server_stats* out);
 /* Stops accepting, finishes every queued request, joins the workers, frees s. */
 tc_status tc_server_stop(tc_server* s);
+/*
+ * One request alone on the caller's stream: the plain per-graph path that the serving
+ * loop is measured against.  Generates the request's graph on the device, builds it,
+ * counts T, t[] and LCC[] (tc_graph_create_from_edges, tc_count, lcc_compute) and
+ * releases it; *out gets the fields a served request's result has (T, m_simple and
+ * the checksums of t[] and LCC[]; status in out->status; end_s = seconds the call
+ * took, submit_s = start_s = 0).  Synchronises the stream.  Errors: TC_EINVAL for a
+ * NULL pointer or a bad request, TC_ECUDA.
+ */
+tc_status tc_request_run(const tc_request* r, void* cuda_stream, tc_result* out);
 
 /*
  * Count without allocating (an addition of this library; the paper has no

@@ -33,7 +33,7 @@ EXPORTS = ["tc_graph_create_from_edges", "tc_graph_create_from_csr", "tc_count",
            "tc_graph_set_tuning", "tc_graph_autotune", "tc_batch_run", "tc_release_cached_graphs",
            "tc_generate_edges", "tc_server_start", "tc_server_submit", "tc_server_poll", "tc_server_wait",
            "tc_server_get_stats", "tc_server_stop", "tc_graph_build_timing", "tc_count_vertex_formula",
-           "tc_edge_support", "tc_directed_lcc", "tc_remote_cache"]
+           "tc_edge_support", "tc_directed_lcc", "tc_remote_cache", "tc_request_run"]
 BUILD_PHASES = ["ingest_ms", "rank_ms", "count_ms", "fill_ms", "sort_ms", "degree_ms", "total_ms"]
 TC_GEN_RMAT, TC_GEN_ER_REPLACE = 0, 1
 GEN_KINDS = {"rmat": TC_GEN_RMAT, "er_replace": TC_GEN_ER_REPLACE}
@@ -199,6 +199,8 @@ def load(path: str | None = None):
     lib.tc_server_get_stats.argtypes = [P, ctypes.POINTER(TcServerStats)]
     lib.tc_server_stop.restype = st
     lib.tc_server_stop.argtypes = [P]
+    lib.tc_request_run.restype = st
+    lib.tc_request_run.argtypes = [ctypes.POINTER(TcRequest), P, ctypes.POINTER(TcResult)]
     lib.tc_count_noalloc.restype = st
     lib.tc_count_noalloc.argtypes = [i32, i64, P, P, ctypes.POINTER(u64), P, P, P]
     _lib = lib
@@ -573,6 +575,16 @@ class Server:
         if self._h:
             _check(_lib.tc_server_stop(self._h))
             self._h = ctypes.c_void_p()
+
+
+def tc_request_run(rid: int, workload, stream=None) -> dict:
+    """One serving request alone on ``stream`` (the plain per-graph path): the same
+    result fields as a served request's; ``end_s`` = seconds the call took."""
+    load()
+    r = TcRequest(rid, GEN_KINDS[workload.kind], workload.n, workload.m, workload.seed, workload.stream)
+    out = TcResult()
+    _check(_lib.tc_request_run(ctypes.byref(r), _stream_ptr(stream), ctypes.byref(out)))
+    return out.to_dict()
 
 
 def tc_launch_count() -> int:

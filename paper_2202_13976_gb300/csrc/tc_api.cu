@@ -739,6 +739,7 @@ tc_status tc_remote_cache(tc_graph* g, int32_t parts, int32_t ncap, const uint64
     if (st != TC_OK) return st;
     if (h.err & ERR_BAD_ID) return TC_EINVAL;
     const size_t cells = (size_t)TC_CACHE_KINDS * (size_t)parts * (size_t)ncap;
+    const size_t half = cells / 2;  // per policy: 2 caches x processes x capacities
     if (hits) memset(hits, 0, sizeof(uint64_t) * cells);
     if (hit_bytes) memset(hit_bytes, 0, sizeof(uint64_t) * cells);
     if (part_stats) memset(part_stats, 0, sizeof(tc_remote_part) * (size_t)parts);
@@ -767,7 +768,8 @@ tc_status tc_remote_cache(tc_graph* g, int32_t parts, int32_t ncap, const uint64
         (st = dalloc(g, &R.item, (size_t)R.ms2, &tmp)) || (st = dalloc(g, &R.part, (size_t)R.ms2, &tmp)) ||
         (st = dalloc(g, &R.pc, (size_t)parts, &tmp)) || (st = dalloc(g, &rtmp, radix_tmp_bytes(big), &tmp)) ||
         (st = dalloc(g, &stmp, scan_tmp_bytes(big + 1), &tmp)) || (st = dalloc(g, &dcaps, (size_t)ncap, &tmp)) ||
-        (st = dalloc(g, &R.cnt, cells, &tmp)) || (st = dalloc(g, &R.byt, cells, &tmp))) {
+        (st = dalloc(g, &R.cnt, half, &tmp)) || (st = dalloc(g, &R.byt, half, &tmp)) ||
+        (st = dalloc(g, &R.sc_cnt, half, &tmp)) || (st = dalloc(g, &R.sc_byt, half, &tmp))) {
         free_list(g, &tmp);
         return st;
     }
@@ -778,8 +780,10 @@ tc_status tc_remote_cache(tc_graph* g, int32_t parts, int32_t ncap, const uint64
     if (ncap > 0) e = cudaMemcpyAsync(dcaps, capacity_bytes, sizeof(uint64_t) * (size_t)ncap, cudaMemcpyHostToDevice,
                                       g->stream);
     cudaMemsetAsync(R.pc, 0, sizeof(PartCounters) * (size_t)parts, g->stream);
-    cudaMemsetAsync(R.cnt, 0, sizeof(unsigned long long) * cells, g->stream);
-    cudaMemsetAsync(R.byt, 0, sizeof(unsigned long long) * cells, g->stream);
+    cudaMemsetAsync(R.cnt, 0, sizeof(unsigned long long) * half, g->stream);
+    cudaMemsetAsync(R.byt, 0, sizeof(unsigned long long) * half, g->stream);
+    cudaMemsetAsync(R.sc_cnt, 0, sizeof(unsigned long long) * half, g->stream);
+    cudaMemsetAsync(R.sc_byt, 0, sizeof(unsigned long long) * half, g->stream);
     launch_rc_stream(R, g->L);
     uint32_t N32 = 0;
     if (e == cudaSuccess) e = cudaMemcpyAsync(&N32, R.pos + R.ms2, sizeof(uint32_t), cudaMemcpyDeviceToHost, g->stream);
@@ -792,44 +796,79 @@ tc_status tc_remote_cache(tc_graph* g, int32_t parts, int32_t ncap, const uint64
     if (N > 0) {
         const size_t n1 = (size_t)N;
         if ((st = dalloc(g, &R.prev, n1, &tmp)) || (st = dalloc(g, &R.pstart, (size_t)parts + 1, &tmp)) ||
-            (st = dalloc(g, &R.key_lru, n1, &tmp)) || (st = dalloc(g, &R.key_score, n1, &tmp)) ||
-            (st = dalloc(g, &R.wdeg, n1, &tmp)) ||
+            (st = dalloc(g, &R.key_lru, n1, &tmp)) || (st = dalloc(g, &R.wdeg, n1, &tmp)) ||
             (st = dalloc(g, &R.q_lru, n1, &tmp)) || (st = dalloc(g, &R.th_lru, n1, &tmp)) ||
-            (st = dalloc(g, &R.q_score, 2 * n1, &tmp)) || (st = dalloc(g, &R.th_score, 2 * n1, &tmp)) ||
             (st = dalloc(g, &R.e0deg, n1 + 1, &tmp)) ||
             (st = dalloc(g, &R.lk, (size_t)rc_levels(N) * n1, &tmp)) ||
             (st = dalloc(g, &R.le, (size_t)rc_levels(N) * (n1 + 1), &tmp)) || (st = dalloc(g, &R.la[0], n1, &tmp)) ||
-            (st = dalloc(g, &R.la[1], n1, &tmp)) ||
-            (st = dalloc(g, &R.f_lru_deg, n1, &tmp)) ||
-            (st = dalloc(g, &R.f_lru_one, n1, &tmp)) || (st = dalloc(g, &R.f_sc_deg, 2 * n1, &tmp)) ||
-            (st = dalloc(g, &R.f_sc_one, 2 * n1, &tmp))) {
+            (st = dalloc(g, &R.la[1], n1, &tmp)) || (st = dalloc(g, &R.f_lru_deg, n1, &tmp)) ||
+            (st = dalloc(g, &R.f_lru_one, n1, &tmp)) || (st = dalloc(g, &R.ukeys, n1, &tmp)) ||
+            (st = dalloc(g, &R.udeg, n1, &tmp)) || (st = dalloc(g, &R.ubase, (size_t)parts + 1, &tmp)) ||
+            (st = dalloc(g, &R.lr, n1, &tmp))) {
             free_list(g, &tmp);
             return st;
         }
         launch_rc_caches(R, N, g->L);
+        // the score simulations size their bitmaps by the largest process's count of
+        // distinct entries
+        std::vector<int64_t> ub((size_t)parts + 1);
+        e = cudaMemcpyAsync(ub.data(), R.ubase, sizeof(int64_t) * ub.size(), cudaMemcpyDeviceToHost, g->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(g->stream);
+        if (e != cudaSuccess) {
+            free_list(g, &tmp);
+            return cuda_fail("tc_remote_cache: distinct entries", e);
+        }
+        int64_t dmax = 0;
+        for (int32_t k = 0; k < parts; ++k) dmax = std::max(dmax, ub[(size_t)k + 1] - ub[(size_t)k]);
+        const RcSimShape S = rc_sim_shape(dmax);
+        if (!S.shared && (st = dalloc(g, &R.sim_state, S.bytes / 4 * half, &tmp))) {
+            free_list(g, &tmp);
+            return st;
+        }
+        launch_rc_score(R, S, g->L);
     }
-    std::vector<unsigned long long> hc(cells), hb(cells);
+    std::vector<unsigned long long> hc(half), hb(half), sc(half), sb(half);
     std::vector<PartCounters> hp((size_t)parts);
     e = cudaGetLastError();
-    if (e == cudaSuccess && cells)
-        e = cudaMemcpyAsync(hc.data(), R.cnt, sizeof(unsigned long long) * cells, cudaMemcpyDeviceToHost, g->stream);
-    if (e == cudaSuccess && cells)
-        e = cudaMemcpyAsync(hb.data(), R.byt, sizeof(unsigned long long) * cells, cudaMemcpyDeviceToHost, g->stream);
+    const size_t hbytes = sizeof(unsigned long long) * half;
+    if (e == cudaSuccess && half) e = cudaMemcpyAsync(hc.data(), R.cnt, hbytes, cudaMemcpyDeviceToHost, g->stream);
+    if (e == cudaSuccess && half) e = cudaMemcpyAsync(hb.data(), R.byt, hbytes, cudaMemcpyDeviceToHost, g->stream);
+    if (e == cudaSuccess && half) e = cudaMemcpyAsync(sc.data(), R.sc_cnt, hbytes, cudaMemcpyDeviceToHost, g->stream);
+    if (e == cudaSuccess && half) e = cudaMemcpyAsync(sb.data(), R.sc_byt, hbytes, cudaMemcpyDeviceToHost, g->stream);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(hp.data(), R.pc, sizeof(PartCounters) * (size_t)parts, cudaMemcpyDeviceToHost, g->stream);
     free_list(g, &tmp);
     if (e == cudaSuccess) e = cudaStreamSynchronize(g->stream);
     if (e != cudaSuccess) return cuda_fail("tc_remote_cache", e);
-    // a read that fits capacity c fits every larger one: hits are prefix sums over c
-    for (size_t row = 0; ncap > 0 && row < (size_t)TC_CACHE_KINDS * (size_t)parts; ++row) {
-        uint64_t sc = 0, sb = 0;
-        for (int32_t c = 0; c < ncap; ++c) {
-            sc += hc[row * (size_t)ncap + (size_t)c];
-            sb += hb[row * (size_t)ncap + (size_t)c];
-            if (hits) hits[row * (size_t)ncap + (size_t)c] = sc;
-            if (hit_bytes) hit_bytes[row * (size_t)ncap + (size_t)c] = sb;
+    for (size_t i = 0; i < half; ++i)
+        if (sc[i] == RC_SIM_BROKEN) {
+            snprintf(g_last_error, sizeof(g_last_error), "tc_remote_cache: a score simulation found no entry to evict");
+            return TC_EINTERNAL;
         }
-    }
+    // rows of the policy arrays: cache 0 = adjacency lists, 1 = offsets
+    const int lru_kind[2] = {TC_CACHE_ADJ_LRU, TC_CACHE_OFF_LRU};
+    const int score_kind[2] = {TC_CACHE_ADJ_SCORE, TC_CACHE_OFF_SCORE};
+    for (int w = 0; ncap > 0 && w < 2; ++w)
+        for (int32_t k = 0; k < parts; ++k) {
+            const size_t src = ((size_t)w * (size_t)parts + (size_t)k) * (size_t)ncap;
+            const size_t dl = ((size_t)lru_kind[w] * (size_t)parts + (size_t)k) * (size_t)ncap;
+            const size_t ds = ((size_t)score_kind[w] * (size_t)parts + (size_t)k) * (size_t)ncap;
+            // LRU: a read that fits capacity c fits every larger one, so its hits are
+            // prefix sums of the histogram; the score caches are simulated per capacity
+            uint64_t cs = 0, bs = 0;
+            for (int32_t c = 0; c < ncap; ++c) {
+                cs += hc[src + (size_t)c];
+                bs += hb[src + (size_t)c];
+                if (hits) {
+                    hits[dl + (size_t)c] = cs;
+                    hits[ds + (size_t)c] = sc[src + (size_t)c];
+                }
+                if (hit_bytes) {
+                    hit_bytes[dl + (size_t)c] = bs;
+                    hit_bytes[ds + (size_t)c] = sb[src + (size_t)c];
+                }
+            }
+        }
     if (part_stats)
         for (int32_t k = 0; k < parts; ++k) {
             part_stats[k].reads = (int64_t)hp[(size_t)k].reads;

@@ -220,8 +220,12 @@ struct PartCounters {  // per process; four 64-bit fields, nothing else (indexed
 };
 static_assert(sizeof(PartCounters) == 32, "PartCounters layout");
 
-// Cells of the shared-memory hit histogram (4 caches x processes x capacities).
+// Cells of the shared-memory hit histogram (2 LRU caches x processes x capacities).
 constexpr int RC_HIST_SHARED = 3072;
+// Hit count a score simulation reports when its state broke an invariant.
+constexpr unsigned long long RC_SIM_BROKEN = ~0ull;
+// Largest bitmap set of one score simulation kept in shared memory.
+constexpr size_t RC_SIM_SHARED_MAX = 200 * 1024;
 
 struct RemoteCacheBuffers {
     int32_t n, parts, ncap;
@@ -238,8 +242,9 @@ struct RemoteCacheBuffers {
     int32_t* prank;              // n: position in (degree, id) order
     uint64_t* vkeys;             // n
     uint64_t* vkeys_alt;         // n
+    const uint64_t* vsorted;     // set by launch_rc_stream: (degree << b) | id in score order
     int64_t* estart;             // n + 1
-    uint64_t* keys;              // ms2 (later: N item keys)
+    uint64_t* keys;              // ms2 (later: N item keys, then N score keys)
     uint64_t* keys_alt;          // ms2
     uint32_t* flag;              // ms2
     uint32_t* pos;               // ms2 + 1
@@ -248,28 +253,41 @@ struct RemoteCacheBuffers {
     PartCounters* pc;            // parts
     void* radix_tmp;             // radix_tmp_bytes(max(ms2, n))
     void* scan_tmp;              // scan_tmp_bytes(max(ms2, n) + 1)
-    // cache phase (N reads)
+    // LRU caches (N reads)
     int64_t* prev;               // N
     int64_t* pstart;             // parts + 1
-    uint32_t *key_lru, *key_score, *wdeg;  // N each
+    uint32_t *key_lru, *wdeg;    // N each
     int64_t* q_lru;              // N
     uint32_t* th_lru;            // N
-    int64_t* q_score;            // 2 N
-    uint32_t* th_score;          // 2 N
     int64_t* e0deg;              // N + 1
     uint32_t* lk;                // rc_levels(N) * N: the tree's keys, level RC_LOW + j at j * N
     int64_t* le;                 // rc_levels(N) * (N + 1): prefix sums of each level's entry sizes
     uint32_t* la[2];             // N each: entry sizes of the current and the next level
     int64_t *f_lru_deg, *f_lru_one;  // N each
-    int64_t *f_sc_deg, *f_sc_one;    // 2 N each
-    unsigned long long *cnt, *byt;   // 4 * parts * ncap each
+    unsigned long long *cnt, *byt;   // 2 * parts * ncap each (adjacency, offsets)
+    // score caches (N reads)
+    uint64_t* ukeys;             // N: distinct (process << b | score position) keys, sorted
+    uint32_t* udeg;              // N: degree of the entry of each distinct key
+    int64_t* ubase;              // parts + 1: first distinct key of each process
+    int32_t* lr;                 // N: score rank of each read's entry within its process
+    uint32_t* sim_state;         // bitmaps of every simulation when they exceed shared memory
+    unsigned long long *sc_cnt, *sc_byt;  // 2 * parts * ncap each (adjacency, offsets)
 };
 int rc_key_bits(int32_t n);
 // Levels of the merge-sort tree kept for N reads (levels 5 .. floor(log2 N)).
 int rc_levels(int64_t N);
-// The read stream (N = pos[ms2] reads), then, once N is known, the caches.
-void launch_rc_stream(const RemoteCacheBuffers& R, const Launch& L);
+// The read stream (N = pos[ms2] reads), then, once N is known, the LRU caches and the
+// score ranks; then, once the largest count of distinct entries of a process is known,
+// the score simulations.
+void launch_rc_stream(RemoteCacheBuffers& R, const Launch& L);
 void launch_rc_caches(const RemoteCacheBuffers& R, int64_t N, const Launch& L);
+struct RcSimShape {
+    uint32_t W1, W2;      // words of the two bitmap levels
+    size_t bytes;         // per simulation
+    bool shared;          // bitmaps in shared memory (else sim_state, bytes per job)
+};
+RcSimShape rc_sim_shape(int64_t max_distinct);
+void launch_rc_score(const RemoteCacheBuffers& R, const RcSimShape& S, const Launch& L);
 
 // ---- batch (tc_batch.cu) -------------------------------------------------------
 void launch_batch_relabel(int32_t G, const int64_t* edge_off, const int32_t* vbase, const int32_t* src,

@@ -83,10 +83,10 @@ struct tc_server {
 
 namespace {
 
-void run_one(tc_server* s, cudaStream_t stream, const tc_request& r, tc_result* out) {
+void run_one(cudaMemPool_t pool, int sms, cudaStream_t stream, const tc_request& r, tc_result* out) {
     out->status = TC_OK;
     const size_t n = (size_t)r.n;
-    Launch L{stream, s->sms};
+    Launch L{stream, sms};
     int32_t *src = nullptr, *dst = nullptr;
     unsigned long long* t = nullptr;
     double* lcc = nullptr;
@@ -98,11 +98,11 @@ void run_one(tc_server* s, cudaStream_t stream, const tc_request& r, tc_result* 
     auto fail = [&](tc_status st) { out->status = st; };
     do {
         const size_t me = r.m > 0 ? (size_t)r.m : 1;
-        if ((e = cudaMallocFromPoolAsync((void**)&src, 4 * me, s->pool, stream)) != cudaSuccess ||
-            (e = cudaMallocFromPoolAsync((void**)&dst, 4 * me, s->pool, stream)) != cudaSuccess ||
-            (e = cudaMallocFromPoolAsync((void**)&t, 8 * (n ? n : 1), s->pool, stream)) != cudaSuccess ||
-            (e = cudaMallocFromPoolAsync((void**)&lcc, 8 * (n ? n : 1), s->pool, stream)) != cudaSuccess ||
-            (e = cudaMallocFromPoolAsync((void**)&sums, 16, s->pool, stream)) != cudaSuccess) {
+        if ((e = cudaMallocFromPoolAsync((void**)&src, 4 * me, pool, stream)) != cudaSuccess ||
+            (e = cudaMallocFromPoolAsync((void**)&dst, 4 * me, pool, stream)) != cudaSuccess ||
+            (e = cudaMallocFromPoolAsync((void**)&t, 8 * (n ? n : 1), pool, stream)) != cudaSuccess ||
+            (e = cudaMallocFromPoolAsync((void**)&lcc, 8 * (n ? n : 1), pool, stream)) != cudaSuccess ||
+            (e = cudaMallocFromPoolAsync((void**)&sums, 16, pool, stream)) != cudaSuccess) {
             cudaGetLastError();
             fail(TC_ENOMEM);
             break;
@@ -122,7 +122,7 @@ void run_one(tc_server* s, cudaStream_t stream, const tc_request& r, tc_result* 
             break;
         }
         cudaMemsetAsync(sums, 0, 16, stream);
-        k_checksum<<<grid_for(r.n, 256, s->sms), 256, 0, stream>>>(r.n, t, lcc, sums);
+        k_checksum<<<grid_for(r.n, 256, sms), 256, 0, stream>>>(r.n, t, lcc, sums);
         count_launch();
         if ((e = cudaMemcpyAsync(h, sums, 16, cudaMemcpyDeviceToHost, stream)) != cudaSuccess ||
             (e = cudaStreamSynchronize(stream)) != cudaSuccess) {
@@ -176,7 +176,7 @@ void worker_main(tc_server* s, int slot) {
         res.bytes = bytes;
         res.submit_s = submit;
         res.start_s = now_s(s->t0);
-        run_one(s, stream, r, &res);
+        run_one(s->pool, s->sms, stream, r, &res);
         res.end_s = now_s(s->t0);
         {
             std::lock_guard<std::mutex> lock(s->mu);
@@ -271,6 +271,24 @@ extern "C" tc_status tc_server_stop(tc_server* s) {
     s->cv_work.notify_all();
     for (auto& w : s->workers) w.join();
     delete s;
+    return TC_OK;
+}
+
+extern "C" tc_status tc_request_run(const tc_request* r, void* cuda_stream, tc_result* out) {
+    if (!r || !out || r->n < 0 || r->m < 0 || r->m > INT32_MAX || (r->kind != TC_GEN_RMAT && r->kind != TC_GEN_ER_REPLACE) ||
+        (r->m > 0 && r->n == 0))
+        return TC_EINVAL;
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return TC_ECUDA;
+    cudaMemPool_t pool = device_pool(dev);
+    if (!pool) return TC_ECUDA;
+    *out = tc_result{};
+    out->id = r->id;
+    out->bytes = serve_estimate_bytes(r->n, r->m);
+    const auto t0 = std::chrono::steady_clock::now();
+    run_one(pool, sms, static_cast<cudaStream_t>(cuda_stream), *r, out);
+    out->end_s = now_s(t0);
     return TC_OK;
 }
 

@@ -124,3 +124,23 @@ def test_bad_requests_are_rejected(tc):
             srv.submit(1, w)
     finally:
         srv.stop()
+
+
+def test_plain_request_run_matches_the_server(tc):
+    """tc_request_run (one request alone on the caller's stream, the path the serving
+    loop is measured against) reports the same T, edges and checksums as the server
+    and the oracle."""
+    import torch
+    reqs = _requests(12)
+    served, _ = _serve(tc, reqs, slots=4, alone=False)
+    side = torch.cuda.Stream()
+    for r in reqs:
+        x = tc.tc_request_run(r.id, r.workload, side)
+        assert x["status"] == 0 and x["id"] == r.id
+        for k in ("T", "m_simple", "t_hash", "lcc_hash"):
+            assert x[k] == served[r.id][k], (r.id, k)
+        ref = oracle.triangles(r.workload.n, *r.workload.edges())
+        assert x["T"] == ref["T"] and x["m_simple"] == ref["m_simple"]
+        assert (x["t_hash"], x["lcc_hash"]) == checksums(ref["t"], ref["lcc"])
+    with pytest.raises(tc.TCError):
+        tc.tc_request_run(0, graphgen.Workload("bad", "rmat", 0, 10, 5, 1, scale=1))
