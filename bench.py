@@ -424,6 +424,29 @@ def gen_batch(G, seed=4):
     return n, off, src, dst
 
 
+def batch_oracle_check(G, T_batch, t_out, l_out):
+    """The batch's per-graph T, t[] and LCC[] against the digests of the oracle's
+    results on the same 20,000 graphs (tests/golden/batch_workload.json, written by
+    tests/golden/make_golden.py --batch); None for another batch size."""
+    import hashlib
+
+    import numpy as np
+    path = os.path.join(ROOT, "tests", "golden", "batch_workload.json")
+    try:
+        gold = json.load(open(path))
+    except Exception:
+        return None
+    if gold.get("graphs") != G:
+        return None
+
+    def digest(a):
+        return hashlib.sha256(np.ascontiguousarray(a).tobytes()).hexdigest()
+
+    return {"T": digest(T_batch) == gold["T_sha256"],
+            "t": digest(t_out.cpu().numpy().view(np.uint64)) == gold["t_sha256"],
+            "lcc": digest(l_out.cpu().numpy()) == gold["lcc_sha256"]}
+
+
 def run_batch(args, rank, world, local):
     """Batched workload: all graphs per step through the batch entry point, against
     the plain per-graph path (one create/count/LCC/destroy per graph) on the same GPU."""
@@ -490,6 +513,7 @@ def run_batch(args, rank, world, local):
     clk = clocks.stop()
     launches = tc.tc_launch_count() - launches0
     T_batch = T_dev.cpu().numpy().view(np.uint64).copy()
+    oracle_match = batch_oracle_check(G, T_batch, t_out, l_out)
     for _ in range(2):
         batched_eager()
     ms_eager = timed(batched_eager, stream)
@@ -531,6 +555,7 @@ def run_batch(args, rank, world, local):
             "per_graph_path": {"graphs_per_s": G / plain_s, "edges_per_s": m_simple / plain_s, "s": plain_s},
             "speedup_vs_per_graph": plain_s / (ms_batch / 1000.0),
             "identical_T": bool((T_batch == T_plain).all()),
+            "oracle_digests_match": oracle_match,
             "gpu_launches": launches, "clocks": clk, "impl": "ours"}
     print(json.dumps(line), flush=True)
 

@@ -246,21 +246,28 @@ const char* tc_last_error_detail(void);
  *                      search with every element of the streamed list
  *   TC_STRAT_BITMAP    the staged list is a bitmap over its rank window, probed
  *                      with one shared-memory load per streamed element
+ *   TC_STRAT_HASH      (small bucket) for sources with more than 16 entries, N+(u)
+ *                      is a hash set in shared memory and the rows N+(v) of all of
+ *                      u's edges are read end to end, one element per lane, each
+ *                      probed once in the set; shorter sources as AUTO
  */
 enum {
     TC_STRAT_AUTO = 0,
     TC_STRAT_MERGE = 1,
     TC_STRAT_SEARCH = 2,
     TC_STRAT_PROBE = 3,
-    TC_STRAT_BITMAP = 4
+    TC_STRAT_BITMAP = 4,
+    TC_STRAT_HASH = 5
 };
 
 /*
  * Buckets of the planner.  Vertices are ranked by (degree, id); every edge is
  * oriented from the lower to the higher rank, and N+(u) is the oriented row of u.
- *   TC_BUCKET_SMALL  edges (u, v), v not a hub, 2 <= |N+(u)| <= 32: groups of 8, 16
- *                    or 32 lanes per source vertex, one lane per edge
- *                    (strategies AUTO, MERGE, SEARCH)
+ *   TC_BUCKET_SMALL  edges (u, v), v not a hub, 2 <= |N+(u)| <= 256: groups of 8, 16
+ *                    or 32 lanes per source vertex; HASH (the default) reads the
+ *                    rows of all of u's edges end to end across the lanes (sources
+ *                    of more than 16 entries), AUTO, MERGE and SEARCH take one edge
+ *                    per lane
  *   TC_BUCKET_CTA    edges (u, v), v not a hub, |N+(u)| > 32: one thread block per
  *                    source vertex, N+(u) staged in shared memory, one warp per
  *                    edge (AUTO, MERGE, SEARCH, PROBE, BITMAP)

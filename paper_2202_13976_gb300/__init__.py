@@ -17,12 +17,12 @@ from ._build import LIB, build as _build_lib, source_digest, up_to_date
 
 TC_OK, TC_EINVAL, TC_ENOMEM, TC_ECUDA, TC_ETIMEOUT, TC_EBUSY, TC_EINTERNAL = range(7)
 TC_MEM_HOST, TC_MEM_DEVICE = 0, 1
-TC_STRAT_AUTO, TC_STRAT_MERGE, TC_STRAT_SEARCH, TC_STRAT_PROBE, TC_STRAT_BITMAP = range(5)
+TC_STRAT_AUTO, TC_STRAT_MERGE, TC_STRAT_SEARCH, TC_STRAT_PROBE, TC_STRAT_BITMAP, TC_STRAT_HASH = range(6)
 TC_BUCKET_SMALL, TC_BUCKET_CTA, TC_BUCKET_HUB = 0, 1, 2
 BUCKETS = {"small": TC_BUCKET_SMALL, "cta": TC_BUCKET_CTA, "hub": TC_BUCKET_HUB}
 PHASES = ["plan_ms", "small_ms", "cta_ms", "hub_ms", "total_ms"]
 STRATEGIES = {"auto": TC_STRAT_AUTO, "merge": TC_STRAT_MERGE, "search": TC_STRAT_SEARCH,
-              "probe": TC_STRAT_PROBE, "bitmap": TC_STRAT_BITMAP}
+              "probe": TC_STRAT_PROBE, "bitmap": TC_STRAT_BITMAP, "hash": TC_STRAT_HASH}
 
 # Every symbol include/tc.h declares.
 EXPORTS = ["tc_graph_create_from_edges", "tc_graph_create_from_csr", "tc_count", "lcc_compute",

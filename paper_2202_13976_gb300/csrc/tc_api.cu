@@ -191,6 +191,7 @@ tc_status new_graph(int32_t n, void* stream, tc_graph** out) {
         g->strat.strat[b] = TC_STRAT_AUTO;
         g->strat.factor[b] = 1.0f;
     }
+    g->strat.strat[TC_BUCKET_SMALL] = TC_STRAT_HASH;
     g->strat.strat[TC_BUCKET_CTA] = TC_STRAT_BITMAP;
     g->strat.hub_min_degree = 32;
     g->strat.hub_max = HUB_BM_BITS;
@@ -353,7 +354,7 @@ tc_status build_graph(tc_graph* g, const int32_t* src, const int32_t* dst, int64
         const double mean = n > 0 ? 2.0 * (double)m / (double)n : 0.0;
         B.bucket_fill = m > 0 && (double)h.max_deg <= 64.0 * mean;
     }
-    if (B.bucket_fill && (st = dalloc(g, &B.oriented, (size_t)m, &scratch)) != TC_OK) {
+    if (m > 0 && (st = dalloc(g, &B.oriented, (size_t)m, &scratch)) != TC_OK) {
         free_list(g, &scratch);
         return st;
     }
@@ -920,10 +921,11 @@ const char* tc_status_str(tc_status s) {
 const char* tc_last_error_detail(void) { return g_last_error; }
 
 tc_status tc_graph_set_strategy(tc_graph* g, int bucket, int strategy, double factor) {
-    if (!g || bucket < 0 || bucket >= TC_NUM_BUCKETS || strategy < TC_STRAT_AUTO || strategy > TC_STRAT_BITMAP ||
+    if (!g || bucket < 0 || bucket >= TC_NUM_BUCKETS || strategy < TC_STRAT_AUTO || strategy > TC_STRAT_HASH ||
         !(factor > 0.0))
         return TC_EINVAL;
     if (bucket == TC_BUCKET_SMALL && (strategy == TC_STRAT_PROBE || strategy == TC_STRAT_BITMAP)) return TC_EINVAL;
+    if (bucket != TC_BUCKET_SMALL && strategy == TC_STRAT_HASH) return TC_EINVAL;
     if (bucket == TC_BUCKET_HUB && (strategy == TC_STRAT_MERGE || strategy == TC_STRAT_SEARCH)) return TC_EINVAL;
     g->strat.strat[bucket] = strategy;
     g->strat.factor[bucket] = (float)factor;
@@ -1145,8 +1147,9 @@ static tc_status tuning_check(const tc_tuning* t) {
     if (!t) return TC_EINVAL;
     for (int b = 0; b < TC_NUM_BUCKETS; ++b) {
         const int s = t->strategy[b];
-        if (s < TC_STRAT_AUTO || s > TC_STRAT_BITMAP || !(t->factor[b] > 0.0)) return TC_EINVAL;
+        if (s < TC_STRAT_AUTO || s > TC_STRAT_HASH || !(t->factor[b] > 0.0)) return TC_EINVAL;
         if (b == TC_BUCKET_SMALL && (s == TC_STRAT_PROBE || s == TC_STRAT_BITMAP)) return TC_EINVAL;
+        if (b != TC_BUCKET_SMALL && s == TC_STRAT_HASH) return TC_EINVAL;
         if (b == TC_BUCKET_HUB && (s == TC_STRAT_MERGE || s == TC_STRAT_SEARCH)) return TC_EINVAL;
     }
     if (t->hub_min_degree < 0 || t->hub_max < 0 || t->hub_big_in < 1 || t->hub_core < 0) return TC_EINVAL;
@@ -1185,6 +1188,7 @@ static tc_tuning default_tuning() {
         t.strategy[b] = TC_STRAT_AUTO;
         t.factor[b] = 1.0;
     }
+    t.strategy[TC_BUCKET_SMALL] = TC_STRAT_HASH;
     t.strategy[TC_BUCKET_CTA] = TC_STRAT_BITMAP;
     t.hub_min_degree = 32;
     t.hub_max = HUB_BM_BITS;
@@ -1265,8 +1269,8 @@ extern "C" tc_status tc_graph_autotune(tc_graph* g, int32_t force, tc_tuning* ou
         }
     }
     // 2. per-bucket strategy, each bucket judged by its own kernel time
-    const int sm_s[] = {TC_STRAT_AUTO, TC_STRAT_AUTO, TC_STRAT_AUTO, TC_STRAT_MERGE, TC_STRAT_SEARCH};
-    const double sm_f[] = {1.0, 4.0, 0.25, 1.0, 1.0};
+    const int sm_s[] = {TC_STRAT_HASH, TC_STRAT_AUTO, TC_STRAT_AUTO, TC_STRAT_MERGE, TC_STRAT_AUTO};
+    const double sm_f[] = {1.0, 4.0, 0.25, 1.0, 1.0};  // AUTO at factors 4, 1/4 and 1
     const int cta_s[] = {TC_STRAT_BITMAP, TC_STRAT_AUTO, TC_STRAT_PROBE, TC_STRAT_SEARCH, TC_STRAT_MERGE};
     const int hub_s[] = {TC_STRAT_BITMAP, TC_STRAT_PROBE, TC_STRAT_BITMAP, TC_STRAT_PROBE, TC_STRAT_BITMAP};
     float best_b[3] = {1e30f, 1e30f, 1e30f};

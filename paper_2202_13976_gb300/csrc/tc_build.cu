@@ -158,9 +158,14 @@ __global__ void k_rank_invert(const uint64_t* __restrict__ sorted, int32_t n, in
 
 // Both passes take PAIR_UNROLL pairs per thread and round (pair i0 + k * stride), so
 // that the loads, the rank gathers and the atomics of the pairs are in flight
-// together instead of one dependent chain per pair.
+// together instead of one dependent chain per pair.  The count pass keeps every
+// pair's oriented form (source rank, target rank) in input order ((-1, -1): a loop
+// or a bad id), so the scatter pass reads it back in order instead of gathering the
+// two ranks again; the scatter's cursors start at the rows' first slots, so one
+// atomic gives the slot.
 __global__ void k_orient_count(const int32_t* __restrict__ src, const int32_t* __restrict__ dst, int64_t m,
-                               int32_t n, const int32_t* __restrict__ rank, uint32_t* __restrict__ rowcnt) {
+                               int32_t n, const int32_t* __restrict__ rank, uint32_t* __restrict__ rowcnt,
+                               int2* __restrict__ oriented) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i0 < m; i0 += PAIR_UNROLL * stride) {
         int32_t u[PAIR_UNROLL], v[PAIR_UNROLL];
@@ -172,43 +177,45 @@ __global__ void k_orient_count(const int32_t* __restrict__ src, const int32_t* _
         }
 #pragma unroll
         for (int k = 0; k < PAIR_UNROLL; ++k) {
-            if (u[k] == v[k] || (uint32_t)u[k] >= (uint32_t)n || (uint32_t)v[k] >= (uint32_t)n) continue;
-            atomicAdd(&rowcnt[min(rank[u[k]], rank[v[k]])], 1u);
+            const int64_t i = i0 + k * stride;
+            if (i >= m) break;
+            int2 o = make_int2(-1, -1);
+            if (u[k] != v[k] && (uint32_t)u[k] < (uint32_t)n && (uint32_t)v[k] < (uint32_t)n) {
+                const int32_t a = rank[u[k]], b = rank[v[k]];
+                o = make_int2(min(a, b), max(a, b));
+                atomicAdd(&rowcnt[o.x], 1u);
+            }
+            oriented[i] = o;
         }
     }
 }
 
-__global__ void k_orient_scatter(const int32_t* __restrict__ src, const int32_t* __restrict__ dst, int64_t m,
-                                 int32_t n, const int32_t* __restrict__ rank, const int64_t* __restrict__ rowstart,
-                                 uint32_t* __restrict__ cursor, int32_t* __restrict__ col) {
+__global__ void k_orient_scatter(const int2* __restrict__ oriented, int64_t m,
+                                 unsigned long long* __restrict__ cursor, int32_t* __restrict__ col,
+                                 DevStats* stats) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    int err = 0;
     for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i0 < m; i0 += PAIR_UNROLL * stride) {
-        int32_t s[PAIR_UNROLL], t[PAIR_UNROLL];
+        int2 o[PAIR_UNROLL];
 #pragma unroll
         for (int k = 0; k < PAIR_UNROLL; ++k) {
             const int64_t i = i0 + k * stride;
-            s[k] = i < m ? src[i] : 0;
-            t[k] = i < m ? dst[i] : 0;
+            o[k] = i < m ? oriented[i] : make_int2(-1, -1);
         }
+        unsigned long long p[PAIR_UNROLL];
+#pragma unroll
+        for (int k = 0; k < PAIR_UNROLL; ++k) p[k] = o[k].x >= 0 ? atomicAdd(&cursor[o[k].x], 1ull) : 0ull;
 #pragma unroll
         for (int k = 0; k < PAIR_UNROLL; ++k) {
-            const bool ok = s[k] != t[k] && (uint32_t)s[k] < (uint32_t)n && (uint32_t)t[k] < (uint32_t)n;
-            if (ok) {
-                const int32_t a = rank[s[k]], b = rank[t[k]];
-                s[k] = min(a, b);
-                t[k] = max(a, b);
-            } else {
-                s[k] = -1;
-            }
+            if (o[k].x < 0) continue;
+            if (p[k] < (unsigned long long)m)  // always true unless the passes disagree
+                col[p[k]] = o[k].y;
+            else
+                err = ERR_OVERFLOW;
         }
-        int64_t p[PAIR_UNROLL];
-#pragma unroll
-        for (int k = 0; k < PAIR_UNROLL; ++k)
-            p[k] = s[k] >= 0 ? rowstart[s[k]] + atomicAdd(&cursor[s[k]], 1u) : 0;
-#pragma unroll
-        for (int k = 0; k < PAIR_UNROLL; ++k)
-            if (s[k] >= 0 && p[k] < rowstart[s[k] + 1]) col[p[k]] = t[k];  // always true unless the passes disagree
     }
+    err = __reduce_or_sync(FULL, err);
+    if (err && lane_id() == 0) atomicOr(&stats->err, err);
 }
 
 // Row counts and row fill by buckets of consecutive source ranks (2^shift rows each,
@@ -847,14 +854,17 @@ void launch_orient(const BuildBuffers& B, const Launch& L, cudaEvent_t* ev) {
         cudaMemsetAsync(B.rowcnt, 0, sizeof(uint32_t) * (size_t)B.n, L.stream);
         if (B.m > 0) {
             k_orient_count<<<grid_for(B.m, THREADS, L.sms), THREADS, 0, L.stream>>>(B.src, B.dst, B.m, B.n, B.rank,
-                                                                                  B.rowcnt);
+                                                                                  B.rowcnt, B.oriented);
             count_launch();
         }
         scan_u32_to_i64(B.rowcnt, B.rowstart, B.n, B.tmp, L);
         if (ev) cudaEventRecord(ev[BP_COUNT], L.stream);
         if (B.m > 0) {
+            // 64-bit cursors in the rank keys' buffer (free once the ranks are known),
+            // starting at every row's first slot
+            cudaMemcpyAsync(B.keys, B.rowstart, sizeof(int64_t) * (size_t)B.n, cudaMemcpyDeviceToDevice, L.stream);
             k_orient_scatter<<<grid_for(B.m, THREADS, L.sms), THREADS, 0, L.stream>>>(
-                B.src, B.dst, B.m, B.n, B.rank, B.rowstart, B.cursor, B.col);
+                B.oriented, B.m, reinterpret_cast<unsigned long long*>(B.keys), B.col, B.stats);
             count_launch();
         }
     }

@@ -773,6 +773,138 @@ struct HashProbe {
     }
 };
 
+// ---- small bucket, hash strategy: N+(u) as a hash set, target rows end to end ----
+//
+// A group of G lanes takes one source u at a time.  N+(u) (at most AMAX entries) goes
+// into an open-addressing hash set of SL >= 2 AMAX slots in shared memory.  Its edges
+// (u, v) into non-hubs are taken G at a time; their rows N+(v) are laid end to end and
+// the group reads G entries per round, one per lane, each entry probed once in the
+// set (entries above max N+(u) are skipped).  A hit at x in N+(v) is a triangle: x is
+// above v, so it lies in the suffix of N+(u) after v, which is W for the edge (u, v).
+// Hits add to the slot's counter (t[x], flushed once per source) and to the edge's
+// counter (t[v]); their sum goes to t[u].  Every lane reads at every round, so the
+// lanes stay busy whatever the lengths of the rows.
+template <int G, int SL>
+__global__ void __launch_bounds__(SMALL_WARPS * 32) k_tc_small_hash(int32_t n, const int2* __restrict__ rowinfo,
+                                                                   const int32_t* __restrict__ col,
+                                                                   const int32_t* __restrict__ list, int cls,
+                                                                   unsigned long long* __restrict__ t,
+                                                                   DevStats* stats) {
+    static_assert(G == 8 || G == 16 || G == 32, "lane groups within a warp");
+    static_assert((SL & (SL - 1)) == 0 && SL >= 2 * G, "power-of-two table");
+    constexpr int GROUPS = SMALL_WARPS * 32 / G;
+    constexpr int LG = SL == 16 ? 4 : SL == 32 ? 5 : SL == 64 ? 6 : SL == 128 ? 7 : SL == 256 ? 8 : 9;
+    static_assert((1 << LG) == SL, "table size");
+    __shared__ int32_t skeys[GROUPS][SL];
+    __shared__ uint32_t shcnt[GROUPS][SL];
+    __shared__ uint32_t secnt[GROUPS][G];
+    const int lane = lane_id(), w = threadIdx.x >> 5;
+    const int grp = lane / G, g = lane % G;
+    const int gi = w * (32 / G) + grp;
+    const unsigned gmask = G == 32 ? FULL : (((1u << G) - 1u) << (grp * G));
+    const unsigned below = (1u << g) - 1u;  // group lanes under this one (group-relative bits)
+    int32_t* keys = skeys[gi];
+    uint32_t* hcnt = shcnt[gi];
+    uint32_t* ecnt = secnt[gi];
+    for (int i = g; i < SL; i += G) {
+        keys[i] = -1;
+        hcnt[i] = 0;
+    }
+    ecnt[g] = 0;
+    __syncwarp(gmask);
+    const unsigned count = stats->small_count[cls];
+    const int32_t R = n - (int32_t)stats->hub_count;
+    const unsigned groups = gridDim.x * GROUPS;
+    const HashProbe P{keys, 32u - LG, SL - 1u};
+    auto gballot = [&](bool p) { return (__ballot_sync(gmask, p) >> (grp * G)) & (G == 32 ? FULL : ((1u << G) - 1u)); };
+    for (unsigned q = blockIdx.x * GROUPS + gi; q < count; q += groups) {
+        const int32_t u = list[q];
+        const int2 ru = rowinfo[u];
+        const int du = ru.y;
+        const int64_t base = ru.x;
+        int jh = 0;  // entries below the hubs: the rows are sorted, so they come first
+        for (int i0 = 0; i0 < du; i0 += G) {  // every lane of the group takes every round
+            const bool valid = i0 + g < du;
+            const int32_t x = valid ? col[base + i0 + g] : INT_MAX;
+            if (valid) {
+                unsigned h = ((unsigned)x * 0x9e3779b1u) >> (32 - LG);
+                while (atomicCAS(&keys[h], -1, x) != -1) h = (h + 1) & (SL - 1);  // keys are distinct
+            }
+            jh += __popc(gballot(x < R));
+        }
+        const int32_t maxu = col[base + du - 1];
+        const int ne = min(jh, du - 1);  // the last entry has an empty suffix
+        __syncwarp(gmask);
+        uint32_t cu = 0;
+        for (int e0 = 0; e0 < ne; e0 += G) {
+            const bool has = e0 + g < ne;
+            int32_t v = has ? col[base + e0 + g] : 0;
+            int2 rv = has ? rowinfo[v] : make_int2(0, 0);
+            // the edges with a non-empty row first: lane i holds the i-th of them
+            const unsigned nz = gballot(has && rv.y > 0);
+            const int cz = __popc(nz);
+            if (cz == 0) continue;
+            {
+                const int src = g < cz ? (int)__fns(nz, 0, g + 1) : g;
+                v = __shfl_sync(gmask, v, src, G);
+                rv.x = __shfl_sync(gmask, rv.x, src, G);
+                rv.y = __shfl_sync(gmask, rv.y, src, G);
+                if (g >= cz) rv.y = 0;
+            }
+            int incl = rv.y;
+#pragma unroll
+            for (int o = 1; o < G; o <<= 1) {
+                const int y = __shfl_up_sync(gmask, incl, o, G);
+                if (g >= o) incl += y;
+            }
+            const int total = __shfl_sync(gmask, incl, G - 1, G);
+            const int excl = incl - rv.y;
+            for (int r = 0; r < total; r += G) {
+                // the edge of entry r + g: i0 holds entry r, and every later edge that
+                // starts inside the round marks its first entry in mk
+                const int i0 = __popc(gballot(g < cz && incl <= r));
+                const unsigned mk = __reduce_or_sync(gmask, (g > i0 && g < cz && excl - r < G) ? (1u << (excl - r)) : 0u);
+                const int idx = min(i0 + __popc(mk & (below | (1u << g))), G - 1);
+                const int bs = __shfl_sync(gmask, rv.x, idx, G);
+                const int bx = __shfl_sync(gmask, excl, idx, G);
+                const int k = r + g;
+                if (k < total) {
+                    const int32_t x = col[(int64_t)bs + (k - bx)];
+                    if (x <= maxu) {
+                        const int h = P(x);
+                        if (h >= 0) {
+                            atomicAdd(&hcnt[h], 1u);
+                            atomicAdd(&ecnt[idx], 1u);
+                        }
+                    }
+                }
+            }
+            __syncwarp(gmask);
+            const uint32_t ce = ecnt[g];
+            ecnt[g] = 0;
+            if (g < cz && ce) {
+                atomicAdd(&t[v], (unsigned long long)ce);
+                cu += ce;
+            }
+            __syncwarp(gmask);
+        }
+#pragma unroll
+        for (int o = G / 2; o > 0; o >>= 1) cu += __shfl_down_sync(gmask, cu, o, G);
+        if (g == 0 && cu) atomicAdd(&t[u], (unsigned long long)cu);
+        for (int i = g; i < SL; i += G) {  // flush the per-entry counts, empty the set
+            const int32_t x = keys[i];
+            if (x >= 0) {
+                const uint32_t c = hcnt[i];
+                if (c) atomicAdd(&t[x], (unsigned long long)c);
+                keys[i] = -1;
+                hcnt[i] = 0;
+            }
+        }
+        __syncwarp(gmask);
+    }
+}
+
+
 // Warp per edge: the entries of B = N+(v) (sorted) are probed in a set of the
 // staged N+(u), two per lane per round, stopping above max N+(u); hits add to the
 // set's per-slot counter.  Returns the edge's count (all lanes).
@@ -973,19 +1105,29 @@ __device__ uint32_t hub_batch(int64_t k0, int64_t e1, const int4* __restrict__ i
     int32_t b0 = rec.y;
     int a = rec.z - rec.y;
     uint32_t total_c = 0;
-    unsigned longm = __ballot_sync(FULL, a >= HUB_LONG);
+    const bool islong = a >= HUB_LONG;
+    const int nlong = __popc(__ballot_sync(FULL, islong));
+    // the long suffixes by decreasing length (bitonic sort of (length, lane) keys across
+    // the warp), so that the groups that run their rounds together take suffixes of
+    // similar length and wait less for each other
+    uint32_t key = islong ? ((uint32_t)min(a, (1 << 26) - 1) << 5) | (uint32_t)lane : 0u;
+#pragma unroll
+    for (int k = 2; k <= 32; k <<= 1) {
+#pragma unroll
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            const uint32_t other = __shfl_xor_sync(FULL, key, j);
+            const bool keep_max = ((lane & j) == 0) == ((lane & k) == 0);
+            key = keep_max ? max(key, other) : min(key, other);
+        }
+    }
     // HUB_GROUPS long suffixes at a time, one per group of HUB_GLANES lanes, each lane
     // reading HUB_UNROLL entries per round with all loads in flight before any is used
     const int g = lane / HUB_GLANES, gl = lane % HUB_GLANES;
     const unsigned gmask = (HUB_GLANES == 32 ? FULL : ((1u << HUB_GLANES) - 1u)) << (g * HUB_GLANES);
-    while (longm) {
-        int my = -1;  // batch lane holding this group's in-edge
-#pragma unroll
-        for (int j = 0; j < HUB_GROUPS; ++j) {
-            const int f = longm ? __ffs(longm) - 1 : -1;
-            if (j == g) my = f;
-            longm &= longm - 1;  // no-op once empty
-        }
+    for (int k0 = 0; k0 < nlong; k0 += HUB_GROUPS) {
+        const int pos = k0 + g;
+        const uint32_t kp = __shfl_sync(FULL, key, min(pos, 31));
+        const int my = pos < nlong ? (int)(kp & 31u) : -1;  // batch lane holding this group's in-edge
         const int src = my < 0 ? 0 : my;
         const int32_t bL = __shfl_sync(FULL, b0, src);
         int aL = __shfl_sync(FULL, a, src);
@@ -1361,18 +1503,36 @@ void launch_intersect(const CountBuffers& C, const Strategy& S, cudaEvent_t* ev,
     if (ev) cudaEventRecord(ev[PH_SMALL], L.stream);
     const int ss = S.strat[TC_BUCKET_SMALL];
     const float sf = S.factor[TC_BUCKET_SMALL];
-    k_tc_small<8><<<L.sms * SMALL_BLOCKS, SMALL_WARPS * 32, 0, L.stream>>>(C.n, C.rowstart, C.rowlen, C.rowinfo, C.col, C.small_list[0],
-                                                               0, C.t_rank, C.stats, ss, sf);
-    count_launch();
-    k_tc_small<16><<<L.sms * SMALL_BLOCKS, SMALL_WARPS * 32, 0, L.stream>>>(C.n, C.rowstart, C.rowlen, C.rowinfo, C.col, C.small_list[1],
-                                                                1, C.t_rank, C.stats, ss, sf);
-    count_launch();
-    k_tc_small<32><<<L.sms * SMALL_BLOCKS, SMALL_WARPS * 32, 0, L.stream>>>(C.n, C.rowstart, C.rowlen, C.rowinfo, C.col, C.small_list[2],
-                                                                2, C.t_rank, C.stats, ss, sf);
-    count_launch();
-    k_tc_small_wide<<<L.sms * SMALL_WIDE_BLOCKS, SMALL_WARPS * 32, 2 * SMALL_WIDE_GROUPS * SMALL_WIDE_MAX * sizeof(int32_t),
-                      L.stream>>>(C.n, C.rowinfo, C.col, C.small_list[3], C.t_rank, C.stats, ss, sf);
-    count_launch();
+    if (ss == TC_STRAT_HASH) {
+        // sources of at most 16 entries: one edge per lane (Eq. 3 per edge), whose
+        // short merges cost less than building and flushing a set per source
+        k_tc_small<8><<<L.sms * SMALL_BLOCKS, SMALL_WARPS * 32, 0, L.stream>>>(
+            C.n, C.rowstart, C.rowlen, C.rowinfo, C.col, C.small_list[0], 0, C.t_rank, C.stats, TC_STRAT_AUTO, sf);
+        count_launch();
+        k_tc_small<16><<<L.sms * SMALL_BLOCKS, SMALL_WARPS * 32, 0, L.stream>>>(
+            C.n, C.rowstart, C.rowlen, C.rowinfo, C.col, C.small_list[1], 1, C.t_rank, C.stats, TC_STRAT_AUTO, sf);
+        count_launch();
+        k_tc_small_hash<32, 64><<<L.sms * SMALL_BLOCKS, SMALL_WARPS * 32, 0, L.stream>>>(
+            C.n, C.rowinfo, C.col, C.small_list[2], 2, C.t_rank, C.stats);
+        count_launch();
+        k_tc_small_hash<32, 2 * SMALL_WIDE_MAX><<<L.sms * SMALL_WIDE_BLOCKS, SMALL_WARPS * 32, 0, L.stream>>>(
+            C.n, C.rowinfo, C.col, C.small_list[3], 3, C.t_rank, C.stats);
+        count_launch();
+    } else {
+        k_tc_small<8><<<L.sms * SMALL_BLOCKS, SMALL_WARPS * 32, 0, L.stream>>>(
+            C.n, C.rowstart, C.rowlen, C.rowinfo, C.col, C.small_list[0], 0, C.t_rank, C.stats, ss, sf);
+        count_launch();
+        k_tc_small<16><<<L.sms * SMALL_BLOCKS, SMALL_WARPS * 32, 0, L.stream>>>(
+            C.n, C.rowstart, C.rowlen, C.rowinfo, C.col, C.small_list[1], 1, C.t_rank, C.stats, ss, sf);
+        count_launch();
+        k_tc_small<32><<<L.sms * SMALL_BLOCKS, SMALL_WARPS * 32, 0, L.stream>>>(
+            C.n, C.rowstart, C.rowlen, C.rowinfo, C.col, C.small_list[2], 2, C.t_rank, C.stats, ss, sf);
+        count_launch();
+        k_tc_small_wide<<<L.sms * SMALL_WIDE_BLOCKS, SMALL_WARPS * 32,
+                          2 * SMALL_WIDE_GROUPS * SMALL_WIDE_MAX * sizeof(int32_t), L.stream>>>(
+            C.n, C.rowinfo, C.col, C.small_list[3], C.t_rank, C.stats, ss, sf);
+        count_launch();
+    }
     if (ev) cudaEventRecord(ev[PH_CTA], L.stream);
     cudaMemsetAsync(&C.stats->cta_next, 0, sizeof(unsigned), L.stream);
     k_tc_cta<<<L.sms * 4, CTA_THREADS, sizeof(CtaShared), L.stream>>>(C.n, C.rowstart, C.rowlen, C.rowinfo, C.col,

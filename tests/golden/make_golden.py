@@ -6,7 +6,11 @@ edge-centric count (Sec. II-C, Alg. 2) and the paper's unoriented per-vertex for
 (Alg. 3 with the Sec. II-C offset, Eq. 3 hybrid).  Calls only graphgen (inputs) and
 oracle (results).
 
-    python tests/golden/make_golden.py [--large] [--threads N]
+With --batch, tests/golden/batch_workload.json: the oracle's results on every graph
+of the 20,000-graph batch (seed 4), as digests of the per-graph T and of t[] and
+LCC[] concatenated graph by graph.
+
+    python tests/golden/make_golden.py [--large] [--batch] [--threads N]
 """
 import argparse
 import hashlib
@@ -83,13 +87,56 @@ def large(threads):
         f.write("\n")
 
 
+def _batch_one(i):
+    w = graphgen.batch_workloads(BATCH_G, seed=BATCH_SEED)[i] if _BATCH is None else _BATCH[i]
+    s, d = w.edges()
+    r = oracle.triangles(w.n, s, d)
+    return i, r["T"], r["m_simple"], r["t"], r["lcc"]
+
+
+BATCH_G, BATCH_SEED = 20000, 4
+_BATCH = None
+
+
+def _batch_init():
+    global _BATCH
+    _BATCH = graphgen.batch_workloads(BATCH_G, seed=BATCH_SEED)
+
+
+def batch(threads):
+    import multiprocessing as mp
+    G = BATCH_G
+    T = np.zeros(G, dtype=np.uint64)
+    ms = np.zeros(G, dtype=np.int64)
+    ts, ls = [None] * G, [None] * G
+    t0 = time.perf_counter()
+    with mp.get_context("spawn").Pool(threads, initializer=_batch_init) as pool:
+        for i, Ti, mi, ti, li in pool.imap_unordered(_batch_one, range(G), chunksize=16):
+            T[i], ms[i], ts[i], ls[i] = Ti, mi, ti, li
+    t_all = np.concatenate(ts).astype(np.uint64)
+    l_all = np.concatenate(ls).astype(np.float64)
+    out = {"graphs": G, "seed": BATCH_SEED, "vertices": int(t_all.size), "m_simple": int(ms.sum()),
+           "T_total": int(T.sum(dtype=np.uint64)), "T_sha256": digest(T), "m_simple_sha256": digest(ms),
+           "t_sha256": digest(t_all), "lcc_sha256": digest(l_all),
+           "seconds": round(time.perf_counter() - t0, 1)}
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "batch_workload.json")
+    with open(path, "w") as f:
+        json.dump(out, f, indent=1, sort_keys=True)
+        f.write("\n")
+    print(out, flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--large", action="store_true")
+    ap.add_argument("--batch", action="store_true")
     ap.add_argument("--threads", type=int, default=len(os.sched_getaffinity(0)))
     args = ap.parse_args()
     if args.large:
         large(args.threads)
+        return
+    if args.batch:
+        batch(args.threads)
         return
     out = {}
     for name, spec in SPECS.items():

@@ -170,3 +170,45 @@ def test_batch_run_reports_bad_ids(tc):
         tc.tc_batch_run(n, off, s, d, T, stream=torch.cuda.Stream(), graph=True)
     assert e.value.status == tc.TC_EINVAL
     tc.tc_release_cached_graphs()
+
+
+@pytest.mark.slow
+def test_whole_batch_matches_the_oracle_digests(tc):
+    """All 20,000 graphs of the batched workload (seed 4) in one batch call, through
+    the CUDA-graph path the benchmark times: per-graph T and every t[v] and LCC[v]
+    against tests/golden/batch_workload.json, which make_golden.py --batch wrote from
+    the oracle's count of every graph."""
+    import hashlib
+    import json
+    import os
+    from concurrent.futures import ThreadPoolExecutor
+
+    import torch
+    gold = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "batch_workload.json")))
+    ws = graphgen.batch_workloads(gold["graphs"], seed=gold["seed"])
+    with ThreadPoolExecutor(max_workers=len(os.sched_getaffinity(0))) as ex:
+        edges = list(ex.map(lambda w: w.edges(), ws))
+    n = np.array([w.n for w in ws], dtype=np.int32)
+    off = np.zeros(len(ws) + 1, dtype=np.int64)
+    off[1:] = np.cumsum([len(e[0]) for e in edges])
+    src = torch.from_numpy(np.concatenate([e[0] for e in edges]).astype(np.int32)).cuda()
+    dst = torch.from_numpy(np.concatenate([e[1] for e in edges]).astype(np.int32)).cuda()
+    del edges
+    nt = int(n.sum())
+    assert nt == gold["vertices"]
+    T = torch.empty(len(ws), dtype=torch.int64, device="cuda")
+    t = torch.empty(nt, dtype=torch.int64, device="cuda")
+    lc = torch.empty(nt, dtype=torch.float64, device="cuda")
+    side = torch.cuda.Stream()
+    tc.tc_batch_run(n, off, src, dst, T, t, lc, stream=side, graph=True)
+    side.synchronize()
+
+    def digest(a):
+        return hashlib.sha256(np.ascontiguousarray(a).tobytes()).hexdigest()
+
+    Th = T.cpu().numpy().view(np.uint64)
+    assert int(Th.sum(dtype=np.uint64)) == gold["T_total"]
+    assert digest(Th) == gold["T_sha256"]
+    assert digest(t.cpu().numpy().view(np.uint64)) == gold["t_sha256"]
+    assert digest(lc.cpu().numpy()) == gold["lcc_sha256"]
+    tc.tc_release_cached_graphs()

@@ -12,7 +12,7 @@ from tests.gpu_util import assert_matches_oracle, gpu_run
 
 pytestmark = pytest.mark.gpu
 
-SMALL_STRATEGIES = [("auto", 1.0), ("auto", 8.0), ("auto", 0.125), ("merge", 1.0), ("search", 1.0)]
+SMALL_STRATEGIES = [("hash", 1.0), ("auto", 1.0), ("auto", 8.0), ("auto", 0.125), ("merge", 1.0), ("search", 1.0)]
 CTA_STRATEGIES = [("auto", 1.0), ("auto", 4.0), ("auto", 0.25), ("merge", 1.0), ("search", 1.0),
                   ("probe", 1.0), ("bitmap", 1.0)]
 HUB_STRATEGIES = [("auto", 1.0), ("bitmap", 1.0), ("probe", 1.0)]
@@ -99,7 +99,8 @@ def test_dense_core_closed_forms(tc, make, core):
 def test_strategy_rejects_unsupported_pairs(tc, er4096):
     n, s, d, _ = er4096
     g = tc.Graph.from_edges(n, s, d)
-    for bucket, strat in [("small", "bitmap"), ("small", "probe"), ("hub", "merge"), ("hub", "search")]:
+    for bucket, strat in [("small", "bitmap"), ("small", "probe"), ("hub", "merge"), ("hub", "search"),
+                          ("cta", "hash"), ("hub", "hash")]:
         with pytest.raises(tc.TCError):
             g.set_strategy(bucket, strat)
     with pytest.raises(tc.TCError):
