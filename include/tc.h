@@ -122,9 +122,11 @@ tc_status tc_count_vertex_formula(tc_graph* g, uint64_t* t_out, int mem_kind, ui
  * contain it, |adj(u) ∩ adj(v)|.  Writes m_simple entries (tc_graph_info): u_out[k] <
  * v_out[k] in the caller's ids, support_out[k] (uint32), each edge once, in an order
  * of the library's choosing (row by row in its internal rank order); all three
- * arrays in mem_kind memory.  Builds the symmetric rows for the call (as
- * tc_count_vertex_formula) and releases them; synchronises the stream.  Errors:
- * TC_EINVAL (NULL output, bad mem_kind), TC_ENOMEM, TC_ECUDA.
+ * arrays in mem_kind memory.  Runs the oriented count once more with every triangle
+ * also added to its three edges (the dense core off, since it counts words of bits
+ * without naming triangles); the graph's tuning is restored afterwards.
+ * Synchronises the stream.  Errors: TC_EINVAL (NULL output, bad mem_kind),
+ * TC_ENOMEM, TC_ECUDA, TC_EINTERNAL.
  */
 tc_status tc_edge_support(tc_graph* g, int32_t* u_out, int32_t* v_out, uint32_t* support_out, int mem_kind);
 

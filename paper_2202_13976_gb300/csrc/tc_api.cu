@@ -698,24 +698,53 @@ tc_status tc_edge_support(tc_graph* g, int32_t* u_out, int32_t* v_out, uint32_t*
     if (st != TC_OK) return st;
     if (h.err & ERR_BAD_ID) return TC_EINVAL;
     const size_t nn = (size_t)g->n, me = (size_t)h.m_simple;
-    VertexFormulaBuffers V;
+    // the oriented count with every triangle also added to its three edges; the dense
+    // core counts words of bits and names no triangle, so it is switched off here
+    const Strategy saved = g->strat;
+    Strategy S = saved;
+    S.strat[TC_BUCKET_SMALL] = TC_STRAT_HASH;
+    S.strat[TC_BUCKET_CTA] = TC_STRAT_BITMAP;
+    S.strat[TC_BUCKET_HUB] = TC_STRAT_BITMAP;
+    S.hub_core = 0;
     std::vector<void*> tmp;
+    uint32_t* sup = nullptr;
     int32_t* id_of = nullptr;
     int64_t* estart = nullptr;
+    char* stmp = nullptr;
     int32_t *du = nullptr, *dv = nullptr;
     uint32_t* ds = nullptr;
-    if ((st = symmetric_buffers(g, h, &V, &tmp)) || (st = dalloc(g, &id_of, nn, &tmp)) ||
-        (st = dalloc(g, &estart, nn + 1, &tmp))) {
-        free_list(g, &tmp);
-        return st;
-    }
     const bool dev = mem_kind == TC_MEM_DEVICE;
-    if (!dev && ((st = dalloc(g, &du, me, &tmp)) || (st = dalloc(g, &dv, me, &tmp)) || (st = dalloc(g, &ds, me, &tmp)))) {
+    if ((st = dalloc(g, &sup, (size_t)g->m_alloc, &tmp)) || (st = dalloc(g, &id_of, nn, &tmp)) ||
+        (st = dalloc(g, &estart, nn + 1, &tmp)) || (st = dalloc(g, &stmp, scan_tmp_bytes((int64_t)nn + 1), &tmp)) ||
+        (!dev && ((st = dalloc(g, &du, me, &tmp)) || (st = dalloc(g, &dv, me, &tmp)) || (st = dalloc(g, &ds, me, &tmp))))) {
         free_list(g, &tmp);
         return st;
     }
-    launch_edge_support(V, g->rank, id_of, estart, dev ? u_out : du, dev ? v_out : dv, dev ? support_out : ds, g->L);
-    cudaError_t e = cudaGetLastError();
+    const bool replan = saved.hub_core != 0;
+    g->strat = S;
+    if (replan) g->planned = false;
+    g->counted = false;
+    cudaError_t e = cudaMemsetAsync(sup, 0, sizeof(uint32_t) * (size_t)g->m_alloc, g->stream);
+    if (e == cudaSuccess && (st = run_plan(g)) == TC_OK) {
+        e = cudaMemsetAsync(g->t_rank, 0, sizeof(unsigned long long) * nn, g->stream);
+        if (e == cudaSuccess) e = cudaMemsetAsync(&g->stats->sum_t, 0, sizeof(unsigned long long), g->stream);
+        if (e == cudaSuccess) {
+            CountBuffers C = count_buffers(g);
+            C.sup = sup;
+            launch_intersect(C, g->strat, nullptr, g->L);
+            launch_sum_t(C, g->L);
+            launch_support_out(g->n, g->rank, g->rowlen, g->rowinfo, g->col, sup, id_of, estart, stmp,
+                               dev ? u_out : du, dev ? v_out : dv, dev ? support_out : ds, g->L);
+            e = cudaGetLastError();
+        }
+    }
+    g->strat = saved;
+    if (replan) g->planned = false;  // the next count plans with the dense core again
+    g->counted = false;
+    if (st != TC_OK) {
+        free_list(g, &tmp);
+        return st;
+    }
     if (e == cudaSuccess && !dev && me > 0) {
         e = cudaMemcpyAsync(u_out, du, sizeof(int32_t) * me, cudaMemcpyDeviceToHost, g->stream);
         if (e == cudaSuccess) e = cudaMemcpyAsync(v_out, dv, sizeof(int32_t) * me, cudaMemcpyDeviceToHost, g->stream);
@@ -725,6 +754,10 @@ tc_status tc_edge_support(tc_graph* g, int32_t* u_out, int32_t* v_out, uint32_t*
     free_list(g, &tmp);
     if (e == cudaSuccess) e = cudaStreamSynchronize(g->stream);
     if (e != cudaSuccess) return cuda_fail("tc_edge_support", e);
+    if (read_stats(g, &h) == TC_OK && (h.err & ERR_OVERFLOW)) {
+        snprintf(g_last_error, sizeof(g_last_error), "internal count mismatch (overflow guard)");
+        return TC_EINTERNAL;
+    }
     return TC_OK;
 }
 

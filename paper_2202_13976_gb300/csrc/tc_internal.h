@@ -167,6 +167,7 @@ struct CountBuffers {
     int32_t* core_hiout;     // core_cap: highest core out-neighbour (-1: none)
     unsigned long long* t_rank;  // n
     DevStats* stats;
+    uint32_t* sup;           // null, or m_cap per-edge supports indexed like col (tc_edge_support)
 };
 
 enum { PH_PLAN = 0, PH_SMALL, PH_CTA, PH_HUB, PH_END, PH_EVENTS };
@@ -210,9 +211,12 @@ struct VertexFormulaBuffers {
 int vf_key_bits(int32_t n);
 void launch_symmetric_rows(const VertexFormulaBuffers& V, const Launch& L);
 void launch_vertex_formula(const VertexFormulaBuffers& V, const Launch& L);
-// Per-edge support over the symmetric rows; id_of (n) and estart (n + 1) are scratch.
-void launch_edge_support(const VertexFormulaBuffers& V, const int32_t* rank, int32_t* id_of, int64_t* estart,
-                         int32_t* eu, int32_t* ev, uint32_t* support, const Launch& L);
+// Per-edge supports recorded by the count (sup, indexed like col) written out as the
+// edge list {u, v, support} in the caller's ids, row by row in rank order; id_of (n),
+// estart (n + 1) and scan_tmp (scan_tmp_bytes(n + 1)) are scratch.
+void launch_support_out(int32_t n, const int32_t* rank, const int32_t* rowlen, const int2* rowinfo, const int32_t* col,
+                        const uint32_t* sup, int32_t* id_of, int64_t* estart, void* scan_tmp, int32_t* eu, int32_t* ev,
+                        uint32_t* support, const Launch& L);
 
 // ---- remote reads and caches of the 1D partition (tc_cache.cu) -------------------
 struct PartCounters {  // per process; four 64-bit fields, nothing else (indexed as such)

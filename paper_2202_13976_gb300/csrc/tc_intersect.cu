@@ -67,11 +67,18 @@ struct Sink {
     uint32_t* cnt;               // per-position counters (shared), or null
     unsigned long long* t;       // global counts, used when cnt is null
     const int32_t* Lu;           // N+(u) (shared or global)
+    uint32_t* supA;              // per-edge support of the entries of N+(u) when cnt is null, or null
+    uint32_t* supB;              // per-edge support of the entries of N+(v), or null
     __device__ __forceinline__ void hit(int p) const {
-        if (cnt)
+        if (cnt) {
             atomicAdd(&cnt[p], 1u);
-        else
+        } else {
             atomicAdd(&t[Lu[p]], 1ull);
+            if (supA) atomicAdd(&supA[p], 1u);
+        }
+    }
+    __device__ __forceinline__ void hitB(int k) const {
+        if (supB) atomicAdd(&supB[k], 1u);
     }
 };
 
@@ -125,6 +132,7 @@ __device__ uint32_t edge_merge(const Sink& S, int a0, int du, const int32_t* __r
         if (i < a && A[i] <= bj) {
             if (A[i] == bj) {
                 S.hit(a0 + i);
+                S.hitB(j);
                 ++c;
             }
             ++i;
@@ -146,6 +154,7 @@ __device__ uint32_t edge_search(const Sink& S, int a0, int du, const int32_t* __
         lo = p;  // keys of this lane increase
         if (p < b && B[p] == y) {
             S.hit(k);
+            S.hitB(p);
             ++c;
         }
     }
@@ -163,6 +172,7 @@ __device__ uint32_t edge_probe(const Sink& S, int a0, int du, const int32_t* __r
             int p = lower_bound(S.Lu, a0, du, x);
             if (S.Lu[p] == x) {  // p < du because x <= max
                 S.hit(p);
+                S.hitB(k);
                 ++c;
             }
         }
@@ -174,7 +184,7 @@ __device__ uint32_t edge_probe(const Sink& S, int a0, int du, const int32_t* __r
 // Bitmap over ranks (u, maxu]: bit (x - u - 1) set iff x in N+(u); pre[w] = number of
 // set bits in the words before w, i.e. the position in N+(u) of the word's first member.
 __device__ uint32_t edge_bitmap(const uint32_t* bm, const uint16_t* pre, int32_t u, int32_t maxu,
-                                uint32_t* cnt, const int32_t* __restrict__ B, int b) {
+                                uint32_t* cnt, const int32_t* __restrict__ B, int b, uint32_t* __restrict__ supB) {
     const int lane = lane_id();
     uint32_t c = 0;
     for (int k0 = 0; k0 < b; k0 += 32) {
@@ -185,6 +195,7 @@ __device__ uint32_t edge_bitmap(const uint32_t* bm, const uint16_t* pre, int32_t
             uint32_t w = bm[off >> 5], bit = 1u << (off & 31);
             if (w & bit) {
                 atomicAdd(&cnt[pre[off >> 5] + __popc(w & (bit - 1))], 1u);
+                if (supB) atomicAdd(&supB[k], 1u);
                 ++c;
             }
         }
@@ -272,7 +283,7 @@ __device__ uint32_t lane_merge(const int32_t* Lu, int a0, int du, const int32_t*
 
 // Merge with B read eight entries at a time (independent loads), A in shared memory.
 __device__ uint32_t lane_merge_batched(const int32_t* Lu, int a0, int du, const int32_t* __restrict__ B, int b,
-                                       uint32_t* cnt) {
+                                       uint32_t* cnt, uint32_t* __restrict__ supB) {
     uint32_t c = 0;
     int i = a0;
     const int32_t mx = Lu[du - 1];
@@ -285,6 +296,7 @@ __device__ uint32_t lane_merge_batched(const int32_t* Lu, int a0, int du, const 
             while (i < du && Lu[i] < y[q]) ++i;
             if (i < du && Lu[i] == y[q]) {
                 atomicAdd(&cnt[i], 1u);
+                if (supB) atomicAdd(&supB[k0 + q], 1u);
                 ++c;
                 ++i;
             }
@@ -296,7 +308,7 @@ __device__ uint32_t lane_merge_batched(const int32_t* Lu, int a0, int du, const 
 
 // keys of A looked up in B
 __device__ uint32_t lane_search(const int32_t* Lu, int a0, int du, const int32_t* __restrict__ B, int b,
-                                uint32_t* cnt) {
+                                uint32_t* cnt, uint32_t* __restrict__ supB) {
     uint32_t c = 0;
     int lo = 0;
     for (int i = a0; i < du && lo < b; ++i) {
@@ -305,6 +317,7 @@ __device__ uint32_t lane_search(const int32_t* Lu, int a0, int du, const int32_t
         lo = p;
         if (p < b && B[p] == x) {
             atomicAdd(&cnt[i], 1u);
+            if (supB) atomicAdd(&supB[p], 1u);
             ++c;
         }
     }
@@ -313,7 +326,7 @@ __device__ uint32_t lane_search(const int32_t* Lu, int a0, int du, const int32_t
 
 // keys of B looked up in A
 __device__ uint32_t lane_search_rev(const int32_t* Lu, int a0, int du, const int32_t* __restrict__ B, int b,
-                                    uint32_t* cnt) {
+                                    uint32_t* cnt, uint32_t* __restrict__ supB) {
     uint32_t c = 0;
     int lo = a0;
     const int32_t mx = Lu[du - 1];
@@ -324,6 +337,7 @@ __device__ uint32_t lane_search_rev(const int32_t* Lu, int a0, int du, const int
         lo = p;
         if (p < du && Lu[p] == y) {
             atomicAdd(&cnt[p], 1u);
+            if (supB) atomicAdd(&supB[k], 1u);
             ++c;
         }
     }
@@ -628,14 +642,16 @@ __global__ void __launch_bounds__(THREADS) k_plan(int32_t n, const int64_t* __re
 
 // ---- small bucket: groups of G lanes, one lane per edge -----------------------
 
-template <int G>
+template <int G, bool SUP>
 __global__ void __launch_bounds__(SMALL_WARPS * 32, SMALL_BLOCKS) k_tc_small(int32_t n, const int64_t* __restrict__ rowstart,
                                                                const int32_t* __restrict__ rowlen,
                                                                const int2* __restrict__ rowinfo,
                                                                const int32_t* __restrict__ col,
                                                                const int32_t* __restrict__ list, int cls,
                                                                unsigned long long* __restrict__ t, DevStats* stats,
-                                                               int strategy, float factor) {
+                                                               int strategy, float factor,
+                                                               uint32_t* __restrict__ sup_arg) {
+    uint32_t* const sup = SUP ? sup_arg : nullptr;  // per-edge support (tc_edge_support) or none
     constexpr int GPW = 32 / G;
     __shared__ int32_t sLu[SMALL_WARPS * 32];
     __shared__ uint32_t sCnt[SMALL_WARPS * 32];
@@ -667,13 +683,15 @@ __global__ void __launch_bounds__(SMALL_WARPS * 32, SMALL_BLOCKS) k_tc_small(int
             const int dv = ri.y;
             if (dv > 0) {
                 const int32_t* B = col + ri.x;
+                uint32_t* supB = sup ? sup + ri.x : nullptr;
                 const int a = du - g - 1;
                 int method = strategy;
                 if (method == TC_STRAT_AUTO) method = small_auto(a, dv, factor);
                 if (method == TC_STRAT_MERGE)
-                    c = lane_merge_batched(Lu, g + 1, du, B, dv, cnt);
+                    c = lane_merge_batched(Lu, g + 1, du, B, dv, cnt, supB);
                 else
-                    c = a <= dv ? lane_search(Lu, g + 1, du, B, dv, cnt) : lane_search_rev(Lu, g + 1, du, B, dv, cnt);
+                    c = a <= dv ? lane_search(Lu, g + 1, du, B, dv, cnt, supB)
+                                : lane_search_rev(Lu, g + 1, du, B, dv, cnt, supB);
                 if (c) atomicAdd(&cnt[g], c);
             }
         }
@@ -681,7 +699,10 @@ __global__ void __launch_bounds__(SMALL_WARPS * 32, SMALL_BLOCKS) k_tc_small(int
         for (int o = G / 2; o > 0; o >>= 1) c += __shfl_down_sync(gmask, c, o, G);
         __syncwarp(gmask);
         const uint32_t cv = cnt[g];
-        if (g < du && cv) atomicAdd(&t[Lu[g]], (unsigned long long)cv);
+        if (g < du && cv) {
+            atomicAdd(&t[Lu[g]], (unsigned long long)cv);
+            if (sup) atomicAdd(&sup[base + g], cv);  // edge (u, Lu[g]): as v of its edge and as w of others
+        }
         if (g == 0 && c) atomicAdd(&t[u], (unsigned long long)c);
         __syncwarp(gmask);
         u = un;
@@ -699,11 +720,14 @@ constexpr int SMALL_WIDE_G = 16;
 constexpr int SMALL_WIDE_BLOCKS = 6;  // blocks per SM
 constexpr int SMALL_WIDE_GROUPS = SMALL_WARPS * 32 / SMALL_WIDE_G;  // per block
 
+template <bool SUP>
 __global__ void __launch_bounds__(SMALL_WARPS * 32) k_tc_small_wide(int32_t n, const int2* __restrict__ rowinfo,
                                                                    const int32_t* __restrict__ col,
                                                                    const int32_t* __restrict__ list,
                                                                    unsigned long long* __restrict__ t,
-                                                                   DevStats* stats, int strategy, float factor) {
+                                                                   DevStats* stats, int strategy, float factor,
+                                                                   uint32_t* __restrict__ sup_arg) {
+    uint32_t* const sup = SUP ? sup_arg : nullptr;
     extern __shared__ __align__(16) unsigned char wide_sh[];
     constexpr int G = SMALL_WIDE_G;
     const int lane = lane_id(), w = threadIdx.x >> 5;
@@ -732,13 +756,14 @@ __global__ void __launch_bounds__(SMALL_WARPS * 32) k_tc_small_wide(int32_t n, c
             const int dv = ri.y;
             if (dv == 0) continue;
             const int32_t* B = col + ri.x;
+            uint32_t* supB = sup ? sup + ri.x : nullptr;
             const int a = du - j - 1;
             int method = strategy;
             if (method == TC_STRAT_AUTO) method = small_auto(a, dv, factor);
             const uint32_t cj = method == TC_STRAT_MERGE
-                                    ? lane_merge_batched(Lu, j + 1, du, B, dv, cnt)
-                                    : (a <= dv ? lane_search(Lu, j + 1, du, B, dv, cnt)
-                                               : lane_search_rev(Lu, j + 1, du, B, dv, cnt));
+                                    ? lane_merge_batched(Lu, j + 1, du, B, dv, cnt, supB)
+                                    : (a <= dv ? lane_search(Lu, j + 1, du, B, dv, cnt, supB)
+                                               : lane_search_rev(Lu, j + 1, du, B, dv, cnt, supB));
             if (cj) atomicAdd(&cnt[j], cj);
             c += cj;
         }
@@ -747,7 +772,10 @@ __global__ void __launch_bounds__(SMALL_WARPS * 32) k_tc_small_wide(int32_t n, c
         __syncwarp(gmask);
         for (int p = g; p < du; p += G) {
             const uint32_t cv = cnt[p];
-            if (cv) atomicAdd(&t[Lu[p]], (unsigned long long)cv);
+            if (cv) {
+                atomicAdd(&t[Lu[p]], (unsigned long long)cv);
+                if (sup) atomicAdd(&sup[ru.x + p], cv);
+            }
         }
         if (g == 0 && c) atomicAdd(&t[u], (unsigned long long)c);
         __syncwarp(gmask);
@@ -784,12 +812,13 @@ struct HashProbe {
 // Hits add to the slot's counter (t[x], flushed once per source) and to the edge's
 // counter (t[v]); their sum goes to t[u].  Every lane reads at every round, so the
 // lanes stay busy whatever the lengths of the rows.
-template <int G, int SL>
+template <int G, int SL, bool SUP>
 __global__ void __launch_bounds__(SMALL_WARPS * 32) k_tc_small_hash(int32_t n, const int2* __restrict__ rowinfo,
                                                                    const int32_t* __restrict__ col,
                                                                    const int32_t* __restrict__ list, int cls,
                                                                    unsigned long long* __restrict__ t,
-                                                                   DevStats* stats) {
+                                                                   DevStats* stats, uint32_t* __restrict__ sup_arg) {
+    uint32_t* const sup = SUP ? sup_arg : nullptr;
     static_assert(G == 8 || G == 16 || G == 32, "lane groups within a warp");
     static_assert((SL & (SL - 1)) == 0 && SL >= 2 * G, "power-of-two table");
     constexpr int GROUPS = SMALL_WARPS * 32 / G;
@@ -798,6 +827,7 @@ __global__ void __launch_bounds__(SMALL_WARPS * 32) k_tc_small_hash(int32_t n, c
     __shared__ int32_t skeys[GROUPS][SL];
     __shared__ uint32_t shcnt[GROUPS][SL];
     __shared__ uint32_t secnt[GROUPS][G];
+    __shared__ uint16_t shpos[GROUPS][SL];  // position in N+(u) of each key (support only)
     const int lane = lane_id(), w = threadIdx.x >> 5;
     const int grp = lane / G, g = lane % G;
     const int gi = w * (32 / G) + grp;
@@ -806,6 +836,7 @@ __global__ void __launch_bounds__(SMALL_WARPS * 32) k_tc_small_hash(int32_t n, c
     int32_t* keys = skeys[gi];
     uint32_t* hcnt = shcnt[gi];
     uint32_t* ecnt = secnt[gi];
+    uint16_t* hpos = shpos[gi];
     for (int i = g; i < SL; i += G) {
         keys[i] = -1;
         hcnt[i] = 0;
@@ -829,6 +860,7 @@ __global__ void __launch_bounds__(SMALL_WARPS * 32) k_tc_small_hash(int32_t n, c
             if (valid) {
                 unsigned h = ((unsigned)x * 0x9e3779b1u) >> (32 - LG);
                 while (atomicCAS(&keys[h], -1, x) != -1) h = (h + 1) & (SL - 1);  // keys are distinct
+                if (sup) hpos[h] = (uint16_t)(i0 + g);
             }
             jh += __popc(gballot(x < R));
         }
@@ -840,6 +872,7 @@ __global__ void __launch_bounds__(SMALL_WARPS * 32) k_tc_small_hash(int32_t n, c
             const bool has = e0 + g < ne;
             int32_t v = has ? col[base + e0 + g] : 0;
             int2 rv = has ? rowinfo[v] : make_int2(0, 0);
+            int jv = e0 + g;  // position of v in N+(u)
             // the edges with a non-empty row first: lane i holds the i-th of them
             const unsigned nz = gballot(has && rv.y > 0);
             const int cz = __popc(nz);
@@ -847,6 +880,7 @@ __global__ void __launch_bounds__(SMALL_WARPS * 32) k_tc_small_hash(int32_t n, c
             {
                 const int src = g < cz ? (int)__fns(nz, 0, g + 1) : g;
                 v = __shfl_sync(gmask, v, src, G);
+                jv = __shfl_sync(gmask, jv, src, G);
                 rv.x = __shfl_sync(gmask, rv.x, src, G);
                 rv.y = __shfl_sync(gmask, rv.y, src, G);
                 if (g >= cz) rv.y = 0;
@@ -869,12 +903,14 @@ __global__ void __launch_bounds__(SMALL_WARPS * 32) k_tc_small_hash(int32_t n, c
                 const int bx = __shfl_sync(gmask, excl, idx, G);
                 const int k = r + g;
                 if (k < total) {
-                    const int32_t x = col[(int64_t)bs + (k - bx)];
+                    const int64_t px = (int64_t)bs + (k - bx);
+                    const int32_t x = col[px];
                     if (x <= maxu) {
                         const int h = P(x);
                         if (h >= 0) {
                             atomicAdd(&hcnt[h], 1u);
                             atomicAdd(&ecnt[idx], 1u);
+                            if (sup) atomicAdd(&sup[px], 1u);  // edge (v, x)
                         }
                     }
                 }
@@ -884,6 +920,7 @@ __global__ void __launch_bounds__(SMALL_WARPS * 32) k_tc_small_hash(int32_t n, c
             ecnt[g] = 0;
             if (g < cz && ce) {
                 atomicAdd(&t[v], (unsigned long long)ce);
+                if (sup) atomicAdd(&sup[base + jv], ce);  // edge (u, v)
                 cu += ce;
             }
             __syncwarp(gmask);
@@ -895,7 +932,10 @@ __global__ void __launch_bounds__(SMALL_WARPS * 32) k_tc_small_hash(int32_t n, c
             const int32_t x = keys[i];
             if (x >= 0) {
                 const uint32_t c = hcnt[i];
-                if (c) atomicAdd(&t[x], (unsigned long long)c);
+                if (c) {
+                    atomicAdd(&t[x], (unsigned long long)c);
+                    if (sup) atomicAdd(&sup[base + hpos[i]], c);  // edge (u, x)
+                }
                 keys[i] = -1;
                 hcnt[i] = 0;
             }
@@ -909,7 +949,8 @@ __global__ void __launch_bounds__(SMALL_WARPS * 32) k_tc_small_hash(int32_t n, c
 // staged N+(u), two per lane per round, stopping above max N+(u); hits add to the
 // set's per-slot counter.  Returns the edge's count (all lanes).
 template <class Probe>
-__device__ uint32_t edge_probe_set(const Probe& P, int32_t maxu, uint32_t* hcnt, const int32_t* __restrict__ B, int b) {
+__device__ uint32_t edge_probe_set(const Probe& P, int32_t maxu, uint32_t* hcnt, const int32_t* __restrict__ B, int b,
+                               uint32_t* __restrict__ supB) {
     const int lane = lane_id();
     uint32_t c = 0;
     for (int k0 = 0; k0 < b; k0 += 64) {
@@ -920,6 +961,7 @@ __device__ uint32_t edge_probe_set(const Probe& P, int32_t maxu, uint32_t* hcnt,
             const int p = P(x1);
             if (p >= 0) {
                 atomicAdd(&hcnt[p], 1u);
+                if (supB) atomicAdd(&supB[k1], 1u);
                 ++c;
             }
         }
@@ -927,6 +969,7 @@ __device__ uint32_t edge_probe_set(const Probe& P, int32_t maxu, uint32_t* hcnt,
             const int p = P(x2);
             if (p >= 0) {
                 atomicAdd(&hcnt[p], 1u);
+                if (supB) atomicAdd(&supB[k2], 1u);
                 ++c;
             }
         }
@@ -953,13 +996,16 @@ struct CtaShared {
     int q;
 };
 
+template <bool SUP>
 __global__ void __launch_bounds__(CTA_THREADS) k_tc_cta(int32_t n, const int64_t* __restrict__ rowstart,
                                                         const int32_t* __restrict__ rowlen,
                                                         const int2* __restrict__ rowinfo,
                                                         const int32_t* __restrict__ col,
                                                         const int32_t* __restrict__ list,
                                                         unsigned long long* __restrict__ t,
-                                                        DevStats* stats, int strategy, float factor) {
+                                                        DevStats* stats, int strategy, float factor,
+                                                        uint32_t* __restrict__ sup_arg) {
+    uint32_t* const sup = SUP ? sup_arg : nullptr;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     CtaShared& sh = *reinterpret_cast<CtaShared*>(smem_raw);
     const int lane = lane_id(), w = threadIdx.x >> 5;
@@ -1006,7 +1052,8 @@ __global__ void __launch_bounds__(CTA_THREADS) k_tc_cta(int32_t n, const int64_t
             }
             __syncthreads();
         }
-        Sink S{staged ? sh.cnt : nullptr, t, Lu};
+        uint32_t* supA = sup ? sup + base : nullptr;
+        Sink S{staged ? sh.cnt : nullptr, t, Lu, staged ? nullptr : supA, nullptr};
         unsigned long long utot = 0;
         for (int j = w; j < jh; j += CTA_WARPS) {
             const int32_t v = Lu[j];
@@ -1014,11 +1061,13 @@ __global__ void __launch_bounds__(CTA_THREADS) k_tc_cta(int32_t n, const int64_t
             const int dv = ri.y;
             if (dv == 0) continue;
             const int32_t* B = col + ri.x;
+            uint32_t* supB = sup ? sup + ri.x : nullptr;
+            S.supB = supB;
             uint32_t c;
             if (bitmap) {
-                c = edge_bitmap(sh.s.b.bm, sh.s.b.pre, u, maxu, sh.cnt, B, dv);
+                c = edge_bitmap(sh.s.b.bm, sh.s.b.pre, u, maxu, sh.cnt, B, dv, supB);
             } else if (hashed) {
-                c = edge_probe_set(HashProbe{sh.s.h.keys, hshift, hmask}, maxu, sh.s.h.hcnt, B, dv);
+                c = edge_probe_set(HashProbe{sh.s.h.keys, hshift, hmask}, maxu, sh.s.h.hcnt, B, dv, supB);
             } else {
                 int method = strategy;
                 if (method == TC_STRAT_AUTO) {
@@ -1031,10 +1080,12 @@ __global__ void __launch_bounds__(CTA_THREADS) k_tc_cta(int32_t n, const int64_t
                 c = edge_dispatch(method, S, j + 1, du, B, dv);
             }
             if (lane == 0 && c) {
-                if (staged)
+                if (staged) {
                     atomicAdd(&sh.cnt[j], c);
-                else
+                } else {
                     atomicAdd(&t[v], (unsigned long long)c);
+                    if (supA) atomicAdd(&supA[j], c);  // edge (u, v)
+                }
             }
             utot += c;
         }
@@ -1043,14 +1094,20 @@ __global__ void __launch_bounds__(CTA_THREADS) k_tc_cta(int32_t n, const int64_t
         if (staged) {
             for (int p = threadIdx.x; p < du; p += CTA_THREADS) {
                 const uint32_t cv = sh.cnt[p];
-                if (cv) atomicAdd(&t[sh.Lu[p]], (unsigned long long)cv);
+                if (cv) {
+                    atomicAdd(&t[sh.Lu[p]], (unsigned long long)cv);
+                    if (supA) atomicAdd(&supA[p], cv);
+                }
             }
         }
         if (hashed) {
             for (int p = threadIdx.x; p <= (int)hmask; p += CTA_THREADS) {
                 const int32_t x = sh.s.h.keys[p];
                 const uint32_t cv = sh.s.h.hcnt[p];
-                if (x >= 0 && cv) atomicAdd(&t[x], (unsigned long long)cv);
+                if (x >= 0 && cv) {
+                    atomicAdd(&t[x], (unsigned long long)cv);
+                    if (supA) atomicAdd(&supA[lower_bound(sh.Lu, 0, du, x)], cv);
+                }
             }
         }
         if (threadIdx.x == 0) {
@@ -1094,10 +1151,12 @@ struct ListProbe {
 // (the read stops above max N+(v)); shorter ones are laid end to end and read 32
 // entries at a time.  Matches add to cnt[p] (or t[x] when cnt is null) and to the
 // per-in-edge total, which goes to t[u].  Returns the batch total (all lanes).
-template <class Probe>
+template <bool SUP, class Probe>
 __device__ uint32_t hub_batch(int64_t k0, int64_t e1, const int4* __restrict__ in_rec,
                               const int32_t* __restrict__ col, int32_t maxv, const Probe& probe, uint32_t* cnt,
-                              unsigned long long* __restrict__ t, uint32_t* cw) {
+                              unsigned long long* __restrict__ t, uint32_t* cw, uint32_t* __restrict__ sup_arg,
+                              int64_t vbase) {
+    uint32_t* const sup = SUP ? sup_arg : nullptr;
     const int lane = lane_id();
     const int64_t k = k0 + lane;
     const int4 rec = k < e1 ? in_rec[k] : make_int4(0, 0, 0, 0);
@@ -1146,10 +1205,13 @@ __device__ uint32_t hub_batch(int64_t k0, int64_t e1, const int4* __restrict__ i
                 if (x[j] <= maxv) {
                     const int p = probe(x[j]);
                     if (p >= 0) {
-                        if (cnt)
+                        if (cnt) {
                             atomicAdd(&cnt[p], 1u);
-                        else
+                        } else {
                             atomicAdd(&t[x[j]], 1ull);
+                            if (sup) atomicAdd(&sup[vbase + p], 1u);  // edge (v, x)
+                        }
+                        if (sup) atomicAdd(&sup[bL + o0 + j * HUB_GLANES + gl], 1u);  // edge (u, x)
                         ++c;
                     }
                 }
@@ -1161,7 +1223,10 @@ __device__ uint32_t hub_batch(int64_t k0, int64_t e1, const int4* __restrict__ i
         }
 #pragma unroll
         for (int off = HUB_GLANES / 2; off > 0; off >>= 1) c += __shfl_xor_sync(FULL, c, off);
-        if (gl == 0 && my >= 0 && c) atomicAdd(&t[uL], (unsigned long long)c);
+        if (gl == 0 && my >= 0 && c) {
+            atomicAdd(&t[uL], (unsigned long long)c);
+            if (sup) atomicAdd(&sup[bL - 1], c);  // edge (u, v): bL is the entry after v
+        }
         total_c += __reduce_add_sync(FULL, gl == 0 ? c : 0u);
     }
     if (a >= HUB_LONG) a = 0;  // done above
@@ -1193,10 +1258,13 @@ __device__ uint32_t hub_batch(int64_t k0, int64_t e1, const int4* __restrict__ i
             if (x <= maxv) {
                 const int p = probe(x);
                 if (p >= 0) {
-                    if (cnt)
+                    if (cnt) {
                         atomicAdd(&cnt[p], 1u);
-                    else
+                    } else {
                         atomicAdd(&t[x], 1ull);
+                        if (sup) atomicAdd(&sup[vbase + p], 1u);  // edge (v, x)
+                    }
+                    if (sup) atomicAdd(&sup[bi + (item - xi)], 1u);  // edge (u, x)
                     atomicAdd(&cw[idx], 1u);
                 }
             }
@@ -1204,7 +1272,10 @@ __device__ uint32_t hub_batch(int64_t k0, int64_t e1, const int4* __restrict__ i
     }
     __syncwarp();
     const uint32_t cu = cw[lane];
-    if (lane < cz && cu) atomicAdd(&t[uu], (unsigned long long)cu);
+    if (lane < cz && cu) {
+        atomicAdd(&t[uu], (unsigned long long)cu);
+        if (sup) atomicAdd(&sup[b0 - 1], cu);  // edge (u, v)
+    }
     __syncwarp();
     return total_c + __reduce_add_sync(FULL, lane < cz ? cu : 0u);
 }
@@ -1233,6 +1304,7 @@ struct HubShared {
     unsigned bq;  // next batch of the current big hub
 };
 
+template <bool SUP>
 __global__ void __launch_bounds__(HUB_THREADS) k_tc_hub(int32_t n, int32_t hub_cap, const int64_t* __restrict__ rowstart,
                                                         const int32_t* __restrict__ rowlen,
                                                         const int32_t* __restrict__ col,
@@ -1241,7 +1313,8 @@ __global__ void __launch_bounds__(HUB_THREADS) k_tc_hub(int32_t n, int32_t hub_c
                                                         const int32_t* __restrict__ med_list,
                                                         const int4* __restrict__ in_rec,
                                                         unsigned long long* __restrict__ t, DevStats* stats,
-                                                        int probe_mode) {
+                                                        int probe_mode, uint32_t* __restrict__ sup_arg) {
+    uint32_t* const sup = SUP ? sup_arg : nullptr;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     HubShared& sh = *reinterpret_cast<HubShared*>(smem_raw);
     const int lane = lane_id(), w = threadIdx.x >> 5;
@@ -1287,7 +1360,7 @@ __global__ void __launch_bounds__(HUB_THREADS) k_tc_hub(int32_t n, int32_t hub_c
                 if (lane == 0) k = atomicAdd(&sh.bq, 1u);
                 const int64_t bb = e0 + (int64_t)__shfl_sync(FULL, k, 0) * bs;
                 if (bb >= e1) break;
-                vtot += hub_batch(bb, min(bb + bs, e1), in_rec, col, maxv, P, cnt, t, sh.cw[w]);
+                vtot += hub_batch<SUP>(bb, min(bb + bs, e1), in_rec, col, maxv, P, cnt, t, sh.cw[w], sup, base);
             }
         } else {
             const ListProbe P{staged ? sh.u.big.s.list : col + base, dv};
@@ -1296,7 +1369,7 @@ __global__ void __launch_bounds__(HUB_THREADS) k_tc_hub(int32_t n, int32_t hub_c
                 if (lane == 0) k = atomicAdd(&sh.bq, 1u);
                 const int64_t bb = e0 + (int64_t)__shfl_sync(FULL, k, 0) * bs;
                 if (bb >= e1) break;
-                vtot += hub_batch(bb, min(bb + bs, e1), in_rec, col, maxv, P, cnt, t, sh.cw[w]);
+                vtot += hub_batch<SUP>(bb, min(bb + bs, e1), in_rec, col, maxv, P, cnt, t, sh.cw[w], sup, base);
             }
         }
         if (lane == 0) sh.vt[w] = vtot;
@@ -1311,13 +1384,19 @@ __global__ void __launch_bounds__(HUB_THREADS) k_tc_hub(int32_t n, int32_t hub_c
                         rest &= rest - 1;
                         const int p = sh.u.big.s.b.pre[i] + __popc(word & ((1u << bpos) - 1u));
                         const uint32_t c = sh.u.big.cnt[p];
-                        if (c) atomicAdd(&t[v + 1 + i * 32 + bpos], (unsigned long long)c);
+                        if (c) {
+                            atomicAdd(&t[v + 1 + i * 32 + bpos], (unsigned long long)c);
+                            if (sup) atomicAdd(&sup[base + p], c);  // edge (v, x)
+                        }
                     }
                 }
             } else {
                 for (int p = threadIdx.x; p < dv; p += HUB_THREADS) {
                     const uint32_t c = sh.u.big.cnt[p];
-                    if (c) atomicAdd(&t[sh.u.big.s.list[p]], (unsigned long long)c);
+                    if (c) {
+                        atomicAdd(&t[sh.u.big.s.list[p]], (unsigned long long)c);
+                        if (sup) atomicAdd(&sup[base + p], c);  // edge (v, x)
+                    }
                 }
             }
         }
@@ -1364,13 +1443,17 @@ __global__ void __launch_bounds__(HUB_THREADS) k_tc_hub(int32_t n, int32_t hub_c
         __syncwarp();
         const HashProbe P{K, shift, mask};
         unsigned long long vtot = 0;
-        for (int64_t bb = e0; bb < e1; bb += 32) vtot += hub_batch(bb, e1, in_rec, col, maxv, P, cnt, t, sh.cw[w]);
+        for (int64_t bb = e0; bb < e1; bb += 32)
+            vtot += hub_batch<SUP>(bb, e1, in_rec, col, maxv, P, cnt, t, sh.cw[w], sup, base);
         __syncwarp();
         for (int p = lane; p <= (int)mask; p += 32) {
             const int32_t x = K[p];
             if (x >= 0) {
                 const uint32_t c = cnt[p];
-                if (c) atomicAdd(&t[x], (unsigned long long)c);
+                if (c) {
+                    atomicAdd(&t[x], (unsigned long long)c);
+                    if (sup) atomicAdd(&sup[base + lower_bound(col + base, 0, dv, x)], c);  // edge (v, x)
+                }
                 K[p] = -1;
                 cnt[p] = 0;
             }
@@ -1490,15 +1573,19 @@ void launch_plan(const CountBuffers& C, const Strategy& S, const Launch& L) {
 }
 
 cudaError_t intersect_init_attributes() {
-    cudaError_t e = cudaFuncSetAttribute(k_tc_cta, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(CtaShared));
-    if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(k_tc_small_wide, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             2 * SMALL_WIDE_GROUPS * SMALL_WIDE_MAX * (int)sizeof(int32_t));
-    if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(k_tc_hub, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(HubShared));
+    const int wide = 2 * SMALL_WIDE_GROUPS * SMALL_WIDE_MAX * (int)sizeof(int32_t);
+    cudaError_t e = cudaSuccess;
+    if ((e = cudaFuncSetAttribute(k_tc_cta<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(CtaShared))) ||
+        (e = cudaFuncSetAttribute(k_tc_cta<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(CtaShared))) ||
+        (e = cudaFuncSetAttribute(k_tc_small_wide<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, wide)) ||
+        (e = cudaFuncSetAttribute(k_tc_small_wide<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, wide)) ||
+        (e = cudaFuncSetAttribute(k_tc_hub<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(HubShared))))
+        return e;
+    return cudaFuncSetAttribute(k_tc_hub<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(HubShared));
 }
 
-void launch_intersect(const CountBuffers& C, const Strategy& S, cudaEvent_t* ev, const Launch& L) {
+template <bool SUP>
+void intersect_impl(const CountBuffers& C, const Strategy& S, cudaEvent_t* ev, const Launch& L) {
     if (C.n <= 0) return;
     if (ev) cudaEventRecord(ev[PH_SMALL], L.stream);
     const int ss = S.strat[TC_BUCKET_SMALL];
@@ -1506,50 +1593,59 @@ void launch_intersect(const CountBuffers& C, const Strategy& S, cudaEvent_t* ev,
     if (ss == TC_STRAT_HASH) {
         // sources of at most 16 entries: one edge per lane (Eq. 3 per edge), whose
         // short merges cost less than building and flushing a set per source
-        k_tc_small<8><<<L.sms * SMALL_BLOCKS, SMALL_WARPS * 32, 0, L.stream>>>(
-            C.n, C.rowstart, C.rowlen, C.rowinfo, C.col, C.small_list[0], 0, C.t_rank, C.stats, TC_STRAT_AUTO, sf);
+        k_tc_small<8, SUP><<<L.sms * SMALL_BLOCKS, SMALL_WARPS * 32, 0, L.stream>>>(
+            C.n, C.rowstart, C.rowlen, C.rowinfo, C.col, C.small_list[0], 0, C.t_rank, C.stats, TC_STRAT_AUTO, sf, C.sup);
         count_launch();
-        k_tc_small<16><<<L.sms * SMALL_BLOCKS, SMALL_WARPS * 32, 0, L.stream>>>(
-            C.n, C.rowstart, C.rowlen, C.rowinfo, C.col, C.small_list[1], 1, C.t_rank, C.stats, TC_STRAT_AUTO, sf);
+        k_tc_small<16, SUP><<<L.sms * SMALL_BLOCKS, SMALL_WARPS * 32, 0, L.stream>>>(
+            C.n, C.rowstart, C.rowlen, C.rowinfo, C.col, C.small_list[1], 1, C.t_rank, C.stats, TC_STRAT_AUTO, sf, C.sup);
         count_launch();
-        k_tc_small_hash<32, 64><<<L.sms * SMALL_BLOCKS, SMALL_WARPS * 32, 0, L.stream>>>(
-            C.n, C.rowinfo, C.col, C.small_list[2], 2, C.t_rank, C.stats);
+        k_tc_small_hash<32, 64, SUP><<<L.sms * SMALL_BLOCKS, SMALL_WARPS * 32, 0, L.stream>>>(
+            C.n, C.rowinfo, C.col, C.small_list[2], 2, C.t_rank, C.stats, C.sup);
         count_launch();
-        k_tc_small_hash<32, 2 * SMALL_WIDE_MAX><<<L.sms * SMALL_WIDE_BLOCKS, SMALL_WARPS * 32, 0, L.stream>>>(
-            C.n, C.rowinfo, C.col, C.small_list[3], 3, C.t_rank, C.stats);
+        k_tc_small_hash<32, 2 * SMALL_WIDE_MAX, SUP><<<L.sms * SMALL_WIDE_BLOCKS, SMALL_WARPS * 32, 0, L.stream>>>(
+            C.n, C.rowinfo, C.col, C.small_list[3], 3, C.t_rank, C.stats, C.sup);
         count_launch();
     } else {
-        k_tc_small<8><<<L.sms * SMALL_BLOCKS, SMALL_WARPS * 32, 0, L.stream>>>(
-            C.n, C.rowstart, C.rowlen, C.rowinfo, C.col, C.small_list[0], 0, C.t_rank, C.stats, ss, sf);
+        k_tc_small<8, SUP><<<L.sms * SMALL_BLOCKS, SMALL_WARPS * 32, 0, L.stream>>>(
+            C.n, C.rowstart, C.rowlen, C.rowinfo, C.col, C.small_list[0], 0, C.t_rank, C.stats, ss, sf, C.sup);
         count_launch();
-        k_tc_small<16><<<L.sms * SMALL_BLOCKS, SMALL_WARPS * 32, 0, L.stream>>>(
-            C.n, C.rowstart, C.rowlen, C.rowinfo, C.col, C.small_list[1], 1, C.t_rank, C.stats, ss, sf);
+        k_tc_small<16, SUP><<<L.sms * SMALL_BLOCKS, SMALL_WARPS * 32, 0, L.stream>>>(
+            C.n, C.rowstart, C.rowlen, C.rowinfo, C.col, C.small_list[1], 1, C.t_rank, C.stats, ss, sf, C.sup);
         count_launch();
-        k_tc_small<32><<<L.sms * SMALL_BLOCKS, SMALL_WARPS * 32, 0, L.stream>>>(
-            C.n, C.rowstart, C.rowlen, C.rowinfo, C.col, C.small_list[2], 2, C.t_rank, C.stats, ss, sf);
+        k_tc_small<32, SUP><<<L.sms * SMALL_BLOCKS, SMALL_WARPS * 32, 0, L.stream>>>(
+            C.n, C.rowstart, C.rowlen, C.rowinfo, C.col, C.small_list[2], 2, C.t_rank, C.stats, ss, sf, C.sup);
         count_launch();
-        k_tc_small_wide<<<L.sms * SMALL_WIDE_BLOCKS, SMALL_WARPS * 32,
+        k_tc_small_wide<SUP><<<L.sms * SMALL_WIDE_BLOCKS, SMALL_WARPS * 32,
                           2 * SMALL_WIDE_GROUPS * SMALL_WIDE_MAX * sizeof(int32_t), L.stream>>>(
-            C.n, C.rowinfo, C.col, C.small_list[3], C.t_rank, C.stats, ss, sf);
+            C.n, C.rowinfo, C.col, C.small_list[3], C.t_rank, C.stats, ss, sf, C.sup);
         count_launch();
     }
     if (ev) cudaEventRecord(ev[PH_CTA], L.stream);
     cudaMemsetAsync(&C.stats->cta_next, 0, sizeof(unsigned), L.stream);
-    k_tc_cta<<<L.sms * 4, CTA_THREADS, sizeof(CtaShared), L.stream>>>(C.n, C.rowstart, C.rowlen, C.rowinfo, C.col,
+    k_tc_cta<SUP><<<L.sms * 4, CTA_THREADS, sizeof(CtaShared), L.stream>>>(C.n, C.rowstart, C.rowlen, C.rowinfo, C.col,
                                                                      C.cta_list,
                                                                      C.t_rank, C.stats, S.strat[TC_BUCKET_CTA],
-                                                                     S.factor[TC_BUCKET_CTA]);
+                                                                     S.factor[TC_BUCKET_CTA], C.sup);
     count_launch();
     if (ev) cudaEventRecord(ev[PH_HUB], L.stream);
     if (C.hub_cap > 0) {
         if (S.hub_core > 0) launch_core_count(C, L);
         cudaMemsetAsync(&C.stats->hub_next, 0, 2 * sizeof(unsigned), L.stream);
-        k_tc_hub<<<L.sms * HUB_BLOCKS, HUB_THREADS, sizeof(HubShared), L.stream>>>(
+        k_tc_hub<SUP><<<L.sms * HUB_BLOCKS, HUB_THREADS, sizeof(HubShared), L.stream>>>(
             C.n, C.hub_cap, C.rowstart, C.rowlen, C.col, C.hub_start, C.big_list, C.med_list, C.in_rec, C.t_rank,
-            C.stats, S.strat[TC_BUCKET_HUB] == TC_STRAT_PROBE ? 1 : 0);
+            C.stats, S.strat[TC_BUCKET_HUB] == TC_STRAT_PROBE ? 1 : 0, C.sup);
         count_launch();
     }
     if (ev) cudaEventRecord(ev[PH_END], L.stream);
+}
+
+// The plain count, or the count that also records every triangle's three edges in
+// C.sup (tc_edge_support), from the same kernels compiled twice.
+void launch_intersect(const CountBuffers& C, const Strategy& S, cudaEvent_t* ev, const Launch& L) {
+    if (C.sup)
+        intersect_impl<true>(C, S, ev, L);
+    else
+        intersect_impl<false>(C, S, ev, L);
 }
 
 void launch_sum_t(const CountBuffers& C, const Launch& L) {

@@ -124,40 +124,24 @@ __global__ void k_vf_id_of(int32_t n, const int32_t* __restrict__ rank, int32_t*
     for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride) id_of[rank[v]] = (int32_t)v;
 }
 
-// Per-edge support: one warp per source row x (highest rank first, through a
-// counter), a lane per oriented entry x -> y; support = |adj(x) ∩ adj(y)| over the
-// symmetric rows, by the same per-pair Eq. 3 choice.  Edge k of the compact order
-// (row by row) is written at estart[x] + position, in the caller's ids, smaller first.
-__global__ void __launch_bounds__(VF_THREADS) k_edge_support(int32_t n, const int64_t* __restrict__ sym_start,
-                                                             const int32_t* __restrict__ sym,
-                                                             const int2* __restrict__ rowinfo,
-                                                             const int32_t* __restrict__ col,
-                                                             const int32_t* __restrict__ id_of,
-                                                             const int64_t* __restrict__ estart,
-                                                             int32_t* __restrict__ eu, int32_t* __restrict__ ev,
-                                                             uint32_t* __restrict__ support,
-                                                             unsigned* __restrict__ counter) {
+// Per-edge supports out of the count: the oriented entry x -> y at col index e is the
+// undirected edge {x, y}; it goes to estart[x] + position in x's row, in the caller's
+// ids, smaller first, with the support the count recorded at e.
+__global__ void k_support_out(int32_t n, const int2* __restrict__ rowinfo,
+                              const int32_t* __restrict__ col, const uint32_t* __restrict__ sup,
+                              const int32_t* __restrict__ id_of, const int64_t* __restrict__ estart,
+                              int32_t* __restrict__ eu, int32_t* __restrict__ ev, uint32_t* __restrict__ support) {
     const int lane = lane_id();
-    for (;;) {
-        unsigned q = 0;
-        if (lane == 0) q = atomicAdd(counter, 1u);
-        q = __shfl_sync(FULL, q, 0);
-        if (q >= (unsigned)n) break;
-        const int32_t x = n - 1 - (int32_t)q;
+    const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t x = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; x < n; x += warps) {
         const int2 rx = rowinfo[x];
-        if (rx.y == 0) continue;
-        const int64_t a0 = sym_start[x];
-        const int da = (int)(sym_start[x + 1] - a0);
         const int32_t idx = id_of[x];
         const int64_t e0 = estart[x];
         for (int p = lane; p < rx.y; p += 32) {
-            const int32_t y = col[rx.x + p];
-            const int64_t b0 = sym_start[y];
-            const uint32_t c = lane_count_hybrid(sym + a0, da, sym + b0, (int)(sym_start[y + 1] - b0));
-            const int32_t idy = id_of[y];
+            const int32_t idy = id_of[col[rx.x + p]];
             eu[e0 + p] = min(idx, idy);
             ev[e0 + p] = max(idx, idy);
-            support[e0 + p] = c;
+            support[e0 + p] = sup[rx.x + p];
         }
     }
 }
@@ -212,16 +196,15 @@ void launch_vertex_formula(const VertexFormulaBuffers& V, const Launch& L) {
     count_launch();
 }
 
-void launch_edge_support(const VertexFormulaBuffers& V, const int32_t* rank, int32_t* id_of, int64_t* estart,
-                         int32_t* eu, int32_t* ev, uint32_t* support, const Launch& L) {
-    if (V.n <= 0) return;
-    launch_symmetric_rows(V, L);
-    k_vf_id_of<<<grid_for(V.n, VF_THREADS, L.sms), VF_THREADS, 0, L.stream>>>(V.n, rank, id_of);
+void launch_support_out(int32_t n, const int32_t* rank, const int32_t* rowlen, const int2* rowinfo, const int32_t* col,
+                        const uint32_t* sup, int32_t* id_of, int64_t* estart, void* scan_tmp, int32_t* eu, int32_t* ev,
+                        uint32_t* support, const Launch& L) {
+    if (n <= 0) return;
+    k_vf_id_of<<<grid_for(n, VF_THREADS, L.sms), VF_THREADS, 0, L.stream>>>(n, rank, id_of);
     count_launch();
-    scan_u32_to_i64(reinterpret_cast<const uint32_t*>(V.rowlen), estart, V.n, V.tmp, L);
-    cudaMemsetAsync(V.counter, 0, sizeof(unsigned), L.stream);
-    k_edge_support<<<L.sms * 8, VF_THREADS, 0, L.stream>>>(V.n, V.sym_start, V.sym, V.rowinfo, V.col, id_of, estart,
-                                                          eu, ev, support, V.counter);
+    scan_u32_to_i64(reinterpret_cast<const uint32_t*>(rowlen), estart, n, scan_tmp, L);
+    k_support_out<<<grid_for((int64_t)n * 32, VF_THREADS, L.sms), VF_THREADS, 0, L.stream>>>(
+        n, rowinfo, col, sup, id_of, estart, eu, ev, support);
     count_launch();
 }
 

@@ -294,16 +294,41 @@ def test_vertex_formula_rmat_and_er(tc, rmat14, er4096):
         np.testing.assert_array_equal(td.cpu().numpy().view(np.uint64), ref["t"])
 
 
-def _assert_support_matches(tc, n, s, d):
+def _assert_support_matches(tc, n, s, d, hubs=None):
     ru, rv, rs = oracle.edge_support(n, s, d)
     g = tc.Graph.from_edges(n, s, d)
     try:
+        if hubs:
+            g.set_hubs(*hubs[:2])
+            if len(hubs) > 2:
+                t = g.tuning()
+                t["hub_big_in"] = hubs[2]
+                g.set_tuning(t)
+        T0 = g.count()
         u, v, sup = g.edge_support()
+        assert g.count() == T0  # the graph's own tuning (dense core included) is back
     finally:
         g.close()
     np.testing.assert_array_equal(u, ru)
     np.testing.assert_array_equal(v, rv)
     np.testing.assert_array_equal(sup, rs)
+
+
+@pytest.mark.parametrize("hubs", [(32, 0), (2, 131072, 1 << 30), (2, 131072, 1), (8, 64), (32, 131072)])
+def test_edge_support_every_bucket(tc, hubs):
+    """The support recorded by each count kernel: hubs off (small and block buckets
+    only), every hub a warp's hash set, every hub a block's bitmap, a few hubs, the
+    default; on an R-MAT whose sources reach past 256 out-entries."""
+    n = 1 << 13
+    s, d = graphgen.rmat(13, 24 * n, seed=17)
+    _assert_support_matches(tc, n, s, d, hubs)
+
+
+def test_edge_support_hub_longer_than_shared_counters(tc):
+    """K_1100 with every vertex a big hub: N+(v) of up to 1098 entries exceeds the
+    1024 shared-memory counters, so matches count globally."""
+    n, (s, d) = F.complete(1100)
+    _assert_support_matches(tc, n, s, d, (2, 131072, 1))
 
 
 @pytest.mark.parametrize("make", [
@@ -344,3 +369,30 @@ def test_hub_longer_than_shared_counters(tc, core):
     whole graph is one dense core (core on)."""
     n, (s, d) = F.complete(1100)
     assert_matches_oracle(tc, n, s, d, hubs=(1, 131072), tuning={"hub_core": core})
+
+
+def test_edge_support_full_size_rmat20(tc):
+    """R-MAT scale 20 (the paper's S20 EF16): the supports sum to 3T, and a sample of
+    4000 edges matches |adj(u) ∩ adj(v)| computed by the oracle's Alg. 2 on its CSR."""
+    import torch
+    w = graphgen.workload("rmat20")
+    s, d = w.edges()
+    g = tc.Graph.from_edges(w.n, torch.from_numpy(s).cuda(), torch.from_numpy(d).cuda())
+    try:
+        T = g.count()
+        m = g.info()["m_simple"]
+        bufs = [torch.empty(m, dtype=torch.int32, device="cuda") for _ in range(3)]
+        u, v, sup = g.edge_support(*bufs)
+        torch.cuda.synchronize()
+        assert g.count() == T
+    finally:
+        g.close()
+    u, v, sup = u.cpu().numpy(), v.cpu().numpy(), sup.cpu().numpy().view(np.uint32)
+    assert int(sup.sum(dtype=np.uint64)) == 3 * T
+    assert (u < v).all()
+    offsets, adj, _ = oracle.build_csr(w.n, s, d)
+    rng = np.random.default_rng(7)
+    for k in rng.choice(m, 4000, replace=False):
+        a, b = int(u[k]), int(v[k])
+        want = oracle.ssi(adj[offsets[a]:offsets[a + 1]], adj[offsets[b]:offsets[b + 1]])
+        assert int(sup[k]) == want, (a, b)
