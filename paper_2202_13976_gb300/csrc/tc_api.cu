@@ -108,6 +108,7 @@ struct tc_graph {
     uint32_t* hub_cnt = nullptr;
     int64_t* hub_start = nullptr;
     uint32_t* hub_cur = nullptr;
+    unsigned long long* hub_cur64 = nullptr;
     int32_t* big_list = nullptr;
     int32_t* med_list = nullptr;
     int4* in_rec = nullptr;
@@ -256,7 +257,8 @@ tc_status build_graph(tc_graph* g, const int32_t* src, const int32_t* dst, int64
         (st = dalloc(g, &g->small_list[2], nn, &keep)) || (st = dalloc(g, &g->small_list[3], nn, &keep)) ||
         (st = dalloc(g, &g->cta_list, nn, &keep)) ||
         (st = dalloc(g, &g->hub_cnt, hc + 1, &keep)) || (st = dalloc(g, &g->hub_start, hc + 1, &keep)) ||
-        (st = dalloc(g, &g->hub_cur, hc + 1, &keep)) || (st = dalloc(g, &g->big_list, hc + 1, &keep)) ||
+        (st = dalloc(g, &g->hub_cur, hc + 1, &keep)) || (st = dalloc(g, &g->hub_cur64, hc + 1, &keep)) ||
+        (st = dalloc(g, &g->big_list, hc + 1, &keep)) ||
         (st = dalloc(g, &g->med_list, hc + 1, &keep)) || (st = dalloc(g, &g->in_rec, (size_t)m, &keep)) ||
         (st = dalloc(g, &g->rowof, (size_t)m, &keep)) ||
         (st = dalloc(g, (char**)&g->plan_tmp, scan_tmp_bytes((int64_t)hc + 1), &keep)) ||
@@ -385,6 +387,7 @@ CountBuffers count_buffers(tc_graph* g) {
     C.hub_cnt = g->hub_cnt;
     C.hub_start = g->hub_start;
     C.hub_cur = g->hub_cur;
+    C.hub_cur64 = g->hub_cur64;
     C.big_list = g->big_list;
     C.med_list = g->med_list;
     C.in_rec = g->in_rec;

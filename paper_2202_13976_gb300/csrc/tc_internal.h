@@ -151,6 +151,7 @@ struct CountBuffers {
     uint32_t* hub_cnt;       // hub_cap + 1
     int64_t* hub_start;      // hub_cap + 1
     uint32_t* hub_cur;       // hub_cap + 1
+    unsigned long long* hub_cur64;  // hub_cap + 1: next free slot of every hub's segment (planner)
     int32_t* big_list;       // hub_cap: big hubs, highest rank first
     int32_t* med_list;       // hub_cap: the other hubs, highest rank first
     int4* in_rec;            // m: in-edge {u, first suffix entry, end of N+(u), 0} (indices into col)

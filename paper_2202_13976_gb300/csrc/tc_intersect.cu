@@ -434,8 +434,8 @@ __global__ void __launch_bounds__(SCAT_THREADS) k_hub_scatter(int32_t n, int32_t
                                                               const int32_t* __restrict__ col,
                                                               const int32_t* __restrict__ rowof,
                                                               const int64_t* __restrict__ hub_start,
-                                                              uint32_t* __restrict__ hub_cur, int4* __restrict__ in_rec,
-                                                              DevStats* stats) {
+                                                              unsigned long long* __restrict__ cur,
+                                                              int4* __restrict__ in_rec, DevStats* stats) {
     __shared__ uint32_t lcnt[SCAT_TOP];
     __shared__ int64_t gbase[SCAT_TOP];
     const int32_t R = n - (int32_t)stats->hub_count;
@@ -445,6 +445,7 @@ __global__ void __launch_bounds__(SCAT_THREADS) k_hub_scatter(int32_t n, int32_t
     const int32_t H0 = n - hub_cap;  // rank of hub slot 0
     if (!scatter_by_tiles(hub_start, hub_cap, rowstart, c0)) return;
     const int64_t mend = rowstart[c0];
+    const int64_t total = hub_start[hub_cap];
     for (int64_t t0 = (int64_t)blockIdx.x * SCAT_TILE; t0 < mend; t0 += (int64_t)gridDim.x * SCAT_TILE) {
         for (int h = threadIdx.x; h < top; h += SCAT_THREADS) lcnt[h] = 0;
         __syncthreads();
@@ -473,9 +474,8 @@ __global__ void __launch_bounds__(SCAT_THREADS) k_hub_scatter(int32_t n, int32_t
             if (x[e] >= T0) {
                 loc[e] = atomicAdd(&lcnt[x[e] - T0], 1u);
             } else if (x[e] >= R) {
-                const int i = x[e] - H0;
-                const int64_t slot = hub_start[i] + atomicAdd(&hub_cur[i], 1u);
-                if (slot < hub_start[i + 1])  // counts and entries disagree only on a bug: never write outside
+                const int64_t slot = (int64_t)atomicAdd(&cur[x[e] - H0], 1ull);
+                if (slot < total)  // counts and entries disagree only on a bug: never write outside
                     in_rec[slot] = make_int4(u[e], (int32_t)(p + 1), end[e], 0);
                 else
                     atomicOr(&stats->err, ERR_OVERFLOW);
@@ -484,25 +484,30 @@ __global__ void __launch_bounds__(SCAT_THREADS) k_hub_scatter(int32_t n, int32_t
         __syncthreads();
         for (int h = threadIdx.x; h < top; h += SCAT_THREADS) {
             const uint32_t c = lcnt[h];
-            if (c) {
-                const int i = T0 + h - H0;
-                gbase[h] = hub_start[i] + atomicAdd(&hub_cur[i], c);
-            }
+            if (c) gbase[h] = (int64_t)atomicAdd(&cur[T0 + h - H0], (unsigned long long)c);
         }
         __syncthreads();
 #pragma unroll
         for (int e = 0; e < SCAT_ITEMS; ++e) {
             if (x[e] < T0) continue;
             const int64_t p = t0 + ((int64_t)(e >> 2) * SCAT_THREADS + threadIdx.x) * 4 + (e & 3);
-            const int i = x[e] - H0;
             const int64_t slot = gbase[x[e] - T0] + loc[e];
-            if (slot < hub_start[i + 1])
+            if (slot < total)
                 in_rec[slot] = make_int4(u[e], (int32_t)(p + 1), end[e], 0);
             else
                 atomicOr(&stats->err, ERR_OVERFLOW);
         }
         __syncthreads();  // lcnt and gbase are reused by the next tile
     }
+}
+
+// After the scatter every hub's cursor must stand at the start of the next segment:
+// a count and a scatter that disagree are reported instead of trusted.
+__global__ void k_hub_cur_check(int32_t hub_cap, const int64_t* __restrict__ hub_start,
+                                const unsigned long long* __restrict__ cur, DevStats* stats) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < hub_cap; i += stride)
+        if (cur[i] != (unsigned long long)hub_start[i + 1]) atomicOr(&stats->err, ERR_OVERFLOW);
 }
 
 // The same records when hub entries are a small share of the entries (flat degree
@@ -512,11 +517,12 @@ __global__ void __launch_bounds__(SCAT_THREADS) k_hub_scatter(int32_t n, int32_t
 // hub in a step reserve their slots with one atomic.
 __global__ void k_hub_scatter_rows(int32_t n, int32_t hub_cap, const int64_t* __restrict__ rowstart,
                                    const int32_t* __restrict__ rowlen, const int32_t* __restrict__ col,
-                                   const int64_t* __restrict__ hub_start, uint32_t* __restrict__ hub_cur,
+                                   const int64_t* __restrict__ hub_start, unsigned long long* __restrict__ cur,
                                    int4* __restrict__ in_rec, DevStats* stats) {
     const int32_t R = n - (int32_t)stats->hub_count;
     const int32_t c0 = n - (int32_t)stats->core_n;  // rows of the dense core are counted there
     if (scatter_by_tiles(hub_start, hub_cap, rowstart, c0)) return;
+    const int64_t total = hub_start[hub_cap];
     const int lane = lane_id();
     const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
     for (int64_t w0 = (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 32; w0 < c0; w0 += warps * 32) {
@@ -542,15 +548,14 @@ __global__ void k_hub_scatter_rows(int32_t n, int32_t hub_cap, const int64_t* __
                 peers[j] = __match_any_sync(FULL, active && step + j < 16 ? x[j] : -1 - lane);
                 slot0[j] = 0;
                 if (active && lane == __ffs(peers[j]) - 1)
-                    slot0[j] = (int64_t)atomicAdd(&hub_cur[x[j] - (n - hub_cap)], (unsigned)__popc(peers[j]));
+                    slot0[j] = (int64_t)atomicAdd(&cur[x[j] - (n - hub_cap)], (unsigned long long)__popc(peers[j]));
             }
 #pragma unroll
             for (int j = 0; j < SCAT_STEPS; ++j) {
                 slot0[j] = __shfl_sync(FULL, slot0[j], __ffs(peers[j]) - 1);
                 if (x[j] >= R) {
-                    const int i = x[j] - (n - hub_cap);
-                    const int64_t slot = hub_start[i] + slot0[j] + __popc(peers[j] & lanemask_lt());
-                    if (slot < hub_start[i + 1])  // counts and entries disagree only on a bug: never write outside
+                    const int64_t slot = slot0[j] + __popc(peers[j] & lanemask_lt());
+                    if (slot < total)  // counts and entries disagree only on a bug: never write outside
                         in_rec[slot] = make_int4((int32_t)u, (int32_t)(base + p - j + 1), (int32_t)(base + du), 0);
                     else
                         atomicOr(&stats->err, ERR_OVERFLOW);
@@ -1545,15 +1550,20 @@ void launch_plan(const CountBuffers& C, const Strategy& S, const Launch& L) {
                                                                                   C.core_cnt, C.hub_cnt, C.stats);
         count_launch();
         scan_u32_to_i64(C.hub_cnt, C.hub_start, C.hub_cap, C.tmp, L);
-        cudaMemsetAsync(C.hub_cur, 0, sizeof(uint32_t) * (size_t)C.hub_cap, L.stream);
+        // 64-bit cursors starting at every hub's first slot
+        cudaMemcpyAsync(C.hub_cur64, C.hub_start, sizeof(int64_t) * (size_t)C.hub_cap, cudaMemcpyDeviceToDevice,
+                        L.stream);
         k_row_of<<<grid_for((int64_t)C.n, THREADS, L.sms), THREADS, 0, L.stream>>>(C.n, C.hub_cap, C.rowstart,
                                                                                   C.hub_start, C.rowof, C.stats);
         count_launch();
         k_hub_scatter_rows<<<grid_for(C.n, THREADS, L.sms), THREADS, 0, L.stream>>>(
-            C.n, C.hub_cap, C.rowstart, C.rowlen, C.col, C.hub_start, C.hub_cur, C.in_rec, C.stats);
+            C.n, C.hub_cap, C.rowstart, C.rowlen, C.col, C.hub_start, C.hub_cur64, C.in_rec, C.stats);
         count_launch();
         k_hub_scatter<<<grid_for((int64_t)C.m_cap / SCAT_ITEMS + 1, SCAT_THREADS, L.sms), SCAT_THREADS, 0, L.stream>>>(
-            C.n, C.hub_cap, C.rowstart, C.rowinfo, C.col, C.rowof, C.hub_start, C.hub_cur, C.in_rec, C.stats);
+            C.n, C.hub_cap, C.rowstart, C.rowinfo, C.col, C.rowof, C.hub_start, C.hub_cur64, C.in_rec, C.stats);
+        count_launch();
+        k_hub_cur_check<<<grid_for(C.hub_cap, THREADS, L.sms), THREADS, 0, L.stream>>>(C.hub_cap, C.hub_start,
+                                                                                      C.hub_cur64, C.stats);
         count_launch();
         // hub_cur is free again: it holds the big flags, hub_cnt (still the in-degrees
         // until here) is overwritten by their exclusive scan
