@@ -44,6 +44,7 @@ constexpr int THREADS = 256;
 constexpr int SMALL_WARPS = 8;         // warps per block in the small-bucket kernel
 constexpr int SMALL_BLOCKS = 8;        // its resident blocks per SM (the grid is one wave of them)
 constexpr int SMALL_WIDE_MAX = 256;    // longest N+(u) the warp-per-source kernel stages
+constexpr int HASH_CUT = 64;           // rows longer than this are cut at max N+(u) by the hash kernel
 constexpr int CTA_THREADS = 256;       // block push kernel
 constexpr int CTA_WARPS = CTA_THREADS / 32;
 constexpr int CTA_LIST_MAX = 2048;     // staged list capacity of the block push kernel
@@ -58,7 +59,7 @@ constexpr int HUB_HASH_LOAD = 2;       // its hash table has at least this many 
 constexpr int HUB_HASH_MAX = HUB_HASH_LOAD * HUB_WARP_MAX;
 constexpr int SCAT_STEPS = 4;          // lockstep steps of the row-walk scatter in flight together
 constexpr int HUB_BATCH = 32;          // in-edges per batch of a big hub
-constexpr int HUB_LONG = 32;           // suffixes at least this long are read by lane groups
+constexpr int HUB_LONG = 16;           // suffixes at least this long are read by lane groups
 constexpr int HUB_GROUPS = 4;          // long suffixes one warp reads at a time
 constexpr int HUB_GLANES = 32 / HUB_GROUPS;
 constexpr int HUB_UNROLL = 8;          // entries a lane reads per round of a long suffix
@@ -875,36 +876,47 @@ __global__ void __launch_bounds__(SMALL_WARPS * 32) k_tc_small_hash(int32_t n, c
         uint32_t cu = 0;
         for (int e0 = 0; e0 < ne; e0 += G) {
             const bool has = e0 + g < ne;
-            int32_t v = has ? col[base + e0 + g] : 0;
-            int2 rv = has ? rowinfo[v] : make_int2(0, 0);
-            int jv = e0 + g;  // position of v in N+(u)
-            // the edges with a non-empty row first: lane i holds the i-th of them
-            const unsigned nz = gballot(has && rv.y > 0);
-            const int cz = __popc(nz);
-            if (cz == 0) continue;
-            {
-                const int src = g < cz ? (int)__fns(nz, 0, g + 1) : g;
-                v = __shfl_sync(gmask, v, src, G);
-                jv = __shfl_sync(gmask, jv, src, G);
-                rv.x = __shfl_sync(gmask, rv.x, src, G);
-                rv.y = __shfl_sync(gmask, rv.y, src, G);
-                if (g >= cz) rv.y = 0;
-            }
-            int incl = rv.y;
+            const int32_t v0 = has ? col[base + e0 + g] : 0;
+            const int2 r0 = has ? rowinfo[v0] : make_int2(0, 0);
+            // only entries up to max N+(u) can match: long rows are cut there; an edge
+            // whose cut row is longer than the suffix a of N+(u) after v by more than
+            // Eq. 3 allows (factor 8: one lane's dependent search steps cost more than the
+            // group's parallel probes) is left to its own lane, which searches the a keys
+            // in the row (a log b instead of b probes)
+            int b0 = r0.y;
+            if (b0 > HASH_CUT) b0 = lower_bound(col + r0.x, 0, b0, maxu + 1);
+            const int a0 = du - (e0 + g) - 1;
+            const bool live = has && b0 > 0;
+            const bool srch0 = live && a0 > 0 && b0 > a0 && !eq3_prefers_merge(a0, b0, 8.0f);
+            // lanes reordered: the streamed edges first (ce of them), then the searching
+            // ones (cq), then nothing
+            const unsigned sm = gballot(live && !srch0);
+            const unsigned qm = gballot(srch0);
+            const int ce_n = __popc(sm), cq = __popc(qm);
+            if (ce_n + cq == 0) continue;
+            const int src = g < ce_n ? (int)__fns(sm, 0, g + 1) : (g < ce_n + cq ? (int)__fns(qm, 0, g - ce_n + 1) : g);
+            const int32_t v = __shfl_sync(gmask, v0, src, G);
+            const int jv = e0 + src;  // position of v in N+(u)
+            const int rs = __shfl_sync(gmask, r0.x, src, G);
+            int b = __shfl_sync(gmask, b0, src, G);
+            if (g >= ce_n + cq) b = 0;
+            const bool search = g >= ce_n && g < ce_n + cq;
+            const int streamed = g < ce_n ? b : 0;
+            int incl = streamed;
 #pragma unroll
             for (int o = 1; o < G; o <<= 1) {
                 const int y = __shfl_up_sync(gmask, incl, o, G);
                 if (g >= o) incl += y;
             }
             const int total = __shfl_sync(gmask, incl, G - 1, G);
-            const int excl = incl - rv.y;
+            const int excl = incl - streamed;
             for (int r = 0; r < total; r += G) {
-                // the edge of entry r + g: i0 holds entry r, and every later edge that
-                // starts inside the round marks its first entry in mk
-                const int i0 = __popc(gballot(g < cz && incl <= r));
-                const unsigned mk = __reduce_or_sync(gmask, (g > i0 && g < cz && excl - r < G) ? (1u << (excl - r)) : 0u);
+                // the edge of entry r + g: i0 holds entry r, and every later streamed
+                // edge that starts inside the round marks its first entry in mk
+                const int i0 = __popc(gballot(g < ce_n && incl <= r));
+                const unsigned mk = __reduce_or_sync(gmask, (g > i0 && g < ce_n && excl - r < G) ? (1u << (excl - r)) : 0u);
                 const int idx = min(i0 + __popc(mk & (below | (1u << g))), G - 1);
-                const int bs = __shfl_sync(gmask, rv.x, idx, G);
+                const int bs = __shfl_sync(gmask, rs, idx, G);
                 const int bx = __shfl_sync(gmask, excl, idx, G);
                 const int k = r + g;
                 if (k < total) {
@@ -920,10 +932,25 @@ __global__ void __launch_bounds__(SMALL_WARPS * 32) k_tc_small_hash(int32_t n, c
                     }
                 }
             }
+            uint32_t cs = 0;  // a searching lane: the suffix keys after v looked up in N+(v)
+            if (search) {
+                const int32_t* B = col + rs;
+                int lo = 0;
+                for (int i = jv + 1; i < du && lo < b; ++i) {
+                    const int32_t y = col[base + i];
+                    const int p = lower_bound(B, lo, b, y);
+                    lo = p;
+                    if (p < b && B[p] == y) {
+                        atomicAdd(&hcnt[P(y)], 1u);
+                        if (sup) atomicAdd(&sup[rs + p], 1u);  // edge (v, y)
+                        ++cs;
+                    }
+                }
+            }
             __syncwarp(gmask);
-            const uint32_t ce = ecnt[g];
+            const uint32_t ce = ecnt[g] + cs;
             ecnt[g] = 0;
-            if (g < cz && ce) {
+            if (ce) {
                 atomicAdd(&t[v], (unsigned long long)ce);
                 if (sup) atomicAdd(&sup[base + jv], ce);  // edge (u, v)
                 cu += ce;
