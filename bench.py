@@ -38,6 +38,7 @@ DEVSTATS_BYTES = 96  # sizeof(DevStats): the library reads it back after the bui
 FALLBACK_HBM_GBS = 6800.0
 WORKLOAD_TEXT = {
     "rmat20": "R-MAT scale 20, edge factor 16, (a,b,c,d)=(0.57,0.19,0.19,0.05), seed 2",
+    "rmat22": "R-MAT scale 22, edge factor 8, (a,b,c,d)=(0.57,0.19,0.19,0.05), seed 3 (profiling case)",
     "rmat23": "R-MAT scale 23, edge factor 8, (a,b,c,d)=(0.57,0.19,0.19,0.05), seed 3",
     "er23": "Erdos-Renyi G(8388608, 60000000), seed 3 stream 1",
     "er4096": "Erdos-Renyi G(4096, 32768), seed 1",
@@ -329,9 +330,13 @@ def run_ours(args, rank, world, local):
     # dominant intersection kernel and its roofline (algorithmic bytes per oriented
     # edge: 4 (d+u + d+v) adjacency bytes + 8 edge bytes + 16 offset bytes)
     phase = {k: statistics.mean(t[k] for t in timings) for k in timings[0]}
-    # each bucket phase, timed by events around its launches: small = three group
-    # widths, hub = the dense-core count followed by the hub kernel
-    kernels = {"k_tc_small<8>+k_tc_small<16>+k_tc_small<32>": ("small_ms", "small"), "k_tc_cta": ("cta_ms", "cta"),
+    # each bucket phase, timed by events around its launches: small = the lane-per-edge
+    # kernels for sources of at most 16 entries and the hash kernels for longer ones
+    # (the default strategy), hub = the dense-core count followed by the hub kernel
+    small_name = ("k_tc_small<8>+k_tc_small<16>+k_tc_small_hash<32,64>+k_tc_small_hash<32,512>"
+                  if not args.strategy or "small:" not in args.strategy
+                  else "k_tc_small<8>+k_tc_small<16>+k_tc_small<32>+k_tc_small_wide")
+    kernels = {small_name: ("small_ms", "small"), "k_tc_cta": ("cta_ms", "cta"),
                "k_core_count+k_tc_hub": ("hub_ms", "hub")}
     name = max(kernels, key=lambda k: phase[kernels[k][0]])
     kms = phase[kernels[name][0]]

@@ -148,6 +148,9 @@ WORKLOADS = {
     "er4096": Workload("er4096", "er", 4096, 32768, 1, 0),
     # R-MAT scale 20, edge factor 16, seed 2.
     "rmat20": Workload("rmat20", "rmat", 1 << 20, 16 << 20, 2, 0, scale=20),
+    # R-MAT scale 22, edge factor 8, seed 3: the profiling case (its oriented rows just
+    # exceed the 129 MB L2, the whole graph takes about 2 GB of device memory).
+    "rmat22": Workload("rmat22", "rmat", 1 << 22, 8 << 22, 3, 0, scale=22),
     # R-MAT scale 23, edge factor 8, seed 3.
     "rmat23": Workload("rmat23", "rmat", 1 << 23, 8 << 23, 3, 0, scale=23),
     # Uniform G(8,388,608, 60,000,000) of the same size, seed 3, stream 1.
