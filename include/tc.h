@@ -101,6 +101,42 @@ tc_status tc_count(tc_graph* g, uint64_t* T_out);
 tc_status lcc_compute(tc_graph* g, uint64_t* t_out, double* lcc_out, int mem_kind);
 
 /*
+ * One shard of the count, for a graph replicated on several GPUs (one process per
+ * GPU).
+ * The shards partition the triangles. Each triangle is counted once, from its
+ * lowest-ranked vertex u, the source of the oriented edges (Alg. 2 on the
+ * degree-oriented graph, Sec. III).
+ * Shard `shard` of `nshards` counts the triangles whose u lies in one range of
+ * ranks. The ranges are cut where the prefix of the per-source cost
+ * d+(u) (d+(u) + 1) / 2 + 1 crosses equal shares of the total. This balances work
+ * rather than vertices, unlike the paper's 1D partition, whose imbalance Sec. V
+ * reports.
+ *   shard, nshards  0 <= shard < nshards; nshards = 1 counts the whole graph
+ *   t_out           NULL, or n uint64: this shard's share of t(v) in the caller's
+ *                   vertex ids. Summed over all shards it equals t(v).
+ *   mem_kind        where t_out lives (as lcc_compute)
+ *   T_out           NULL, or the host scalar that receives this shard's triangles.
+ *                   Summed over all shards it equals T.
+ * The graph is not changed: a later tc_count or lcc_compute counts the whole graph
+ * again. Synchronises the graph's stream to read the shard's bounds.
+ * Errors: TC_EINVAL (NULL graph, shard out of range, bad mem_kind), TC_ENOMEM,
+ * TC_ECUDA, TC_EINTERNAL.
+ */
+tc_status tc_count_shard(tc_graph* g, int32_t shard, int32_t nshards, uint64_t* t_out, int mem_kind,
+                         uint64_t* T_out);
+
+/*
+ * LCC[n] (fp64, Eq. 2) in the caller's vertex ids, from per-vertex counts t[n]
+ * (uint64, caller's ids). t is typically the sum of the shards' t_out of
+ * tc_count_shard.
+ * The arithmetic is the same as lcc_compute's: LCC(v) = 2 t(v) / (d(v) (d(v) - 1)),
+ * one correctly rounded division, and +0.0 for d(v) < 2 or t(v) = 0.
+ * t and lcc_out both live where mem_kind says.
+ * Errors: TC_EINVAL (NULL, bad mem_kind), TC_ENOMEM, TC_ECUDA.
+ */
+tc_status tc_lcc_from_counts(tc_graph* g, const uint64_t* t, double* lcc_out, int mem_kind);
+
+/*
  * Per-vertex triangle counts by the paper's unoriented per-vertex formula (Alg. 3
  * with the Sec. II-C offset): t(v_i) = sum over v_j in adj(v_i) of
  * |adj(v_i) ∩ {v_k in adj(v_j) : k > j}|, each intersection chosen per pair by Eq. 3

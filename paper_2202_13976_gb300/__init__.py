@@ -33,7 +33,8 @@ EXPORTS = ["tc_graph_create_from_edges", "tc_graph_create_from_csr", "tc_count",
            "tc_graph_set_tuning", "tc_graph_autotune", "tc_batch_run", "tc_release_cached_graphs",
            "tc_generate_edges", "tc_server_start", "tc_server_submit", "tc_server_poll", "tc_server_wait",
            "tc_server_get_stats", "tc_server_stop", "tc_graph_build_timing", "tc_count_vertex_formula",
-           "tc_edge_support", "tc_directed_lcc", "tc_remote_cache", "tc_request_run"]
+           "tc_edge_support", "tc_directed_lcc", "tc_remote_cache", "tc_request_run", "tc_count_shard",
+           "tc_lcc_from_counts"]
 BUILD_PHASES = ["ingest_ms", "rank_ms", "count_ms", "fill_ms", "sort_ms", "degree_ms", "total_ms"]
 TC_GEN_RMAT, TC_GEN_ER_REPLACE = 0, 1
 GEN_KINDS = {"rmat": TC_GEN_RMAT, "er_replace": TC_GEN_ER_REPLACE}
@@ -137,6 +138,10 @@ def load(path: str | None = None):
     lib.tc_count.argtypes = [P, ctypes.POINTER(u64)]
     lib.lcc_compute.restype = st
     lib.lcc_compute.argtypes = [P, P, P, ctypes.c_int]
+    lib.tc_count_shard.restype = st
+    lib.tc_count_shard.argtypes = [P, i32, i32, P, ctypes.c_int, ctypes.POINTER(u64)]
+    lib.tc_lcc_from_counts.restype = st
+    lib.tc_lcc_from_counts.argtypes = [P, P, P, ctypes.c_int]
     lib.tc_count_vertex_formula.restype = st
     lib.tc_count_vertex_formula.argtypes = [P, P, ctypes.c_int, ctypes.POINTER(u64)]
     lib.tc_edge_support.restype = st
@@ -295,6 +300,32 @@ def lcc_compute(g: int, t_out=None, lcc_out=None):
         _check_room(lcc_out, n, "lcc_out")
     (pt, pl), kind = _ptr_kind(t_out, lcc_out)
     _check(_lib.lcc_compute(g, pt, pl, kind))
+
+
+def tc_count_shard(g: int, shard: int, nshards: int, t_out=None):
+    """Triangles of one shard of the sources (cost-balanced rank ranges) and, when
+    t_out (uint64[n] as int64, host numpy or CUDA tensor) is given, the shard's share
+    of t(v); returns (T_shard, t_out).  The shares of all shards sum to t(v) and T."""
+    if t_out is not None:
+        _check_dtype(t_out, "int64")
+        n, _ = tc_graph_size(g)
+        _check_room(t_out, n, "t_out")
+    (pt,), kind = _ptr_kind(t_out)
+    T = ctypes.c_uint64()
+    _check(_lib.tc_count_shard(g, shard, nshards, pt, kind, ctypes.byref(T)))
+    return int(T.value), t_out
+
+
+def tc_lcc_from_counts(g: int, t, lcc_out):
+    """LCC (Eq. 2) into lcc_out (float64[n]) from per-vertex counts t (uint64[n] as
+    int64 or uint64), both on the host or both CUDA tensors."""
+    _check_dtype(t, "int64")
+    _check_dtype(lcc_out, "float64")
+    n, _ = tc_graph_size(g)
+    _check_room(t, n, "t")
+    _check_room(lcc_out, n, "lcc_out")
+    (pt, pl), kind = _ptr_kind(t, lcc_out)
+    _check(_lib.tc_lcc_from_counts(g, pt, pl, kind))
 
 
 def tc_count_vertex_formula(g: int, t_out=None):
@@ -623,6 +654,19 @@ class Graph:
             lcc_out = np.empty(self.n, dtype=np.float64)
         lcc_compute(self.handle, t_out, lcc_out)
         return t_out, lcc_out
+
+    def count_shard(self, shard: int, nshards: int, t_out=None):
+        """(T_shard, t_share) of one shard; a host uint64 array when t_out is None."""
+        if t_out is None:
+            t_out = np.empty(self.n, dtype=np.uint64)
+        return tc_count_shard(self.handle, shard, nshards, t_out)
+
+    def lcc_from_counts(self, t, lcc_out=None):
+        """LCC from summed per-vertex counts; a host float64 array when lcc_out is None."""
+        if lcc_out is None:
+            lcc_out = np.empty(self.n, dtype=np.float64)
+        tc_lcc_from_counts(self.handle, t, lcc_out)
+        return lcc_out
 
     def vertex_formula(self, t_out=None):
         """(T, t) by the paper's unoriented per-vertex formula (for comparison)."""

@@ -114,6 +114,7 @@ struct tc_graph {
     int4* in_rec = nullptr;
     int32_t* rowof = nullptr;
     void* plan_tmp = nullptr;
+    int32_t src_lo = 0, src_hi = -1;  // ranks of the sources counted (-1: up to n); tc_count_shard
     int32_t core_cap = 0;
     int32_t core_words = 0;
     uint32_t* core_bits = nullptr;  // adjacency rows, core in-degrees
@@ -404,6 +405,8 @@ CountBuffers count_buffers(tc_graph* g) {
     C.core_hiout = g->core_lohi + 2 * (size_t)g->core_cap;
     C.t_rank = g->t_rank;
     C.stats = g->stats;
+    C.src_lo = g->src_lo;
+    C.src_hi = g->src_hi < 0 ? g->n : g->src_hi;
     return C;
 }
 
@@ -624,6 +627,103 @@ tc_status lcc_compute(tc_graph* g, uint64_t* t_out, double* lcc_out, int mem_kin
     free_list(g, &tmp);
     if (e == cudaSuccess) e = cudaStreamSynchronize(g->stream);
     if (e != cudaSuccess) return cuda_fail("lcc_compute copy", e);
+    return TC_OK;
+}
+
+// Counts one shard, then restores the whole source range on every path out (the
+// next count plans again).
+struct ShardRange {
+    tc_graph* g;
+    ShardRange(tc_graph* g_, int32_t lo, int32_t hi) : g(g_) { set(lo, hi); }
+    ~ShardRange() { set(0, -1); }
+    void set(int32_t lo, int32_t hi) {
+        g->src_lo = lo;
+        g->src_hi = hi;
+        g->planned = false;
+        g->counted = false;
+    }
+};
+
+tc_status tc_count_shard(tc_graph* g, int32_t shard, int32_t nshards, uint64_t* t_out, int mem_kind,
+                         uint64_t* T_out) {
+    if (!g || nshards < 1 || shard < 0 || shard >= nshards) return TC_EINVAL;
+    if (t_out && mem_kind != TC_MEM_HOST && mem_kind != TC_MEM_DEVICE) return TC_EINVAL;
+    const int32_t n = g->n;
+    int32_t hb[2] = {0, n};
+    if (nshards > 1 && n > 0) {
+        std::vector<void*> tmp;
+        uint32_t* cost = nullptr;
+        int64_t* prefix = nullptr;
+        int32_t* bounds = nullptr;
+        char* stmp = nullptr;
+        tc_status st;
+        if ((st = dalloc(g, &cost, (size_t)n, &tmp)) || (st = dalloc(g, &prefix, (size_t)n + 1, &tmp)) ||
+            (st = dalloc(g, &bounds, 2, &tmp)) || (st = dalloc(g, &stmp, scan_tmp_bytes((int64_t)n), &tmp))) {
+            free_list(g, &tmp);
+            return st;
+        }
+        launch_shard_bounds(n, g->rowlen, cost, prefix, stmp, shard, nshards, bounds, g->L);
+        cudaError_t e = cudaMemcpyAsync(hb, bounds, sizeof(hb), cudaMemcpyDeviceToHost, g->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(g->stream);
+        free_list(g, &tmp);
+        if (e != cudaSuccess) return cuda_fail("shard bounds", e);
+        if (hb[0] < 0 || hb[1] < hb[0] || hb[1] > n) return TC_EINTERNAL;
+    }
+    ShardRange range(g, hb[0], hb[1]);
+    tc_status st = run_count(g);
+    if (st != TC_OK) return st;
+    DevStats h;
+    if ((st = read_stats(g, &h)) != TC_OK) return st;
+    if ((h.err & ERR_OVERFLOW) || h.sum_t % 3 != 0) {
+        snprintf(g_last_error, sizeof(g_last_error), "internal count mismatch in a shard");
+        return TC_EINTERNAL;
+    }
+    if (T_out) *T_out = h.sum_t / 3;
+    if (!t_out || n == 0) return TC_OK;
+    if (mem_kind == TC_MEM_DEVICE) {
+        launch_finalize(n, g->rank, g->t_rank, g->deg, reinterpret_cast<unsigned long long*>(t_out), nullptr, g->L);
+        TC_CK(cudaGetLastError());
+        return TC_OK;
+    }
+    std::vector<void*> tmp;
+    unsigned long long* dt = nullptr;
+    if ((st = dalloc(g, &dt, (size_t)n, &tmp))) return st;
+    launch_finalize(n, g->rank, g->t_rank, g->deg, dt, nullptr, g->L);
+    cudaError_t e = cudaMemcpyAsync(t_out, dt, sizeof(uint64_t) * (size_t)n, cudaMemcpyDeviceToHost, g->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(g->stream);
+    free_list(g, &tmp);
+    if (e != cudaSuccess) return cuda_fail("count_shard copy", e);
+    return TC_OK;
+}
+
+tc_status tc_lcc_from_counts(tc_graph* g, const uint64_t* t, double* lcc_out, int mem_kind) {
+    if (!g || !t || !lcc_out || (mem_kind != TC_MEM_HOST && mem_kind != TC_MEM_DEVICE)) return TC_EINVAL;
+    const int32_t n = g->n;
+    if (n == 0) return TC_OK;
+    const unsigned long long* tt = reinterpret_cast<const unsigned long long*>(t);
+    if (mem_kind == TC_MEM_DEVICE) {
+        launch_lcc_from_counts(n, g->rank, g->deg, tt, lcc_out, g->L);
+        TC_CK(cudaGetLastError());
+        return TC_OK;
+    }
+    std::vector<void*> tmp;
+    unsigned long long* dt = nullptr;
+    double* dl = nullptr;
+    tc_status st;
+    if ((st = dalloc(g, &dt, (size_t)n, &tmp)) || (st = dalloc(g, &dl, (size_t)n, &tmp))) {
+        free_list(g, &tmp);
+        return st;
+    }
+    cudaError_t e = cudaMemcpyAsync(dt, t, sizeof(uint64_t) * (size_t)n, cudaMemcpyHostToDevice, g->stream);
+    if (e == cudaSuccess) {
+        launch_lcc_from_counts(n, g->rank, g->deg, dt, dl, g->L);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(lcc_out, dl, sizeof(double) * (size_t)n, cudaMemcpyDeviceToHost, g->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(g->stream);
+    free_list(g, &tmp);
+    if (e != cudaSuccess) return cuda_fail("lcc_from_counts", e);
     return TC_OK;
 }
 

@@ -88,7 +88,8 @@ __global__ void __launch_bounds__(CORE_THREADS) k_core_count(int32_t n, const in
                                                              const int32_t* __restrict__ lo,
                                                              const int32_t* __restrict__ hi,
                                                              const int32_t* __restrict__ hiout,
-                                                             unsigned long long* __restrict__ t, const DevStats* stats) {
+                                                             unsigned long long* __restrict__ t, int32_t src_lo,
+                                                             int32_t src_hi, const DevStats* stats) {
     __shared__ unsigned long long tx_w[CORE_WARPS];
     const int core_n = (int)stats->core_n;
     const int32_t c0 = n - core_n;
@@ -96,7 +97,7 @@ __global__ void __launch_bounds__(CORE_THREADS) k_core_count(int32_t n, const in
     const int first = lane * CORE_LANE_WORDS;
     for (int64_t i = blockIdx.x; i < core_n; i += gridDim.x) {
         const int32_t x = c0 + (int32_t)i;
-        const int d = rowlen[x];
+        const int d = x >= src_lo && x < src_hi ? rowlen[x] : 0;  // sources outside the counted shard: none
         if (d < 2) continue;  // no triangle has x lowest; uniform across the block
         const int64_t base = rowstart[x];
         uint32_t ox[CORE_LANE_WORDS];
@@ -160,7 +161,8 @@ void launch_core_plan(const CountBuffers& C, const Launch& L) {
 void launch_core_count(const CountBuffers& C, const Launch& L) {
     if (C.core_cap <= 0) return;
     k_core_count<<<C.core_cap, CORE_THREADS, 0, L.stream>>>(C.n, C.rowstart, C.rowlen, C.col, C.core_words, C.core_z,
-                                                           C.core_lo, C.core_hi, C.core_hiout, C.t_rank, C.stats);
+                                                           C.core_lo, C.core_hi, C.core_hiout, C.t_rank, C.src_lo,
+                                                           C.src_hi, C.stats);
     count_launch();
 }
 

@@ -169,12 +169,22 @@ struct CountBuffers {
     unsigned long long* t_rank;  // n
     DevStats* stats;
     uint32_t* sup;           // null, or m_cap per-edge supports indexed like col (tc_edge_support)
+    int32_t src_lo, src_hi;  // only triangles whose lowest vertex has a rank in [src_lo, src_hi) are counted
 };
 
 enum { PH_PLAN = 0, PH_SMALL, PH_CTA, PH_HUB, PH_END, PH_EVENTS };
 
 // Builds the bucket lists and the hub in-edge lists.
 void launch_plan(const CountBuffers& C, const Strategy& S, const Launch& L);
+// Shards of the sources (tc_vertex.cu): cost[u] = d+(u) (d+(u) + 1) / 2 + 1 (saturated),
+// then the rank range [bounds[0], bounds[1]) of shard `shard` of `nshards`, cut where
+// the prefix of the cost crosses shard / nshards of the total.  cost needs n entries,
+// prefix n + 1, tmp scan_tmp_bytes(n).
+void launch_shard_bounds(int32_t n, const int32_t* rowlen, uint32_t* cost, int64_t* prefix, void* tmp, int32_t shard,
+                         int32_t nshards, int32_t* bounds, const Launch& L);
+// LCC (Eq. 2) of every vertex id from per-id triangle counts t (the sum of the shards').
+void launch_lcc_from_counts(int32_t n, const int32_t* rank, const int32_t* deg, const unsigned long long* t,
+                            double* lcc_out, const Launch& L);
 // Dense core (tc_core.cu): bit matrices after the hub count is known, and the count.
 int core_words_for(int32_t core_cap);
 void launch_core_plan(const CountBuffers& C, const Launch& L);

@@ -436,7 +436,8 @@ __global__ void __launch_bounds__(SCAT_THREADS) k_hub_scatter(int32_t n, int32_t
                                                               const int32_t* __restrict__ rowof,
                                                               const int64_t* __restrict__ hub_start,
                                                               unsigned long long* __restrict__ cur,
-                                                              int4* __restrict__ in_rec, DevStats* stats) {
+                                                              int4* __restrict__ in_rec, int32_t src_lo,
+                                                              int32_t src_hi, DevStats* stats) {
     __shared__ uint32_t lcnt[SCAT_TOP];
     __shared__ int64_t gbase[SCAT_TOP];
     const int32_t R = n - (int32_t)stats->hub_count;
@@ -471,6 +472,8 @@ __global__ void __launch_bounds__(SCAT_THREADS) k_hub_scatter(int32_t n, int32_t
                 const int2 ri = rowinfo[u[e]];
                 end[e] = ri.x + ri.y;
                 if (p >= end[e]) x[e] = -1;  // a slot freed by deduplication
+                // a source outside the counted shard keeps its slot with an empty suffix
+                if (u[e] < src_lo || u[e] >= src_hi) end[e] = (int32_t)(p + 1);
             }
             if (x[e] >= T0) {
                 loc[e] = atomicAdd(&lcnt[x[e] - T0], 1u);
@@ -519,7 +522,8 @@ __global__ void k_hub_cur_check(int32_t hub_cap, const int64_t* __restrict__ hub
 __global__ void k_hub_scatter_rows(int32_t n, int32_t hub_cap, const int64_t* __restrict__ rowstart,
                                    const int32_t* __restrict__ rowlen, const int32_t* __restrict__ col,
                                    const int64_t* __restrict__ hub_start, unsigned long long* __restrict__ cur,
-                                   int4* __restrict__ in_rec, DevStats* stats) {
+                                   int4* __restrict__ in_rec, int32_t src_lo, int32_t src_hi,
+                                   DevStats* stats) {
     const int32_t R = n - (int32_t)stats->hub_count;
     const int32_t c0 = n - (int32_t)stats->core_n;  // rows of the dense core are counted there
     if (scatter_by_tiles(hub_start, hub_cap, rowstart, c0)) return;
@@ -530,6 +534,7 @@ __global__ void k_hub_scatter_rows(int32_t n, int32_t hub_cap, const int64_t* __
         const int64_t u = w0 + lane;
         const int du = u < c0 ? rowlen[u] : 0;
         const int64_t base = u < n ? rowstart[u] : 0;
+        const bool inshard = u >= src_lo && u < src_hi;  // else its records get empty suffixes
         int p = du - 1;
         // SCAT_STEPS steps at a time: their loads, then their slot reservations, are
         // independent and in flight together.  Walking backwards, the hub entries of a
@@ -557,7 +562,8 @@ __global__ void k_hub_scatter_rows(int32_t n, int32_t hub_cap, const int64_t* __
                 if (x[j] >= R) {
                     const int64_t slot = slot0[j] + __popc(peers[j] & lanemask_lt());
                     if (slot < total)  // counts and entries disagree only on a bug: never write outside
-                        in_rec[slot] = make_int4((int32_t)u, (int32_t)(base + p - j + 1), (int32_t)(base + du), 0);
+                        in_rec[slot] = make_int4((int32_t)u, (int32_t)(base + p - j + 1),
+                                                 inshard ? (int32_t)(base + du) : (int32_t)(base + p - j + 1), 0);
                     else
                         atomicOr(&stats->err, ERR_OVERFLOW);
                 }
@@ -606,7 +612,8 @@ __global__ void __launch_bounds__(THREADS) k_plan(int32_t n, const int64_t* __re
                                                   const int32_t* __restrict__ rowlen, const int32_t* __restrict__ col,
                                                   int32_t* __restrict__ l8, int32_t* __restrict__ l16,
                                                   int32_t* __restrict__ l32, int32_t* __restrict__ l256,
-                                                  int32_t* __restrict__ lcta, DevStats* stats) {
+                                                  int32_t* __restrict__ lcta, int32_t src_lo, int32_t src_hi,
+                                                  DevStats* stats) {
     __shared__ unsigned bcount[PLAN_LISTS];
     __shared__ unsigned bbase[PLAN_LISTS];
     const int32_t R = n - (int32_t)stats->hub_count;
@@ -623,7 +630,7 @@ __global__ void __launch_bounds__(THREADS) k_plan(int32_t n, const int64_t* __re
 #pragma unroll
         for (int k = 0; k < PLAN_ITEMS; ++k) {
             const int64_t u = t0 + (int64_t)k * THREADS + threadIdx.x;
-            int d = u < n ? rowlen[u] : 0;
+            int d = u < n && u >= src_lo && u < src_hi ? rowlen[u] : 0;  // sources outside the shard: none
             if (d >= 2 && col[rowstart[u]] >= R) d = 0;  // every target is a hub
             cls[k] = d < 2 ? -1 : d <= 8 ? 0 : d <= 16 ? 1 : d <= 32 ? 2 : d <= SMALL_WIDE_MAX ? 3 : 4;
 #pragma unroll
@@ -1584,10 +1591,12 @@ void launch_plan(const CountBuffers& C, const Strategy& S, const Launch& L) {
                                                                                   C.hub_start, C.rowof, C.stats);
         count_launch();
         k_hub_scatter_rows<<<grid_for(C.n, THREADS, L.sms), THREADS, 0, L.stream>>>(
-            C.n, C.hub_cap, C.rowstart, C.rowlen, C.col, C.hub_start, C.hub_cur64, C.in_rec, C.stats);
+            C.n, C.hub_cap, C.rowstart, C.rowlen, C.col, C.hub_start, C.hub_cur64, C.in_rec, C.src_lo, C.src_hi,
+            C.stats);
         count_launch();
         k_hub_scatter<<<grid_for((int64_t)C.m_cap / SCAT_ITEMS + 1, SCAT_THREADS, L.sms), SCAT_THREADS, 0, L.stream>>>(
-            C.n, C.hub_cap, C.rowstart, C.rowinfo, C.col, C.rowof, C.hub_start, C.hub_cur64, C.in_rec, C.stats);
+            C.n, C.hub_cap, C.rowstart, C.rowinfo, C.col, C.rowof, C.hub_start, C.hub_cur64, C.in_rec, C.src_lo,
+            C.src_hi, C.stats);
         count_launch();
         k_hub_cur_check<<<grid_for(C.hub_cap, THREADS, L.sms), THREADS, 0, L.stream>>>(C.hub_cap, C.hub_start,
                                                                                       C.hub_cur64, C.stats);
@@ -1605,7 +1614,7 @@ void launch_plan(const CountBuffers& C, const Strategy& S, const Launch& L) {
     k_plan<<<grid_for(C.n, THREADS * PLAN_ITEMS, L.sms), THREADS, 0, L.stream>>>(C.n, C.rowstart, C.rowlen, C.col,
                                                                    C.small_list[0], C.small_list[1],
                                                                    C.small_list[2], C.small_list[3], C.cta_list,
-                                                                   C.stats);
+                                                                   C.src_lo, C.src_hi, C.stats);
     count_launch();
 }
 

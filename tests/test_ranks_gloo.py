@@ -5,11 +5,16 @@
    the oriented graph, count their edges independently (the oracle's oriented
    count restricted to a range), and one sum of t[] gives the full result -- the
    only exchange the path needs when it is spread over several GPUs.
+3. The library's exchange step (paper_2202_13976_gb300.dist): every rank checks
+   in through the store before the sum; a rank that left between steps is reported
+   (RankLost, naming it) to the others within the deadline, and none of them enters
+   the collective.  The failure is made on the host: the rank simply exits.
 """
 from __future__ import annotations
 
 import os
 import socket
+import time
 
 import numpy as np
 import pytest
@@ -93,3 +98,75 @@ def test_edge_shards_sum_to_the_full_count():
     out = _run(_shard_worker)
     assert all(ok for _, ok, _ in out)
     assert all(edges > 0 for _, _, edges in out)
+
+
+def _exchange_worker(rank, world, port, q, absent):
+    """All ranks join the group; `absent` (if any) then leaves before the exchange."""
+    import torch
+    import torch.distributed as dist
+
+    from paper_2202_13976_gb300 import dist as tcd
+    store = dist.TCPStore("127.0.0.1", port, world, rank == 0)
+    dist.init_process_group("gloo", store=store, rank=rank, world_size=world)
+    if rank == absent:
+        q.put((rank, "left", None))
+        q.close()
+        q.join_thread()  # the message is out before the process goes
+        os._exit(0)  # gone between steps, with nothing in flight
+    t = torch.arange(5, dtype=torch.int64) * (rank + 1)
+    t0 = time.monotonic()
+    try:
+        tcd.sum_counts(t, store=store, rank=rank, world=world, step=7, timeout_s=2.0)
+        q.put((rank, "sum", t.tolist()))
+    except tcd.RankLost as e:
+        q.put((rank, "lost", (e.missing, e.step, time.monotonic() - t0)))
+    q.close()
+    q.join_thread()
+    if absent is None:
+        dist.destroy_process_group()
+    else:
+        os._exit(0)  # the group has a dead member: leave without a collective teardown
+
+
+def _run_exchange(world, absent):
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_exchange_worker, args=(r, world, port, q, absent)) for r in range(world)]
+    for p in procs:
+        p.start()
+    out = [q.get(timeout=120) for _ in procs]
+    for p in procs:
+        p.join(timeout=60)
+    return sorted(out)
+
+
+def test_exchange_sums_when_every_rank_checks_in():
+    out = _run_exchange(3, None)
+    want = [sum(i * (r + 1) for r in range(3)) for i in range(5)]
+    assert out == [(r, "sum", want) for r in range(3)]
+
+
+def test_a_rank_that_left_is_reported_not_waited_for():
+    out = _run_exchange(3, 2)
+    assert out[2] == (2, "left", None)
+    for rank, kind, info in out[:2]:
+        assert kind == "lost"
+        missing, step, waited = info
+        assert missing == [2] and step == 7
+        assert 1.5 < waited < 30.0  # the deadline, not a hang
+
+
+def test_check_in_needs_a_shared_store():
+    """Single-process checks of the deadline logic on a HashStore."""
+    import torch.distributed as dist
+
+    from paper_2202_13976_gb300 import dist as tcd
+    st = dist.HashStore()
+    st.set("tc/check_in/a/1", b"1")
+    tcd.check_in(st, 0, 2, "a", timeout_s=1.0)  # rank 1 is already there
+    t0 = time.monotonic()
+    with pytest.raises(tcd.RankLost) as e:
+        tcd.check_in(st, 0, 3, "b", timeout_s=0.2)
+    assert e.value.missing == [1, 2]
+    assert time.monotonic() - t0 < 5.0
