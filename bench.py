@@ -385,6 +385,8 @@ def run_ours(args, rank, world, local):
 
     if rank != 0:
         return
+    # the last end-to-end step's outputs against the oracle's digests (outside the timing)
+    golden = golden_check(args.workload, sorted(Ts)[0], t_np, l_np) if len(Ts) == 1 else {"T": False}
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
         cpu, ref = cpu_baseline(w, src_h, dst_h)
@@ -405,6 +407,7 @@ def run_ours(args, rank, world, local):
                    "step_spread": step_spread(step_ms),
                    "plan": plan,
                    "vs_baseline_ref": "Table II, R-MAT S20 EF16, hybrid, 0.425 edges/us, 16-thread Xeon Gold 6154"},
+        "oracle_digests_match": golden,
         "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
         "gpu_launches_per_step": launches / args.steps, "clocks": clk, "impl": "ours",
     }
@@ -427,6 +430,26 @@ def gen_batch(G, seed=4):
     src = np.concatenate([e[0] for e in edges]).astype(np.int32)
     dst = np.concatenate([e[1] for e in edges]).astype(np.int32)
     return n, off, src, dst
+
+
+def golden_check(workload, T, t_host, lcc_host):
+    """The end-to-end step's T, t[] and LCC[] (host arrays in the caller's ids) against
+    the digests of the oracle's results on the same workload (tests/golden/
+    large_workloads.json, written by tests/golden/make_golden.py --large from two
+    oracle formulas); None for a workload without a record."""
+    import hashlib
+
+    import numpy as np
+    try:
+        gold = json.load(open(os.path.join(ROOT, "tests", "golden", "large_workloads.json")))[workload]
+    except Exception:
+        return None
+
+    def digest(a):
+        return hashlib.sha256(np.ascontiguousarray(a).tobytes()).hexdigest()
+
+    return {"T": int(T) == gold["T"], "t": digest(t_host) == gold["t_sha256"],
+            "lcc": digest(lcc_host) == gold["lcc_sha256"]}
 
 
 def batch_oracle_check(G, T_batch, t_out, l_out):

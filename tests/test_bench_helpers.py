@@ -65,3 +65,15 @@ def test_reference_sample_ranges_cover_the_sources_once():
     total = sum(oracle.tc_oriented_ranges(n, op, ap, ranges[k::bench.REF_SAMPLES], threads=2)
                 for k in range(bench.REF_SAMPLES))
     np.testing.assert_array_equal(total, oracle.tc_oriented(n, op, ap))
+
+
+def test_golden_check_reads_the_oracle_digests():
+    import json
+    import os
+
+    import numpy as np
+    gold = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "large_workloads.json")))
+    assert bench.golden_check("er4096", 0, np.zeros(1, np.uint64), np.zeros(1)) is None
+    rec = gold["rmat20"]
+    bad = bench.golden_check("rmat20", rec["T"], np.zeros(rec["n"], np.uint64), np.zeros(rec["n"]))
+    assert bad == {"T": True, "t": False, "lcc": False}
