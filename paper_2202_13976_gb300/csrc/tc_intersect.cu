@@ -475,15 +475,26 @@ __global__ void __launch_bounds__(SCAT_THREADS) k_hub_scatter(int32_t n, int32_t
                 // a source outside the counted shard keeps its slot with an empty suffix
                 if (u[e] < src_lo || u[e] >= src_hi) end[e] = (int32_t)(p + 1);
             }
-            if (x[e] >= T0) {
+        }
+        // the slot reservations of all items first, so that their round trips overlap,
+        // then the records of the hubs below the top ones
+        unsigned long long gslot[SCAT_ITEMS];
+#pragma unroll
+        for (int e = 0; e < SCAT_ITEMS; ++e) {
+            gslot[e] = 0;
+            if (x[e] >= T0)
                 loc[e] = atomicAdd(&lcnt[x[e] - T0], 1u);
-            } else if (x[e] >= R) {
-                const int64_t slot = (int64_t)atomicAdd(&cur[x[e] - H0], 1ull);
-                if (slot < total)  // counts and entries disagree only on a bug: never write outside
-                    in_rec[slot] = make_int4(u[e], (int32_t)(p + 1), end[e], 0);
-                else
-                    atomicOr(&stats->err, ERR_OVERFLOW);
-            }
+            else if (x[e] >= R)
+                gslot[e] = atomicAdd(&cur[x[e] - H0], 1ull);
+        }
+#pragma unroll
+        for (int e = 0; e < SCAT_ITEMS; ++e) {
+            if (x[e] < R || x[e] >= T0) continue;
+            const int64_t p = t0 + ((int64_t)(e >> 2) * SCAT_THREADS + threadIdx.x) * 4 + (e & 3);
+            if ((int64_t)gslot[e] < total)  // counts and entries disagree only on a bug: never write outside
+                in_rec[gslot[e]] = make_int4(u[e], (int32_t)(p + 1), end[e], 0);
+            else
+                atomicOr(&stats->err, ERR_OVERFLOW);
         }
         __syncthreads();
         for (int h = threadIdx.x; h < top; h += SCAT_THREADS) {
