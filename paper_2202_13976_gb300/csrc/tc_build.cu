@@ -64,7 +64,7 @@ __global__ void k_expand_csr(const int64_t* __restrict__ offsets, int32_t n, int
 // looked at); hub vertices occur often enough to take a slot early, so their many
 // increments stay in shared memory and reach dmulti with one atomic per block.
 // Vertices that find no slot add to dmulti directly.
-constexpr int PAIR_UNROLL = 4;  // pairs per thread and round in the pair passes
+constexpr int PAIR_UNROLL = 8;  // pairs per thread and round in the pair passes
 constexpr int DEG_SLOTS = 4096;
 constexpr int DEG_PROBES = 4;
 
@@ -175,14 +175,22 @@ __global__ void k_orient_count(const int32_t* __restrict__ src, const int32_t* _
             u[k] = i < m ? src[i] : 0;
             v[k] = i < m ? dst[i] : 0;
         }
+        // every pair's two rank gathers first, so that they are in flight together
+        int32_t a[PAIR_UNROLL], b[PAIR_UNROLL];
+#pragma unroll
+        for (int k = 0; k < PAIR_UNROLL; ++k) {
+            const bool ok = i0 + k * stride < m && u[k] != v[k] && (uint32_t)u[k] < (uint32_t)n &&
+                            (uint32_t)v[k] < (uint32_t)n;
+            a[k] = ok ? rank[u[k]] : -1;
+            b[k] = ok ? rank[v[k]] : -1;
+        }
 #pragma unroll
         for (int k = 0; k < PAIR_UNROLL; ++k) {
             const int64_t i = i0 + k * stride;
             if (i >= m) break;
             int2 o = make_int2(-1, -1);
-            if (u[k] != v[k] && (uint32_t)u[k] < (uint32_t)n && (uint32_t)v[k] < (uint32_t)n) {
-                const int32_t a = rank[u[k]], b = rank[v[k]];
-                o = make_int2(min(a, b), max(a, b));
+            if (a[k] >= 0) {
+                o = make_int2(min(a[k], b[k]), max(a[k], b[k]));
                 atomicAdd(&rowcnt[o.x], 1u);
             }
             oriented[i] = o;
