@@ -135,6 +135,10 @@ struct tc_graph {
     int32_t* batch_vbase = nullptr;   // device, G + 1
     int* batch_err = nullptr;         // device flag of the relabel and the per-graph reduction
     bool capture = false;             // work is being recorded into a CUDA graph: no events
+    // the planner's second stream (single graphs only): hub lists and dense core
+    cudaStream_t side = nullptr;
+    cudaEvent_t plan_fork = nullptr, plan_join = nullptr;
+    bool plan_forked = false;         // the last plan ran its hub part on `side`
 };
 
 namespace {
@@ -407,6 +411,7 @@ CountBuffers count_buffers(tc_graph* g) {
     C.stats = g->stats;
     C.src_lo = g->src_lo;
     C.src_hi = g->src_hi < 0 ? g->n : g->src_hi;
+    C.hub_ready = g->plan_forked ? g->plan_join : nullptr;
     return C;
 }
 
@@ -417,15 +422,49 @@ tc_status ensure_events(tc_graph* g) {
     return TC_OK;
 }
 
+// Orders the main stream after the hub part of the last plan (no-op when it ran on
+// the main stream): before a replan, before the graph's memory is released, and
+// wherever the hub lists are read outside the count.
+void join_plan(tc_graph* g) {
+    if (g->plan_forked) cudaStreamWaitEvent(g->stream, g->plan_join, 0);
+}
+
 // Planning (a4): bucket lists and hub in-edge lists; rerun when hub settings change.
 tc_status run_plan(tc_graph* g) {
     if (g->planned) return TC_OK;
     tc_status st = ensure_events(g);
     if (st != TC_OK) return st;
+    join_plan(g);  // a previous plan's hub part writes the buffers this one rewrites
     const size_t off = offsetof(DevStats, small_count);
     TC_CK(cudaMemsetAsync(reinterpret_cast<char*>(g->stats) + off, 0, sizeof(DevStats) - off, g->stream));
     if (!g->capture) TC_CK(cudaEventRecord(g->ev[PH_PLAN], g->stream));
-    launch_plan(count_buffers(g), g->strat, g->L);
+    // single graphs build their hub lists on a second stream while the push buckets
+    // are counted; batches (which may be recorded into a CUDA graph) keep one stream
+    const PlanStreams* ps = nullptr;
+    PlanStreams psv{};
+    if (!g->capture && g->batch_G < 0) {
+        if (!g->side) {
+            cudaStream_t s = nullptr;
+            cudaEvent_t f = nullptr, j = nullptr;
+            if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) == cudaSuccess &&
+                cudaEventCreateWithFlags(&f, cudaEventDisableTiming) == cudaSuccess &&
+                cudaEventCreateWithFlags(&j, cudaEventDisableTiming) == cudaSuccess) {
+                g->side = s;
+                g->plan_fork = f;
+                g->plan_join = j;
+            } else {  // one stream then; the failure is not the caller's
+                if (j) cudaEventDestroy(j);
+                if (f) cudaEventDestroy(f);
+                if (s) cudaStreamDestroy(s);
+                cudaGetLastError();
+            }
+        }
+        if (g->side) {
+            psv = PlanStreams{g->side, g->plan_fork, g->plan_join};
+            ps = &psv;
+        }
+    }
+    g->plan_forked = launch_plan(count_buffers(g), g->strat, g->L, ps);
     TC_CK(cudaGetLastError());
     g->planned = true;
     g->counted = false;
@@ -454,11 +493,15 @@ tc_status run_count(tc_graph* g) {
 
 void destroy(tc_graph* g) {
     if (!g) return;
+    join_plan(g);
     free_list(g, &g->blocks);
     for (int i = 0; i < PH_EVENTS; ++i)
         if (g->ev[i]) cudaEventDestroy(g->ev[i]);
     for (int i = 0; i < BP_EVENTS; ++i)
         if (g->bev[i]) cudaEventDestroy(g->bev[i]);
+    if (g->plan_join) cudaEventDestroy(g->plan_join);
+    if (g->plan_fork) cudaEventDestroy(g->plan_fork);
+    if (g->side) cudaStreamDestroy(g->side);
     delete g;
 }
 
@@ -1106,6 +1149,7 @@ tc_status tc_graph_plan_stats(tc_graph* g, int64_t* edges, int64_t* ids) {
     if (!g || !edges || !ids) return TC_EINVAL;
     tc_status st = run_plan(g);
     if (st != TC_OK) return st;
+    join_plan(g);
     const int nb = TC_NUM_BUCKETS + 1;
     unsigned long long* d = nullptr;
     TC_CK(cudaMallocFromPoolAsync((void**)&d, sizeof(unsigned long long) * 2 * nb, g->pool, g->stream));

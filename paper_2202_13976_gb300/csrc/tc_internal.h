@@ -170,12 +170,23 @@ struct CountBuffers {
     DevStats* stats;
     uint32_t* sup;           // null, or m_cap per-edge supports indexed like col (tc_edge_support)
     int32_t src_lo, src_hi;  // only triangles whose lowest vertex has a rank in [src_lo, src_hi) are counted
+    cudaEvent_t hub_ready;   // null, or recorded once the hub lists and the dense core are built (PlanStreams)
+};
+
+// A second stream for the planner: the hub in-edge lists and the dense core are
+// built on `side` (after `fork` is recorded on the main stream) while the main
+// stream lists the push sources and counts the small and block buckets; `join` is
+// recorded on `side` when they are complete.
+struct PlanStreams {
+    cudaStream_t side;
+    cudaEvent_t fork, join;
 };
 
 enum { PH_PLAN = 0, PH_SMALL, PH_CTA, PH_HUB, PH_END, PH_EVENTS };
 
-// Builds the bucket lists and the hub in-edge lists.
-void launch_plan(const CountBuffers& C, const Strategy& S, const Launch& L);
+// Builds the bucket lists and the hub in-edge lists; with ps, the hub part runs on
+// ps->side.  Returns whether it did (the count must then wait for ps->join).
+bool launch_plan(const CountBuffers& C, const Strategy& S, const Launch& L, const PlanStreams* ps = nullptr);
 // Shards of the sources (tc_vertex.cu): cost[u] = d+(u) (d+(u) + 1) / 2 + 1 (saturated),
 // then the rank range [bounds[0], bounds[1]) of shard `shard` of `nshards`, cut where
 // the prefix of the cost crosses shard / nshards of the total.  cost needs n entries,

@@ -1577,8 +1577,8 @@ void launch_plan_stats(const CountBuffers& C, unsigned long long* out, const Lau
     count_launch();
 }
 
-void launch_plan(const CountBuffers& C, const Strategy& S, const Launch& L) {
-    if (C.n <= 0) return;
+bool launch_plan(const CountBuffers& C, const Strategy& S, const Launch& L, const PlanStreams* ps) {
+    if (C.n <= 0) return false;
     const int hub_max = S.hub_max < 0 ? 0 : S.hub_max;
     const bool hubs = C.hub_cap > 0 && hub_max > 0;
     if (hubs) {
@@ -1589,44 +1589,55 @@ void launch_plan(const CountBuffers& C, const Strategy& S, const Launch& L) {
     const int core_max = hubs && C.core_cap > 0 && S.hub_core > 0 ? (S.hub_core < C.core_cap ? S.hub_core : C.core_cap) : 0;
     k_hub_count<<<1, 1, 0, L.stream>>>(C.hub_cap, hub_max, core_max, C.stats);
     count_launch();
+    // the hub lists and the dense core need only the hub count: with a second stream
+    // they are built while the main stream lists and counts the push buckets
+    const bool forked = hubs && ps != nullptr;
+    Launch H = L;
+    if (forked) {
+        cudaEventRecord(ps->fork, L.stream);
+        cudaStreamWaitEvent(ps->side, ps->fork, 0);
+        H.stream = ps->side;
+    }
     if (hubs) {
-        if (core_max > 0) launch_core_plan(C, L);
-        k_hub_indeg<<<grid_for(C.hub_cap, THREADS, L.sms), THREADS, 0, L.stream>>>(C.n, C.hub_cap, C.deg, C.rowlen,
+        if (core_max > 0) launch_core_plan(C, H);
+        k_hub_indeg<<<grid_for(C.hub_cap, THREADS, H.sms), THREADS, 0, H.stream>>>(C.n, C.hub_cap, C.deg, C.rowlen,
                                                                                   C.core_cnt, C.hub_cnt, C.stats);
         count_launch();
-        scan_u32_to_i64(C.hub_cnt, C.hub_start, C.hub_cap, C.tmp, L);
+        scan_u32_to_i64(C.hub_cnt, C.hub_start, C.hub_cap, C.tmp, H);
         // 64-bit cursors starting at every hub's first slot
         cudaMemcpyAsync(C.hub_cur64, C.hub_start, sizeof(int64_t) * (size_t)C.hub_cap, cudaMemcpyDeviceToDevice,
-                        L.stream);
-        k_row_of<<<grid_for((int64_t)C.n, THREADS, L.sms), THREADS, 0, L.stream>>>(C.n, C.hub_cap, C.rowstart,
+                        H.stream);
+        k_row_of<<<grid_for((int64_t)C.n, THREADS, H.sms), THREADS, 0, H.stream>>>(C.n, C.hub_cap, C.rowstart,
                                                                                   C.hub_start, C.rowof, C.stats);
         count_launch();
-        k_hub_scatter_rows<<<grid_for(C.n, THREADS, L.sms), THREADS, 0, L.stream>>>(
+        k_hub_scatter_rows<<<grid_for(C.n, THREADS, H.sms), THREADS, 0, H.stream>>>(
             C.n, C.hub_cap, C.rowstart, C.rowlen, C.col, C.hub_start, C.hub_cur64, C.in_rec, C.src_lo, C.src_hi,
             C.stats);
         count_launch();
-        k_hub_scatter<<<grid_for((int64_t)C.m_cap / SCAT_ITEMS + 1, SCAT_THREADS, L.sms), SCAT_THREADS, 0, L.stream>>>(
+        k_hub_scatter<<<grid_for((int64_t)C.m_cap / SCAT_ITEMS + 1, SCAT_THREADS, H.sms), SCAT_THREADS, 0, H.stream>>>(
             C.n, C.hub_cap, C.rowstart, C.rowinfo, C.col, C.rowof, C.hub_start, C.hub_cur64, C.in_rec, C.src_lo,
             C.src_hi, C.stats);
         count_launch();
-        k_hub_cur_check<<<grid_for(C.hub_cap, THREADS, L.sms), THREADS, 0, L.stream>>>(C.hub_cap, C.hub_start,
+        k_hub_cur_check<<<grid_for(C.hub_cap, THREADS, H.sms), THREADS, 0, H.stream>>>(C.hub_cap, C.hub_start,
                                                                                       C.hub_cur64, C.stats);
         count_launch();
         // hub_cur is free again: it holds the big flags, hub_cnt (still the in-degrees
         // until here) is overwritten by their exclusive scan
-        k_hub_flags<<<grid_for(C.hub_cap, THREADS, L.sms), THREADS, 0, L.stream>>>(
+        k_hub_flags<<<grid_for(C.hub_cap, THREADS, H.sms), THREADS, 0, H.stream>>>(
             C.n, C.rowlen, C.hub_cnt, C.hub_cap, S.hub_big_in > 0 ? S.hub_big_in : 1, C.hub_cur, C.stats);
         count_launch();
-        scan_u32_to_u32(C.hub_cur, C.hub_cnt, C.hub_cap, C.tmp, L);
-        k_hub_lists<<<grid_for(C.hub_cap, THREADS, L.sms), THREADS, 0, L.stream>>>(C.n, C.hub_cur, C.hub_cnt,
+        scan_u32_to_u32(C.hub_cur, C.hub_cnt, C.hub_cap, C.tmp, H);
+        k_hub_lists<<<grid_for(C.hub_cap, THREADS, H.sms), THREADS, 0, H.stream>>>(C.n, C.hub_cur, C.hub_cnt,
                                                                                   C.big_list, C.med_list, C.stats);
         count_launch();
     }
+    if (forked) cudaEventRecord(ps->join, H.stream);
     k_plan<<<grid_for(C.n, THREADS * PLAN_ITEMS, L.sms), THREADS, 0, L.stream>>>(C.n, C.rowstart, C.rowlen, C.col,
                                                                    C.small_list[0], C.small_list[1],
                                                                    C.small_list[2], C.small_list[3], C.cta_list,
                                                                    C.src_lo, C.src_hi, C.stats);
     count_launch();
+    return forked;
 }
 
 cudaError_t intersect_init_attributes() {
@@ -1684,6 +1695,8 @@ void intersect_impl(const CountBuffers& C, const Strategy& S, cudaEvent_t* ev, c
                                                                      C.t_rank, C.stats, S.strat[TC_BUCKET_CTA],
                                                                      S.factor[TC_BUCKET_CTA], C.sup);
     count_launch();
+    // the hub lists and the dense core come from the planner's second stream
+    if (C.hub_ready) cudaStreamWaitEvent(L.stream, C.hub_ready, 0);
     if (ev) cudaEventRecord(ev[PH_HUB], L.stream);
     if (C.hub_cap > 0) {
         if (S.hub_core > 0) launch_core_count(C, L);
