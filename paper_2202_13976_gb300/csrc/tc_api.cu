@@ -242,6 +242,30 @@ struct SegInfo {
     int seg_bits, deg_bits, local_bits;
 };
 
+// The graph's second stream and its two events, created at first use; null when
+// they cannot be created (the work then stays on the graph's stream).
+const PlanStreams* side_streams(tc_graph* g, PlanStreams* out) {
+    if (!g->side) {
+        cudaStream_t s = nullptr;
+        cudaEvent_t f = nullptr, j = nullptr;
+        if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) == cudaSuccess &&
+            cudaEventCreateWithFlags(&f, cudaEventDisableTiming) == cudaSuccess &&
+            cudaEventCreateWithFlags(&j, cudaEventDisableTiming) == cudaSuccess) {
+            g->side = s;
+            g->plan_fork = f;
+            g->plan_join = j;
+        } else {  // one stream then; the failure is not the caller's
+            if (j) cudaEventDestroy(j);
+            if (f) cudaEventDestroy(f);
+            if (s) cudaStreamDestroy(s);
+            cudaGetLastError();
+            return nullptr;
+        }
+    }
+    *out = PlanStreams{g->side, g->plan_fork, g->plan_join};
+    return out;
+}
+
 tc_status build_graph(tc_graph* g, const int32_t* src, const int32_t* dst, int64_t m, bool checked = true,
                       const HostPairs* host = nullptr, const SegInfo* seg = nullptr) {
     const int32_t n = g->n;
@@ -367,7 +391,8 @@ tc_status build_graph(tc_graph* g, const int32_t* src, const int32_t* dst, int64
     }
     launch_rank(B, deg_bits, g->L);
     if (bev) cudaEventRecord(bev[BP_RANK], g->stream);
-    launch_orient(B, g->L, bev);
+    PlanStreams psv{};
+    launch_orient(B, g->L, bev, !g->capture && !seg ? side_streams(g, &psv) : nullptr);
     if (bev) {
         cudaEventRecord(bev[BP_END], g->stream);
         g->build_timed = true;
@@ -440,30 +465,8 @@ tc_status run_plan(tc_graph* g) {
     if (!g->capture) TC_CK(cudaEventRecord(g->ev[PH_PLAN], g->stream));
     // single graphs build their hub lists on a second stream while the push buckets
     // are counted; batches (which may be recorded into a CUDA graph) keep one stream
-    const PlanStreams* ps = nullptr;
     PlanStreams psv{};
-    if (!g->capture && g->batch_G < 0) {
-        if (!g->side) {
-            cudaStream_t s = nullptr;
-            cudaEvent_t f = nullptr, j = nullptr;
-            if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) == cudaSuccess &&
-                cudaEventCreateWithFlags(&f, cudaEventDisableTiming) == cudaSuccess &&
-                cudaEventCreateWithFlags(&j, cudaEventDisableTiming) == cudaSuccess) {
-                g->side = s;
-                g->plan_fork = f;
-                g->plan_join = j;
-            } else {  // one stream then; the failure is not the caller's
-                if (j) cudaEventDestroy(j);
-                if (f) cudaEventDestroy(f);
-                if (s) cudaStreamDestroy(s);
-                cudaGetLastError();
-            }
-        }
-        if (g->side) {
-            psv = PlanStreams{g->side, g->plan_fork, g->plan_join};
-            ps = &psv;
-        }
-    }
+    const PlanStreams* ps = !g->capture && g->batch_G < 0 ? side_streams(g, &psv) : nullptr;
     g->plan_forked = launch_plan(count_buffers(g), g->strat, g->L, ps);
     TC_CK(cudaGetLastError());
     g->planned = true;

@@ -833,7 +833,7 @@ void bucket_shape(int32_t n, int* shift, int* nb) {
     *nb = b <= BUCKET_MAX ? (int)b : 0;  // 0: too many rows for the bucket path
 }
 
-void launch_orient(const BuildBuffers& B, const Launch& L, cudaEvent_t* ev) {
+void launch_orient(const BuildBuffers& B, const Launch& L, cudaEvent_t* ev, const PlanStreams* ps) {
     if (B.n <= 0) return;
     cudaMemsetAsync(B.cursor, 0, sizeof(uint32_t) * (size_t)B.n, L.stream);
     cudaMemsetAsync(B.dupin, 0, sizeof(uint32_t) * (size_t)B.n, L.stream);
@@ -880,17 +880,27 @@ void launch_orient(const BuildBuffers& B, const Launch& L, cudaEvent_t* ev) {
     k_segsort_thread<<<grid_for(B.n, THREADS, L.sms), THREADS, 0, L.stream>>>(
         B.n, B.rowstart, B.rowcnt, B.col, B.rowlen, B.rowinfo, B.dupin, B.midlist, B.midlist2, B.longlist, B.stats);
     count_launch();
-    k_segsort_warp<8><<<L.sms * 4, SEG_WARPS * 32, 0, L.stream>>>(B.rowstart, B.rowcnt, B.col, B.rowlen, B.rowinfo,
-                                                                 B.dupin, B.midlist, &B.stats->mid_count, B.stats);
-    count_launch();
-    k_segsort_warp<WARP_SORT_MAX / 32><<<L.sms * 2, SEG_WARPS * 32, 0, L.stream>>>(B.rowstart, B.rowcnt, B.col,
+    // the three sorters take disjoint rows: with a second stream the long rows are
+    // sorted there while the main stream sorts the rows of 17..256
+    Launch S = L;
+    if (ps) {
+        cudaEventRecord(ps->fork, L.stream);
+        cudaStreamWaitEvent(ps->side, ps->fork, 0);
+        S.stream = ps->side;
+    }
+    k_segsort_warp<WARP_SORT_MAX / 32><<<S.sms * 2, SEG_WARPS * 32, 0, S.stream>>>(B.rowstart, B.rowcnt, B.col,
                                                                                   B.rowlen, B.rowinfo, B.dupin,
                                                                                   B.midlist2, &B.stats->mid2_count,
                                                                                   B.stats);
     count_launch();
-    k_segsort_block<<<L.sms * 2, 1024, CTA_SORT_MAX * sizeof(int32_t), L.stream>>>(
+    k_segsort_block<<<S.sms * 2, 1024, CTA_SORT_MAX * sizeof(int32_t), S.stream>>>(
         B.rowstart, B.rowcnt, B.col, B.rowlen, B.rowinfo, B.dupin, B.longlist, B.stats);
     count_launch();
+    if (ps) cudaEventRecord(ps->join, S.stream);
+    k_segsort_warp<8><<<L.sms * 4, SEG_WARPS * 32, 0, L.stream>>>(B.rowstart, B.rowcnt, B.col, B.rowlen, B.rowinfo,
+                                                                 B.dupin, B.midlist, &B.stats->mid_count, B.stats);
+    count_launch();
+    if (ps) cudaStreamWaitEvent(L.stream, ps->join, 0);
     if (ev) cudaEventRecord(ev[BP_SORT], L.stream);
     k_degree<<<grid_for(B.n, THREADS, L.sms), THREADS, 0, L.stream>>>(B.n, B.rowlen, B.dmulti, B.rowcnt, B.dupin,
                                                                      B.deg);

@@ -43,6 +43,17 @@ struct Launch {
     int sms;  // multiprocessors of the device
 };
 
+// A second stream for work that does not depend on what the main stream does next:
+// it starts after `fork` is recorded on the main stream and records `join` when its
+// part is done, which the main stream waits for before it uses the results.  The
+// planner builds the hub in-edge lists and the dense core there while the main
+// stream lists and counts the push buckets; the build sorts the rows of 257 entries
+// or more there while the main stream sorts the rows of 17..256.
+struct PlanStreams {
+    cudaStream_t side;
+    cudaEvent_t fork, join;
+};
+
 // ---- primitives (tc_prims.cu) ------------------------------------------------
 // Exclusive scan of `count` uint32 values into int64 (out has count + 1 entries;
 // out[count] = total).  `tmp` needs scan_tmp_bytes(count) bytes.
@@ -111,7 +122,7 @@ void launch_canon_degree(const BuildBuffers& B, const Launch& L);
 void launch_canon_degree_part(const BuildBuffers& B, int64_t first, int64_t count, const Launch& L);
 void launch_max_deg(const BuildBuffers& B, const Launch& L);
 void launch_rank(const BuildBuffers& B, int deg_bits, const Launch& L);
-void launch_orient(const BuildBuffers& B, const Launch& L, cudaEvent_t* ev = nullptr);
+void launch_orient(const BuildBuffers& B, const Launch& L, cudaEvent_t* ev = nullptr, const PlanStreams* ps = nullptr);
 // Row fill by source buckets: at most BUCKET_MAX buckets of at most BUCKET_ROWS_MAX
 // rows (2^BUCKET_BITS buckets when that fits); nb = 0 selects the direct fill.
 constexpr int BUCKET_BITS = 11;
@@ -173,14 +184,6 @@ struct CountBuffers {
     cudaEvent_t hub_ready;   // null, or recorded once the hub lists and the dense core are built (PlanStreams)
 };
 
-// A second stream for the planner: the hub in-edge lists and the dense core are
-// built on `side` (after `fork` is recorded on the main stream) while the main
-// stream lists the push sources and counts the small and block buckets; `join` is
-// recorded on `side` when they are complete.
-struct PlanStreams {
-    cudaStream_t side;
-    cudaEvent_t fork, join;
-};
 
 enum { PH_PLAN = 0, PH_SMALL, PH_CTA, PH_HUB, PH_END, PH_EVENTS };
 
