@@ -520,6 +520,26 @@ tc_status finish_create(tc_graph* g, tc_status st, tc_graph** out) {
 
 }  // namespace
 
+namespace tcg {
+
+tc_status build_undirected_rows(int32_t n, int64_t m, const int32_t* src, const int32_t* dst, cudaStream_t stream,
+                                tc_graph** g, UndirectedRows* out) {
+    *g = nullptr;
+    tc_status st = tc_graph_create_from_edges(n, m, src, dst, TC_MEM_DEVICE, stream, g);
+    if (st != TC_OK) return st;
+    DevStats h;
+    if ((st = read_stats(*g, &h)) != TC_OK) return st;
+    out->m_simple = (int64_t)h.m_simple;
+    out->loops = (int64_t)h.loops;
+    out->rank = (*g)->rank;
+    out->rowinfo = (*g)->rowinfo;
+    out->rowlen = (*g)->rowlen;
+    out->col = (*g)->col;
+    return TC_OK;
+}
+
+}  // namespace tcg
+
 extern "C" {
 
 tc_status tc_graph_create_from_edges(int32_t n, int64_t m, const int32_t* src, const int32_t* dst,

@@ -5,25 +5,25 @@
 //   c(i) = |{e_jk in E : v_j, v_k in adj(v_i)}|,   C(i) = c(i) / (deg+(i) (deg+(i) - 1)).
 // Every pair counted in c(i) closes a triangle {i, j, k} of the undirected graph U
 // that underlies G, so the count runs on U with the undirected path's orientation
-// (rank = (degree in U, id); every triangle met once, at the edge joining its two
-// lowest ranks, Sec. II-C's offset).  Each edge of U carries two direction bits
-// relative to rank order: bit 0 = lower -> higher exists in G, bit 1 = higher -> lower.
-// A triangle u < v < w (ranks) found at the oriented edge (u, v) adds to each corner
-// x, with y and z the other two corners, the number of its ordered pairs:
+// (every triangle met once, at the edge joining its two lowest ranks, Sec. II-C's
+// offset).  Each edge of U carries two direction bits relative to rank order:
+// bit 0 = lower -> higher exists in G, bit 1 = higher -> lower.  A triangle
+// u < v < w (ranks) found at the oriented edge (u, v) adds to each corner x, with y
+// and z the other two corners, the number of its ordered pairs:
 //   [x -> y] [x -> z] ([y -> z] + [z -> y]).
 //
-// Phases (all on the device; one host synchronisation after phase 1 reads the error
-// flag and the size of U):
-//  1. pairs -> keys (min id, max id, direction), radix sorted on (min, max); a run of
-//     keys with the same (min, max) is one edge of U whose bits are the OR of its
-//     directions; degrees in U are counted from the runs;
-//  2. rank by (degree in U, id): stable radix sort of the degree field;
-//  3. oriented keys (lower rank, higher rank, bits in rank order) radix sorted, which
-//     lays the oriented rows out in order (distinct directed edges and out-degrees
-//     counted from the bits on the way); row starts by binary search;
+// Phases (all on the device):
+//  1. U itself by the undirected build (ids checked, loops and repeats dropped,
+//     vertices ranked by (degree, id), oriented rows sorted; one synchronisation
+//     reads its size); its rows are laid out without gaps as keys
+//     (lower rank, higher rank, bits) and as col;
+//  2. every input pair finds its oriented entry by binary search in its lower end's
+//     row and sets the bit of its direction; the bits give dirf, the distinct
+//     directed edges and the out-degrees;
+//  3. in-edge lists of the hubs: a stable sort of the entries by target;
 //  4. count, pull: vertices with many in-edges (hubs) stage N+(v) as a 2-bit map of
 //     direction bits in shared memory, and every in-edge (u -> v) streams N+(u) after v
-//     against it (the in-edges come from a stable sort of the entries by target);
+//     against it;
 //     count, push: a thread per other oriented entry (u, v), highest ranks first: N+(u)
 //     after v against N+(v), by a merge (Alg. 2) or a binary search of the shorter
 //     list (Alg. 1), as Eq. 3 decides, the direction bits read at the matched positions;
@@ -42,7 +42,6 @@ namespace tcg {
 namespace {
 
 constexpr int DG_THREADS = 256;
-constexpr uint64_t DG_NONE = ~0ull;  // key of a dropped pair: sorts after every edge
 constexpr int DGH_WINDOW = 131072;   // ranks above a hub covered by its 2-bit map (32 KB)
 constexpr int DGH_MIN_IN = 32;       // in-edges that make a vertex a hub
 constexpr int DGH_BLOCKS = 5;        // resident hub blocks per SM (40.1 KB shared memory each)
@@ -64,153 +63,77 @@ int key_bits(int32_t n) {
     return b;
 }
 
-// Phase 1a: key = (min << (b + 1)) | (max << 1) | (src > dst) per pair; loops and
-// bad ids get DG_NONE.
-__global__ void k_dg_keys(int64_t m, const int32_t* __restrict__ src, const int32_t* __restrict__ dst, int32_t n,
-                          int b, uint64_t* __restrict__ keys, DgStats* st) {
+// Phase 1: the rows of U without gaps: col[k] and okeys[k] = (u << (b + 2)) |
+// (v << 2) for the k-th entry, rowstart the exclusive scan of the row lengths.  One
+// warp per row.
+__global__ void k_dg_compact(int32_t n, const int2* __restrict__ rowinfo, const int32_t* __restrict__ ucol,
+                             const int64_t* __restrict__ rowstart, int b, int32_t* __restrict__ col,
+                             uint64_t* __restrict__ okeys) {
+    const int lane = lane_id();
+    const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t u = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; u < n; u += warps) {
+        const int2 ri = rowinfo[u];
+        const int64_t d0 = rowstart[u];
+        const uint64_t hi = (uint64_t)u << (b + 2);
+        for (int i = lane; i < ri.y; i += 32) {
+            const int32_t x = ucol[(int64_t)ri.x + i];
+            col[d0 + i] = x;
+            okeys[d0 + i] = hi | ((uint64_t)(uint32_t)x << 2);
+        }
+    }
+}
+
+// Phase 2a: every non-loop pair a -> c sets its direction bit at the entry of
+// {a, c}: bit 0 when a has the lower rank, bit 1 otherwise.  The ids were checked by
+// the build; the entry exists because the build kept one entry per distinct pair.
+__global__ void k_dg_bits(int64_t m, const int32_t* __restrict__ src, const int32_t* __restrict__ dst,
+                          const int32_t* __restrict__ rank, const int64_t* __restrict__ rowstart,
+                          const int32_t* __restrict__ col, unsigned long long* __restrict__ okeys) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    unsigned long long loops = 0;
-    int err = 0;
     for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < m; k += stride) {
         const int32_t a = src[k], c = dst[k];
-        uint64_t key = DG_NONE;
-        if ((uint32_t)a >= (uint32_t)n || (uint32_t)c >= (uint32_t)n) {
-            err = 1;
-        } else if (a == c) {
-            ++loops;
-        } else {
-            const uint64_t lo = (uint32_t)min(a, c), hi = (uint32_t)max(a, c);
-            key = (lo << (b + 1)) | (hi << 1) | (uint64_t)(a > c);
-        }
-        keys[k] = key;
-    }
-    loops = warp_sum(loops);
-    err = __any_sync(FULL, err);
-    if (lane_id() == 0) {
-        if (loops) atomicAdd(&st->loops, loops);
-        if (err) atomicOr(&st->err, 1);
+        if (a == c) continue;
+        const int32_t ra = rank[a], rc = rank[c];
+        const int32_t lo = min(ra, rc), hi = max(ra, rc);
+        const int64_t s0 = rowstart[lo];
+        const int len = (int)(rowstart[lo + 1] - s0);
+        const int p = lower_bound(col + s0, 0, len, hi);
+        if (p < len && col[s0 + p] == hi) atomicOr(&okeys[s0 + p], ra < rc ? 1ull : 2ull);
     }
 }
 
-// Phase 1b: head[k] = 1 where a run of equal (min, max) starts.  The sort leaves the
-// direction bit out, so the keys of one run stay in input order.
-__global__ void k_dg_heads(int64_t m, const uint64_t* __restrict__ keys, uint32_t* __restrict__ head) {
+// idof[rank[v]] = v.
+__global__ void k_dg_idof(int32_t n, const int32_t* __restrict__ rank, int32_t* __restrict__ idof) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < m; k += stride) {
-        const uint64_t key = keys[k];
-        head[k] = key != DG_NONE && (k == 0 || (key >> 1) != (keys[k - 1] >> 1)) ? 1u : 0u;
-    }
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride) idof[rank[v]] = (int32_t)v;
 }
 
-// Phase 1c: edge e = idx[k] + head[k] - 1 of U gets its ends at the run's head and the
-// direction bit of the last key of every group of equal adjacent keys (together they
-// give the OR over the run); degrees in U are counted at the heads (the min ends
-// aggregated per warp: the keys are sorted by min).
-__global__ void k_dg_unique(int64_t m, const uint64_t* __restrict__ keys, int b, const uint32_t* __restrict__ head,
-                            const uint32_t* __restrict__ idx, int32_t* __restrict__ ulo, int32_t* __restrict__ uhi,
-                            uint32_t* __restrict__ flags, uint32_t* __restrict__ deg) {
+// Phase 2b: dirf[k] = the bits of entry k; each bit is one distinct directed edge,
+// counted with its tail's out-degree (by id; the lower ends aggregated per warp: the
+// entries are sorted by their lower end).
+__global__ void k_dg_flags(int64_t mu, const uint64_t* __restrict__ okeys, int b, const int32_t* __restrict__ idof,
+                           uint8_t* __restrict__ dirf, uint32_t* __restrict__ dout, DgStats* st) {
     const int lane = lane_id();
     const int64_t warp0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t wstride = ((int64_t)gridDim.x * blockDim.x) >> 5;
     const uint64_t mask = (1ull << b) - 1;
-    for (int64_t base = warp0 * 32; base < m; base += wstride * 32) {
-        const int64_t k = base + lane;
-        const uint64_t key = k < m ? keys[k] : DG_NONE;
-        const bool valid = key != DG_NONE;
-        int32_t lo = -1;
-        if (valid) {
-            const uint32_t h = head[k];
-            const int64_t e = (int64_t)idx[k] + h - 1;
-            const int32_t hi = (int32_t)((key >> 1) & mask);
-            lo = (int32_t)(key >> (b + 1));
-            if (k + 1 == m || keys[k + 1] != key) atomicOr(&flags[e], 1u << (key & 1));
-            if (h) {
-                ulo[e] = lo;
-                uhi[e] = hi;
-                atomicAdd(&deg[hi], 1u);
-            } else {
-                lo = -1;
-            }
-        }
-        const unsigned same = __match_any_sync(FULL, lo);
-        if (lo >= 0 && lane == __ffs(same) - 1) atomicAdd(&deg[lo], (unsigned)__popc(same));
-    }
-}
-
-// Phase 2: vkey = (degree << b) | id; a stable sort of the degree field alone gives
-// (degree, id) order because the keys start in id order.
-__global__ void k_dg_rank_keys(int32_t n, const uint32_t* __restrict__ deg, int b, uint64_t* __restrict__ vkeys) {
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride)
-        vkeys[v] = ((uint64_t)deg[v] << b) | (uint64_t)v;
-}
-
-__global__ void k_dg_rank(int32_t n, const uint64_t* __restrict__ vkeys, int b, int32_t* __restrict__ rank) {
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    const uint64_t mask = (1ull << b) - 1;
-    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += stride)
-        rank[vkeys[p] & mask] = (int32_t)p;
-}
-
-// Phase 3a: okey = (lower rank << (b + 2)) | (higher rank << 2) | bits in rank order;
-// each bit of an edge of U is one distinct directed edge, counted with its tail's
-// out-degree (the min ends aggregated per warp: the edges are sorted by min).
-__global__ void k_dg_orient(int64_t mu, const int32_t* __restrict__ ulo, const int32_t* __restrict__ uhi,
-                            const uint32_t* __restrict__ flags, const int32_t* __restrict__ rank, int b,
-                            uint64_t* __restrict__ okeys, uint32_t* __restrict__ dout, DgStats* st) {
-    const int lane = lane_id();
-    const int64_t warp0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int64_t wstride = ((int64_t)gridDim.x * blockDim.x) >> 5;
     unsigned long long distinct = 0;
     for (int64_t base = warp0 * 32; base < mu; base += wstride * 32) {  // uniform per warp
         const int64_t e = base + lane;
         int32_t lo_tail = -1;
         if (e < mu) {
-            const int32_t x = ulo[e], y = uhi[e];
-            const int32_t rx = rank[x], ry = rank[y];
-            const uint32_t f = flags[e];  // bit 0: min id -> max id, bit 1: max id -> min id
-            const bool keep = rx < ry;
-            const uint64_t a = (uint32_t)(keep ? rx : ry), c = (uint32_t)(keep ? ry : rx);
-            const uint32_t of = keep ? f : ((f & 1u) << 1) | (f >> 1);
-            okeys[e] = (a << (b + 2)) | (c << 2) | of;
+            const uint64_t key = okeys[e];
+            const uint32_t f = (uint32_t)(key & 3);
+            dirf[e] = (uint8_t)f;
             distinct += __popc(f);
-            if (f & 1u) lo_tail = x;
-            if (f & 2u) atomicAdd(&dout[y], 1u);
+            if (f & 1u) lo_tail = idof[key >> (b + 2)];
+            if (f & 2u) atomicAdd(&dout[idof[(key >> 2) & mask]], 1u);
         }
         const unsigned same = __match_any_sync(FULL, lo_tail);
         if (lo_tail >= 0 && lane == __ffs(same) - 1) atomicAdd(&dout[lo_tail], (unsigned)__popc(same));
     }
     distinct = warp_sum(distinct);
     if (lane == 0 && distinct) atomicAdd(&st->m_directed, distinct);
-}
-
-// Phase 3b: the sorted keys become the rows: col (higher rank) and dirf (bits).
-__global__ void k_dg_rows(int64_t mu, const uint64_t* __restrict__ okeys, int b, int32_t* __restrict__ col,
-                          uint8_t* __restrict__ dirf) {
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    const uint64_t mask = (1ull << b) - 1;
-    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < mu; k += stride) {
-        const uint64_t key = okeys[k];
-        col[k] = (int32_t)((key >> 2) & mask);
-        dirf[k] = (uint8_t)(key & 3);
-    }
-}
-
-// rowstart[a] = first sorted entry whose lower rank is >= a (a = 0 .. n).
-__global__ void k_dg_rowstart(int32_t n, int64_t mu, const uint64_t* __restrict__ okeys, int b,
-                              int64_t* __restrict__ rowstart) {
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t a = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; a <= n; a += stride) {
-        int64_t lo = 0, hi = mu;
-        while (lo < hi) {
-            const int64_t mid = (lo + hi) >> 1;
-            if ((int64_t)(okeys[mid] >> (b + 2)) < a)
-                lo = mid + 1;
-            else
-                hi = mid;
-        }
-        rowstart[a] = lo;
-    }
 }
 
 // One matched corner w of the triangle (u, v, w): fa = bits of (u, w), fb = bits of
@@ -595,54 +518,31 @@ extern "C" tc_status tc_directed_lcc(int32_t n, int64_t m, const int32_t* src, c
         dsrc = s;
         ddst = d;
     }
-    const int64_t big = m > (int64_t)n + 1 ? m : (int64_t)n + 1;
-    uint64_t* keys = A.get<uint64_t>(mm);
-    uint64_t* alt = A.get<uint64_t>(mm);
-    void* radix_tmp = A.get<char>(radix_tmp_bytes(big));
-    void* scan_tmp = A.get<char>(scan_tmp_bytes(big + 1));
-    uint32_t* head = A.get<uint32_t>(mm + 1);
-    uint32_t* idx = A.get<uint32_t>(mm + 1);
-    uint32_t* ebits = A.get<uint32_t>(mm);
-    int32_t* ulo = A.get<int32_t>(mm);
-    int32_t* uhi = A.get<int32_t>(mm);
-    uint32_t* deg = A.get<uint32_t>(nn);
-    uint32_t* dout = A.get<uint32_t>(nn);
-    DgStats* st = A.get<DgStats>(1);
-    if (A.failed) return TC_ENOMEM;
-    DgStats hst_v{};
-    uint32_t hmu_v = 0;
-    DgStats* hst = &hst_v;  // host copies are read only after the stream is synchronised
-    uint32_t* hmu = &hmu_v;
-
     Events ev(timed);
     if (!ev.ok) return fail("tc_directed_lcc: events", cudaErrorMemoryAllocation);
     ev.record(0, stream);
-    cudaMemsetAsync(st, 0, sizeof(DgStats), stream);
-    cudaMemsetAsync(ebits, 0, sizeof(uint32_t) * mm, stream);
-    cudaMemsetAsync(deg, 0, sizeof(uint32_t) * nn, stream);
-    cudaMemsetAsync(dout, 0, sizeof(uint32_t) * nn, stream);
-    // phase 1
-    k_dg_keys<<<grid_for(m, DG_THREADS, sms), DG_THREADS, 0, stream>>>(m, dsrc, ddst, n, b, keys, st);
-    count_launch();
-    uint64_t* sorted = radix_sort_u64(keys, alt, m, 1, 2 * b + 1, radix_tmp, L);
-    k_dg_heads<<<grid_for(m, DG_THREADS, sms), DG_THREADS, 0, stream>>>(m, sorted, head);
-    count_launch();
-    scan_u32_to_u32(head, idx, m, scan_tmp, L);
-    k_dg_unique<<<grid_for(m, DG_THREADS, sms), DG_THREADS, 0, stream>>>(m, sorted, b, head, idx, ulo, uhi, ebits,
-                                                                          deg);
-    count_launch();
-    e = cudaMemcpyAsync(hst, st, sizeof(DgStats), cudaMemcpyDeviceToHost, stream);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(hmu, idx + m, sizeof(uint32_t), cudaMemcpyDeviceToHost, stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
-    if (e != cudaSuccess) return fail("tc_directed_lcc: phase 1", e);
-    if (hst->err) return TC_EINVAL;
-    const int64_t mu = (int64_t)*hmu;
-    const unsigned long long loops = hst->loops;
-
-    // phase 2: ranks (the key buffers of phase 1 are free again)
-    uint64_t* vkeys = A.get<uint64_t>(nn);
-    uint64_t* valt = A.get<uint64_t>(nn);
-    int32_t* rank = A.get<int32_t>(nn);
+    // phase 1: U by the undirected build (its graph object is released with the call)
+    tc_graph* ug = nullptr;
+    UndirectedRows U{};
+    tc_status ust = build_undirected_rows(n, m, dsrc, ddst, stream, &ug, &U);
+    struct GraphHold {
+        tc_graph* g;
+        ~GraphHold() {
+            if (g) tc_graph_destroy(g);
+        }
+    } hold{ug};
+    if (ust != TC_OK) return ust;
+    const int64_t mu = U.m_simple;
+    const unsigned long long loops = (unsigned long long)U.loops;
+    const int32_t* rank = U.rank;
+    const int64_t big = mu > (int64_t)n + 1 ? mu : (int64_t)n + 1;
+    void* radix_tmp = A.get<char>(radix_tmp_bytes(big));
+    void* scan_tmp = A.get<char>(scan_tmp_bytes(big + 1));
+    uint64_t* keys = A.get<uint64_t>((size_t)mu);
+    uint64_t* alt = A.get<uint64_t>((size_t)mu);
+    uint32_t* dout = A.get<uint32_t>(nn);
+    int32_t* idof = A.get<int32_t>(nn);
+    DgStats* st = A.get<DgStats>(1);
     int64_t* rowstart = A.get<int64_t>(nn + 1);
     int32_t* col = A.get<int32_t>((size_t)mu);
     uint8_t* dirf = A.get<uint8_t>((size_t)mu);
@@ -652,20 +552,23 @@ extern "C" tc_status tc_directed_lcc(int32_t n, int64_t m, const int32_t* src, c
     if (host && c_out) dc = A.get<unsigned long long>(nn);
     if (host && lcc_out) dl = A.get<double>(nn);
     if (A.failed) return TC_ENOMEM;
-    k_dg_rank_keys<<<grid_for(n, DG_THREADS, sms), DG_THREADS, 0, stream>>>(n, deg, b, vkeys);
+    DgStats hst_v{};
+    DgStats* hst = &hst_v;  // the host copy is read only after the stream is synchronised
+    cudaMemsetAsync(st, 0, sizeof(DgStats), stream);
+    cudaMemsetAsync(dout, 0, sizeof(uint32_t) * nn, stream);
+    scan_u32_to_i64(reinterpret_cast<const uint32_t*>(U.rowlen), rowstart, n, scan_tmp, L);
+    k_dg_compact<<<grid_for((int64_t)n * 32, DG_THREADS, sms), DG_THREADS, 0, stream>>>(n, U.rowinfo, U.col, rowstart, b,
+                                                                                      col, keys);
     count_launch();
-    uint64_t* vsorted = radix_sort_u64(vkeys, valt, n, b, 2 * b, radix_tmp, L);
-    k_dg_rank<<<grid_for(n, DG_THREADS, sms), DG_THREADS, 0, stream>>>(n, vsorted, b, rank);
+    // phase 2: direction bits
+    k_dg_bits<<<grid_for(m, DG_THREADS, sms), DG_THREADS, 0, stream>>>(m, dsrc, ddst, rank, rowstart, col,
+                                                                        reinterpret_cast<unsigned long long*>(keys));
     count_launch();
-    // phase 3: oriented rows
-    k_dg_orient<<<grid_for(mu, DG_THREADS, sms), DG_THREADS, 0, stream>>>(mu, ulo, uhi, ebits, rank, b, keys, dout,
-                                                                           st);
+    k_dg_idof<<<grid_for(n, DG_THREADS, sms), DG_THREADS, 0, stream>>>(n, rank, idof);
     count_launch();
-    uint64_t* osorted = radix_sort_u64(keys, alt, mu, 2, 2 * b + 2, radix_tmp, L);
-    k_dg_rows<<<grid_for(mu, DG_THREADS, sms), DG_THREADS, 0, stream>>>(mu, osorted, b, col, dirf);
+    k_dg_flags<<<grid_for(mu, DG_THREADS, sms), DG_THREADS, 0, stream>>>(mu, keys, b, idof, dirf, dout, st);
     count_launch();
-    k_dg_rowstart<<<grid_for((int64_t)n + 1, DG_THREADS, sms), DG_THREADS, 0, stream>>>(n, mu, osorted, b, rowstart);
-    count_launch();
+    uint64_t* osorted = keys;  // the rows are laid out in (lower, higher) order already
     // in-edge lists and hubs (the phase-1 buffer that does not hold osorted is free)
     uint64_t* ikeys = osorted == keys ? alt : keys;
     uint64_t* ialt = A.get<uint64_t>((size_t)mu);

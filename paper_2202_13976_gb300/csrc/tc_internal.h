@@ -43,6 +43,21 @@ struct Launch {
     int sms;  // multiprocessors of the device
 };
 
+// The simple undirected graph of a pair list, built by the same path as
+// tc_graph_create_from_edges (used by the directed count, whose triangles are those
+// of this graph): vertices ranked by (degree, id), oriented rows N+(u) in rank space.
+struct UndirectedRows {
+    int64_t m_simple, loops;
+    const int32_t* rank;    // n: the rank of each vertex id
+    const int2* rowinfo;    // n, by rank: {first entry of the row in col, entries}
+    const int32_t* rowlen;  // n, by rank: entries of the row
+    const int32_t* col;     // the rows' entries (ranks), ascending within each row
+};
+// Builds it on `stream` from device pairs; *g receives the graph object that holds
+// the rows (the caller destroys it).  Synchronises the stream to read the sizes.
+tc_status build_undirected_rows(int32_t n, int64_t m, const int32_t* src, const int32_t* dst, cudaStream_t stream,
+                                tc_graph** g, UndirectedRows* out);
+
 // A second stream for work that does not depend on what the main stream does next:
 // it starts after `fork` is recorded on the main stream and records `join` when its
 // part is done, which the main stream waits for before it uses the results.  The
