@@ -396,3 +396,30 @@ def test_edge_support_full_size_rmat20(tc):
         a, b = int(u[k]), int(v[k])
         want = oracle.ssi(adj[offsets[a]:offsets[a + 1]], adj[offsets[b]:offsets[b + 1]])
         assert int(sup[k]) == want, (a, b)
+
+
+def test_planner_streams_in_any_call_order(tc, rmat14):
+    """The hub lists are built on a second stream: every order of plan, count,
+    replan and destroy must see them complete (destroy right after a plan, plan
+    statistics before the count, replans between counts, a count after a replan
+    that turned the hubs off and on again)."""
+    n, s, d, ref = rmat14
+    g = tc.Graph.from_edges(n, s, d)
+    g.plan_stats()
+    g.close()  # released while nothing waited for the second stream yet
+    g = tc.Graph.from_edges(n, s, d)
+    try:
+        stats = g.plan_stats()
+        assert sum(stats[b]["edges"] for b in ("small", "cta", "hub", "trivial")) == ref["m_simple"]
+        assert g.count() == ref["T"]
+        for md, mx in [(32, 0), (1, 131072), (64, 50), (32, 131072)]:
+            g.set_hubs(md, mx)
+            assert g.count() == ref["T"]
+            t, lcc = g.lcc()
+            np.testing.assert_array_equal(t, ref["t"])
+        for k in range(3):
+            T, _ = g.count_shard(k, 3)
+            assert T >= 0
+        assert g.count() == ref["T"]
+    finally:
+        g.close()
