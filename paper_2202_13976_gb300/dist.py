@@ -38,13 +38,21 @@ def check_in(store, rank: int, world: int, step, timeout_s: float = 30.0, poll_s
 
     Raises RankLost, naming the absent ranks, once `timeout_s` has passed.  `store` is
     any torch.distributed Store shared by the ranks (TCPStore, FileStore); `step` is
-    any value that names the exchange uniquely (a step counter, a tag)."""
+    any value that names the exchange uniquely (a step counter, a tag): a key, once
+    set, stays set, so reusing a step value would find the old check-ins.  Each rank
+    removes its key of the step before the previous one once this step is complete
+    (every rank has passed that earlier check-in by then), when steps are integers."""
     store.set(_key(step, rank), b"1")
     keys = [_key(step, r) for r in range(world)]
     deadline = time.monotonic() + timeout_s
     while True:
         missing = [r for r, k in enumerate(keys) if not store.check([k])]
         if not missing:
+            if isinstance(step, int) and step >= 2:
+                try:
+                    store.delete_key(_key(step - 2, rank))
+                except Exception:  # stores without deletion keep the key
+                    pass
             return
         if time.monotonic() >= deadline:
             raise RankLost(missing, step)

@@ -170,3 +170,8 @@ def test_check_in_needs_a_shared_store():
         tcd.check_in(st, 0, 3, "b", timeout_s=0.2)
     assert e.value.missing == [1, 2]
     assert time.monotonic() - t0 < 5.0
+    # integer steps: a rank drops its key of two steps back once a step completes
+    for step in range(4):
+        tcd.check_in(st, 0, 1, step, timeout_s=1.0)
+    assert not st.check(["tc/check_in/0/0"]) and not st.check(["tc/check_in/1/0"])
+    assert st.check(["tc/check_in/2/0"]) and st.check(["tc/check_in/3/0"])
