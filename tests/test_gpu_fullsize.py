@@ -36,3 +36,17 @@ def test_full_workload(tc, name):
     assert int(t.sum()) == 3 * T
     deg = ref["degree"]
     assert (t <= deg * (deg - 1) // 2).all()
+
+
+def test_sparse_graph_with_many_vertices(tc):
+    """2^27 vertex ids, 2^22 R-MAT pairs: most vertices are isolated, the rank sort
+    covers 27-bit ids, the hub capacity stops at its cap far below n, and every
+    n-sized pass runs over 134 M entries.  Device buffers in and out."""
+    n = 1 << 27
+    s, d = graphgen.rmat(27, 1 << 22, seed=11)
+    T, t, lc, info = gpu_run(tc, n, s, d, device_io=True)
+    ref = oracle.triangles(n, s, d, threads=len(os.sched_getaffinity(0)))
+    assert T == ref["T"]
+    assert info["m_simple"] == ref["m_simple"]
+    np.testing.assert_array_equal(t, ref["t"])
+    np.testing.assert_array_equal(lc.view(np.uint64), ref["lcc"].view(np.uint64))
