@@ -235,7 +235,7 @@ typedef struct tc_directed_stats {
     int64_t loops_dropped;   /* self-loops in the input */
     uint64_t total;          /* sum over i of c(i) */
     uint64_t list_entries;   /* TC_DIRECTED_TIMED: sum over oriented edges (u, v) of d+(u) + d+(v) */
-    float build_ms;          /* TC_DIRECTED_TIMED: keys, ranks and oriented rows (input copy excluded) */
+    float build_ms;          /* TC_DIRECTED_TIMED: undirected build, direction bits, in-edge lists (input copy excluded) */
     float count_ms;          /* TC_DIRECTED_TIMED: the intersection kernel */
     float finalize_ms;       /* TC_DIRECTED_TIMED: c and C in the caller's ids */
     float pad;
