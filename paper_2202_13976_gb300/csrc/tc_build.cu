@@ -199,7 +199,7 @@ __global__ void k_orient_count(const int32_t* __restrict__ src, const int32_t* _
 }
 
 __global__ void k_orient_scatter(const int2* __restrict__ oriented, int64_t m,
-                                 unsigned long long* __restrict__ cursor, int32_t* __restrict__ col,
+                                 uint32_t* __restrict__ cursor, int32_t* __restrict__ col,
                                  DevStats* stats) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     int err = 0;
@@ -210,13 +210,13 @@ __global__ void k_orient_scatter(const int2* __restrict__ oriented, int64_t m,
             const int64_t i = i0 + k * stride;
             o[k] = i < m ? oriented[i] : make_int2(-1, -1);
         }
-        unsigned long long p[PAIR_UNROLL];
+        uint32_t p[PAIR_UNROLL];
 #pragma unroll
-        for (int k = 0; k < PAIR_UNROLL; ++k) p[k] = o[k].x >= 0 ? atomicAdd(&cursor[o[k].x], 1ull) : 0ull;
+        for (int k = 0; k < PAIR_UNROLL; ++k) p[k] = o[k].x >= 0 ? atomicAdd(&cursor[o[k].x], 1u) : 0u;
 #pragma unroll
         for (int k = 0; k < PAIR_UNROLL; ++k) {
             if (o[k].x < 0) continue;
-            if (p[k] < (unsigned long long)m)  // always true unless the passes disagree
+            if ((int64_t)p[k] < m)  // always true unless the passes disagree
                 col[p[k]] = o[k].y;
             else
                 err = ERR_OVERFLOW;
@@ -868,11 +868,11 @@ void launch_orient(const BuildBuffers& B, const Launch& L, cudaEvent_t* ev, cons
         scan_u32_to_i64(B.rowcnt, B.rowstart, B.n, B.tmp, L);
         if (ev) cudaEventRecord(ev[BP_COUNT], L.stream);
         if (B.m > 0) {
-            // 64-bit cursors in the rank keys' buffer (free once the ranks are known),
-            // starting at every row's first slot
-            cudaMemcpyAsync(B.keys, B.rowstart, sizeof(int64_t) * (size_t)B.n, cudaMemcpyDeviceToDevice, L.stream);
+            // 32-bit cursors in the rank keys' buffer (free once the ranks are known),
+            // starting at every row's first slot (slots stay below m <= 2^31 - 1)
+            scan_u32_to_u32(B.rowcnt, reinterpret_cast<uint32_t*>(B.keys), B.n, B.tmp, L);
             k_orient_scatter<<<grid_for(B.m, THREADS, L.sms), THREADS, 0, L.stream>>>(
-                B.oriented, B.m, reinterpret_cast<unsigned long long*>(B.keys), B.col, B.stats);
+                B.oriented, B.m, reinterpret_cast<uint32_t*>(B.keys), B.col, B.stats);
             count_launch();
         }
     }
