@@ -267,7 +267,7 @@ const PlanStreams* side_streams(tc_graph* g, PlanStreams* out) {
 }
 
 tc_status build_graph(tc_graph* g, const int32_t* src, const int32_t* dst, int64_t m, bool checked = true,
-                      const HostPairs* host = nullptr, const SegInfo* seg = nullptr) {
+                      const HostPairs* host = nullptr, const SegInfo* seg = nullptr, bool dir_bits = false) {
     const int32_t n = g->n;
     const size_t nn = (size_t)n;
     tc_status st;
@@ -300,6 +300,7 @@ tc_status build_graph(tc_graph* g, const int32_t* src, const int32_t* dst, int64
     B.src = src;
     B.dst = dst;
     B.m = m;
+    B.dir_bits = dir_bits;
     B.n = n;
     if (seg) {
         // graph by graph ranks keep every graph's rows together, so the bucket fill's
@@ -523,9 +524,18 @@ tc_status finish_create(tc_graph* g, tc_status st, tc_graph** out) {
 namespace tcg {
 
 tc_status build_undirected_rows(int32_t n, int64_t m, const int32_t* src, const int32_t* dst, cudaStream_t stream,
-                                tc_graph** g, UndirectedRows* out) {
+                                bool dir_bits, tc_graph** g, UndirectedRows* out) {
     *g = nullptr;
-    tc_status st = tc_graph_create_from_edges(n, m, src, dst, TC_MEM_DEVICE, stream, g);
+    tc_status st;
+    if (!dir_bits) {
+        st = tc_graph_create_from_edges(n, m, src, dst, TC_MEM_DEVICE, stream, g);
+    } else {
+        if (n < 0 || n > (1 << 29) || m < 0 || m > INT_MAX || (m > 0 && (!src || !dst))) return TC_EINVAL;
+        tc_graph* h = nullptr;
+        if ((st = new_graph(n, stream, &h)) != TC_OK) return st;
+        h->m_in = m;
+        st = finish_create(h, build_graph(h, src, dst, m, true, nullptr, nullptr, true), g);
+    }
     if (st != TC_OK) return st;
     DevStats h;
     if ((st = read_stats(*g, &h)) != TC_OK) return st;

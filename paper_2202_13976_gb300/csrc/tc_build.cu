@@ -165,7 +165,7 @@ __global__ void k_rank_invert(const uint64_t* __restrict__ sorted, int32_t n, in
 // atomic gives the slot.
 __global__ void k_orient_count(const int32_t* __restrict__ src, const int32_t* __restrict__ dst, int64_t m,
                                int32_t n, const int32_t* __restrict__ rank, uint32_t* __restrict__ rowcnt,
-                               int2* __restrict__ oriented) {
+                               int2* __restrict__ oriented, bool dir_bits) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i0 < m; i0 += PAIR_UNROLL * stride) {
         int32_t u[PAIR_UNROLL], v[PAIR_UNROLL];
@@ -191,6 +191,7 @@ __global__ void k_orient_count(const int32_t* __restrict__ src, const int32_t* _
             int2 o = make_int2(-1, -1);
             if (a[k] >= 0) {
                 o = make_int2(min(a[k], b[k]), max(a[k], b[k]));
+                if (dir_bits) o.y = (o.y << 2) | (a[k] < b[k] ? 1 : 2);
                 atomicAdd(&rowcnt[o.x], 1u);
             }
             oriented[i] = o;
@@ -249,7 +250,8 @@ constexpr int FILL_THREADS = 1024;
 __global__ void __launch_bounds__(THREADS) k_bucket_count(const int32_t* __restrict__ src,
                                                           const int32_t* __restrict__ dst, int64_t m, int32_t n,
                                                           const int32_t* __restrict__ rank, int shift, int nb,
-                                                          uint32_t* __restrict__ bcount, int2* __restrict__ oriented) {
+                                                          uint32_t* __restrict__ bcount, int2* __restrict__ oriented,
+                                                          bool dir_bits) {
     extern __shared__ uint32_t hist[];  // nb
     for (int b = threadIdx.x; b < nb; b += THREADS) hist[b] = 0;
     __syncthreads();
@@ -270,6 +272,7 @@ __global__ void __launch_bounds__(THREADS) k_bucket_count(const int32_t* __restr
             if (u[k] != v[k] && (uint32_t)u[k] < (uint32_t)n && (uint32_t)v[k] < (uint32_t)n) {
                 const int32_t a = rank[u[k]], b = rank[v[k]];
                 o = make_int2(min(a, b), max(a, b));
+                if (dir_bits) o.y = (o.y << 2) | (a < b ? 1 : 2);
                 atomicAdd(&hist[o.x >> shift], 1u);
             }
             oriented[i] = o;  // the partition pass reads these instead of gathering ranks again
@@ -507,7 +510,7 @@ __device__ __forceinline__ int sort_row_regs(int32_t* __restrict__ row, int len,
         if (i < len) {
             if (v[i] != prev)
                 row[kept++] = v[i];
-            else
+            else if (dupin)
                 atomicAdd(&dupin[v[i]], 1u);
         }
         prev = v[i];
@@ -608,7 +611,7 @@ __device__ __forceinline__ int warp_sort_row(int32_t* __restrict__ row, int len,
             if (v[r] != prev) {
                 keepmask |= 1u << r;
                 ++nk;
-            } else {
+            } else if (dupin) {
                 atomicAdd(&dupin[v[r]], 1u);
             }
         }
@@ -721,7 +724,7 @@ __global__ void __launch_bounds__(1024) k_segsort_block(const int64_t* __restric
             __syncthreads();
             if (keep)
                 col[base + kept + before + __popc(mk & lanemask_lt())] = x;
-            else if (i < len)
+            else if (i < len && dupin)
                 atomicAdd(&dupin[x], 1u);
             kept += tot;
             if (threadIdx.x == 0) boundary = last;
@@ -844,7 +847,7 @@ void launch_orient(const BuildBuffers& B, const Launch& L, cudaEvent_t* ev, cons
         cudaMemsetAsync(B.bcur, 0, sizeof(uint32_t) * (size_t)nb, L.stream);
         if (B.m > 0) {
             k_bucket_count<<<grid_for(B.m, THREADS * PAIR_UNROLL, L.sms, 8), THREADS, sizeof(uint32_t) * nb, L.stream>>>(
-                B.src, B.dst, B.m, B.n, B.rank, shift, nb, B.bcount, B.oriented);
+                B.src, B.dst, B.m, B.n, B.rank, shift, nb, B.bcount, B.oriented, B.dir_bits);
             count_launch();
         }
         scan_u32_to_i64(B.bcount, B.bstart, nb, B.tmp, L);
@@ -862,7 +865,7 @@ void launch_orient(const BuildBuffers& B, const Launch& L, cudaEvent_t* ev, cons
         cudaMemsetAsync(B.rowcnt, 0, sizeof(uint32_t) * (size_t)B.n, L.stream);
         if (B.m > 0) {
             k_orient_count<<<grid_for(B.m, THREADS, L.sms), THREADS, 0, L.stream>>>(B.src, B.dst, B.m, B.n, B.rank,
-                                                                                  B.rowcnt, B.oriented);
+                                                                                  B.rowcnt, B.oriented, B.dir_bits);
             count_launch();
         }
         scan_u32_to_i64(B.rowcnt, B.rowstart, B.n, B.tmp, L);
@@ -877,8 +880,10 @@ void launch_orient(const BuildBuffers& B, const Launch& L, cudaEvent_t* ev, cons
         }
     }
     if (ev) cudaEventRecord(ev[BP_FILL], L.stream);
+    // with direction bits the entries are not ranks: repeats are not counted at targets
+    uint32_t* const dupin = B.dir_bits ? nullptr : B.dupin;
     k_segsort_thread<<<grid_for(B.n, THREADS, L.sms), THREADS, 0, L.stream>>>(
-        B.n, B.rowstart, B.rowcnt, B.col, B.rowlen, B.rowinfo, B.dupin, B.midlist, B.midlist2, B.longlist, B.stats);
+        B.n, B.rowstart, B.rowcnt, B.col, B.rowlen, B.rowinfo, dupin, B.midlist, B.midlist2, B.longlist, B.stats);
     count_launch();
     // the three sorters take disjoint rows: with a second stream the long rows are
     // sorted there while the main stream sorts the rows of 17..256
@@ -889,16 +894,16 @@ void launch_orient(const BuildBuffers& B, const Launch& L, cudaEvent_t* ev, cons
         S.stream = ps->side;
     }
     k_segsort_warp<WARP_SORT_MAX / 32><<<S.sms * 2, SEG_WARPS * 32, 0, S.stream>>>(B.rowstart, B.rowcnt, B.col,
-                                                                                  B.rowlen, B.rowinfo, B.dupin,
+                                                                                  B.rowlen, B.rowinfo, dupin,
                                                                                   B.midlist2, &B.stats->mid2_count,
                                                                                   B.stats);
     count_launch();
     k_segsort_block<<<S.sms * 2, 1024, CTA_SORT_MAX * sizeof(int32_t), S.stream>>>(
-        B.rowstart, B.rowcnt, B.col, B.rowlen, B.rowinfo, B.dupin, B.longlist, B.stats);
+        B.rowstart, B.rowcnt, B.col, B.rowlen, B.rowinfo, dupin, B.longlist, B.stats);
     count_launch();
     if (ps) cudaEventRecord(ps->join, S.stream);
     k_segsort_warp<8><<<L.sms * 4, SEG_WARPS * 32, 0, L.stream>>>(B.rowstart, B.rowcnt, B.col, B.rowlen, B.rowinfo,
-                                                                 B.dupin, B.midlist, &B.stats->mid_count, B.stats);
+                                                                 dupin, B.midlist, &B.stats->mid_count, B.stats);
     count_launch();
     if (ps) cudaStreamWaitEvent(L.stream, ps->join, 0);
     if (ev) cudaEventRecord(ev[BP_SORT], L.stream);

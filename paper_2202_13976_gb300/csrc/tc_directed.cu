@@ -102,6 +102,81 @@ __global__ void k_dg_bits(int64_t m, const int32_t* __restrict__ src, const int3
     }
 }
 
+// Phase 1-2 with carried bits: the entries of a row are (rank << 2) | bit, sorted,
+// exact repeats dropped, so a pair read in both directions left (v, 1) and (v, 2)
+// next to each other.  A row keeps one entry per v, whose bits are the OR of the two.
+// One warp per row; merge_count gives the merged lengths, merge_write the rows
+// without gaps (col, dirf and the keys (u << (b + 2)) | (v << 2) | bits), the
+// distinct directed edges and the out-degrees by id.
+__global__ void k_dg_merge_count(int32_t n, const int2* __restrict__ rowinfo, const int32_t* __restrict__ ucol,
+                                 uint32_t* __restrict__ merged) {
+    const int lane = lane_id();
+    const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t u = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; u < n; u += warps) {
+        const int2 ri = rowinfo[u];
+        uint32_t kept = 0;
+        for (int i0 = 0; i0 < ri.y; i0 += 32) {  // ri.y is the same in every lane
+            const int i = i0 + lane;
+            bool keep = false;
+            if (i < ri.y) {
+                const int64_t p = (int64_t)ri.x + i;
+                keep = i == 0 || (ucol[p - 1] >> 2) != (ucol[p] >> 2);
+            }
+            kept += __popc(__ballot_sync(FULL, keep));
+        }
+        if (lane == 0) merged[u] = kept;
+    }
+}
+
+__global__ void k_dg_merge_write(int32_t n, const int2* __restrict__ rowinfo, const int32_t* __restrict__ ucol,
+                                 const int64_t* __restrict__ rowstart, int b, const int32_t* __restrict__ idof,
+                                 int32_t* __restrict__ col, uint8_t* __restrict__ dirf, uint64_t* __restrict__ okeys,
+                                 uint32_t* __restrict__ dout, DgStats* st) {
+    const int lane = lane_id();
+    const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    unsigned long long distinct = 0;
+    for (int64_t u = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; u < n; u += warps) {
+        const int2 ri = rowinfo[u];
+        int64_t d = rowstart[u];
+        const uint64_t hi = (uint64_t)u << (b + 2);
+        uint32_t out_u = 0;  // entries with bit 0: u -> v, tail u
+        for (int i0 = 0; i0 < ri.y; i0 += 32) {
+            const int i = i0 + lane;
+            bool keep = false;
+            int32_t v = 0;
+            uint32_t f = 0;
+            if (i < ri.y) {
+                const int64_t p = (int64_t)ri.x + i;
+                const int32_t x = ucol[p];
+                v = x >> 2;
+                keep = i == 0 || (ucol[p - 1] >> 2) != v;
+                if (keep) {
+                    f = (uint32_t)(x & 3);
+                    if (i + 1 < ri.y) {
+                        const int32_t y = ucol[p + 1];
+                        if ((y >> 2) == v) f |= (uint32_t)(y & 3);
+                    }
+                }
+            }
+            const unsigned km = __ballot_sync(FULL, keep);
+            if (keep) {
+                const int64_t q = d + __popc(km & lanemask_lt());
+                col[q] = v;
+                dirf[q] = (uint8_t)f;
+                okeys[q] = hi | ((uint64_t)(uint32_t)v << 2) | f;
+                distinct += __popc(f);
+                if (f & 1u) ++out_u;
+                if (f & 2u) atomicAdd(&dout[idof[v]], 1u);  // v -> u, tail v
+            }
+            d += __popc(km);
+        }
+        out_u = __reduce_add_sync(FULL, out_u);
+        if (lane == 0 && out_u) atomicAdd(&dout[idof[u]], out_u);
+    }
+    distinct = warp_sum(distinct);
+    if (lane == 0 && distinct) atomicAdd(&st->m_directed, distinct);
+}
+
 // idof[rank[v]] = v.
 __global__ void k_dg_idof(int32_t n, const int32_t* __restrict__ rank, int32_t* __restrict__ idof) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -521,10 +596,12 @@ extern "C" tc_status tc_directed_lcc(int32_t n, int64_t m, const int32_t* src, c
     Events ev(timed);
     if (!ev.ok) return fail("tc_directed_lcc: events", cudaErrorMemoryAllocation);
     ev.record(0, stream);
-    // phase 1: U by the undirected build (its graph object is released with the call)
+    // phase 1: U by the undirected build (its graph object is released with the call);
+    // up to 2^29 vertices its entries carry the direction bits of their pairs
+    const bool carried = n <= (1 << 29);
     tc_graph* ug = nullptr;
     UndirectedRows U{};
-    tc_status ust = build_undirected_rows(n, m, dsrc, ddst, stream, &ug, &U);
+    tc_status ust = build_undirected_rows(n, m, dsrc, ddst, stream, carried, &ug, &U);
     struct GraphHold {
         tc_graph* g;
         ~GraphHold() {
@@ -532,18 +609,32 @@ extern "C" tc_status tc_directed_lcc(int32_t n, int64_t m, const int32_t* src, c
         }
     } hold{ug};
     if (ust != TC_OK) return ust;
-    const int64_t mu = U.m_simple;
     const unsigned long long loops = (unsigned long long)U.loops;
     const int32_t* rank = U.rank;
-    const int64_t big = mu > (int64_t)n + 1 ? mu : (int64_t)n + 1;
-    void* radix_tmp = A.get<char>(radix_tmp_bytes(big));
-    void* scan_tmp = A.get<char>(scan_tmp_bytes(big + 1));
-    uint64_t* keys = A.get<uint64_t>((size_t)mu);
-    uint64_t* alt = A.get<uint64_t>((size_t)mu);
+    void* scan_tmp = A.get<char>(scan_tmp_bytes((int64_t)nn + 1));
     uint32_t* dout = A.get<uint32_t>(nn);
     int32_t* idof = A.get<int32_t>(nn);
     DgStats* st = A.get<DgStats>(1);
     int64_t* rowstart = A.get<int64_t>(nn + 1);
+    uint32_t* merged = carried ? A.get<uint32_t>(nn) : nullptr;
+    if (A.failed) return TC_ENOMEM;
+    int64_t mu = U.m_simple;
+    if (carried) {
+        // a pair read in both directions left two neighbouring entries: rows merged
+        k_dg_merge_count<<<grid_for((int64_t)n * 32, DG_THREADS, sms), DG_THREADS, 0, stream>>>(n, U.rowinfo, U.col,
+                                                                                              merged);
+        count_launch();
+        scan_u32_to_i64(merged, rowstart, n, scan_tmp, L);
+        e = cudaMemcpyAsync(&mu, rowstart + n, sizeof(int64_t), cudaMemcpyDeviceToHost, stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+        if (e != cudaSuccess) return fail("tc_directed_lcc: merged rows", e);
+    } else {
+        scan_u32_to_i64(reinterpret_cast<const uint32_t*>(U.rowlen), rowstart, n, scan_tmp, L);
+    }
+    const int64_t big = mu > (int64_t)n + 1 ? mu : (int64_t)n + 1;
+    void* radix_tmp = A.get<char>(radix_tmp_bytes(big));
+    uint64_t* keys = A.get<uint64_t>((size_t)mu);
+    uint64_t* alt = A.get<uint64_t>((size_t)mu);
     int32_t* col = A.get<int32_t>((size_t)mu);
     uint8_t* dirf = A.get<uint8_t>((size_t)mu);
     unsigned long long* c_rank = A.get<unsigned long long>(nn);
@@ -556,18 +647,24 @@ extern "C" tc_status tc_directed_lcc(int32_t n, int64_t m, const int32_t* src, c
     DgStats* hst = &hst_v;  // the host copy is read only after the stream is synchronised
     cudaMemsetAsync(st, 0, sizeof(DgStats), stream);
     cudaMemsetAsync(dout, 0, sizeof(uint32_t) * nn, stream);
-    scan_u32_to_i64(reinterpret_cast<const uint32_t*>(U.rowlen), rowstart, n, scan_tmp, L);
-    k_dg_compact<<<grid_for((int64_t)n * 32, DG_THREADS, sms), DG_THREADS, 0, stream>>>(n, U.rowinfo, U.col, rowstart, b,
-                                                                                      col, keys);
-    count_launch();
-    // phase 2: direction bits
-    k_dg_bits<<<grid_for(m, DG_THREADS, sms), DG_THREADS, 0, stream>>>(m, dsrc, ddst, rank, rowstart, col,
-                                                                        reinterpret_cast<unsigned long long*>(keys));
-    count_launch();
     k_dg_idof<<<grid_for(n, DG_THREADS, sms), DG_THREADS, 0, stream>>>(n, rank, idof);
     count_launch();
-    k_dg_flags<<<grid_for(mu, DG_THREADS, sms), DG_THREADS, 0, stream>>>(mu, keys, b, idof, dirf, dout, st);
-    count_launch();
+    if (carried) {
+        // phase 2 from the carried bits: merged rows, keys, dirf, out-degrees
+        k_dg_merge_write<<<grid_for((int64_t)n * 32, DG_THREADS, sms), DG_THREADS, 0, stream>>>(
+            n, U.rowinfo, U.col, rowstart, b, idof, col, dirf, keys, dout, st);
+        count_launch();
+    } else {
+        k_dg_compact<<<grid_for((int64_t)n * 32, DG_THREADS, sms), DG_THREADS, 0, stream>>>(n, U.rowinfo, U.col,
+                                                                                          rowstart, b, col, keys);
+        count_launch();
+        // phase 2: direction bits by a binary search per pair
+        k_dg_bits<<<grid_for(m, DG_THREADS, sms), DG_THREADS, 0, stream>>>(m, dsrc, ddst, rank, rowstart, col,
+                                                                            reinterpret_cast<unsigned long long*>(keys));
+        count_launch();
+        k_dg_flags<<<grid_for(mu, DG_THREADS, sms), DG_THREADS, 0, stream>>>(mu, keys, b, idof, dirf, dout, st);
+        count_launch();
+    }
     uint64_t* osorted = keys;  // the rows are laid out in (lower, higher) order already
     // in-edge lists and hubs (the phase-1 buffer that does not hold osorted is free)
     uint64_t* ikeys = osorted == keys ? alt : keys;

@@ -55,8 +55,11 @@ struct UndirectedRows {
 };
 // Builds it on `stream` from device pairs; *g receives the graph object that holds
 // the rows (the caller destroys it).  Synchronises the stream to read the sizes.
+// With dir_bits (n <= 2^29) every entry is (rank << 2) | direction bit of its pair
+// (BuildBuffers::dir_bits): a pair read in both directions leaves two neighbouring
+// entries, and m_simple counts entries, not edges.
 tc_status build_undirected_rows(int32_t n, int64_t m, const int32_t* src, const int32_t* dst, cudaStream_t stream,
-                                tc_graph** g, UndirectedRows* out);
+                                bool dir_bits, tc_graph** g, UndirectedRows* out);
 
 // A second stream for work that does not depend on what the main stream does next:
 // it starts after `fork` is recorded on the main stream and records `join` when its
@@ -107,6 +110,11 @@ struct BuildBuffers {
     int2* pairs;          // m: (source rank, target rank) grouped by bucket
     int2* oriented;       // m: (source rank, target rank) in input order ((-1, -1): no entry)
     bool bucket_fill;     // rows counted and filled by source buckets (flat degree distributions)
+    // directed input (tc_directed_lcc): every entry is (target rank << 2) | direction
+    // bit of its pair (1: source rank below target rank, 2: above), so a pair read in
+    // both directions leaves two entries; repeats are dropped as usual, but not
+    // counted into the degrees (they are not used then).  Needs n <= 2^29.
+    bool dir_bits;
     // batches: vertices are ranked within their own graph (graph, degree, id), so each
     // graph keeps a contiguous block of ranks and rows; seg_vbase null for one graph
     const int32_t* seg_vbase;  // G + 1: first union id of every graph
