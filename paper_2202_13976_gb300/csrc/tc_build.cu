@@ -9,8 +9,9 @@
 //  3. orient        every non-loop pair {u, v} becomes the oriented entry
 //                   min(rank u, rank v) -> max(rank u, rank v); rows are filled by a
 //                   counting sort on the source rank
-//  4. segsort       each row is sorted (bitonic network in shared memory or, for very
-//                   long rows, in global memory) and repeated entries are removed;
+//  4. segsort       each row is sorted (bitonic networks in a thread's or a warp's
+//                   registers, in a block's shared memory or, for very long rows, in
+//                   global memory) and repeated entries are removed;
 //                   the simple-graph degree of every vertex is its distinct
 //                   out-entries plus its in-entries before deduplication minus the
 //                   repeats dropped at it
