@@ -21,12 +21,17 @@ __all__ = ["RankLost", "check_in", "sum_counts", "sharded_lcc"]
 
 
 class RankLost(RuntimeError):
-    """Ranks that did not check in for a step before the deadline."""
+    """Ranks that did not check in for a step before the deadline.
 
-    def __init__(self, missing, step):
+    `store_error` is set when the store itself stopped answering (the process that
+    hosts it is gone); `missing` then lists the ranks not seen before that."""
+
+    def __init__(self, missing, step, store_error=None):
         self.missing = list(missing)
         self.step = step
-        super().__init__(f"ranks {self.missing} did not check in for step {step!r}")
+        self.store_error = store_error
+        why = f" (store lost: {store_error})" if store_error is not None else ""
+        super().__init__(f"ranks {self.missing} did not check in for step {step!r}{why}")
 
 
 def _key(step, rank: int) -> str:
@@ -36,17 +41,28 @@ def _key(step, rank: int) -> str:
 def check_in(store, rank: int, world: int, step, timeout_s: float = 30.0, poll_s: float = 0.005):
     """Marks this rank as present for `step` and waits until every rank of `world` is.
 
-    Raises RankLost, naming the absent ranks, once `timeout_s` has passed.  `store` is
-    any torch.distributed Store shared by the ranks (TCPStore, FileStore); `step` is
-    any value that names the exchange uniquely (a step counter, a tag): a key, once
-    set, stays set, so reusing a step value would find the old check-ins.  Each rank
-    removes its key of the step before the previous one once this step is complete
-    (every rank has passed that earlier check-in by then), when steps are integers."""
-    store.set(_key(step, rank), b"1")
+    Raises RankLost, naming the absent ranks, once `timeout_s` has passed, or as soon
+    as the store stops answering.  `store` is any torch.distributed Store shared by
+    the ranks (TCPStore, FileStore); `step` is any value that names the exchange
+    uniquely (a step counter, a tag): a key, once set, stays set, so reusing a step
+    value would find the old check-ins.  Each rank removes its key of the step before
+    the previous one once this step is complete (every rank has passed that earlier
+    check-in by then), when steps are integers."""
     keys = [_key(step, r) for r in range(world)]
+    seen = set()
     deadline = time.monotonic() + timeout_s
+    try:
+        store.set(keys[rank], b"1")
+    except Exception as e:  # no store: nobody can be confirmed
+        raise RankLost([r for r in range(world) if r != rank], step, store_error=e) from e
     while True:
-        missing = [r for r, k in enumerate(keys) if not store.check([k])]
+        try:
+            for r, k in enumerate(keys):
+                if r not in seen and store.check([k]):
+                    seen.add(r)
+        except Exception as e:  # the store stopped answering: its host rank is gone
+            raise RankLost([r for r in range(world) if r not in seen], step, store_error=e) from e
+        missing = [r for r in range(world) if r not in seen]
         if not missing:
             if isinstance(step, int) and step >= 2:
                 try:
@@ -68,11 +84,13 @@ def sum_counts(t, *, store, rank: int, world: int, step, timeout_s: float = 30.0
     return t
 
 
-def sharded_lcc(graph, *, store, rank: int, world: int, step=0, timeout_s: float = 30.0, group=None,
+def sharded_lcc(graph, *, store, rank: int, world: int, step, timeout_s: float = 30.0, group=None,
                 reduce_device: str = "cpu"):
     """(T, t, lcc) of the whole graph on every rank, from this rank's shard.
 
-    `graph` is a `Graph` that every rank built from the same edges.  The per-vertex
+    `graph` is a `Graph` that every rank built from the same edges.  `step` names this
+    exchange and must differ between calls on one store (see `check_in`), so it has
+    no default.  The per-vertex
     counts and the shard's triangles travel as one int64 tensor on `reduce_device`
     ("cpu" for gloo, "cuda" for NCCL).  t is returned as uint64 and lcc as float64,
     both numpy arrays on the host."""

@@ -100,8 +100,10 @@ def test_edge_shards_sum_to_the_full_count():
     assert all(edges > 0 for _, _, edges in out)
 
 
-def _exchange_worker(rank, world, port, q, absent):
-    """All ranks join the group; `absent` (if any) then leaves before the exchange."""
+def _exchange_worker(rank, world, port, q, absent, release):
+    """All ranks join the group; `absent` (if any) then leaves before the exchange.
+    The others stay until the parent has every report (`release`): rank 0 hosts the
+    store, and its exit would cut the others' check-ins short."""
     import torch
     import torch.distributed as dist
 
@@ -122,6 +124,7 @@ def _exchange_worker(rank, world, port, q, absent):
         q.put((rank, "lost", (e.missing, e.step, time.monotonic() - t0)))
     q.close()
     q.join_thread()
+    release.wait(120)
     if absent is None:
         dist.destroy_process_group()
     else:
@@ -131,11 +134,15 @@ def _exchange_worker(rank, world, port, q, absent):
 def _run_exchange(world, absent):
     ctx = mp.get_context("spawn")
     q = ctx.Queue()
+    release = ctx.Event()
     port = _free_port()
-    procs = [ctx.Process(target=_exchange_worker, args=(r, world, port, q, absent)) for r in range(world)]
+    procs = [ctx.Process(target=_exchange_worker, args=(r, world, port, q, absent, release)) for r in range(world)]
     for p in procs:
         p.start()
-    out = [q.get(timeout=120) for _ in procs]
+    try:
+        out = [q.get(timeout=120) for _ in procs]
+    finally:
+        release.set()
     for p in procs:
         p.join(timeout=60)
     return sorted(out)
@@ -175,3 +182,38 @@ def test_check_in_needs_a_shared_store():
         tcd.check_in(st, 0, 1, step, timeout_s=1.0)
     assert not st.check(["tc/check_in/0/0"]) and not st.check(["tc/check_in/1/0"])
     assert st.check(["tc/check_in/2/0"]) and st.check(["tc/check_in/3/0"])
+
+
+class _StoreThatDies:
+    """A store that answers `live` checks, then fails as a TCPStore client does once
+    the process hosting the store has exited."""
+
+    def __init__(self, present, live):
+        self.keys = {f"tc/check_in/s/{r}" for r in present}
+        self.live = live
+
+    def set(self, key, value):
+        self.keys.add(key)
+
+    def check(self, keys):
+        if self.live == 0:
+            raise RuntimeError("Connection reset by peer")
+        self.live -= 1
+        return all(k in self.keys for k in keys)
+
+
+def test_a_store_that_stops_answering_is_reported_as_lost():
+    from paper_2202_13976_gb300 import dist as tcd
+    # ranks 0 and 1 are seen before the store goes; rank 2 never checked in
+    t0 = time.monotonic()
+    with pytest.raises(tcd.RankLost) as e:
+        tcd.check_in(_StoreThatDies([0], live=3), 1, 3, "s", timeout_s=60.0)
+    assert e.value.missing == [2] and e.value.store_error is not None
+    assert time.monotonic() - t0 < 5.0  # at once, not at the deadline
+    # a store that is gone before the first check-in confirms nobody else
+    class Gone(_StoreThatDies):
+        def set(self, key, value):
+            raise RuntimeError("Connection refused")
+    with pytest.raises(tcd.RankLost) as e:
+        tcd.check_in(Gone([], live=0), 0, 3, "s", timeout_s=60.0)
+    assert e.value.missing == [1, 2]
