@@ -186,18 +186,50 @@ def step_spread(step_ms):
     return {"median_ms": med, "ci95_ms": half, "within_5pct": half <= 0.05 * med}
 
 
+ONE_CORE_PIECES = 64  # the single-thread figure counts 1/64 of the oriented-count work
+
+
 def cpu_baseline(workload, src, dst):
-    """The oracle as it stands, whole pipeline on the same workload, host cores."""
+    """The oracle as it stands, whole pipeline on the same workload, host cores.
+
+    The steps are those of oracle.triangles, timed one by one: the CSR build,
+    orientation and LCC run on one thread, the oriented count (Alg. 2) is split over
+    all cores.  `one_thread` adds the same pipeline on one core, its count estimated
+    from a bounded sample: every 64th of 512 source ranges of equal work (1/64 of the
+    work, spread over the ranks), run on one thread and scaled by 64."""
+    import numpy as np
+
     import oracle
     cores = len(os.sched_getaffinity(0))
     oracle.build()
+    n = workload.n
     t0 = time.perf_counter()
-    r = oracle.triangles(workload.n, src, dst, threads=cores)
-    dt = time.perf_counter() - t0
-    return {"value": r["m_simple"] / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+    offsets, adj, stats = oracle.build_csr(n, src, dst)
+    off_plus, adj_plus = oracle.orient(n, offsets, adj)
+    t1 = time.perf_counter()
+    t = oracle.tc_oriented(n, off_plus, adj_plus, threads=cores)
+    t2 = time.perf_counter()
+    total = int(t.sum(dtype=np.uint64))
+    assert total % 3 == 0, "sum of per-vertex counts is not a multiple of 3"
+    oracle.lcc(n, offsets, t)
+    t3 = time.perf_counter()
+    dt = t3 - t0
+    m = stats["m_simple"]
+    ranges = oracle.work_ranges(off_plus, 8 * ONE_CORE_PIECES)
+    picked = ranges[::ONE_CORE_PIECES]
+    s0 = time.perf_counter()
+    oracle.tc_oriented_ranges(n, off_plus, adj_plus, picked, threads=1)
+    one_count = (time.perf_counter() - s0) * len(ranges) / max(1, len(picked))
+    one = (t1 - t0) + (t3 - t2) + one_count
+    return {"value": m / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": f"full {workload.name} workload, whole pipeline (std::sort CSR build, orientation, "
-                      f"Alg. 2 oriented count split over {cores} threads, LCC) in {dt:.2f} s",
-            "T": r["T"]}, r
+                      f"Alg. 2 oriented count split over {cores} threads, LCC) in {dt:.2f} s "
+                      f"(count {t2 - t1:.2f} s)",
+            "one_thread": {"value": m / one, "cores": 1,
+                           "sample": f"the same pipeline on one thread: build, orientation and LCC as "
+                                     f"timed above, the count estimated as {one_count:.2f} s from "
+                                     f"{len(picked)} of {len(ranges)} equal-work source ranges"},
+            "T": total // 3}
 
 
 REF_SAMPLES = 8  # the reference arm counts 1/REF_SAMPLES of the sources per step
@@ -389,7 +421,7 @@ def run_ours(args, rank, world, local):
     golden = golden_check(args.workload, sorted(Ts)[0], t_np, l_np) if len(Ts) == 1 else {"T": False}
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
-        cpu, ref = cpu_baseline(w, src_h, dst_h)
+        cpu = cpu_baseline(w, src_h, dst_h)
         ok = (cpu["T"] in Ts and len(Ts) == 1)
         cpu["parity_T"] = ok
         del cpu["T"]

@@ -1,5 +1,5 @@
 """Host-side helpers of the benchmark (no GPU): the timing-rule summary, the peak
-lookup and the sampled CPU baseline of the directed mode."""
+lookup and the CPU baselines (single-graph and the sampled one of the directed mode)."""
 from __future__ import annotations
 
 import numpy as np
@@ -29,6 +29,18 @@ def test_directed_cpu_baseline_samples_the_oracle():
     cpu = bench.directed_cpu_baseline(n, s, d, sample_vertices=200, seed=1)
     assert cpu["kind"] == "oracle" and cpu["unit"] == "edges/s" and cpu["value"] > 0
     assert "200 random vertices" in cpu["sample"]
+
+
+def test_cpu_baseline_times_the_oracle_on_all_cores_and_on_one():
+    import oracle
+    w = graphgen.workload("er4096")
+    s, d = w.edges()
+    cpu = bench.cpu_baseline(w, s, d)
+    assert cpu["T"] == oracle.triangles(w.n, s, d)["T"]
+    assert cpu["kind"] == "oracle" and cpu["value"] > 0 and cpu["cores"] >= 1
+    one = cpu["one_thread"]
+    assert one["cores"] == 1 and one["value"] > 0
+    assert f"of {8 * bench.ONE_CORE_PIECES} equal-work source ranges" in one["sample"]
 
 
 def test_bench_defaults_are_one_gpu_and_minutes():
