@@ -64,8 +64,11 @@ def parse_args():
     p.add_argument("--budget-gb", type=float, default=120.0)
     p.add_argument("--serve-deadline", type=float, default=900.0,
                    help="give up waiting for the backlog after this many seconds")
-    p.add_argument("--serve-verify", type=int, default=24,
-                   help="check this many of the smallest served requests against the oracle")
+    p.add_argument("--serve-verify-seconds", type=float, default=1.0,
+                   help="check every served request of at most 50,000 vertices that arrived in the "
+                        "first this many seconds against the oracle (0: none)")
+    p.add_argument("--serve-verify-random", type=int, default=16,
+                   help="also check this many seeded random requests of the whole stream")
     p.add_argument("--serve-compare-seconds", type=float, default=5.0,
                    help="the first this many seconds of the stream are also run closed-loop through the "
                         "server and one request at a time through the plain per-graph path (0: skip)")
@@ -662,6 +665,68 @@ def serve_compare(tc, reqs, slots, budget_bytes, timeout_s=600.0):
             "peak_admitted_bytes": stats["peak_bytes"]}
 
 
+SERVE_SMALL_N = 50000  # every request up to this many vertices in the first window is checked
+SERVE_GAMMA = 0x9e3779b97f4a7c15
+
+
+def serve_checksums(t, lcc):
+    """The server's order-independent digests of t[] and LCC[] (by vertex id v:
+    sum of mix(v * gamma ^ bits) over v, mix being SplitMix64's finaliser)."""
+    import numpy as np
+
+    def mix(z):
+        z = (z ^ (z >> np.uint64(30))) * np.uint64(0xbf58476d1ce4e5b9)
+        z = (z ^ (z >> np.uint64(27))) * np.uint64(0x94d049bb133111eb)
+        return z ^ (z >> np.uint64(31))
+
+    with np.errstate(over="ignore"):
+        key = np.arange(len(t), dtype=np.uint64) * np.uint64(SERVE_GAMMA)
+        a = mix(key ^ np.asarray(t).astype(np.uint64)).sum(dtype=np.uint64)
+        b = mix(key ^ np.asarray(lcc, dtype=np.float64).view(np.uint64)).sum(dtype=np.uint64)
+    return int(a), int(b)
+
+
+def serve_oracle_one(job):
+    """(request id, T, m_simple, t digest, LCC digest) of one request by the oracle;
+    runs in a spawned worker or in the parent."""
+    import oracle
+    q, w, threads = job
+    r = oracle.triangles(w.n, *w.edges(), threads=threads)
+    return (q, r["T"], r["m_simple"], *serve_checksums(r["t"], r["lcc"]))
+
+
+def serve_verify(reqs, results, window_s, n_random, seed=5):
+    """The served results against the oracle on the host (same generator): every
+    request of at most SERVE_SMALL_N vertices that arrived in the first window_s
+    seconds, through a pool of spawned processes, and n_random requests drawn from the
+    whole stream (seeded), each on all cores.  Returns (checked, mismatches, desc)."""
+    import multiprocessing as mp
+
+    import numpy as np
+
+    import oracle
+    oracle.build()
+    cores = len(os.sched_getaffinity(0))
+    served = [q for q, x in results.items() if x["status"] == 0]
+    small = [q for q in served if reqs[q].arrival < window_s and reqs[q].workload.n <= SERVE_SMALL_N]
+    rest = sorted(set(served) - set(small))
+    rng = np.random.default_rng(seed)
+    rand = [int(q) for q in rng.choice(rest, size=min(n_random, len(rest)), replace=False)] if rest else []
+    out = []
+    if small:
+        with mp.get_context("spawn").Pool(cores) as pool:
+            out += pool.map(serve_oracle_one, [(q, reqs[q].workload, 1) for q in small], chunksize=8)
+    out += [serve_oracle_one((q, reqs[q].workload, cores)) for q in rand]
+    bad = 0
+    for q, T, m, th, lh in out:
+        x = results[q]
+        bad += int((x["T"], x["m_simple"], x["t_hash"], x["lcc_hash"]) != (T, m, th, lh))
+    desc = (f"T, simple edges and the t[] and LCC[] digests of every request of at most {SERVE_SMALL_N} "
+            f"vertices among the first {window_s:g} s ({len(small)}) and of {len(rand)} seeded random "
+            f"requests of the whole stream")
+    return len(out), bad, desc
+
+
 def run_serve(args, rank, world, local):
     """Serving: Poisson arrivals submitted at their arrival times; latency from
     submission to the result on the host; the backlog is drained and reported."""
@@ -707,20 +772,12 @@ def run_serve(args, rank, world, local):
     first = min(x["submit_s"] for x in ok)
     last = max(x["end_s"] for x in ok)
     edges = sum(x["m_simple"] for x in ok)
-    # verification: the smallest requests against the oracle (same generator on the host)
-    verified = 0
-    bad = 0
-    if args.serve_verify > 0:
-        import oracle
-        sys.path.insert(0, os.path.join(ROOT, "tests"))
-        small = sorted(ok, key=lambda x: reqs[x["id"]].workload.m)[: args.serve_verify]
-        for x in small:
-            w = reqs[x["id"]].workload
-            ref = oracle.triangles(w.n, *w.edges())
-            verified += 1
-            bad += int(ref["T"] != x["T"] or ref["m_simple"] != x["m_simple"])
     if rank != 0:
         return
+    # verification against the oracle (same generator on the host), after the timing
+    verified, bad, vdesc = 0, 0, None
+    if args.serve_verify_seconds > 0 or args.serve_verify_random > 0:
+        verified, bad, vdesc = serve_verify(reqs, results, args.serve_verify_seconds, args.serve_verify_random)
     line = {"metric": "serve p50/p99 latency", "value": float(np.percentile(lat, 50)), "unit": "ms",
             "p99_ms": float(np.percentile(lat, 99)), "p50_ms": float(np.percentile(lat, 50)),
             "higher_is_better": False, "n_gpus": world, "steps": 1, "warmup": 0,
@@ -736,7 +793,8 @@ def run_serve(args, rank, world, local):
             "submit_phase_s": submit_end, "drain_s": last - submit_end,
             "saturated": bool((last - first) > 1.2 * args.serve_seconds),
             "max_queue": stats["max_queue"], "peak_admitted_bytes": stats["peak_bytes"],
-            "oracle_checked": verified, "oracle_mismatches": bad, "vs_plain_per_graph": compare,
+            "oracle_checked": verified, "oracle_mismatches": bad, "oracle_sample": vdesc,
+            "vs_plain_per_graph": compare,
             "gpu_launches": launches, "clocks": clk, "impl": "ours"}
     print(json.dumps(line), flush=True)
 

@@ -43,6 +43,24 @@ def test_cpu_baseline_times_the_oracle_on_all_cores_and_on_one():
     assert f"of {8 * bench.ONE_CORE_PIECES} equal-work source ranges" in one["sample"]
 
 
+def test_serve_verification_compares_with_the_oracle():
+    """The serve check recomputes each sampled request on the host and compares T,
+    edges and both digests; a wrong value in any of them counts as a mismatch."""
+    reqs = graphgen.serve_requests(seconds=0.01, rate=2000.0, n_range=(1000, 60000))
+    assert len(reqs) >= 4
+    results = {}
+    for r in reqs:
+        q, T, m, th, lh = bench.serve_oracle_one((r.id, r.workload, 1))
+        results[q] = {"status": 0, "T": T, "m_simple": m, "t_hash": th, "lcc_hash": lh}
+    checked, bad, desc = bench.serve_verify(reqs, results, 1.0, 1)
+    small = sum(r.workload.n <= bench.SERVE_SMALL_N for r in reqs)
+    assert checked == small + min(1, len(reqs) - small) and bad == 0
+    assert f"({small})" in desc
+    q0 = next(r.id for r in reqs if r.workload.n <= bench.SERVE_SMALL_N)
+    results[q0] = dict(results[q0], lcc_hash=results[q0]["lcc_hash"] ^ 1)
+    assert bench.serve_verify(reqs, results, 1.0, 0)[1] == 1
+
+
 def test_bench_defaults_are_one_gpu_and_minutes():
     import sys
     argv = sys.argv
