@@ -813,7 +813,10 @@ VERTEX_FORMULA = "per-vertex formula (Alg. 3, unoriented, symmetric CSR built pe
 
 def run_ablation(args, rank, world, local):
     """Table II on the GPU: the count phase (plan + intersection kernels) of one
-    resident graph under each method; edges/s = simple edges / count time."""
+    resident graph under each method; edges/s = simple edges / count time.  Every
+    repetition plans and counts again (a count of an unchanged, counted graph would
+    return its cached result), and the phase times are medians over the repetitions,
+    split by bucket: sources with |N+(u)| <= 256, sources with more, edges into hubs."""
     import numpy as np
     import torch
 
@@ -828,6 +831,17 @@ def run_ablation(args, rank, world, local):
     m_simple = g.info()["m_simple"]
     base = g.tuning()
     rows = []
+
+    def fresh_count():
+        # a change of a hub setting and back: the next count plans and counts again
+        t = g.tuning()
+        alt = dict(t)
+        alt["hub_core"] = 1 if t["hub_core"] != 1 else 2
+        g.set_tuning(alt)
+        g.set_tuning(t)
+        assert g.count() == T0
+        return g.timing()
+
     for name, spec, over in ABLATION:
         g.set_tuning(base)
         g.set_hubs(base["hub_min_degree"], base["hub_max"])
@@ -836,17 +850,15 @@ def run_ablation(args, rank, world, local):
             t = g.tuning()
             t.update(over)
             g.set_tuning(t)
-        times = []
-        plan_ms = 0.0
-        for k in range(max(args.warmup, 1) + args.steps):
-            assert g.count() == T0
-            tim = g.timing()
-            if k == 0:
-                plan_ms = tim["plan_ms"]  # the first count after a change of settings plans
-            if k >= max(args.warmup, 1):
-                times.append(tim["total_ms"])
-        ms = plan_ms + float(np.median(times))
-        rows.append({"method": name, "count_ms": ms, "plan_ms": plan_ms, "intersect_ms": ms - plan_ms,
+        tims = [fresh_count() for _ in range(max(args.warmup, 1) + args.steps)][max(args.warmup, 1):]
+
+        def med(key):
+            return float(np.median([x[key] for x in tims]))
+
+        ms = med("total_ms")
+        rows.append({"method": name, "count_ms": ms, "plan_ms": med("plan_ms"), "intersect_ms": ms - med("plan_ms"),
+                     "bucket_ms": {"small: |N+(u)| <= 256": med("small_ms"), "block: |N+(u)| > 256": med("cta_ms"),
+                                   "hub pull: edges into hubs": med("hub_ms")},
                      "edges_per_s": m_simple / (ms / 1000.0), "tuning": g.tuning()})
     # the paper's unoriented per-vertex formula: whole call (symmetric CSR + count)
     ts = []
@@ -868,8 +880,9 @@ def run_ablation(args, rank, world, local):
             "ms_per_step": best["count_ms"], "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "int32", "data": "synthetic",
             "config": {"workload": w.name, "m_simple": m_simple, "T": T0,
-                       "timed": "plan (first count after the settings change) + median of the "
-                                "intersection kernels of later counts, resident graph"},
+                       "timed": "median over the repetitions of plan + intersection kernels, each "
+                                "repetition planning again, resident graph; with hubs the small "
+                                "bucket's time includes the hub lists built beside it"},
             "methods": rows, "impl": "ours"}
     print(json.dumps(line), flush=True)
 
