@@ -61,6 +61,48 @@ def test_serve_verification_compares_with_the_oracle():
     assert bench.serve_verify(reqs, results, 1.0, 0)[1] == 1
 
 
+class _FakeGraph:
+    """The library's caching rule: a count runs only when the graph has not counted
+    under its current settings, and plans again only when a hub setting changed."""
+
+    def __init__(self):
+        self.t = {"strategy": {"small": "auto"}, "hub_min_degree": 32, "hub_max": 131072,
+                  "hub_big_in": 128, "hub_core": 8192}
+        self.planned = self.counted = False
+        self.plans = self.counts = 0
+
+    def tuning(self):
+        return dict(self.t)
+
+    def set_tuning(self, t):
+        hub = ("hub_min_degree", "hub_max", "hub_big_in", "hub_core")
+        if any(t[k] != self.t[k] for k in hub):
+            self.planned = False
+        self.t = dict(t)
+        self.counted = False
+
+    def count(self):
+        if not self.counted:
+            if not self.planned:
+                self.plans += 1
+                self.planned = True
+            self.counts += 1
+            self.counted = True
+        return 7
+
+    def timing(self):
+        return {"plans": self.plans, "counts": self.counts}
+
+
+def test_recount_plans_and_counts_every_time():
+    g = _FakeGraph()
+    for k in range(1, 4):
+        assert bench.recount(g, 7) == {"plans": k, "counts": k}
+    assert g.t["hub_core"] == 8192  # the settings are left as they were
+    g.t["hub_core"] = 1
+    assert bench.recount(g, 7) == {"plans": 4, "counts": 4} and g.t["hub_core"] == 1
+
+
 def test_bench_defaults_are_one_gpu_and_minutes():
     import sys
     argv = sys.argv
